@@ -1,0 +1,175 @@
+/*
+ * mcpt.h -- C ABI of the GB300 (sm_103a) library for the first-order MCPT(2)
+ * dimer term (Byrd, Jindal, Molt, Bartlett, Sanders, Lotrich, "Molecular
+ * Cluster Perturbation Theory. I. Formalism").
+ *
+ * For every dimer X-Y of a lattice of monomers the library computes
+ *
+ *   (i a|j b) = sum_{mu nu in X, lam sig in Y} C_{mu i} C_{nu a} C_{lam j} C_{sig b} (mu nu|lam sig)
+ *                                                             Eq. (dp2e), p=i r=a q=j s=b
+ *   (i b|j a) = sum C_{mu i} C_{lam b} C_{sig j} C_{nu a} (mu lam|sig nu)   exchange-type form
+ *   D^{ij}_{ab} = 1 / (e_i + e_j - e_a - e_b)                 energy tensor, Sec. II.C
+ *   E_J(XY) = 4 sum (ia|jb)^2 D                                Eq. (ed2) with T = vD (first
+ *                                                              Jacobi step of Eq. (td2))
+ *   E_K(XY) = -2 sum (ia|jb)(ib|ja) D                          exchange completion (2J-K)
+ *
+ * and accumulates half of each dimer term onto each of its two monomers (the
+ * dimer sum of the cluster Hamiltonian, Eq. (clusterH)), with a compensated
+ * lattice total.  Orbitals are monomer-centred and not orthogonalised between
+ * monomers (remark after Eq. (dp2e)), so C is block diagonal and each
+ * monomer's C and eps are given once.
+ *
+ * Conventions
+ *   - All matrices are row-major FP64.  C[mu][p] is nao x nao: row = AO,
+ *     column = MO, the first nocc columns occupied, eps[p] the matching
+ *     orbital energies.
+ *   - A dimer's AO basis is X's functions first, then Y's (n = nX + nY).
+ *     MCPT_AO_FULL: the full tensor G[n][n][n][n] (mu nu|lam sig).
+ *     MCPT_AO_BLOCKS: the two blocks the term reads, back to back:
+ *        A[nX][nX][nY][nY] = G[mu][nu][nX+lam][nX+sig]  (XX|YY)
+ *        K[nX][nY][nY][nX] = G[mu][nX+lam][nX+sig][nu]  (XY|YX)
+ *   - Monomer ids are 0..N-1 in add order; dimer ids 0..D-1 in add order.
+ *
+ * Errors: every call returns a status and never aborts or exits;
+ * mcpt_last_error(h) returns the handle's last message.  A handle is not
+ * thread-safe: one host thread at a time.
+ */
+#ifndef MCPT_H
+#define MCPT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcpt_ctx *mcpt_handle;
+
+typedef enum {
+    MCPT_OK = 0,
+    MCPT_EINVAL = 1,        /* bad argument: size, id, pointer, non-finite value */
+    MCPT_ENOMEM = 2,        /* device or host allocation failed, or the memory cap was hit */
+    MCPT_ECUDA = 3,         /* a CUDA runtime/driver call failed (message has the CUDA error) */
+    MCPT_ESTATE = 4,        /* call out of order (e.g. energies before any run) */
+    MCPT_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    MCPT_EUNSUPPORTED = 6   /* valid request this build/precision does not handle */
+} mcpt_status;
+
+/* Arithmetic of the four-index transformation.  Denominators, the energy
+ * products and every energy sum are FP64 in all forms. */
+typedef enum {
+    MCPT_FP64 = 0,    /* FP64 everywhere (CUDA-core DFMA) */
+    MCPT_TF32 = 1,    /* AO integrals and C rounded to TF32 (round-to-nearest), tcgen05 MMA, FP32 accumulate */
+    MCPT_BF16X3 = 2,  /* hi/lo BF16 split of both operands, 3 tcgen05 MMAs per product, FP32 accumulate */
+    MCPT_FP32C = 3    /* FP32 FMA with error-free TwoProduct/TwoSum compensation (Ogita-Rump-Oishi) */
+} mcpt_precision;
+
+typedef enum {
+    MCPT_AO_FULL = 0,
+    MCPT_AO_BLOCKS = 1
+} mcpt_ao_layout;
+
+typedef struct {
+    int device;               /* CUDA device ordinal */
+    void *stream;             /* cudaStream_t to run on, or NULL for a library-owned stream */
+    mcpt_precision precision; /* see above */
+    int validate;             /* 1: reject non-finite C / eps / integrals (adds a pass over inputs) */
+    size_t wave_bytes;        /* cap on per-run device scratch; dimers run in waves under it (0 = 1 GiB) */
+    const char *tune_cache;   /* path of the tile-choice cache, or NULL for none */
+    int timing;               /* 1: record CUDA events per phase of mcpt_run (see mcpt_run_stats) */
+    size_t mem_cap_bytes;     /* cap on library-owned device memory (0 = no cap) */
+} mcpt_options;
+
+/* Defaults: device 0, own stream, MCPT_FP64, validate 1, 1 GiB waves, no cache, no timing. */
+void mcpt_default_options(mcpt_options *opt);
+
+/* Create a handle.  opt may be NULL (defaults).  *out is NULL on failure.
+ * Errors: EINVAL (out NULL, bad precision), ECUDA (device/stream). */
+mcpt_status mcpt_create(mcpt_handle *out, const mcpt_options *opt);
+
+/* Register monomer `*id_out` (ids are assigned 0, 1, ... in call order).
+ * C: host pointer to nao*nao FP64, row-major C[mu][p] (MO coefficients, the
+ *    monomer Hartree-Fock solution of Sec. III's program flow, step 1);
+ * eps: host pointer to nao FP64 orbital energies (occupied first).
+ * Both are copied before the call returns.
+ * Errors: EINVAL if nao < 2 or nao > 256, nocc not in [1, nao-1], a pointer
+ * is NULL, or (validate) a value is not finite; ESTATE after mcpt_destroy. */
+mcpt_status mcpt_add_monomer(mcpt_handle h, const double *C, const double *eps,
+                             int nao, int nocc, int *id_out);
+
+/* Register dimer X-Y with its AO integrals (Eq. (dp2e) input).
+ * ao_eri: FP64 in `layout` for the (X, Y) order given.  If X > Y the library
+ *   stores the dimer as (Y, X) with the integrals relabelled (Y's functions
+ *   first); the term is symmetric in X and Y.
+ * on_device = 0: host pointer, copied (blocks only) before the call returns.
+ * on_device = 1: device pointer on the handle's device, BORROWED: it must
+ *   stay valid and unmodified until the last mcpt_run that uses it has
+ *   completed (mcpt_energies returns).  Requires X < Y.
+ * Errors: EINVAL (unknown or equal ids, duplicate pair, NULL, bad layout,
+ *   non-finite with validate=1, X > Y with on_device=1), ENOMEM, ECUDA. */
+mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double *ao_eri,
+                           mcpt_ao_layout layout, int on_device, int *id_out);
+
+/* Switch the transformation arithmetic for later runs (no re-upload). */
+mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p);
+
+/* Compute every registered dimer term and the per-monomer accumulation
+ * (Sec. III program flow, steps 2 and 6 at first order) on the handle's
+ * stream.  Asynchronous: returns once the work is enqueued.  Re-running
+ * recomputes everything.
+ * Errors: ESTATE (no dimers), EUNSUPPORTED (precision cannot handle a dimer's
+ * sizes: tensor-core forms need even nX, nY <= 128 and nocc_X*nocc_Y <= 256),
+ * ENOMEM, ECUDA, ETIMEOUT. */
+mcpt_status mcpt_run(mcpt_handle h);
+
+/* Compute only dimers [first, first+count) (resume / partial runs).  Their
+ * terms replace earlier ones; the per-monomer sums cover all dimers and are
+ * valid once every dimer has been computed at least once. */
+mcpt_status mcpt_run_range(mcpt_handle h, int first, int count);
+
+/* Wait for the handle's stream and copy results to host buffers (each may be
+ * NULL): per_monomer_J, per_monomer_K: N each; per_dimer: 2*D as {E_J, E_K};
+ * total: 2 as {sum E_J, sum E_K} (Neumaier-compensated, fixed order).
+ * Errors: ESTATE if a dimer has not been computed since it was added;
+ * ETIMEOUT if a device-side wait gave up during the run; ECUDA. */
+mcpt_status mcpt_energies(mcpt_handle h, double *per_monomer_J, double *per_monomer_K,
+                          double *per_dimer, double *total);
+
+/* Per-phase timing and launch counts of every run since the previous call
+ * (timing requires options.timing = 1; CUDA events are recorded on the
+ * handle's stream around each phase, and this call waits for the stream).
+ * ms[0] = first half (the AO-reading transform kernel), ms[1] = finish
+ * (second half + denominators + energies), ms[2] = per-monomer reduction,
+ * ms[3] = whole run: each summed over the `runs` collected runs;
+ * launches = kernels those runs launched; waves = waves per run;
+ * alg_bytes = algorithmic AO bytes read per run (2 nX^2 nY^2 x 8 B per dimer);
+ * alg_flops = algorithmic flops per run of both halves (occupied-first
+ * factorised count, both forms); alg_flops_half = those of the first half. */
+typedef struct {
+    float ms[4];
+    int runs;
+    int launches;
+    int waves;
+    double alg_bytes;
+    double alg_flops;
+    double alg_flops_half;
+} mcpt_run_stats;
+mcpt_status mcpt_collect_stats(mcpt_handle h, mcpt_run_stats *out);
+
+/* Counts registered so far. */
+int mcpt_num_monomers(mcpt_handle h);
+int mcpt_num_dimers(mcpt_handle h);
+
+/* Last error message of the handle ("" if none); with h == NULL, the last
+ * error of a failed mcpt_create on this thread. */
+const char *mcpt_last_error(mcpt_handle h);
+
+/* Release the handle and every library-owned device buffer.  Borrowed
+ * pointers are not touched.  NULL is a no-op. */
+void mcpt_destroy(mcpt_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCPT_H */

@@ -1,0 +1,226 @@
+"""Python binding of libmcpt, the GB300 library for the first-order MCPT(2)
+dimer term (C ABI in include/mcpt.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libmcpt.so.  There is no CPU fallback; importing works without a
+GPU (so the library can be inspected), but every call that computes needs the
+built library and a Blackwell GPU, and fails loudly otherwise.
+
+Host arrays are numpy float64; device arrays may be torch CUDA tensors (their
+``data_ptr()`` is passed) or raw integer device addresses.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmcpt.so")
+
+MCPT_OK, MCPT_EINVAL, MCPT_ENOMEM, MCPT_ECUDA, MCPT_ESTATE, MCPT_ETIMEOUT, MCPT_EUNSUPPORTED = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
+MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C = range(4)
+PRECISIONS = {"fp64": MCPT_FP64, "tf32": MCPT_TF32, "bf16x3": MCPT_BF16X3, "fp32c": MCPT_FP32C}
+MCPT_AO_FULL, MCPT_AO_BLOCKS = 0, 1
+
+# every symbol include/mcpt.h declares
+EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_set_precision",
+           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats", "mcpt_num_monomers",
+           "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy")
+
+
+class McptError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"MCPT_{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class mcpt_options(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
+                ("validate", ctypes.c_int), ("wave_bytes", ctypes.c_size_t), ("tune_cache", ctypes.c_char_p),
+                ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t)]
+
+
+class mcpt_run_stats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_float * 4), ("runs", ctypes.c_int), ("launches", ctypes.c_int),
+                ("waves", ctypes.c_int), ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double),
+                ("alg_flops_half", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libmcpt.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libmcpt.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        H, I, P, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        L.mcpt_default_options.argtypes = [ctypes.POINTER(mcpt_options)]
+        L.mcpt_default_options.restype = None
+        L.mcpt_create.argtypes = [ctypes.POINTER(H), ctypes.POINTER(mcpt_options)]
+        L.mcpt_add_monomer.argtypes = [H, P, P, I, I, ctypes.POINTER(I)]
+        L.mcpt_add_dimer.argtypes = [H, I, I, P, I, I, ctypes.POINTER(I)]
+        L.mcpt_set_precision.argtypes = [H, I]
+        L.mcpt_run.argtypes = [H]
+        L.mcpt_run_range.argtypes = [H, I, I]
+        L.mcpt_energies.argtypes = [H, P, P, P, P]
+        L.mcpt_collect_stats.argtypes = [H, ctypes.POINTER(mcpt_run_stats)]
+        for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_set_precision", "mcpt_run",
+                  "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats"):
+            getattr(L, f).restype = I
+        L.mcpt_num_monomers.argtypes = [H]
+        L.mcpt_num_monomers.restype = I
+        L.mcpt_num_dimers.argtypes = [H]
+        L.mcpt_num_dimers.restype = I
+        L.mcpt_last_error.argtypes = [H]
+        L.mcpt_last_error.restype = ctypes.c_char_p
+        L.mcpt_destroy.argtypes = [H]
+        L.mcpt_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(h, st):
+    if st != MCPT_OK:
+        raise McptError(st, lib().mcpt_last_error(h).decode())
+
+
+def _ptr(x):
+    """Address of a numpy array, a torch tensor, or an int."""
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+# ----------------------------------------------------------- thin wrappers
+def mcpt_default_options() -> mcpt_options:
+    o = mcpt_options()
+    lib().mcpt_default_options(ctypes.byref(o))
+    return o
+
+
+def mcpt_create(opts: mcpt_options | None = None) -> int:
+    h = ctypes.c_void_p()
+    st = lib().mcpt_create(ctypes.byref(h), ctypes.byref(opts) if opts is not None else None)
+    _check(None, st)
+    return h.value
+
+
+def mcpt_add_monomer(h, C, eps, nao: int, nocc: int) -> int:
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    eps = np.ascontiguousarray(eps, dtype=np.float64)
+    out = ctypes.c_int()
+    _check(h, lib().mcpt_add_monomer(h, _ptr(C), _ptr(eps), nao, nocc, ctypes.byref(out)))
+    return out.value
+
+
+def mcpt_add_dimer(h, X: int, Y: int, ao_eri, layout: int, on_device: int) -> int:
+    if isinstance(ao_eri, np.ndarray):
+        ao_eri = np.ascontiguousarray(ao_eri, dtype=np.float64)
+    out = ctypes.c_int()
+    _check(h, lib().mcpt_add_dimer(h, X, Y, _ptr(ao_eri), layout, on_device, ctypes.byref(out)))
+    return out.value
+
+
+def mcpt_set_precision(h, p: int) -> None:
+    _check(h, lib().mcpt_set_precision(h, p))
+
+
+def mcpt_run(h) -> None:
+    _check(h, lib().mcpt_run(h))
+
+
+def mcpt_run_range(h, first: int, count: int) -> None:
+    _check(h, lib().mcpt_run_range(h, first, count))
+
+
+def mcpt_energies(h):
+    """(per_monomer_J [N], per_monomer_K [N], per_dimer [D,2], total [2])."""
+    N, D = lib().mcpt_num_monomers(h), lib().mcpt_num_dimers(h)
+    mj, mk = np.empty(N), np.empty(N)
+    pd, tot = np.empty((D, 2)), np.empty(2)
+    _check(h, lib().mcpt_energies(h, _ptr(mj), _ptr(mk), _ptr(pd), _ptr(tot)))
+    return mj, mk, pd, tot
+
+
+def mcpt_collect_stats(h) -> mcpt_run_stats:
+    s = mcpt_run_stats()
+    _check(h, lib().mcpt_collect_stats(h, ctypes.byref(s)))
+    return s
+
+
+def mcpt_last_error(h) -> str:
+    return lib().mcpt_last_error(h).decode()
+
+
+def mcpt_destroy(h) -> None:
+    lib().mcpt_destroy(h)
+
+
+# ----------------------------------------------------------- convenience
+class Context:
+    """Owns one mcpt handle.  ``stream`` is a cudaStream_t as an int (e.g.
+    ``torch.cuda.current_stream().cuda_stream``) or None for a library stream."""
+
+    def __init__(self, precision="fp64", device=0, stream=None, validate=True, wave_bytes=0, timing=False,
+                 mem_cap_bytes=0):
+        o = mcpt_default_options()
+        o.device = device
+        o.stream = stream
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.validate = int(bool(validate))
+        o.wave_bytes = wave_bytes
+        o.timing = int(bool(timing))
+        o.mem_cap_bytes = mem_cap_bytes
+        self.h = mcpt_create(o)
+
+    def add_monomer(self, C, eps, nocc):
+        C = np.asarray(C)
+        return mcpt_add_monomer(self.h, C, eps, C.shape[0], nocc)
+
+    def add_dimer(self, X, Y, ao_eri, layout=MCPT_AO_BLOCKS, on_device=None):
+        if on_device is None:
+            on_device = 0 if isinstance(ao_eri, np.ndarray) else 1
+        return mcpt_add_dimer(self.h, X, Y, ao_eri, layout, on_device)
+
+    def set_precision(self, p):
+        mcpt_set_precision(self.h, PRECISIONS[p] if isinstance(p, str) else int(p))
+
+    def run(self, first=None, count=None):
+        if first is None:
+            mcpt_run(self.h)
+        else:
+            mcpt_run_range(self.h, first, count)
+
+    def energies(self):
+        return mcpt_energies(self.h)
+
+    def stats(self):
+        """Timing and launch counts of the runs since the previous call."""
+        return mcpt_collect_stats(self.h)
+
+    def close(self):
+        if self.h:
+            mcpt_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

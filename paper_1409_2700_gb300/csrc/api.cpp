@@ -1,0 +1,779 @@
+// api.cpp -- the C ABI of libmcpt (declared in include/mcpt.h).
+//
+// Host-side runtime: argument validation, the monomer coefficient pool, a
+// device arena for the integral blocks the library owns, the per-run dimer
+// descriptors, wave planning under the scratch cap, kernel launches on the
+// handle's stream, per-phase CUDA-event timing and the result copies.
+#include "mcpt.h"
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <string>
+#include <utility>
+#include <vector>
+
+using namespace mcpt;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct MonomerRec {
+    int nao, nocc;
+    int offC, offE;
+};
+
+struct DimerRec {
+    int X, Y;
+    const double* E[2];
+    long long st[2][3];
+    bool computed;
+};
+
+// Events of the timed runs since the last mcpt_collect_stats: per run
+// [start, (first-half end, finish end) per wave, reduction end].
+struct RunEvents {
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::vector<cudaEvent_t>> pending;
+    int runs = 0, launches = 0;
+};
+
+}  // namespace
+
+struct mcpt_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    mcpt_precision prec = MCPT_FP64;
+    int validate = 1;
+    size_t wave_bytes = (size_t)1 << 30;
+    std::string tune_cache;
+    int timing = 0;
+    size_t mem_cap = 0;
+    size_t mem_used = 0;
+
+    std::vector<MonomerRec> mons;
+    std::vector<double> hC, hE;
+    double* dC = nullptr;
+    double* dE = nullptr;
+    size_t capC = 0, capE = 0;
+    bool mon_dirty = true;
+
+    std::vector<DimerRec> dims;
+    std::set<std::pair<int, int>> pairs;
+    std::vector<void*> owned;        // arena chunks
+    char* arena_ptr = nullptr;
+    size_t arena_left = 0;
+
+    DimerDesc* dDesc = nullptr;
+    size_t capDesc = 0;
+    void* dH = nullptr;
+    size_t capH = 0;
+    void* dWork = nullptr;
+    size_t capWork = 0;
+    double* dE2 = nullptr;
+    size_t capE2 = 0;
+    double* dMon = nullptr;
+    size_t capMon = 0;
+    int* dLists = nullptr;
+    size_t capLists = 0;
+    bool lists_dirty = true;
+    double* dTot = nullptr;
+    int* dFlag = nullptr;            // [0] validation flag, [1] device wait status
+
+    std::vector<DimerDesc> hDesc;
+    struct Wave {
+        int b, nd, max_rows, max_occ, max_ao;
+        TcLaunch tc;
+    };
+    struct Plan {
+        bool valid = false;
+        mcpt_precision prec = MCPT_FP64;
+        int first = 0, count = 0;
+        std::vector<Wave> waves;
+        double alg_bytes = 0, alg_flops = 0, alg_flops_half = 0;
+    } plan;
+    RunEvents rev;
+    mcpt_run_stats stats{};
+    bool ran = false;
+    std::string err;
+};
+
+namespace {
+
+mcpt_status fail(mcpt_ctx* h, mcpt_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_error = buf;
+    return st;
+}
+
+#define CK(h, call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? MCPT_ENOMEM : MCPT_ECUDA,           \
+                        "CUDA error %s (%s) in %s", cudaGetErrorName(e_), cudaGetErrorString(e_), \
+                        #call);                                                                  \
+    } while (0)
+
+mcpt_status dev_alloc(mcpt_ctx* h, void** p, size_t bytes)
+{
+    if (h->mem_cap && h->mem_used + bytes > h->mem_cap)
+        return fail(h, MCPT_ENOMEM, "device memory cap of %zu bytes reached (%zu in use, %zu requested)",
+                    h->mem_cap, h->mem_used, bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, MCPT_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->mem_used += bytes;
+    return MCPT_OK;
+}
+
+void dev_free(mcpt_ctx* h, void* p, size_t bytes)
+{
+    if (p) {
+        cudaFree(p);
+        h->mem_used -= bytes;
+    }
+}
+
+// Grow-only device buffer.
+template <typename T>
+mcpt_status ensure(mcpt_ctx* h, T** p, size_t* cap, size_t bytes)
+{
+    if (*cap >= bytes && *p) return MCPT_OK;
+    dev_free(h, *p, *cap);
+    *p = nullptr;
+    *cap = 0;
+    void* q = nullptr;
+    mcpt_status st = dev_alloc(h, &q, bytes);
+    if (st) return st;
+    *p = static_cast<T*>(q);
+    *cap = bytes;
+    return MCPT_OK;
+}
+
+// Bump allocation from 256-byte aligned arena chunks (integral blocks owned
+// by the library live here until mcpt_destroy).
+mcpt_status arena_alloc(mcpt_ctx* h, size_t bytes, void** out)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes > h->arena_left) {
+        size_t chunk = std::max(bytes, (size_t)512 << 20);
+        void* p = nullptr;
+        mcpt_status st = dev_alloc(h, &p, chunk);
+        if (st) {
+            if (chunk == bytes) return st;
+            h->err.clear();
+            st = dev_alloc(h, &p, bytes);   // retry with the exact size
+            if (st) return st;
+            chunk = bytes;
+        }
+        h->owned.push_back(p);
+        h->arena_ptr = static_cast<char*>(p);
+        h->arena_left = chunk;
+    }
+    *out = h->arena_ptr;
+    h->arena_ptr += bytes;
+    h->arena_left -= bytes;
+    return MCPT_OK;
+}
+
+bool all_finite(const double* x, size_t n)
+{
+    for (size_t k = 0; k < n; k++)
+        if (!std::isfinite(x[k])) return false;
+    return true;
+}
+
+bool is_tensor_form(mcpt_precision p) { return p == MCPT_TF32 || p == MCPT_BF16X3; }
+
+// Row stride of the first-half result for a dimer in a given form.
+int ldh_for(mcpt_precision p, int oX, int oY)
+{
+    const int pairs = oX * oY;
+    if (is_tensor_form(p)) return (pairs + 15) / 16 * 16;   // MMA N is a multiple of 16
+    return pairs;
+}
+
+size_t hbytes_for(mcpt_precision p, int nX, int nY, int oX, int oY)
+{
+    const size_t elem = (p == MCPT_FP64) ? sizeof(double) : sizeof(float);
+    return 2 * (size_t)nX * nY * ldh_for(p, oX, oY) * elem;
+}
+
+mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY, int oX, int oY)
+{
+    switch (h->prec) {
+    case MCPT_FP64:
+        if (nX > 96 || nY > 96)
+            return fail(h, MCPT_EUNSUPPORTED, "dimer %d: the FP64 form handles monomers of up to 96 AO", d);
+        return MCPT_OK;
+    case MCPT_FP32C:
+        return MCPT_OK;
+    case MCPT_TF32:
+    case MCPT_BF16X3:
+        if ((nX & 1) || (nY & 1) || nX > kMaxAOTensor || nY > kMaxAOTensor)
+            return fail(h, MCPT_EUNSUPPORTED,
+                        "dimer %d: tensor-core forms need even AO counts <= %d (got %d, %d)", d,
+                        kMaxAOTensor, nX, nY);
+        if (oX * oY > kMaxPairsTensor)
+            return fail(h, MCPT_EUNSUPPORTED, "dimer %d: tensor-core forms need nocc_X*nocc_Y <= %d", d,
+                        kMaxPairsTensor);
+        return MCPT_OK;
+    }
+    return fail(h, MCPT_EINVAL, "unknown precision");
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+void mcpt_default_options(mcpt_options* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->device = 0;
+    o->stream = nullptr;
+    o->precision = MCPT_FP64;
+    o->validate = 1;
+    o->wave_bytes = (size_t)1 << 30;
+    o->tune_cache = nullptr;
+    o->timing = 0;
+    o->mem_cap_bytes = 0;
+}
+
+mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
+{
+    if (!out) return fail(nullptr, MCPT_EINVAL, "mcpt_create: out is NULL");
+    *out = nullptr;
+    mcpt_options o;
+    mcpt_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision < MCPT_FP64 || o.precision > MCPT_FP32C)
+        return fail(nullptr, MCPT_EINVAL, "mcpt_create: bad precision %d", (int)o.precision);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, MCPT_ECUDA, "mcpt_create: no CUDA device (%s)", cudaGetErrorString(e));
+    }
+    if (o.device < 0 || o.device >= ndev)
+        return fail(nullptr, MCPT_EINVAL, "mcpt_create: device %d out of range (%d devices)", o.device, ndev);
+    if ((e = cudaSetDevice(o.device)) != cudaSuccess)
+        return fail(nullptr, MCPT_ECUDA, "mcpt_create: cudaSetDevice: %s", cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, o.device)) != cudaSuccess)
+        return fail(nullptr, MCPT_ECUDA, "mcpt_create: %s", cudaGetErrorString(e));
+    if (prop.major < 10)
+        return fail(nullptr, MCPT_EUNSUPPORTED, "mcpt_create: device %s (sm_%d%d) is not a Blackwell GPU",
+                    prop.name, prop.major, prop.minor);
+
+    mcpt_ctx* h = new (std::nothrow) mcpt_ctx;
+    if (!h) return fail(nullptr, MCPT_ENOMEM, "mcpt_create: out of host memory");
+    h->device = o.device;
+    h->prec = o.precision;
+    h->validate = o.validate;
+    h->wave_bytes = o.wave_bytes ? o.wave_bytes : ((size_t)1 << 30);
+    h->tune_cache = o.tune_cache ? o.tune_cache : "";
+    h->timing = o.timing;
+    h->mem_cap = o.mem_cap_bytes;
+    if (o.stream) {
+        h->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+            delete h;
+            return fail(nullptr, MCPT_ECUDA, "mcpt_create: stream: %s", cudaGetErrorString(e));
+        }
+        h->own_stream = true;
+    }
+    void* flag = nullptr;
+    if (dev_alloc(h, &flag, 4 * sizeof(int)) != MCPT_OK) {
+        std::string m = h->err;
+        mcpt_destroy(h);
+        return fail(nullptr, MCPT_ENOMEM, "mcpt_create: %s", m.c_str());
+    }
+    h->dFlag = static_cast<int*>(flag);
+    cudaMemsetAsync(h->dFlag, 0, 4 * sizeof(int), h->stream);
+    *out = h;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_add_monomer(mcpt_handle h, const double* C, const double* eps, int nao, int nocc, int* id_out)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_add_monomer: NULL handle");
+    if (!C || !eps) return fail(h, MCPT_EINVAL, "mcpt_add_monomer: C and eps must not be NULL");
+    if (nao < 2 || nao > kMaxAOTensor)
+        return fail(h, MCPT_EINVAL, "mcpt_add_monomer: nao=%d outside [2, %d]", nao, kMaxAOTensor);
+    if (nocc < 1 || nocc > nao - 1)
+        return fail(h, MCPT_EINVAL, "mcpt_add_monomer: nocc=%d outside [1, nao-1=%d]", nocc, nao - 1);
+    if (h->validate && (!all_finite(C, (size_t)nao * nao) || !all_finite(eps, nao)))
+        return fail(h, MCPT_EINVAL, "mcpt_add_monomer: non-finite value in C or eps");
+    MonomerRec m{nao, nocc, (int)h->hC.size(), (int)h->hE.size()};
+    h->hC.insert(h->hC.end(), C, C + (size_t)nao * nao);
+    h->hE.insert(h->hE.end(), eps, eps + nao);
+    h->mons.push_back(m);
+    h->mon_dirty = true;
+    h->plan.valid = false;
+    h->lists_dirty = true;
+    if (id_out) *id_out = (int)h->mons.size() - 1;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_ao_layout layout, int on_device,
+                           int* id_out)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_add_dimer: NULL handle");
+    const int N = (int)h->mons.size();
+    if (X < 0 || X >= N || Y < 0 || Y >= N)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: unknown monomer id (%d, %d) of %d", X, Y, N);
+    if (X == Y) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: X == Y == %d", X);
+    if (!ao) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: ao_eri is NULL");
+    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: bad layout %d", (int)layout);
+    if (on_device && X > Y)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: device integrals must be given with X < Y");
+    const std::pair<int, int> key(std::min(X, Y), std::max(X, Y));
+    if (h->pairs.count(key)) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: duplicate dimer (%d, %d)", X, Y);
+    CK(h, cudaSetDevice(h->device));
+
+    const int nX = h->mons[X].nao, nY = h->mons[Y].nao, n = nX + nY;
+    const size_t blk = (size_t)nX * nX * nY * nY;
+    DimerRec r{};
+    r.X = key.first;
+    r.Y = key.second;
+    r.computed = false;
+    if (on_device) {
+        cudaPointerAttributes pa;
+        cudaError_t e = cudaPointerGetAttributes(&pa, ao);
+        if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != h->device) {
+            cudaGetLastError();
+            return fail(h, MCPT_EINVAL, "mcpt_add_dimer: on_device=1 but ao_eri is not device memory of device %d",
+                        h->device);
+        }
+        const long long n1 = n, n2 = n1 * n, n3 = n2 * n;
+        if (layout == MCPT_AO_FULL) {
+            r.E[0] = ao + nX * n1 + nX;                     // G[mu][nu][nX+lam][nX+sig]
+            r.st[0][0] = n3; r.st[0][1] = n2; r.st[0][2] = n1;
+            r.E[1] = ao + nX * n2 + nX * n1;                // G[mu][nX+lam][nX+sig][nu]
+            r.st[1][0] = n3; r.st[1][1] = n2; r.st[1][2] = n1;
+        } else {
+            r.E[0] = ao;
+            r.st[0][0] = (long long)nX * nY * nY; r.st[0][1] = (long long)nY * nY; r.st[0][2] = nY;
+            r.E[1] = ao + blk;
+            r.st[1][0] = (long long)nY * nY * nX; r.st[1][1] = (long long)nY * nX; r.st[1][2] = nX;
+        }
+        if (h->validate) {
+            CK(h, cudaMemsetAsync(h->dFlag, 0, sizeof(int), h->stream));
+            int dA[4] = {nX, nX, nY, nY}, dK[4] = {nX, nY, nY, nX};
+            CK(h, launch_check_finite4(r.E[0], dA, r.st[0], h->dFlag, h->stream));
+            CK(h, launch_check_finite4(r.E[1], dK, r.st[1], h->dFlag, h->stream));
+            int flag = 0;
+            CK(h, cudaMemcpyAsync(&flag, h->dFlag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            if (flag) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: non-finite integral");
+        }
+    } else {
+        // Host integrals: keep only the two blocks the term reads.  With X > Y
+        // the dimer is stored as (Y, X): Y's functions become the first ones.
+        const bool swap = X > Y;
+        const int fX = swap ? nY : nX, fY = swap ? nX : nY;   // stored (first, second) sizes
+        std::vector<double> tmp;
+        const double* src = ao;
+        if (layout == MCPT_AO_FULL || swap) {
+            tmp.resize(2 * blk);
+            double* A = tmp.data();
+            double* K = tmp.data() + blk;
+            // index of stored-order AO p in the caller's order
+            auto map = [&](int p) { return swap ? (p < fX ? nX + p : p - fX) : p; };
+            if (layout == MCPT_AO_FULL) {
+                auto G = [&](int p, int q, int r_, int s) {
+                    return ao[(((size_t)map(p) * n + map(q)) * n + map(r_)) * n + map(s)];
+                };
+                for (int mu = 0; mu < fX; mu++)
+                    for (int nu = 0; nu < fX; nu++)
+                        for (int la = 0; la < fY; la++)
+                            for (int sg = 0; sg < fY; sg++)
+                                A[(((size_t)mu * fX + nu) * fY + la) * fY + sg] = G(mu, nu, fX + la, fX + sg);
+                for (int mu = 0; mu < fX; mu++)
+                    for (int la = 0; la < fY; la++)
+                        for (int sg = 0; sg < fY; sg++)
+                            for (int nu = 0; nu < fX; nu++)
+                                K[(((size_t)mu * fY + la) * fY + sg) * fX + nu] = G(mu, fX + la, fX + sg, nu);
+            } else {
+                // caller's blocks are (X first): A0[nX][nX][nY][nY], K0[nX][nY][nY][nX];
+                // with real-orbital integral symmetry (pq|rs) = (rs|pq) = (qp|sr):
+                // (YY|XX) = A0 transposed, (YX|XY) = K0 with both pairs swapped.
+                const double* A0 = ao;
+                const double* K0 = ao + blk;
+                for (int mu = 0; mu < fX; mu++)
+                    for (int nu = 0; nu < fX; nu++)
+                        for (int la = 0; la < fY; la++)
+                            for (int sg = 0; sg < fY; sg++)
+                                A[(((size_t)mu * fX + nu) * fY + la) * fY + sg] =
+                                    A0[(((size_t)la * nX + sg) * nY + mu) * nY + nu];
+                for (int mu = 0; mu < fX; mu++)
+                    for (int la = 0; la < fY; la++)
+                        for (int sg = 0; sg < fY; sg++)
+                            for (int nu = 0; nu < fX; nu++)
+                                K[(((size_t)mu * fY + la) * fY + sg) * fX + nu] =
+                                    K0[(((size_t)la * nY + mu) * nY + nu) * nX + sg];
+            }
+            src = tmp.data();
+        }
+        if (h->validate && !all_finite(src, 2 * blk))
+            return fail(h, MCPT_EINVAL, "mcpt_add_dimer: non-finite integral");
+        void* dst = nullptr;
+        mcpt_status st = arena_alloc(h, 2 * blk * sizeof(double), &dst);
+        if (st) return st;
+        CK(h, cudaMemcpyAsync(dst, src, 2 * blk * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));   // the caller may free its buffer on return
+        const double* b = static_cast<const double*>(dst);
+        r.E[0] = b;
+        r.st[0][0] = (long long)fX * fY * fY; r.st[0][1] = (long long)fY * fY; r.st[0][2] = fY;
+        r.E[1] = b + blk;
+        r.st[1][0] = (long long)fY * fY * fX; r.st[1][1] = (long long)fY * fX; r.st[1][2] = fX;
+    }
+    h->dims.push_back(r);
+    h->pairs.insert(key);
+    h->plan.valid = false;
+    h->lists_dirty = true;
+    if (id_out) *id_out = (int)h->dims.size() - 1;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_set_precision: NULL handle");
+    if (p < MCPT_FP64 || p > MCPT_FP32C) return fail(h, MCPT_EINVAL, "mcpt_set_precision: bad precision %d", (int)p);
+    if (h->prec != p) h->plan.valid = false;
+    h->prec = p;
+    return MCPT_OK;
+}
+
+static mcpt_status upload_static(mcpt_handle h)
+{
+    if (h->mon_dirty) {
+        mcpt_status st = ensure(h, &h->dC, &h->capC, h->hC.size() * sizeof(double));
+        if (st) return st;
+        st = ensure(h, &h->dE, &h->capE, h->hE.size() * sizeof(double));
+        if (st) return st;
+        CK(h, cudaMemcpyAsync(h->dC, h->hC.data(), h->hC.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->dE, h->hE.data(), h->hE.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->mon_dirty = false;
+    }
+    if (h->lists_dirty) {
+        // CSR of dimers per monomer, ascending dimer id
+        const int N = (int)h->mons.size(), D = (int)h->dims.size();
+        std::vector<int> cnt(N + 1, 0), lists(N + 1 + 2 * (size_t)D);
+        for (const auto& r : h->dims) { cnt[r.X + 1]++; cnt[r.Y + 1]++; }
+        for (int m = 0; m < N; m++) cnt[m + 1] += cnt[m];
+        std::copy(cnt.begin(), cnt.end(), lists.begin());
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (int d = 0; d < D; d++) {
+            lists[N + 1 + fill[h->dims[d].X]++] = d;
+            lists[N + 1 + fill[h->dims[d].Y]++] = d;
+        }
+        mcpt_status st = ensure(h, &h->dLists, &h->capLists, lists.size() * sizeof(int));
+        if (st) return st;
+        CK(h, cudaMemcpyAsync(h->dLists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->lists_dirty = false;
+    }
+    return MCPT_OK;
+}
+
+// Host work of a run that does not change between runs of the same dimer set:
+// descriptors, wave split under the scratch cap, scratch buffers, and (for
+// the tensor-core forms) tensor maps and ordered work items, all uploaded.
+static mcpt_status build_plan(mcpt_handle h, int first, int count)
+{
+    const int D = (int)h->dims.size();
+    const int N = (int)h->mons.size();
+    const mcpt_precision prec = h->prec;
+    auto& P = h->plan;
+    P.valid = false;
+    P.waves.clear();
+
+    h->hDesc.resize(count);
+    std::vector<std::pair<int, int>> waves;   // [begin, end) into hDesc
+    size_t wave_h = 0, max_wave_h = 0;
+    int wbeg = 0;
+    double alg_bytes = 0.0, alg_flops = 0.0, alg_flops_half = 0.0;
+    for (int k = 0; k < count; k++) {
+        const int d = first + k;
+        const DimerRec& r = h->dims[d];
+        const MonomerRec& mX = h->mons[r.X];
+        const MonomerRec& mY = h->mons[r.Y];
+        mcpt_status st = check_supported(h, d, mX.nao, mY.nao, mX.nocc, mY.nocc);
+        if (st) return st;
+        DimerDesc& dd = h->hDesc[k];
+        dd.E[0] = r.E[0];
+        dd.E[1] = r.E[1];
+        std::memcpy(dd.st, r.st, sizeof dd.st);
+        dd.nX = mX.nao; dd.nY = mY.nao; dd.oX = mX.nocc; dd.oY = mY.nocc;
+        dd.cX = mX.offC; dd.cY = mY.offC; dd.eX = mX.offE; dd.eY = mY.offE;
+        dd.X = r.X; dd.Y = r.Y;
+        dd.ldh = ldh_for(prec, dd.oX, dd.oY);
+        dd.slot = d;
+        const size_t hb = hbytes_for(prec, dd.nX, dd.nY, dd.oX, dd.oY);
+        const size_t elem = prec == MCPT_FP64 ? 8 : 4;
+        if (k > wbeg && (wave_h + hb > h->wave_bytes || k - wbeg >= 65535)) {
+            waves.emplace_back(wbeg, k);
+            max_wave_h = std::max(max_wave_h, wave_h);
+            wbeg = k;
+            wave_h = 0;
+        }
+        dd.h_off = (long long)(wave_h / elem);
+        wave_h += hb;
+        const double nx = dd.nX, ny = dd.nY, ox = dd.oX, oy = dd.oY, vx = nx - ox, vy = ny - oy;
+        alg_bytes += 2.0 * nx * nx * ny * ny * 8.0;
+        alg_flops += 2.0 * 2.0 * (nx * nx * ny * ny * oy + ox * nx * nx * ny * oy + ox * nx * oy * ny * vy +
+                                  ox * vx * oy * vy * nx);
+        alg_flops_half += 2.0 * 2.0 * (nx * nx * ny * ny * oy + ox * nx * nx * ny * oy);
+    }
+    waves.emplace_back(wbeg, count);
+    max_wave_h = std::max(max_wave_h, wave_h);
+
+    mcpt_status st = upload_static(h);
+    if (st) return st;
+    if ((st = ensure(h, &h->dDesc, &h->capDesc, count * sizeof(DimerDesc)))) return st;
+    if ((st = ensure(h, &h->dH, &h->capH, max_wave_h))) return st;
+    if ((st = ensure(h, &h->dE2, &h->capE2, (size_t)2 * D * sizeof(double)))) return st;
+    if ((st = ensure(h, &h->dMon, &h->capMon, (size_t)2 * N * sizeof(double) + 2 * sizeof(double)))) return st;
+    h->dTot = h->dMon + 2 * N;
+    std::vector<size_t> work_off;
+    if (is_tensor_form(prec)) {
+        size_t total = 0;
+        for (auto& w : waves) {
+            work_off.push_back(total);
+            total += (tc_work_bytes(h->hDesc.data() + w.first, w.second - w.first) + 255) & ~(size_t)255;
+        }
+        if ((st = ensure(h, &h->dWork, &h->capWork, total))) return st;
+    }
+    CK(h, cudaMemcpyAsync(h->dDesc, h->hDesc.data(), count * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
+
+    for (size_t w = 0; w < waves.size(); w++) {
+        mcpt_ctx::Wave wv{};
+        wv.b = waves[w].first;
+        wv.nd = waves[w].second - wv.b;
+        for (int k = wv.b; k < wv.b + wv.nd; k++) {
+            const DimerDesc& dd = h->hDesc[k];
+            wv.max_rows = std::max(wv.max_rows, dd.nX * dd.nY);
+            wv.max_occ = std::max(wv.max_occ, std::max(dd.oX, dd.oY));
+            wv.max_ao = std::max(wv.max_ao, std::max(dd.nX, dd.nY));
+        }
+        if (is_tensor_form(prec)) {
+            char tcerr[256] = {0};
+            const size_t end = (w + 1 < work_off.size()) ? work_off[w + 1] : h->capWork;
+            cudaError_t e = tc_prepare(prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3, h->hDesc.data() + wv.b,
+                                       h->dDesc + wv.b, wv.nd, h->dC, static_cast<float*>(h->dH),
+                                       static_cast<char*>(h->dWork) + work_off[w], end - work_off[w], h->dFlag + 1,
+                                       h->stream, &wv.tc, tcerr, sizeof tcerr);
+            if (e != cudaSuccess)
+                return fail(h, MCPT_ECUDA, "tensor-core plan: %s (%s)", cudaGetErrorString(e), tcerr);
+        }
+        P.waves.push_back(wv);
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    P.prec = prec;
+    P.first = first;
+    P.count = count;
+    P.alg_bytes = alg_bytes;
+    P.alg_flops = alg_flops;
+    P.alg_flops_half = alg_flops_half;
+    P.valid = true;
+    return MCPT_OK;
+}
+
+static mcpt_status run_impl(mcpt_handle h, int first, int count)
+{
+    CK(h, cudaSetDevice(h->device));
+    auto& P = h->plan;
+    if (!P.valid || P.first != first || P.count != count || P.prec != h->prec) {
+        mcpt_status st = build_plan(h, first, count);
+        if (st) return st;
+    }
+    const int D = (int)h->dims.size();
+    const int N = (int)h->mons.size();
+    const mcpt_precision prec = h->prec;
+    CK(h, cudaMemsetAsync(h->dFlag + 1, 0, sizeof(int), h->stream));
+
+    RunEvents& re = h->rev;
+    const size_t W = P.waves.size();
+    const size_t nev = 2 + 2 * W;
+    std::vector<cudaEvent_t> ev;
+    if (h->timing) {
+        while (ev.size() < nev) {
+            if (!re.pool.empty()) {
+                ev.push_back(re.pool.back());
+                re.pool.pop_back();
+            } else {
+                cudaEvent_t e;
+                CK(h, cudaEventCreate(&e));
+                ev.push_back(e);
+            }
+        }
+        CK(h, cudaEventRecord(ev[0], h->stream));
+    }
+
+    int launches = 0;
+    for (size_t w = 0; w < W; w++) {
+        const auto& wv = P.waves[w];
+        const DimerDesc* wd = h->dDesc + wv.b;
+        switch (prec) {
+        case MCPT_FP64:
+            CK(h, launch_half_fp64(wd, wv.nd, wv.max_rows, wv.max_occ, h->dC, static_cast<double*>(h->dH), h->stream));
+            break;
+        case MCPT_FP32C:
+            CK(h, launch_half_fp32c(wd, wv.nd, wv.max_rows, wv.max_occ, h->dC, static_cast<float*>(h->dH), h->stream));
+            break;
+        case MCPT_TF32:
+        case MCPT_BF16X3:
+            CK(h, tc_launch(wv.tc, h->stream));
+            break;
+        }
+        launches++;
+        if (h->timing) CK(h, cudaEventRecord(ev[1 + 2 * w], h->stream));
+        if (prec == MCPT_FP64)
+            CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
+                                     h->stream));
+        else
+            CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const float*>(h->dH), h->dE2,
+                                     h->stream));
+        launches++;
+        if (h->timing) CK(h, cudaEventRecord(ev[2 + 2 * w], h->stream));
+    }
+    MonomerLists L{h->dLists, h->dLists + N + 1, N};
+    CK(h, launch_reduce(h->dE2, D, L, h->dMon, h->dTot, h->stream));
+    launches++;
+    if (h->timing) {
+        CK(h, cudaEventRecord(ev[nev - 1], h->stream));
+        re.pending.push_back(std::move(ev));
+    }
+
+    for (int k = 0; k < count; k++) h->dims[first + k].computed = true;
+    re.runs++;
+    re.launches += launches;
+    h->stats.waves = (int)W;
+    h->stats.alg_bytes = P.alg_bytes;
+    h->stats.alg_flops = P.alg_flops;
+    h->stats.alg_flops_half = P.alg_flops_half;
+    h->ran = true;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_run(mcpt_handle h)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_run: NULL handle");
+    if (h->dims.empty()) return fail(h, MCPT_ESTATE, "mcpt_run: no dimers registered");
+    return run_impl(h, 0, (int)h->dims.size());
+}
+
+mcpt_status mcpt_run_range(mcpt_handle h, int first, int count)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_run_range: NULL handle");
+    const int D = (int)h->dims.size();
+    if (D == 0) return fail(h, MCPT_ESTATE, "mcpt_run_range: no dimers registered");
+    if (first < 0 || count < 1 || first + count > D)
+        return fail(h, MCPT_EINVAL, "mcpt_run_range: [%d, %d) outside [0, %d)", first, first + count, D);
+    return run_impl(h, first, count);
+}
+
+mcpt_status mcpt_energies(mcpt_handle h, double* mon_J, double* mon_K, double* per_dimer, double* total)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_energies: NULL handle");
+    if (!h->ran) return fail(h, MCPT_ESTATE, "mcpt_energies: no run yet");
+    for (size_t d = 0; d < h->dims.size(); d++)
+        if (!h->dims[d].computed)
+            return fail(h, MCPT_ESTATE, "mcpt_energies: dimer %zu has not been computed since it was added", d);
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    int status = 0;
+    CK(h, cudaMemcpy(&status, h->dFlag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status)
+        return fail(h, MCPT_ETIMEOUT, "mcpt_energies: a device-side wait gave up (status 0x%x)", status);
+    const int N = (int)h->mons.size(), D = (int)h->dims.size();
+    if (mon_J) CK(h, cudaMemcpy(mon_J, h->dMon, N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (mon_K) CK(h, cudaMemcpy(mon_K, h->dMon + N, N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (per_dimer) CK(h, cudaMemcpy(per_dimer, h->dE2, 2 * (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
+    if (total) CK(h, cudaMemcpy(total, h->dTot, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_collect_stats(mcpt_handle h, mcpt_run_stats* out)
+{
+    if (!h || !out) return fail(h, MCPT_EINVAL, "mcpt_collect_stats: NULL argument");
+    if (!h->ran) return fail(h, MCPT_ESTATE, "mcpt_collect_stats: no run yet");
+    CK(h, cudaSetDevice(h->device));
+    *out = h->stats;
+    for (int k = 0; k < 4; k++) out->ms[k] = 0.f;
+    RunEvents& re = h->rev;
+    out->runs = re.runs;
+    out->launches = re.launches;
+    if (!re.pending.empty()) {
+        CK(h, cudaStreamSynchronize(h->stream));
+        for (auto& ev : re.pending) {
+            const int W = (int)(ev.size() - 2) / 2;
+            float t;
+            for (int w = 0; w < W; w++) {
+                CK(h, cudaEventElapsedTime(&t, ev[2 * w], ev[1 + 2 * w]));
+                out->ms[0] += t;
+                CK(h, cudaEventElapsedTime(&t, ev[1 + 2 * w], ev[2 + 2 * w]));
+                out->ms[1] += t;
+            }
+            CK(h, cudaEventElapsedTime(&t, ev[2 * W], ev[2 * W + 1]));
+            out->ms[2] += t;
+            CK(h, cudaEventElapsedTime(&t, ev[0], ev[2 * W + 1]));
+            out->ms[3] += t;
+            re.pool.insert(re.pool.end(), ev.begin(), ev.end());
+        }
+        re.pending.clear();
+    }
+    re.runs = 0;
+    re.launches = 0;
+    return MCPT_OK;
+}
+
+int mcpt_num_monomers(mcpt_handle h) { return h ? (int)h->mons.size() : 0; }
+int mcpt_num_dimers(mcpt_handle h) { return h ? (int)h->dims.size() : 0; }
+
+const char* mcpt_last_error(mcpt_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void mcpt_destroy(mcpt_handle h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->owned) cudaFree(p);
+    cudaFree(h->dC);
+    cudaFree(h->dE);
+    cudaFree(h->dDesc);
+    cudaFree(h->dH);
+    cudaFree(h->dWork);
+    cudaFree(h->dE2);
+    cudaFree(h->dMon);
+    cudaFree(h->dLists);
+    cudaFree(h->dFlag);
+    for (cudaEvent_t e : h->rev.pool) cudaEventDestroy(e);
+    for (auto& v : h->rev.pending)
+        for (cudaEvent_t e : v) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

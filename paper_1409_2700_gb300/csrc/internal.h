@@ -1,0 +1,105 @@
+// internal.h -- device-side descriptors and kernel launchers of libmcpt.
+//
+// Geometry of one dimer "form" (f = 0: the Coulomb-type block A, giving
+// (i a|j b); f = 1: the exchange-type block K, giving (i b|j a)).  Both are
+// a 4-index block E[p0][p1][p2][p3] whose axes 0 and 2 carry occupied
+// outputs (i from X, j from Y):
+//   f = 0: E = A[mu][nu][lam][sig]   p0=mu->i  p1=nu->a   p2=lam->j  p3=sig->b
+//   f = 1: E = K[mu][lam][sig][nu]   p0=mu->i  p1=lam->b  p2=sig->j  p3=nu->a
+// (Eq. dp2e with (p r|q s) = (i a|j b), resp. its exchange-type form.)
+//
+// The path has two halves:
+//   first half  ("transform", reads every AO byte once):
+//       H_f[(p1,p3)][(i,j)] = sum_{p0,p2} C_X[p0][i] C_Y[p2][j] E[p0][p1][p2][p3]
+//   second half ("finish"):  (i a|j b) = sum_{nu,sig} C_X[nu][a] C_Y[sig][b] H_0[(nu,sig)][(i,j)]
+//                            (i b|j a) = sum_{lam,nu} C_Y[lam][b] C_X[nu][a] H_1[(lam,nu)][(i,j)]
+//       then D = 1/(e_i+e_j-e_a-e_b) and the two energy sums in FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcpt {
+
+constexpr int kMaxAO = 256;          // any form (FP64 / FP32C)
+constexpr int kMaxAOTensor = 128;    // tensor-core forms
+constexpr int kMaxPairsTensor = 256; // nocc_X * nocc_Y for tensor-core forms
+
+struct DimerDesc {
+    const double* E[2];   // block base of form 0 (A) and form 1 (K)
+    long long st[2][3];   // element strides of axes p0, p1, p2 (axis p3 is contiguous)
+    int nX, nY, oX, oY;
+    int cX, cY;           // offsets (doubles) of C_X, C_Y in the coefficient pool
+    int eX, eY;           // offsets (doubles) of eps_X, eps_Y in the energy pool
+    int X, Y;             // monomer ids
+    long long h_off;      // first-half result: form f starts at h_off + f * nX*nY*ldh
+    int ldh;              // row stride of the first-half result (>= oX*oY)
+    int slot;             // index of this dimer's {E_J, E_K} in the per-dimer output
+};
+
+// Per-monomer accumulation lists: dimers touching monomer m are
+// list[start[m] .. start[m+1]) (ascending dimer slot).
+struct MonomerLists {
+    const int* start;
+    const int* list;
+    int n_mon;
+};
+
+// ---- launchers (each returns the launch error; work is asynchronous) ----
+
+// FP64 first half on CUDA cores, one thread per output row.
+cudaError_t launch_half_fp64(const DimerDesc* d_desc, int nd, int max_rows, int max_occ,
+                             const double* Cpool, double* H, cudaStream_t s);
+
+// FP32 first half with compensated (TwoProduct/TwoSum) accumulation.
+cudaError_t launch_half_fp32c(const DimerDesc* d_desc, int nd, int max_rows, int max_occ,
+                              const double* Cpool, float* H, cudaStream_t s);
+
+// Second half + denominators + energies.  H is double (FP64 form) or float.
+cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
+                               const double* Cpool, const double* Epool, const double* H,
+                               double* E2, cudaStream_t s);
+cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
+                               const double* Cpool, const double* Epool, const float* H,
+                               double* E2, cudaStream_t s);
+
+// Per-monomer halves and the compensated lattice total.
+cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists,
+                          double* mon /* 2*n_mon */, double* total /* 2 */, cudaStream_t s);
+
+// Finiteness check of n doubles; sets *flag to 1 if any is NaN/Inf.
+cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s);
+// Same for a strided 4-index block.
+cudaError_t launch_check_finite4(const double* x, const int dims[4], const long long st[3],
+                                 int* flag, cudaStream_t s);
+
+// ---- tensor-core first half (tcgen05) ----
+enum TcKind { TC_TF32 = 0, TC_BF16X3 = 1 };
+
+// Everything one launch of the tensor-core kernel needs; filled by
+// tc_prepare (host work: tensor maps, work items, their upload), replayed by
+// tc_launch (kernel launch only).
+struct TcLaunch {
+    const void* items;          // device TcItem array
+    int n_items;
+    const void* maps;           // device CUtensorMap array, [dimer][form]
+    const DimerDesc* desc;      // device descriptors of the launch's dimers
+    const double* Cpool;
+    float* H;
+    int* status;
+    int sf;                     // FP64 staging stages
+    unsigned f_stage_bytes, w_stage_bytes, tmem_cols;
+    int kind;
+    int grid;
+    size_t smem;
+};
+
+// Bytes of device work space (tensor maps + items) the dimers need.
+size_t tc_work_bytes(const DimerDesc* h_desc, int nd);
+// Encode tensor maps, order work items (longest first), upload them to
+// d_work, and fill *out.  Synchronous w.r.t. the host buffers.
+cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const double* Cpool,
+                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s, TcLaunch* out,
+                       char* err, size_t errlen);
+cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s);
+
+}  // namespace mcpt

@@ -1,0 +1,250 @@
+// k_finish.cu -- second half of the dimer transformation, the FP64 energy
+// epilogue, and the per-monomer accumulation.
+//
+// For each occupied pair (i, j) the first half left two nX x nY matrices
+//   H_0[(nu,sig)][(i,j)]   (nu in X, sig in Y)   from the (XX|YY) block
+//   H_1[(lam,nu)][(i,j)]   (lam in Y, nu in X)   from the (XY|YX) block
+// and the virtual quarter transformations of Eq. (dp2e) finish them:
+//   (i a|j b) = sum_nu C_X[nu][a] sum_sig H_0[nu][sig] C_Y[sig][b]
+//   (i b|j a) = sum_lam C_Y[lam][b] sum_nu H_1[lam][nu] C_X[nu][a]
+// Then, in FP64 (Sec. II.C energy tensor, Eq. (ed2) with T = vD):
+//   D = 1/(e_i + e_j - e_a - e_b),  E_J += 4 (ia|jb)^2 D,  E_K += -2 (ia|jb)(ib|ja) D.
+// One CTA owns one dimer, so the per-dimer energies come out of a fixed-order
+// block reduction: deterministic run to run, no atomics.
+#include "internal.h"
+
+namespace mcpt {
+namespace {
+
+constexpr int kFinThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// T: arithmetic/storage type of the second half (double or float);
+// HT: element type of the first-half result.
+template <typename T, typename HT>
+__global__ void __launch_bounds__(kFinThreads)
+k_finish(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
+         const double* __restrict__ Epool, const HT* __restrict__ H, double* __restrict__ E2)
+{
+    const DimerDesc& d = dd[blockIdx.x];
+    const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
+    const int vX = nX - oX, vY = nY - oY;
+    const int rows = nX * nY, ld = d.ldh;
+    const double* CX = Cpool + d.cX;
+    const double* CY = Cpool + d.cY;
+    const double* eX = Epool + d.eX;
+    const double* eY = Epool + d.eY;
+    const HT* H0 = H + d.h_off;
+    const HT* H1 = H + d.h_off + (long long)rows * ld;
+
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* S = reinterpret_cast<T*>(smraw);                 // [rows]
+    T* Tm = S + rows;                                   // [max(nX*vY, nY*vX)]
+    T* VA = Tm + (nX * vY > nY * vX ? nX * vY : nY * vX);  // [vX][vY]
+
+    double ej = 0.0, ek = 0.0;
+    const int tid = threadIdx.x;
+    for (int i = 0; i < oX; i++) {
+        for (int j = 0; j < oY; j++) {
+            const int col = i * oY + j;
+            const double eij = eX[i] + eY[j];
+            // ---- (i a|j b) from H_0
+            for (int k = tid; k < rows; k += kFinThreads) S[k] = (T)H0[(long long)k * ld + col];
+            __syncthreads();
+            for (int k = tid; k < nX * vY; k += kFinThreads) {
+                const int nu = k / vY, b = k % vY;
+                const T* s = S + nu * nY;
+                T acc = 0;
+                for (int sg = 0; sg < nY; sg++) acc = fma(s[sg], (T)__ldg(CY + sg * nY + oY + b), acc);
+                Tm[k] = acc;
+            }
+            __syncthreads();
+            for (int k = tid; k < vX * vY; k += kFinThreads) {
+                const int a = k / vY, b = k % vY;
+                T acc = 0;
+                for (int nu = 0; nu < nX; nu++) acc = fma((T)__ldg(CX + nu * nX + oX + a), Tm[nu * vY + b], acc);
+                VA[k] = acc;
+                const double v = (double)acc;
+                const double D = 1.0 / (eij - (eX[oX + a] + eY[oY + b]));
+                ej = fma(v * v, D, ej);
+            }
+            __syncthreads();
+            // ---- (i b|j a) from H_1
+            for (int k = tid; k < rows; k += kFinThreads) S[k] = (T)H1[(long long)k * ld + col];
+            __syncthreads();
+            for (int k = tid; k < nY * vX; k += kFinThreads) {
+                const int lam = k / vX, a = k % vX;
+                const T* s = S + lam * nX;
+                T acc = 0;
+                for (int nu = 0; nu < nX; nu++) acc = fma(s[nu], (T)__ldg(CX + nu * nX + oX + a), acc);
+                Tm[k] = acc;
+            }
+            __syncthreads();
+            for (int k = tid; k < vY * vX; k += kFinThreads) {
+                const int b = k / vX, a = k % vX;
+                T acc = 0;
+                for (int lam = 0; lam < nY; lam++) acc = fma((T)__ldg(CY + lam * nY + oY + b), Tm[lam * vX + a], acc);
+                const double D = 1.0 / (eij - (eX[oX + a] + eY[oY + b]));
+                ek = fma((double)VA[a * vY + b] * (double)acc, D, ek);
+            }
+            __syncthreads();
+        }
+    }
+    // fixed-order block reduction
+    __shared__ double red[2][kFinThreads / 32];
+    ej = warp_sum(ej);
+    ek = warp_sum(ek);
+    if ((tid & 31) == 0) { red[0][tid >> 5] = ej; red[1][tid >> 5] = ek; }
+    __syncthreads();
+    if (tid == 0) {
+        double sj = 0.0, sk = 0.0;
+        for (int w = 0; w < kFinThreads / 32; w++) { sj += red[0][w]; sk += red[1][w]; }
+        E2[2 * d.slot + 0] = 4.0 * sj;
+        E2[2 * d.slot + 1] = -2.0 * sk;
+    }
+}
+
+template <typename T, typename HT>
+cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
+                          const double* Epool, const HT* H, double* E2, cudaStream_t s)
+{
+    if (nd <= 0) return cudaSuccess;
+    const size_t smem = (size_t)3 * max_ao * max_ao * sizeof(T);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_finish<T, HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_finish<T, HT><<<nd, kFinThreads, smem, s>>>(d_desc, Cpool, Epool, H, E2);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ reduction
+__device__ __forceinline__ void neumaier_add(double& s, double& c, double v)
+{
+    const double t = s + v;
+    if (fabs(s) >= fabs(v)) c += (s - t) + v;
+    else                    c += (v - t) + s;
+    s = t;
+}
+
+constexpr int kRedThreads = 256;
+
+// Blocks [0, nbm): one thread per monomer sums half of each of its dimers'
+// terms in ascending dimer order.  Last block: lattice totals from a fixed
+// partition of the dimer list into kRedThreads contiguous chunks.
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restrict__ mon,
+         double* __restrict__ total)
+{
+    const int nbm = (L.n_mon + kRedThreads - 1) / kRedThreads;
+    if ((int)blockIdx.x < nbm) {
+        const int m = blockIdx.x * kRedThreads + threadIdx.x;
+        if (m >= L.n_mon) return;
+        double sj = 0, cj = 0, sk = 0, ck = 0;
+        for (int k = L.start[m]; k < L.start[m + 1]; k++) {
+            const int dslot = L.list[k];
+            neumaier_add(sj, cj, 0.5 * E2[2 * dslot]);
+            neumaier_add(sk, ck, 0.5 * E2[2 * dslot + 1]);
+        }
+        mon[m] = sj + cj;
+        mon[L.n_mon + m] = sk + ck;
+        return;
+    }
+    __shared__ double part[4][kRedThreads];
+    const int t = threadIdx.x;
+    const int chunk = (nd + kRedThreads - 1) / kRedThreads;
+    const int lo = t * chunk, hi = min(nd, lo + chunk);
+    double sj = 0, cj = 0, sk = 0, ck = 0;
+    for (int k = lo; k < hi; k++) {
+        neumaier_add(sj, cj, E2[2 * k]);
+        neumaier_add(sk, ck, E2[2 * k + 1]);
+    }
+    part[0][t] = sj; part[1][t] = cj; part[2][t] = sk; part[3][t] = ck;
+    __syncthreads();
+    if (t == 0) {
+        double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+        for (int w = 0; w < kRedThreads; w++) {
+            neumaier_add(s0, c0, part[0][w]);
+            c0 += part[1][w];
+            neumaier_add(s1, c1, part[2][w]);
+            c1 += part[3][w];
+        }
+        total[0] = s0 + c0;
+        total[1] = s1 + c1;
+    }
+}
+
+__global__ void k_check_finite(const double* __restrict__ x, long long n, int* flag)
+{
+    bool bad = false;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(x[k]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_check_finite4(const double* __restrict__ x, int d0, int d1, int d2, int d3,
+                                long long s0, long long s1, long long s2, int* flag)
+{
+    const long long n = (long long)d0 * d1 * d2 * d3;
+    bool bad = false;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long r = k;
+        const int i3 = r % d3; r /= d3;
+        const int i2 = r % d2; r /= d2;
+        const int i1 = r % d1; r /= d1;
+        const int i0 = (int)r;
+        bad |= !isfinite(x[i0 * s0 + i1 * s1 + i2 * s2 + i3]);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
+                               const double* Epool, const double* H, double* E2, cudaStream_t s)
+{
+    return launch_finish<double, double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, s);
+}
+
+cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
+                               const double* Epool, const float* H, double* E2, cudaStream_t s)
+{
+    return launch_finish<float, float>(d_desc, nd, max_ao, Cpool, Epool, H, E2, s);
+}
+
+cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists, double* mon, double* total,
+                          cudaStream_t s)
+{
+    const int nbm = (lists.n_mon + kRedThreads - 1) / kRedThreads;
+    k_reduce<<<nbm + 1, kRedThreads, 0, s>>>(E2, nd, lists, mon, total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_check_finite<<<(int)blocks, 256, 0, s>>>(x, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite4(const double* x, const int dims[4], const long long st[3], int* flag,
+                                 cudaStream_t s)
+{
+    const long long n = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_check_finite4<<<(int)blocks, 256, 0, s>>>(x, dims[0], dims[1], dims[2], dims[3], st[0], st[1], st[2], flag);
+    return cudaGetLastError();
+}
+
+}  // namespace mcpt

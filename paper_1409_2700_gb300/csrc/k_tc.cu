@@ -1,0 +1,698 @@
+// k_tc.cu -- first half of the dimer transformation on the 5th-generation
+// tensor cores (tcgen05, sm_103a), TF32 or BF16x3 operands, FP32 accumulate.
+//
+// The two occupied quarter transformations of Eq. (dp2e) are fused into one
+// GEMM per dimer form (see internal.h for the axis naming):
+//   H[(p1,p3)][(i,j)] = sum_{(p0,p2)} E[p0][p1][p2][p3] * W[(p0,p2)][(i,j)],
+//   W[(p0,p2)][(i,j)] = C_X[p0][i] C_Y[p2][j]            (Kronecker product)
+// M = rows (p1,p3) in tiles of 128, N = nocc_X*nocc_Y padded to 16, K = (p0,p2).
+// It reads every AO integral exactly once and is bound by HBM: the padded
+// tensor-core work (o_X o_Y / o_Y times the factorised flops) stays far below
+// the time the integrals take to stream in.
+//
+// Per CTA (persistent, one per SM), warp roles:
+//   warp 0     TMA producer: 4-D tensor-map loads of FP64 integral boxes
+//              E[p0][p1 range][p2 chunk of 32][all p3] into a staging ring
+//   warp 1     MMA issuer (one thread) and TMEM owner
+//   warps 2-5  converters: FP64 -> TF32 (round to nearest) or BF16 hi/lo,
+//              written as 128-row K-major SWIZZLE_128B operand tiles; they
+//              also build the W tile of each K-block
+//   warps 6-9  epilogue: tcgen05.ld of the FP32 accumulators -> global H
+// Accumulators are double-buffered in TMEM so one work item drains while the
+// next one accumulates.  Every wait is bounded by wall-clock time: on expiry
+// the CTA records an error code, drains its own copies and MMAs, frees TMEM
+// and returns.
+#include "internal.h"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+namespace mcpt {
+
+struct TcItem {
+    int dimer;   // index within the launch's descriptor array
+    int form;    // 0: A block, 1: K block
+    int mt0;     // first M-tile
+    int mts;     // number of M-tiles (accumulators) in this item
+};
+
+namespace {
+
+constexpr int kWarps = 10;
+constexpr int kThreadsTc = kWarps * 32;
+constexpr int kKC = 32;              // p2 values per K-block (128 B of TF32 per operand row)
+constexpr int kAccCols = 256;        // TMEM columns per accumulator set (x2 sets)
+constexpr int kABytes = 128 * 128;   // one 128-row operand tile
+constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s per wait
+
+// error codes written to the status word
+constexpr int kErrTimeoutBase = 0x100;
+
+struct __align__(8) TcShared {
+    unsigned long long full_f[8], empty_f[8];
+    unsigned long long full_a[2], empty_a[2];
+    unsigned long long full_w[2], empty_w[2];
+    unsigned long long tmem_full[2], tmem_empty[2];
+    unsigned long long drain;
+    unsigned int tmem_base;
+    volatile int abort;
+};
+
+struct TcParams {
+    const TcItem* items;
+    int n_items;
+    const CUtensorMap* maps;       // [dimer][form]
+    const DimerDesc* desc;
+    const double* Cpool;
+    float* H;
+    int* status;
+    int sf;                        // FP64 staging stages
+    unsigned int f_stage_bytes;    // bytes per staging slot
+    unsigned int w_stage_bytes;    // bytes per W slot
+    unsigned int tmem_cols;
+    int kind;                      // TC_TF32 / TC_BF16X3
+};
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete; false on timeout/abort.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, TcShared* sh, int* status,
+                                          int where)
+{
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    while (true) {
+        if (mbar_test(b, parity)) return true;
+        if (sh->abort) return false;
+        if (now_ns() - t0 > kWaitNs) {
+            sh->abort = 1;
+            atomicCAS(status, 0, kErrTimeoutBase + where);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar, int c0,
+                                            int c1, int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(unsigned long long* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int KIND>
+__device__ __forceinline__ void tc_mma(unsigned dtmem, unsigned long long adesc, unsigned long long bdesc,
+                                       unsigned idesc, unsigned accum)
+{
+    if (KIND == TC_TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+                dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                dtmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+            : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns per warp
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
+{
+    unsigned r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
+}
+
+// K-major operand with SWIZZLE_128B: 8-row x 128-byte atoms stacked along the
+// row dimension (stride 1024 B); the 16-byte chunk c of row r sits at chunk
+// position c ^ (r % 8).  Matrix-descriptor fields: start address >> 4,
+// leading-dimension offset (unused for this layout, 16 B), stride offset
+// 1024 B >> 4, descriptor version 1, swizzle mode 2 (128 B).
+__device__ __forceinline__ unsigned long long sw128_desc(const void* tile)
+{
+    const unsigned long long a = (smem_u32(tile) & 0x3FFFFu) >> 4;
+    return a | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ unsigned sw128_off(int row, int chunk)
+{
+    return (unsigned)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+// Instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), both K-major,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ unsigned make_idesc(int kind, int N)
+{
+    const unsigned fmt = kind == TC_TF32 ? 2u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned to_tf32(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned short to_bf16_bits(float x)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// Geometry of the current item, derived from its descriptor.
+struct ItemGeo {
+    int n0, n1, n2, n3;
+    int o0, o2;
+    int p1t;          // p1 values per M-tile
+    int kcs;          // p2 chunks
+    int kblocks;      // n0 * kcs
+    int N;            // padded pair count (ldh)
+    int rows;         // n1 * n3
+};
+
+__device__ __forceinline__ ItemGeo geo_of(const DimerDesc& d, int f)
+{
+    ItemGeo g;
+    g.n0 = d.nX;
+    g.n1 = f ? d.nY : d.nX;
+    g.n2 = d.nY;
+    g.n3 = f ? d.nX : d.nY;
+    g.o0 = d.oX;
+    g.o2 = d.oY;
+    g.p1t = 128 / g.n3;
+    g.kcs = (g.n2 + kKC - 1) / kKC;
+    g.kblocks = g.n0 * g.kcs;
+    g.N = d.ldh;
+    g.rows = g.n1 * g.n3;
+    return g;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned carve-out: [F ring][A ring][W ring][TcShared]
+    unsigned char* base = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    unsigned char* Fr = base;
+    unsigned char* Ar = Fr + (size_t)P.sf * P.f_stage_bytes;
+    unsigned char* Wr = Ar + 2 * kABytes;
+    TcShared* sh = reinterpret_cast<TcShared*>(Wr + 2 * P.w_stage_bytes);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.sf; s++) { mbar_init(&sh->full_f[s], 1); mbar_init(&sh->empty_f[s], 4); }
+        for (int s = 0; s < 2; s++) {
+            mbar_init(&sh->full_a[s], 4); mbar_init(&sh->empty_a[s], 1);
+            mbar_init(&sh->full_w[s], 4); mbar_init(&sh->empty_w[s], 1);
+            mbar_init(&sh->tmem_full[s], 1); mbar_init(&sh->tmem_empty[s], 4);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(P.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            unsigned gF = 0;
+            unsigned issued_phase[8];
+            bool issued[8];
+            for (int s = 0; s < 8; s++) issued[s] = false;
+            for (int it = blockIdx.x; it < P.n_items && !sh->abort; it += gridDim.x) {
+                const TcItem item = P.items[it];
+                const DimerDesc& d = P.desc[item.dimer];
+                const ItemGeo g = geo_of(d, item.form);
+                const CUtensorMap* map = P.maps + 2 * item.dimer + item.form;
+                const unsigned box = (unsigned)g.n3 * kKC * g.p1t * 8u;
+                for (int kb = 0; kb < g.kblocks && !sh->abort; kb++) {
+                    const int p0 = kb / g.kcs, kc = kb % g.kcs;
+                    for (int mt = 0; mt < item.mts; mt++, gF++) {
+                        const int s = gF % P.sf;
+                        const unsigned ph = (gF / P.sf) & 1;
+                        if (!mbar_wait(&sh->empty_f[s], ph ^ 1, sh, P.status, 1)) break;
+                        mbar_arrive_tx(&sh->full_f[s], box);
+                        tma_load_4d(Fr + (size_t)s * P.f_stage_bytes, map, &sh->full_f[s], 0, kc * kKC,
+                                    (item.mt0 + mt) * g.p1t, p0);
+                        issued[s] = true;
+                        issued_phase[s] = ph;
+                    }
+                }
+            }
+            // copies in flight must land before the CTA may exit
+            for (int s = 0; s < P.sf; s++)
+                if (issued[s]) {
+                    const unsigned long long t0 = now_ns();
+                    while (!mbar_test(&sh->full_f[s], issued_phase[s]) && now_ns() - t0 < kWaitNs) {}
+                }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            unsigned gA = 0, gW = 0, li = 0;
+            bool any = false;
+            for (int it = blockIdx.x; it < P.n_items && !sh->abort; it += gridDim.x, li++) {
+                const TcItem item = P.items[it];
+                const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
+                const unsigned idesc = make_idesc(KIND, g.N);
+                const int b = li & 1;
+                if (!mbar_wait(&sh->tmem_empty[b], ((li >> 1) & 1) ^ 1, sh, P.status, 2)) break;
+                tc_fence_after();
+                bool ok = true;
+                for (int kb = 0; kb < g.kblocks && ok; kb++, gW++) {
+                    const int ws = gW & 1;
+                    if (!(ok = mbar_wait(&sh->full_w[ws], (gW >> 1) & 1, sh, P.status, 3))) break;
+                    const unsigned long long bdesc = sw128_desc(Wr + (size_t)ws * P.w_stage_bytes);
+                    for (int mt = 0; mt < item.mts; mt++, gA++) {
+                        const int as = gA & 1;
+                        if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, sh, P.status, 4))) break;
+                        tc_fence_after();
+                        const unsigned long long adesc = sw128_desc(Ar + (size_t)as * kABytes);
+                        const unsigned dt = tmem + (unsigned)(b * kAccCols + mt * g.N);
+                        if (KIND == TC_TF32) {
+#pragma unroll
+                            for (int k = 0; k < 4; k++)   // K = 8 per MMA: 32 bytes
+                                tc_mma<KIND>(dt, adesc + 2 * k, bdesc + 2 * k, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 2; k++) {   // K = 16 per MMA; hi at +0, lo at +64 bytes
+                                const unsigned long long ah = adesc + 2 * k, al = adesc + 4 + 2 * k;
+                                const unsigned long long bh = bdesc + 2 * k, bl = bdesc + 4 + 2 * k;
+                                tc_mma<KIND>(dt, ah, bh, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                                tc_mma<KIND>(dt, ah, bl, idesc, 1u);
+                                tc_mma<KIND>(dt, al, bh, idesc, 1u);
+                            }
+                        }
+                        tc_commit(&sh->empty_a[as]);
+                        any = true;
+                    }
+                    if (ok) tc_commit(&sh->empty_w[ws]);
+                }
+                if (!ok) break;
+                tc_commit(&sh->tmem_full[b]);
+            }
+            if (any) {
+                // every issued MMA has retired before TMEM is released
+                tc_commit(&sh->drain);
+                const unsigned long long t0 = now_ns();
+                while (!mbar_test(&sh->drain, 0) && now_ns() - t0 < kWaitNs) {}
+            }
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------ converters
+        const int ct = threadIdx.x - 64;   // 0..127
+        unsigned gF = 0, gA = 0, gW = 0;
+        for (int it = blockIdx.x; it < P.n_items && !sh->abort; it += gridDim.x) {
+            const TcItem item = P.items[it];
+            const DimerDesc& d = P.desc[item.dimer];
+            const ItemGeo g = geo_of(d, item.form);
+            const double* CX = P.Cpool + d.cX;
+            const double* CY = P.Cpool + d.cY;
+            const int npairs = g.o0 * g.o2;
+            const int tile_rows_full = g.p1t * g.n3;
+            bool ok = true;
+            for (int kb = 0; kb < g.kblocks && ok; kb++, gW++) {
+                const int p0 = kb / g.kcs, kc = kb % g.kcs;
+                // ---- W tile of this K-block: row n = (i, j), K = p2 in the chunk
+                const int ws = gW & 1;
+                if (!(ok = mbar_wait(&sh->empty_w[ws], ((gW >> 1) & 1) ^ 1, sh, P.status, 5))) break;
+                unsigned char* W = Wr + (size_t)ws * P.w_stage_bytes;
+                if (KIND == TC_TF32) {
+                    for (int task = ct; task < g.N * 8; task += 128) {
+                        const int n = task >> 3, c = task & 7;
+                        uint4 v = make_uint4(0, 0, 0, 0);
+                        if (n < npairs) {
+                            const int i = n / g.o2, j = n % g.o2;
+                            const float u0 = (float)__ldg(CX + p0 * d.nX + i);
+                            unsigned w4[4];
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                const int p2 = kc * kKC + c * 4 + e;
+                                const float u2 = p2 < g.n2 ? (float)__ldg(CY + p2 * d.nY + j) : 0.f;
+                                w4[e] = to_tf32(u0 * u2);
+                            }
+                            v = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                        }
+                        *reinterpret_cast<uint4*>(W + sw128_off(n, c)) = v;
+                    }
+                } else {
+                    for (int task = ct; task < g.N * 4; task += 128) {
+                        const int n = task >> 2, c = task & 3;
+                        uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+                        if (n < npairs) {
+                            const int i = n / g.o2, j = n % g.o2;
+                            const float u0 = (float)__ldg(CX + p0 * d.nX + i);
+                            unsigned short hb[8], lb[8];
+#pragma unroll
+                            for (int e = 0; e < 8; e++) {
+                                const int p2 = kc * kKC + c * 8 + e;
+                                const float w = p2 < g.n2 ? u0 * (float)__ldg(CY + p2 * d.nY + j) : 0.f;
+                                hb[e] = to_bf16_bits(w);
+                                lb[e] = to_bf16_bits(w - __bfloat162float(__ushort_as_bfloat16(hb[e])));
+                            }
+                            vh = make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16),
+                                            hb[6] | (hb[7] << 16));
+                            vl = make_uint4(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16), lb[4] | (lb[5] << 16),
+                                            lb[6] | (lb[7] << 16));
+                        }
+                        *reinterpret_cast<uint4*>(W + sw128_off(n, c)) = vh;
+                        *reinterpret_cast<uint4*>(W + sw128_off(n, 4 + c)) = vl;
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->full_w[ws]);
+
+                // ---- A tiles of this K-block, one per M-tile of the item
+                for (int mt = 0; mt < item.mts; mt++, gF++, gA++) {
+                    const int s = gF % P.sf;
+                    if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, sh, P.status, 6))) break;
+                    const int as = gA & 1;
+                    if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, sh, P.status, 7))) break;
+                    const double* F = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
+                    unsigned char* A = Ar + (size_t)as * kABytes;
+                    if (KIND == TC_TF32) {
+                        // task = (row r, chunk c): 4 consecutive p2 of row r
+                        for (int task = ct; task < 128 * 8; task += 128) {
+                            const int c = task >> 7, r = task & 127;
+                            uint4 v = make_uint4(0, 0, 0, 0);
+                            if (r < tile_rows_full) {
+                                const int p1l = r / g.n3, p3 = r % g.n3;
+                                const double* src = F + ((size_t)(p1l * kKC + c * 4) * g.n3 + p3);
+                                v.x = to_tf32((float)src[0]);
+                                v.y = to_tf32((float)src[g.n3]);
+                                v.z = to_tf32((float)src[2 * g.n3]);
+                                v.w = to_tf32((float)src[3 * g.n3]);
+                            }
+                            *reinterpret_cast<uint4*>(A + sw128_off(r, c)) = v;
+                        }
+                    } else {
+                        for (int task = ct; task < 128 * 4; task += 128) {
+                            const int c = task >> 7, r = task & 127;
+                            uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+                            if (r < tile_rows_full) {
+                                const int p1l = r / g.n3, p3 = r % g.n3;
+                                const double* src = F + ((size_t)(p1l * kKC + c * 8) * g.n3 + p3);
+                                unsigned short hb[8], lb[8];
+#pragma unroll
+                                for (int e = 0; e < 8; e++) {
+                                    const float x = (float)src[e * g.n3];
+                                    hb[e] = to_bf16_bits(x);
+                                    lb[e] = to_bf16_bits(x - __bfloat162float(__ushort_as_bfloat16(hb[e])));
+                                }
+                                vh = make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16),
+                                                hb[6] | (hb[7] << 16));
+                                vl = make_uint4(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16), lb[4] | (lb[5] << 16),
+                                                lb[6] | (lb[7] << 16));
+                            }
+                            *reinterpret_cast<uint4*>(A + sw128_off(r, c)) = vh;
+                            *reinterpret_cast<uint4*>(A + sw128_off(r, 4 + c)) = vl;
+                        }
+                    }
+                    fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&sh->full_a[as]);
+                        mbar_arrive(&sh->empty_f[s]);
+                    }
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;          // TMEM lane quarter this warp may access
+        const int r = q * 32 + lane;     // accumulator row = TMEM lane
+        unsigned li = 0;
+        for (int it = blockIdx.x; it < P.n_items && !sh->abort; it += gridDim.x, li++) {
+            const TcItem item = P.items[it];
+            const DimerDesc& d = P.desc[item.dimer];
+            const ItemGeo g = geo_of(d, item.form);
+            const int b = li & 1;
+            if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, sh, P.status, 8)) break;
+            tc_fence_after();
+            float* Hf = P.H + d.h_off + (long long)item.form * g.rows * g.N;
+            for (int mt = 0; mt < item.mts; mt++) {
+                const int tile = item.mt0 + mt;
+                const int p1_lo = tile * g.p1t;
+                const int p1_hi = min(g.n1, p1_lo + g.p1t);
+                const int valid = (p1_hi - p1_lo) * g.n3;
+                float* out = Hf + (long long)(p1_lo * g.n3 + r) * g.N;
+                for (int c = 0; c < g.N; c += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * kAccCols + mt * g.N + c), v);
+                    if (r < valid) {
+                        float4* o4 = reinterpret_cast<float4*>(out + c);
+#pragma unroll
+                        for (int k = 0; k < 4; k++) o4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->tmem_empty[b]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int items_per_form(const DimerDesc& d, int f, int* mts_max)
+{
+    const int n1 = f ? d.nY : d.nX, n3 = f ? d.nX : d.nY;
+    const int p1t = 128 / n3;
+    const int tiles = (n1 + p1t - 1) / p1t;
+    const int mmax = std::max(1, std::min(8, kAccCols / d.ldh));
+    *mts_max = mmax;
+    return (tiles + mmax - 1) / mmax;
+}
+
+}  // namespace
+
+size_t tc_work_bytes(const DimerDesc* h, int nd)
+{
+    size_t items = 0;
+    for (int k = 0; k < nd; k++)
+        for (int f = 0; f < 2; f++) {
+            int m;
+            items += items_per_form(h[k], f, &m);
+        }
+    return (size_t)nd * 2 * sizeof(CUtensorMap) + items * sizeof(TcItem) + 256;
+}
+
+cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const double* Cpool,
+                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s, TcLaunch* out,
+                       char* err, size_t errlen)
+{
+    if (nd <= 0) return cudaSuccess;
+    auto encode = get_encode();
+    if (!encode) {
+        snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable");
+        return cudaErrorNotSupported;
+    }
+    std::vector<CUtensorMap> maps((size_t)nd * 2);
+    std::vector<TcItem> items;
+    int maxN = 16;
+    unsigned max_box = 0;
+    for (int k = 0; k < nd; k++) {
+        const DimerDesc& d = h_desc[k];
+        maxN = std::max(maxN, d.ldh);
+        for (int f = 0; f < 2; f++) {
+            const int n0 = d.nX, n1 = f ? d.nY : d.nX, n2 = d.nY, n3 = f ? d.nX : d.nY;
+            const int p1t = 128 / n3;
+            cuuint64_t dims[4] = {(cuuint64_t)n3, (cuuint64_t)n2, (cuuint64_t)n1, (cuuint64_t)n0};
+            cuuint64_t strides[3] = {(cuuint64_t)d.st[f][2] * 8, (cuuint64_t)d.st[f][1] * 8, (cuuint64_t)d.st[f][0] * 8};
+            cuuint32_t box[4] = {(cuuint32_t)n3, (cuuint32_t)kKC, (cuuint32_t)p1t, 1};
+            cuuint32_t estr[4] = {1, 1, 1, 1};
+            CUresult r = encode(&maps[2 * k + f], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, (void*)d.E[f], dims, strides,
+                                box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d) for dimer %d form %d", (int)r, k, f);
+                return cudaErrorInvalidValue;
+            }
+            max_box = std::max(max_box, (unsigned)(n3 * kKC * p1t * 8));
+            int mmax;
+            const int nit = items_per_form(d, f, &mmax);
+            const int tiles = (n1 + p1t - 1) / p1t;
+            for (int q = 0; q < nit; q++) {
+                TcItem it;
+                it.dimer = k;
+                it.form = f;
+                it.mt0 = q * mmax;
+                it.mts = std::min(mmax, tiles - it.mt0);
+                items.push_back(it);
+            }
+        }
+    }
+    // longest items first (cost ~ AO bytes read), stable so equal items keep dimer order
+    std::stable_sort(items.begin(), items.end(), [&](const TcItem& a, const TcItem& b) {
+        auto cost = [&](const TcItem& t) {
+            const DimerDesc& d = h_desc[t.dimer];
+            return (long long)t.mts * d.nX * d.nY * 128;
+        };
+        return cost(a) > cost(b);
+    });
+    const size_t need = maps.size() * sizeof(CUtensorMap) + items.size() * sizeof(TcItem);
+    if (need > work_bytes) {
+        snprintf(err, errlen, "work buffer too small (%zu < %zu)", work_bytes, need);
+        return cudaErrorInvalidValue;
+    }
+    unsigned char* w = static_cast<unsigned char*>(d_work);
+    cudaError_t e = cudaMemcpyAsync(w, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const size_t items_off = maps.size() * sizeof(CUtensorMap);
+    e = cudaMemcpyAsync(w + items_off, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+
+    TcLaunch& P = *out;
+    P.items = w + items_off;
+    P.n_items = (int)items.size();
+    P.maps = w;
+    P.desc = d_desc;
+    P.Cpool = Cpool;
+    P.H = H;
+    P.status = d_status;
+    P.kind = kind;
+    P.f_stage_bytes = (max_box + 1023) & ~1023u;
+    P.w_stage_bytes = (unsigned)(((size_t)maxN * 128 + 1023) & ~(size_t)1023);
+    P.tmem_cols = 2 * kAccCols;   // both accumulator sets at full width
+    const size_t fixed = 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)P.w_stage_bytes + sizeof(TcShared);
+    int sf = (int)(((size_t)max_smem - fixed) / P.f_stage_bytes);
+    sf = std::min(sf, 8);
+    if (sf < 2) {
+        snprintf(err, errlen, "not enough shared memory for the staging ring");
+        return cudaErrorInvalidConfiguration;
+    }
+    P.sf = sf;
+    P.smem = fixed + (size_t)sf * P.f_stage_bytes;
+    P.grid = std::min<int>((int)items.size(), nsm);
+    return cudaSuccess;
+}
+
+cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
+{
+    TcParams P;
+    P.items = static_cast<const TcItem*>(L.items);
+    P.n_items = L.n_items;
+    P.maps = static_cast<const CUtensorMap*>(L.maps);
+    P.desc = L.desc;
+    P.Cpool = L.Cpool;
+    P.H = L.H;
+    P.status = L.status;
+    P.sf = L.sf;
+    P.f_stage_bytes = L.f_stage_bytes;
+    P.w_stage_bytes = L.w_stage_bytes;
+    P.tmem_cols = L.tmem_cols;
+    P.kind = L.kind;
+    cudaError_t e;
+    if (L.kind == TC_TF32) {
+        e = cudaFuncSetAttribute(k_half_tc<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        if (e != cudaSuccess) return e;
+        k_half_tc<TC_TF32><<<L.grid, kThreadsTc, L.smem, s>>>(P);
+    } else {
+        e = cudaFuncSetAttribute(k_half_tc<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        if (e != cudaSuccess) return e;
+        k_half_tc<TC_BF16X3><<<L.grid, kThreadsTc, L.smem, s>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mcpt
