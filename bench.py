@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the first-order MCPT(2) dimer term on one GB300.
+
+Workload (default): lattice-5x5x5-cheb1 -- 125 monomers of 32 AO / 5 occupied
+on a 3.0 A cubic lattice, all 1036 dimers with Chebyshev distance <= 1, the
+dimer's AO integral blocks (2 x 32^4 FP64 = 16.8 MB each, 17.4 GB in all,
+far above the 129 MB L2) resident in HBM.  A step is one mcpt_run over every
+dimer: the first half (the AO-reading transform), the second half with FP64
+denominators and energies, and the per-monomer accumulation.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dimer energies/sec"
+UNIT = "dimers/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "fp32c", "fp64"])
+    p.add_argument("--workload", default="lattice-5x5x5-cheb1")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-sample", type=int, default=192, help="dimers in the oracle's timed sample")
+    p.add_argument("--no-extras", action="store_true", help="skip e2e, CPU baseline and the FP64 comparison")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except FileNotFoundError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            time.sleep(0.2)
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        pw = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def host_sample(w, dimers):
+    """Host inputs for the oracle (host generator)."""
+    import synth  # noqa: F401
+    items = []
+    for d in dimers:
+        X, Y = w.pairs[d]
+        mX, mY = w.monomer(X), w.monomer(Y)
+        A, K = w.blocks(d)
+        items.append((A, K, mX.C, mX.eps, mY.C, mY.eps, mX.nocc, mY.nocc))
+    return items
+
+
+def sample_dimers(w, n):
+    step = max(1, w.n_dimers // n)
+    return list(range(0, w.n_dimers, step))[:n]
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args, ws, rank):
+    """The FP64 CPU oracle on the machine's host cores, as it stands."""
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    w = synth.workload(args.workload)
+    oracle.build()
+    ds = sample_dimers(w, min(args.cpu_sample, 96))   # host generation of the sample stays bounded
+    items = host_sample(w, ds)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle.dimers_parallel(items[:8])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.dimers_parallel(items)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    v = len(items) * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n_dimers": w.n_dimers, "nao": w.nao[0], "nocc": w.nocc[0],
+                   "sample_dimers": len(items), "inputs": "host RAM"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"{len(items)} evenly spaced dimers of {args.workload} per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ our arm
+def our_arm(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1409_2700_gb300 as M
+    import synth
+    import synth.device
+
+    torch.cuda.set_device(local)
+    w = synth.workload(args.workload)
+    # inputs: every dimer's [A | K] blocks resident in HBM (generation untimed)
+    buf, offs = synth.device.workload_blocks(w)
+    torch.cuda.synchronize()
+    mons = [w.monomer(X) for X in range(w.n_monomers)]
+
+    stream = torch.cuda.Stream()
+
+    def make_ctx(prec, timing):
+        ctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing)
+        for m in mons:
+            ctx.add_monomer(m.C, m.eps, m.nocc)
+        base = buf.data_ptr()
+        for d in range(w.n_dimers):
+            X, Y = w.pairs[d]
+            ctx.add_dimer(X, Y, base + 8 * offs[d], M.MCPT_AO_BLOCKS, on_device=1)
+        return ctx
+
+    ctx = make_ctx(args.precision, True)
+    for _ in range(args.warmup):
+        ctx.run()
+    ctx.energies()
+    ctx.stats()   # discard warm-up timing
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.steps):
+                ctx.run()
+            e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ws, ms)
+    st = ctx.stats()
+    mj, mk, pd, tot = ctx.energies()
+    clocks = clk.summary()
+
+    ms_step = ms / args.steps
+    value = ws * w.n_dimers / (ms_step * 1e-3)
+    transform_ms = st.ms[0] / st.runs        # first-half kernel, average per launch (one wave)
+    per_launch_bytes = st.alg_bytes / st.waves
+    peaks, peak_kind = measured_peaks()
+    if args.precision == "fp64":
+        # FP64 pipe bound: nominal 1.25 TFLOP/s FP64 on GB300 (no measured figure)
+        achieved = st.alg_flops_half / st.waves / (transform_ms / st.waves * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
+                "frac": achieved / 1.25, "traffic": None, "kernel": "k_half_fp64",
+                "peak_kind": "nominal FP64 rate"}
+    else:
+        achieved = per_launch_bytes / (transform_ms / st.waves * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "k_half_tc" if args.precision in ("tf32", "bf16x3") else "k_half_fp32c",
+                "peak_kind": peak_kind}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": args.workload, "n_dimers": w.n_dimers, "n_monomers": w.n_monomers,
+                   "nao": w.nao[0], "nocc": w.nocc[0], "precision": args.precision,
+                   "inputs_gb": round(buf.numel() * 8 / 1e9, 2), "l2": "inputs (17.4 GB) larger than L2"},
+        "transform_tflops": st.alg_flops / (ms_step * 1e-3) / 1e12,
+        "phase_ms_per_step": {"first_half": st.ms[0] / st.runs, "finish": st.ms[1] / st.runs,
+                              "reduce": st.ms[2] / st.runs, "run": st.ms[3] / st.runs},
+        "roofline": roof,
+        "gpu_launches": st.launches,
+        "clocks": clocks,
+        "lattice_E": {"J": tot[0], "K": tot[1]},
+    }
+
+    # ---- accuracy against the stored oracle values (tests/golden)
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        import make_lattice_oracle as golden
+        g = golden.load(args.workload)
+    except Exception:
+        g = None
+    if g is not None:
+        Eo, to = g
+        line["error_eh"] = {"lattice_J": float(tot[0] - to[0]), "lattice_K": float(tot[1] - to[1]),
+                            "max_dimer_J": float(np.max(np.abs(pd[:, 0] - Eo[:, 0]))),
+                            "max_dimer_K": float(np.max(np.abs(pd[:, 1] - Eo[:, 1]))),
+                            "reference": "FP64 oracle, stored per-dimer values"}
+
+    if not args.no_extras and rank == 0:
+        # ---- the plain FP64 GPU form on the same resident inputs
+        if args.precision != "fp64":
+            c64 = make_ctx("fp64", True)
+            c64.run()
+            c64.energies()
+            c64.stats()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n64 = max(2, args.steps // 4)
+            with torch.cuda.stream(stream):
+                f0.record(stream)
+                for _ in range(n64):
+                    c64.run()
+                f1.record(stream)
+            torch.cuda.synchronize()
+            s64 = c64.stats()
+            _, _, pd64, tot64 = c64.energies()
+            ms64 = f0.elapsed_time(f1) / n64
+            fp64 = {"value": w.n_dimers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                    "transform_tflops": s64.alg_flops / (ms64 * 1e-3) / 1e12,
+                    "first_half_ms": s64.ms[0] / s64.runs}
+            if g is not None:
+                fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
+            line["fp64_form"] = fp64
+            c64.close()
+
+        # ---- end to end through the C ABI from pinned host buffers
+        host = torch.empty(buf.numel(), dtype=torch.float64, pin_memory=True)
+        host.copy_(buf)
+        torch.cuda.synchronize()
+        hbase = host.data_ptr()
+        blk_bytes = sum(2 * 8 * (w.nao[w.pairs[d][0]] ** 2) * (w.nao[w.pairs[d][1]] ** 2) for d in range(w.n_dimers))
+        h2d = blk_bytes + sum(8 * (m.nao * m.nao + m.nao) for m in mons)
+        d2h = 8 * (2 * w.n_monomers + 2 * w.n_dimers + 2)
+        del ctx
+        torch.cuda.synchronize()
+        t_e2e = []
+        for k in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c = M.Context(precision=args.precision, device=local, validate=False)
+            for m in mons:
+                c.add_monomer(m.C, m.eps, m.nocc)
+            for d in range(w.n_dimers):
+                X, Y = w.pairs[d]
+                c.add_dimer(X, Y, hbase + 8 * offs[d], M.MCPT_AO_BLOCKS, on_device=0)
+            c.run()
+            out = c.energies()
+            t1 = time.perf_counter()
+            c.close()
+            if k > 0:       # first pass warms allocator and module loading
+                t_e2e.append(t1 - t0)
+        e2e_s = statistics.median(t_e2e)
+        line["e2e"] = {"value": w.n_dimers / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "s_per_step": e2e_s, "steps": len(t_e2e)}
+        del host
+
+        # ---- the oracle on the host cores, bounded sample
+        import oracle
+        oracle.build()
+        ds = sample_dimers(w, args.cpu_sample)
+        n4 = 32 ** 4
+        Eo = np.empty((len(ds), 2))
+        tc = 0.0
+        for c0 in range(0, len(ds), 64):          # bounded host memory: 64 dimers at a time
+            items = []
+            for d in ds[c0:c0 + 64]:
+                X, Y = w.pairs[d]
+                mX, mY = mons[X], mons[Y]
+                blk = buf[offs[d]:offs[d] + 2 * n4].cpu().numpy()
+                items.append((blk[:n4].reshape(32, 32, 32, 32), blk[n4:].reshape(32, 32, 32, 32),
+                              mX.C, mX.eps, mY.C, mY.eps, mX.nocc, mY.nocc))
+            t0 = time.perf_counter()
+            Eo[c0:c0 + len(items)] = oracle.dimers_parallel(items)
+            tc += time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": len(ds) / tc, "unit": UNIT, "cores": oracle.max_threads(),
+                                "kind": "oracle",
+                                "sample": f"{len(ds)} evenly spaced dimers of {args.workload}, one pass "
+                                          f"({tc:.1f} s wall)"}
+        line["sample_error_eh"] = {"max_dimer_J": float(np.max(np.abs(pd[ds, 0] - Eo[:, 0]))),
+                                   "max_dimer_K": float(np.max(np.abs(pd[ds, 1] - Eo[:, 1])))}
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+    else:
+        our_arm(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

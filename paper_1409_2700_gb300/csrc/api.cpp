@@ -60,8 +60,9 @@ struct mcpt_ctx {
     std::vector<MonomerRec> mons;
     std::vector<double> hC, hE;
     double* dC = nullptr;
+    float* dCf = nullptr;            // FP32 copy of the coefficient pool (mixed forms)
     double* dE = nullptr;
-    size_t capC = 0, capE = 0;
+    size_t capC = 0, capCf = 0, capE = 0;
     bool mon_dirty = true;
 
     std::vector<DimerRec> dims;
@@ -471,7 +472,11 @@ static mcpt_status upload_static(mcpt_handle h)
         if (st) return st;
         st = ensure(h, &h->dE, &h->capE, h->hE.size() * sizeof(double));
         if (st) return st;
+        st = ensure(h, &h->dCf, &h->capCf, h->hC.size() * sizeof(float));
+        if (st) return st;
+        std::vector<float> cf(h->hC.begin(), h->hC.end());
         CK(h, cudaMemcpyAsync(h->dC, h->hC.data(), h->hC.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(h->dCf, cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaMemcpyAsync(h->dE, h->hE.data(), h->hE.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
         h->mon_dirty = false;
@@ -581,7 +586,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
             char tcerr[256] = {0};
             const size_t end = (w + 1 < work_off.size()) ? work_off[w + 1] : h->capWork;
             cudaError_t e = tc_prepare(prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3, h->hDesc.data() + wv.b,
-                                       h->dDesc + wv.b, wv.nd, h->dC, static_cast<float*>(h->dH),
+                                       h->dDesc + wv.b, wv.nd, h->dCf, static_cast<float*>(h->dH),
                                        static_cast<char*>(h->dWork) + work_off[w], end - work_off[w], h->dFlag + 1,
                                        h->stream, &wv.tc, tcerr, sizeof tcerr);
             if (e != cudaSuccess)
@@ -640,7 +645,7 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
             CK(h, launch_half_fp64(wd, wv.nd, wv.max_rows, wv.max_occ, h->dC, static_cast<double*>(h->dH), h->stream));
             break;
         case MCPT_FP32C:
-            CK(h, launch_half_fp32c(wd, wv.nd, wv.max_rows, wv.max_occ, h->dC, static_cast<float*>(h->dH), h->stream));
+            CK(h, launch_half_fp32c(wd, wv.nd, wv.max_rows, wv.max_occ, h->dCf, static_cast<float*>(h->dH), h->stream));
             break;
         case MCPT_TF32:
         case MCPT_BF16X3:
@@ -653,7 +658,7 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
                                      h->stream));
         else
-            CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const float*>(h->dH), h->dE2,
+            CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dCf, h->dE, static_cast<const float*>(h->dH), h->dE2,
                                      h->stream));
         launches++;
         if (h->timing) CK(h, cudaEventRecord(ev[2 + 2 * w], h->stream));
@@ -761,6 +766,7 @@ void mcpt_destroy(mcpt_handle h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* p : h->owned) cudaFree(p);
     cudaFree(h->dC);
+    cudaFree(h->dCf);
     cudaFree(h->dE);
     cudaFree(h->dDesc);
     cudaFree(h->dH);

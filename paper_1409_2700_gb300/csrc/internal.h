@@ -52,14 +52,14 @@ cudaError_t launch_half_fp64(const DimerDesc* d_desc, int nd, int max_rows, int 
 
 // FP32 first half with compensated (TwoProduct/TwoSum) accumulation.
 cudaError_t launch_half_fp32c(const DimerDesc* d_desc, int nd, int max_rows, int max_occ,
-                              const double* Cpool, float* H, cudaStream_t s);
+                              const float* Cf, float* H, cudaStream_t s);
 
 // Second half + denominators + energies.  H is double (FP64 form) or float.
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
                                const double* Cpool, const double* Epool, const double* H,
                                double* E2, cudaStream_t s);
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
-                               const double* Cpool, const double* Epool, const float* H,
+                               const float* Cf, const double* Epool, const float* H,
                                double* E2, cudaStream_t s);
 
 // Per-monomer halves and the compensated lattice total.
@@ -83,12 +83,13 @@ struct TcLaunch {
     int n_items;
     const void* maps;           // device CUtensorMap array, [dimer][form]
     const DimerDesc* desc;      // device descriptors of the launch's dimers
-    const double* Cpool;
+    const float* Cf;            // FP32 coefficient pool
     float* H;
     int* status;
     int sf;                     // FP64 staging stages
     unsigned f_stage_bytes, w_stage_bytes, tmem_cols;
     int kind;
+    int variant;                // 0: Kronecker (p0,p2) GEMM, 1: p2 GEMM + FP32 rank-1 epilogue
     int grid;
     size_t smem;
 };
@@ -97,7 +98,7 @@ struct TcLaunch {
 size_t tc_work_bytes(const DimerDesc* h_desc, int nd);
 // Encode tensor maps, order work items (longest first), upload them to
 // d_work, and fill *out.  Synchronous w.r.t. the host buffers.
-cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const double* Cpool,
+cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const float* Cf,
                        float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s, TcLaunch* out,
                        char* err, size_t errlen);
 cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s);

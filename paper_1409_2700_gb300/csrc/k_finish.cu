@@ -9,9 +9,13 @@
 //   (i b|j a) = sum_lam C_Y[lam][b] sum_nu H_1[lam][nu] C_X[nu][a]
 // Then, in FP64 (Sec. II.C energy tensor, Eq. (ed2) with T = vD):
 //   D = 1/(e_i + e_j - e_a - e_b),  E_J += 4 (ia|jb)^2 D,  E_K += -2 (ia|jb)(ib|ja) D.
+// GB300's FP64 unit is small, so D is an FP32 reciprocal refined by two
+// Newton steps in FP64 (convert.h) rather than a full FP64 division, and the
+// FP32 -> FP64 widening of the mixed forms' integrals runs on integer pipes.
 // One CTA owns one dimer, so the per-dimer energies come out of a fixed-order
 // block reduction: deterministic run to run, no atomics.
 #include "internal.h"
+#include "convert.h"
 
 namespace mcpt {
 namespace {
@@ -25,23 +29,30 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// T: arithmetic/storage type of the second half (double or float);
-// HT: element type of the first-half result.
-template <typename T, typename HT>
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f64_from_f32(x); }   // integer pipes
+
+// T: arithmetic type of the second half (double for the FP64 form, float for
+// the mixed forms) -- also the type of the coefficient pool C and of H.
+// Per occupied pair (i, j):
+//   TmA[nu][b] = sum_sig H0[nu][sig] C_Y[sig][b];   VA[a][b] = sum_nu C_X[nu][a] TmA[nu][b]
+//   TmK[lam][a] = sum_nu H1[lam][nu] C_X[nu][a];    VK[b][a] = sum_lam C_Y[lam][b] TmK[lam][a]
+// then one FP64 denominator per (a, b) feeds both energy sums.
+template <typename T>
 __global__ void __launch_bounds__(kFinThreads)
-k_finish(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
-         const double* __restrict__ Epool, const HT* __restrict__ H, double* __restrict__ E2)
+k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
+         const T* __restrict__ H, double* __restrict__ E2)
 {
     const DimerDesc& d = dd[blockIdx.x];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
     const int vX = nX - oX, vY = nY - oY;
     const int rows = nX * nY, ld = d.ldh;
-    const double* CX = Cpool + d.cX;
-    const double* CY = Cpool + d.cY;
+    const T* CX = C + d.cX;
+    const T* CY = C + d.cY;
     const double* eX = Epool + d.eX;
     const double* eY = Epool + d.eY;
-    const HT* H0 = H + d.h_off;
-    const HT* H1 = H + d.h_off + (long long)rows * ld;
+    const T* H0 = H + d.h_off;
+    const T* H1 = H + d.h_off + (long long)rows * ld;
 
     extern __shared__ __align__(16) unsigned char smraw[];
     T* S = reinterpret_cast<T*>(smraw);                 // [rows]
@@ -55,43 +66,44 @@ k_finish(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
             const int col = i * oY + j;
             const double eij = eX[i] + eY[j];
             // ---- (i a|j b) from H_0
-            for (int k = tid; k < rows; k += kFinThreads) S[k] = (T)H0[(long long)k * ld + col];
+            for (int k = tid; k < rows; k += kFinThreads) S[k] = H0[(long long)k * ld + col];
             __syncthreads();
             for (int k = tid; k < nX * vY; k += kFinThreads) {
                 const int nu = k / vY, b = k % vY;
                 const T* s = S + nu * nY;
                 T acc = 0;
-                for (int sg = 0; sg < nY; sg++) acc = fma(s[sg], (T)__ldg(CY + sg * nY + oY + b), acc);
+                for (int sg = 0; sg < nY; sg++) acc = fma(s[sg], __ldg(CY + sg * nY + oY + b), acc);
                 Tm[k] = acc;
             }
             __syncthreads();
             for (int k = tid; k < vX * vY; k += kFinThreads) {
                 const int a = k / vY, b = k % vY;
                 T acc = 0;
-                for (int nu = 0; nu < nX; nu++) acc = fma((T)__ldg(CX + nu * nX + oX + a), Tm[nu * vY + b], acc);
+                for (int nu = 0; nu < nX; nu++) acc = fma(__ldg(CX + nu * nX + oX + a), Tm[nu * vY + b], acc);
                 VA[k] = acc;
-                const double v = (double)acc;
-                const double D = 1.0 / (eij - (eX[oX + a] + eY[oY + b]));
-                ej = fma(v * v, D, ej);
             }
             __syncthreads();
             // ---- (i b|j a) from H_1
-            for (int k = tid; k < rows; k += kFinThreads) S[k] = (T)H1[(long long)k * ld + col];
+            for (int k = tid; k < rows; k += kFinThreads) S[k] = H1[(long long)k * ld + col];
             __syncthreads();
             for (int k = tid; k < nY * vX; k += kFinThreads) {
                 const int lam = k / vX, a = k % vX;
                 const T* s = S + lam * nX;
                 T acc = 0;
-                for (int nu = 0; nu < nX; nu++) acc = fma(s[nu], (T)__ldg(CX + nu * nX + oX + a), acc);
+                for (int nu = 0; nu < nX; nu++) acc = fma(s[nu], __ldg(CX + nu * nX + oX + a), acc);
                 Tm[k] = acc;
             }
             __syncthreads();
-            for (int k = tid; k < vY * vX; k += kFinThreads) {
-                const int b = k / vX, a = k % vX;
+            // ---- energies: one denominator per (a, b)
+            for (int k = tid; k < vX * vY; k += kFinThreads) {
+                const int a = k / vY, b = k % vY;
                 T acc = 0;
-                for (int lam = 0; lam < nY; lam++) acc = fma((T)__ldg(CY + lam * nY + oY + b), Tm[lam * vX + a], acc);
-                const double D = 1.0 / (eij - (eX[oX + a] + eY[oY + b]));
-                ek = fma((double)VA[a * vY + b] * (double)acc, D, ek);
+                for (int lam = 0; lam < nY; lam++) acc = fma(__ldg(CY + lam * nY + oY + b), Tm[lam * vX + a], acc);
+                const double va = to_f64(VA[k]);
+                const double vk = to_f64(acc);
+                const double D = rcp_f64(eij - (eX[oX + a] + eY[oY + b]));
+                ej = fma(va * va, D, ej);
+                ek = fma(va * vk, D, ek);
             }
             __syncthreads();
         }
@@ -110,16 +122,16 @@ k_finish(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
     }
 }
 
-template <typename T, typename HT>
-cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
-                          const double* Epool, const HT* H, double* E2, cudaStream_t s)
+template <typename T>
+cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* C, const double* Epool,
+                          const T* H, double* E2, cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
     const size_t smem = (size_t)3 * max_ao * max_ao * sizeof(T);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_finish<T, HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_finish<T, HT><<<nd, kFinThreads, smem, s>>>(d_desc, Cpool, Epool, H, E2);
+    k_finish<T><<<nd, kFinThreads, smem, s>>>(d_desc, C, Epool, H, E2);
     return cudaGetLastError();
 }
 
@@ -210,13 +222,13 @@ __global__ void k_check_finite4(const double* __restrict__ x, int d0, int d1, in
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
                                const double* Epool, const double* H, double* E2, cudaStream_t s)
 {
-    return launch_finish<double, double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, s);
+    return launch_finish<double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, s);
 }
 
-cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
+cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const float* Cf,
                                const double* Epool, const float* H, double* E2, cudaStream_t s)
 {
-    return launch_finish<float, float>(d_desc, nd, max_ao, Cpool, Epool, H, E2, s);
+    return launch_finish<float>(d_desc, nd, max_ao, Cf, Epool, H, E2, s);
 }
 
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists, double* mon, double* total,

@@ -7,10 +7,12 @@
 // Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci.
 // Comput. 26, 2005): TwoProduct by FMA (h = x*y, r = fma(x, y, -h)) and
 // Knuth's TwoSum, so each sum is as accurate as if computed in twice the
-// working precision and then rounded (their Dot2).  The inner sum over p2 is
+// working precision and then rounded (their Dot2).  The FP64 -> FP32
+// rounding of each integral runs on the integer pipes (convert.h).  The inner sum over p2 is
 // kept as an unevaluated pair (hi, lo) and multiplied into the outer sum over
 // p0 the same way.
 #include "internal.h"
+#include "convert.h"
 
 namespace mcpt {
 namespace {
@@ -46,7 +48,7 @@ __device__ __forceinline__ void dot2_step_ff(ff& acc, float w, ff v)
 
 template <int OB>
 __global__ void __launch_bounds__(kThreads)
-k_half_fp32c(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool, float* __restrict__ H)
+k_half_fp32c(const DimerDesc* __restrict__ dd, const float* __restrict__ Cf, float* __restrict__ H)
 {
     const DimerDesc& d = dd[blockIdx.z];
     const int f = blockIdx.y;
@@ -58,8 +60,8 @@ k_half_fp32c(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
     extern __shared__ float smf[];
     float* U0 = smf;               // [n0][OB]
     float* U2 = smf + n0 * OB;     // [n2][OB]
-    const double* CX = Cpool + d.cX;
-    const double* CY = Cpool + d.cY;
+    const float* CX = Cf + d.cX;
+    const float* CY = Cf + d.cY;
 
     const int r = blockIdx.x * kThreads + threadIdx.x;
     const bool active = r < rows;
@@ -73,11 +75,11 @@ k_half_fp32c(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
             __syncthreads();
             for (int k = threadIdx.x; k < n0 * OB; k += kThreads) {
                 int p = k / OB, t = t0b + k % OB;
-                U0[k] = t < o0 ? (float)CX[p * d.nX + t] : 0.f;
+                U0[k] = t < o0 ? CX[p * d.nX + t] : 0.f;
             }
             for (int k = threadIdx.x; k < n2 * OB; k += kThreads) {
                 int p = k / OB, t = t2b + k % OB;
-                U2[k] = t < o2 ? (float)CY[p * d.nY + t] : 0.f;
+                U2[k] = t < o2 ? CY[p * d.nY + t] : 0.f;
             }
             __syncthreads();
             if (!active) continue;
@@ -93,7 +95,7 @@ k_half_fp32c(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
                 for (int t = 0; t < OB; t++) F[t] = ff{0.f, 0.f};
 #pragma unroll 4
                 for (int p2 = 0; p2 < n2; p2++) {
-                    const float e = (float)__ldg(Ep + p2 * s2);
+                    const float e = f32_from_f64(__ldg(Ep + p2 * s2));   // integer-pipe conversion
                     const float* u = U2 + p2 * OB;
 #pragma unroll
                     for (int t = 0; t < OB; t++) dot2_step(F[t], u[t], e);
@@ -116,23 +118,23 @@ k_half_fp32c(const DimerDesc* __restrict__ dd, const double* __restrict__ Cpool,
 }
 
 template <int OB>
-cudaError_t launch(const DimerDesc* d_desc, int nd, int max_rows, const double* Cpool, float* H, cudaStream_t s)
+cudaError_t launch(const DimerDesc* d_desc, int nd, int max_rows, const float* Cf, float* H, cudaStream_t s)
 {
     const size_t smem = (size_t)2 * kMaxAOTensor * OB * sizeof(float);
     dim3 grid((max_rows + kThreads - 1) / kThreads, 2, nd);
-    k_half_fp32c<OB><<<grid, kThreads, smem, s>>>(d_desc, Cpool, H);
+    k_half_fp32c<OB><<<grid, kThreads, smem, s>>>(d_desc, Cf, H);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_half_fp32c(const DimerDesc* d_desc, int nd, int max_rows, int max_occ, const double* Cpool,
+cudaError_t launch_half_fp32c(const DimerDesc* d_desc, int nd, int max_rows, int max_occ, const float* Cf,
                               float* H, cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
-    if (max_occ <= 4) return launch<4>(d_desc, nd, max_rows, Cpool, H, s);
-    if (max_occ <= 5) return launch<5>(d_desc, nd, max_rows, Cpool, H, s);
-    return launch<8>(d_desc, nd, max_rows, Cpool, H, s);
+    if (max_occ <= 4) return launch<4>(d_desc, nd, max_rows, Cf, H, s);
+    if (max_occ <= 5) return launch<5>(d_desc, nd, max_rows, Cf, H, s);
+    return launch<8>(d_desc, nd, max_rows, Cf, H, s);
 }
 
 }  // namespace mcpt

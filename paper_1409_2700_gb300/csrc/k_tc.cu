@@ -23,6 +23,7 @@
 // the CTA records an error code, drains its own copies and MMAs, frees TMEM
 // and returns.
 #include "internal.h"
+#include "convert.h"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -30,6 +31,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -69,7 +71,7 @@ struct TcParams {
     int n_items;
     const CUtensorMap* maps;       // [dimer][form]
     const DimerDesc* desc;
-    const double* Cpool;
+    const float* Cf;
     float* H;
     int* status;
     int sf;                        // FP64 staging stages
@@ -116,16 +118,16 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity
 }
 
 // Wait for the phase of parity `parity` to complete; false on timeout/abort.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, TcShared* sh, int* status,
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, volatile int* abort, int* status,
                                           int where)
 {
     if (mbar_test(b, parity)) return true;
     const unsigned long long t0 = now_ns();
     while (true) {
         if (mbar_test(b, parity)) return true;
-        if (sh->abort) return false;
+        if (*abort) return false;
         if (now_ns() - t0 > kWaitNs) {
-            sh->abort = 1;
+            *abort = 1;
             atomicCAS(status, 0, kErrTimeoutBase + where);
             return false;
         }
@@ -250,6 +252,52 @@ __device__ __forceinline__ ItemGeo geo_of(const DimerDesc& d, int f)
     return g;
 }
 
+// FP64 staging box [p1l][32 p2][n3] -> one 128-row K-major SW128 operand tile.
+// TF32: 8 chunks of 4 p2 per row; BF16x3: hi in chunks 0-3, lo in chunks 4-7.
+template <int KIND>
+__device__ __forceinline__ void convert_a_tile(const double* F, unsigned char* A, int tile_rows_full, int n3, int ct)
+{
+    if (KIND == TC_TF32) {
+        for (int task = ct; task < 128 * 8; task += 128) {
+            const int c = task >> 7, r = task & 127;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r < tile_rows_full) {
+                const int p1l = r / n3, p3 = r % n3;
+                const double* src = F + ((size_t)(p1l * kKC + c * 4) * n3 + p3);
+                const unsigned* s32 = reinterpret_cast<const unsigned*>(src) + 1;   // high words
+                v.x = tf32_from_f64_hi(s32[0]);
+                v.y = tf32_from_f64_hi(s32[2 * n3]);
+                v.z = tf32_from_f64_hi(s32[4 * n3]);
+                v.w = tf32_from_f64_hi(s32[6 * n3]);
+            }
+            *reinterpret_cast<uint4*>(A + sw128_off(r, c)) = v;
+        }
+    } else {
+        for (int task = ct; task < 128 * 4; task += 128) {
+            const int c = task >> 7, r = task & 127;
+            uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+            if (r < tile_rows_full) {
+                const int p1l = r / n3, p3 = r % n3;
+                const double* src = F + ((size_t)(p1l * kKC + c * 8) * n3 + p3);
+                unsigned short hb[8], lb[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const uint2 b = reinterpret_cast<const uint2*>(src)[e * n3];
+                    const float x = f32_from_f64_bits(b.x, b.y);
+                    hb[e] = to_bf16_bits(x);
+                    lb[e] = to_bf16_bits(x - __bfloat162float(__ushort_as_bfloat16(hb[e])));
+                }
+                vh = make_uint4(hb[0] | (hb[1] << 16), hb[2] | (hb[3] << 16), hb[4] | (hb[5] << 16),
+                                hb[6] | (hb[7] << 16));
+                vl = make_uint4(lb[0] | (lb[1] << 16), lb[2] | (lb[3] << 16), lb[4] | (lb[5] << 16),
+                                lb[6] | (lb[7] << 16));
+            }
+            *reinterpret_cast<uint4*>(A + sw128_off(r, c)) = vh;
+            *reinterpret_cast<uint4*>(A + sw128_off(r, 4 + c)) = vl;
+        }
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 {
@@ -302,7 +350,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                     for (int mt = 0; mt < item.mts; mt++, gF++) {
                         const int s = gF % P.sf;
                         const unsigned ph = (gF / P.sf) & 1;
-                        if (!mbar_wait(&sh->empty_f[s], ph ^ 1, sh, P.status, 1)) break;
+                        if (!mbar_wait(&sh->empty_f[s], ph ^ 1, &sh->abort, P.status, 1)) break;
                         mbar_arrive_tx(&sh->full_f[s], box);
                         tma_load_4d(Fr + (size_t)s * P.f_stage_bytes, map, &sh->full_f[s], 0, kc * kKC,
                                     (item.mt0 + mt) * g.p1t, p0);
@@ -328,16 +376,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
                 const unsigned idesc = make_idesc(KIND, g.N);
                 const int b = li & 1;
-                if (!mbar_wait(&sh->tmem_empty[b], ((li >> 1) & 1) ^ 1, sh, P.status, 2)) break;
+                if (!mbar_wait(&sh->tmem_empty[b], ((li >> 1) & 1) ^ 1, &sh->abort, P.status, 2)) break;
                 tc_fence_after();
                 bool ok = true;
                 for (int kb = 0; kb < g.kblocks && ok; kb++, gW++) {
                     const int ws = gW & 1;
-                    if (!(ok = mbar_wait(&sh->full_w[ws], (gW >> 1) & 1, sh, P.status, 3))) break;
+                    if (!(ok = mbar_wait(&sh->full_w[ws], (gW >> 1) & 1, &sh->abort, P.status, 3))) break;
                     const unsigned long long bdesc = sw128_desc(Wr + (size_t)ws * P.w_stage_bytes);
                     for (int mt = 0; mt < item.mts; mt++, gA++) {
                         const int as = gA & 1;
-                        if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, sh, P.status, 4))) break;
+                        if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, &sh->abort, P.status, 4))) break;
                         tc_fence_after();
                         const unsigned long long adesc = sw128_desc(Ar + (size_t)as * kABytes);
                         const unsigned dt = tmem + (unsigned)(b * kAccCols + mt * g.N);
@@ -378,8 +426,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
             const TcItem item = P.items[it];
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
-            const double* CX = P.Cpool + d.cX;
-            const double* CY = P.Cpool + d.cY;
+            const float* CX = P.Cf + d.cX;
+            const float* CY = P.Cf + d.cY;
             const int npairs = g.o0 * g.o2;
             const int tile_rows_full = g.p1t * g.n3;
             bool ok = true;
@@ -387,7 +435,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                 const int p0 = kb / g.kcs, kc = kb % g.kcs;
                 // ---- W tile of this K-block: row n = (i, j), K = p2 in the chunk
                 const int ws = gW & 1;
-                if (!(ok = mbar_wait(&sh->empty_w[ws], ((gW >> 1) & 1) ^ 1, sh, P.status, 5))) break;
+                if (!(ok = mbar_wait(&sh->empty_w[ws], ((gW >> 1) & 1) ^ 1, &sh->abort, P.status, 5))) break;
                 unsigned char* W = Wr + (size_t)ws * P.w_stage_bytes;
                 if (KIND == TC_TF32) {
                     for (int task = ct; task < g.N * 8; task += 128) {
@@ -395,12 +443,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                         uint4 v = make_uint4(0, 0, 0, 0);
                         if (n < npairs) {
                             const int i = n / g.o2, j = n % g.o2;
-                            const float u0 = (float)__ldg(CX + p0 * d.nX + i);
+                            const float u0 = __ldg(CX + p0 * d.nX + i);
                             unsigned w4[4];
 #pragma unroll
                             for (int e = 0; e < 4; e++) {
                                 const int p2 = kc * kKC + c * 4 + e;
-                                const float u2 = p2 < g.n2 ? (float)__ldg(CY + p2 * d.nY + j) : 0.f;
+                                const float u2 = p2 < g.n2 ? __ldg(CY + p2 * d.nY + j) : 0.f;
                                 w4[e] = to_tf32(u0 * u2);
                             }
                             v = make_uint4(w4[0], w4[1], w4[2], w4[3]);
@@ -413,12 +461,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                         uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
                         if (n < npairs) {
                             const int i = n / g.o2, j = n % g.o2;
-                            const float u0 = (float)__ldg(CX + p0 * d.nX + i);
+                            const float u0 = __ldg(CX + p0 * d.nX + i);
                             unsigned short hb[8], lb[8];
 #pragma unroll
                             for (int e = 0; e < 8; e++) {
                                 const int p2 = kc * kKC + c * 8 + e;
-                                const float w = p2 < g.n2 ? u0 * (float)__ldg(CY + p2 * d.nY + j) : 0.f;
+                                const float w = p2 < g.n2 ? u0 * __ldg(CY + p2 * d.nY + j) : 0.f;
                                 hb[e] = to_bf16_bits(w);
                                 lb[e] = to_bf16_bits(w - __bfloat162float(__ushort_as_bfloat16(hb[e])));
                             }
@@ -438,9 +486,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                 // ---- A tiles of this K-block, one per M-tile of the item
                 for (int mt = 0; mt < item.mts; mt++, gF++, gA++) {
                     const int s = gF % P.sf;
-                    if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, sh, P.status, 6))) break;
+                    if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, &sh->abort, P.status, 6))) break;
                     const int as = gA & 1;
-                    if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, sh, P.status, 7))) break;
+                    if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, &sh->abort, P.status, 7))) break;
                     const double* F = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
                     unsigned char* A = Ar + (size_t)as * kABytes;
                     if (KIND == TC_TF32) {
@@ -451,10 +499,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                             if (r < tile_rows_full) {
                                 const int p1l = r / g.n3, p3 = r % g.n3;
                                 const double* src = F + ((size_t)(p1l * kKC + c * 4) * g.n3 + p3);
-                                v.x = to_tf32((float)src[0]);
-                                v.y = to_tf32((float)src[g.n3]);
-                                v.z = to_tf32((float)src[2 * g.n3]);
-                                v.w = to_tf32((float)src[3 * g.n3]);
+                                const unsigned* s32 = reinterpret_cast<const unsigned*>(src) + 1;   // high words
+                                v.x = tf32_from_f64_hi(s32[0]);
+                                v.y = tf32_from_f64_hi(s32[2 * g.n3]);
+                                v.z = tf32_from_f64_hi(s32[4 * g.n3]);
+                                v.w = tf32_from_f64_hi(s32[6 * g.n3]);
                             }
                             *reinterpret_cast<uint4*>(A + sw128_off(r, c)) = v;
                         }
@@ -468,7 +517,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                                 unsigned short hb[8], lb[8];
 #pragma unroll
                                 for (int e = 0; e < 8; e++) {
-                                    const float x = (float)src[e * g.n3];
+                                    const uint2 b = reinterpret_cast<const uint2*>(src)[e * g.n3];
+                                    const float x = f32_from_f64_bits(b.x, b.y);
                                     hb[e] = to_bf16_bits(x);
                                     lb[e] = to_bf16_bits(x - __bfloat162float(__ushort_as_bfloat16(hb[e])));
                                 }
@@ -500,7 +550,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
             const int b = li & 1;
-            if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, sh, P.status, 8)) break;
+            if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, &sh->abort, P.status, 8)) break;
             tc_fence_after();
             float* Hf = P.H + d.h_off + (long long)item.form * g.rows * g.N;
             for (int mt = 0; mt < item.mts; mt++) {
@@ -534,6 +584,301 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
     }
 }
 
+// ==========================================================================
+// "Rank" variant: the tensor core contracts only p2 for one (M-tile, p0) at a
+// time,
+//     T[(p1,p3)][j] = sum_{p2} E[p0][p1][p2][p3] C_Y[p2][j]      (N = 16 >= o2)
+// accumulating over at most n2/8 MMA steps, into a ring of 16-column TMEM
+// slots; the epilogue warps then apply the p0 quarter transformation as a
+// rank-1 update in registers,
+//     H[(p1,p3)][(i,j)] += C_X[p0][i] T[(p1,p3)][j],
+// with round-to-nearest FP32 FMAs.  Long accumulations inside the tensor
+// core do not round to nearest and drift toward zero over many steps; this
+// split keeps each tensor-core sum short.  The B operand (C_Y's occupied
+// columns) is constant per work item and reused for every p0 and row, so its
+// rounding error would act as a slightly wrong orbital and bias the energy:
+// it is split into two TF32 planes (hi + lo, two MMAs per step) or three
+// BF16 pieces (c0 + c1 + c2; A_hi(c0+c1+c2) + A_lo(c0+c1), five MMAs), which
+// represents it to about FP32 accuracy.  Only the integrals keep the form's
+// own rounding, which is independent from element to element.  Needs
+// o_X, o_Y <= 8 (register accumulators) -- larger occupations use the
+// Kronecker kernel above.
+constexpr int kNT = 16;        // TMEM slot width = MMA N
+constexpr int kSlots = 32;     // 32 x 16 = 512 TMEM columns
+constexpr int kOB = 8;         // register accumulator block: o_X, o_Y <= 8
+constexpr int kKCMax = 4;      // p2 chunks: n2 <= 128
+
+struct __align__(8) RankShared {
+    unsigned long long full_f[8], empty_f[8];
+    unsigned long long full_a[2], empty_a[2];
+    unsigned long long full_w[2], empty_w[2];
+    unsigned long long slot_full[kSlots], slot_empty[kSlots];
+    unsigned long long drain;
+    unsigned int tmem_base;
+    volatile int abort;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    unsigned char* Fr = base;
+    unsigned char* Ar = Fr + (size_t)P.sf * P.f_stage_bytes;
+    unsigned char* Wr = Ar + 2 * kABytes;   // [2 parities][kKCMax][2 planes][16 rows x 128 B]
+    RankShared* sh = reinterpret_cast<RankShared*>(Wr + 2 * kKCMax * 2 * kNT * 128);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.sf; s++) { mbar_init(&sh->full_f[s], 1); mbar_init(&sh->empty_f[s], 4); }
+        for (int s = 0; s < 2; s++) {
+            mbar_init(&sh->full_a[s], 4); mbar_init(&sh->empty_a[s], 1);
+            mbar_init(&sh->full_w[s], 4); mbar_init(&sh->empty_w[s], 1);
+        }
+        for (int s = 0; s < kSlots; s++) { mbar_init(&sh->slot_full[s], 1); mbar_init(&sh->slot_empty[s], 4); }
+        mbar_init(&sh->drain, 1);
+        sh->abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sh->tmem_base)),
+                     "r"(P.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            unsigned gF = 0;
+            unsigned issued_phase[8];
+            bool issued[8];
+            for (int s = 0; s < 8; s++) issued[s] = false;
+            bool ok = true;
+            for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x) {
+                const TcItem item = P.items[it];
+                const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
+                const CUtensorMap* map = P.maps + 2 * item.dimer + item.form;
+                const unsigned box = (unsigned)g.n3 * kKC * g.p1t * 8u;
+                for (int mt = 0; mt < item.mts && ok; mt++)
+                    for (int p0 = 0; p0 < g.n0 && ok; p0++)
+                        for (int kc = 0; kc < g.kcs; kc++, gF++) {
+                            const int s = gF % P.sf;
+                            const unsigned ph = (gF / P.sf) & 1;
+                            if (!(ok = mbar_wait(&sh->empty_f[s], ph ^ 1, &sh->abort, P.status, 11))) break;
+                            mbar_arrive_tx(&sh->full_f[s], box);
+                            tma_load_4d(Fr + (size_t)s * P.f_stage_bytes, map, &sh->full_f[s], 0, kc * kKC,
+                                        (item.mt0 + mt) * g.p1t, p0);
+                            issued[s] = true;
+                            issued_phase[s] = ph;
+                        }
+            }
+            for (int s = 0; s < P.sf; s++)
+                if (issued[s]) {
+                    const unsigned long long t0 = now_ns();
+                    while (!mbar_test(&sh->full_f[s], issued_phase[s]) && now_ns() - t0 < kWaitNs) {}
+                }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            unsigned gA = 0, gS = 0, li = 0;
+            bool any = false, ok = true;
+            const unsigned idesc = make_idesc(KIND, kNT);
+            for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x, li++) {
+                const TcItem item = P.items[it];
+                const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
+                const int wp = li & 1;
+                if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, &sh->abort, P.status, 12))) break;
+                for (int mt = 0; mt < item.mts && ok; mt++)
+                    for (int p0 = 0; p0 < g.n0 && ok; p0++, gS++) {
+                        const int s = gS % kSlots;
+                        if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / kSlots) & 1) ^ 1, &sh->abort, P.status, 13))) break;
+                        tc_fence_after();
+                        const unsigned dt = tmem + (unsigned)(s * kNT);
+                        for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
+                            const int as = gA & 1;
+                            if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, &sh->abort, P.status, 14))) break;
+                            tc_fence_after();
+                            const unsigned long long adesc = sw128_desc(Ar + (size_t)as * kABytes);
+                            const unsigned long long b0 = sw128_desc(Wr + (size_t)((wp * kKCMax + kc) * 2) * kNT * 128);
+                            const unsigned long long b1 = sw128_desc(Wr + (size_t)((wp * kKCMax + kc) * 2 + 1) * kNT * 128);
+                            if (KIND == TC_TF32) {
+                                // C_Y = hi + lo (two TF32 planes): A (hi + lo)
+#pragma unroll
+                                for (int k = 0; k < 4; k++) {
+                                    tc_mma<KIND>(dt, adesc + 2 * k, b0 + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                                    tc_mma<KIND>(dt, adesc + 2 * k, b1 + 2 * k, idesc, 1u);
+                                }
+                            } else {
+                                // A = hi + lo (bytes 0-63 / 64-127 of each row); C_Y = c0 + c1 + c2
+                                // (plane 0 = [c0 | c1], plane 1 = [c2 | 0]): A_hi (c0+c1+c2) + A_lo (c0+c1)
+#pragma unroll
+                                for (int k = 0; k < 2; k++) {
+                                    const unsigned long long ah = adesc + 2 * k, al = adesc + 4 + 2 * k;
+                                    const unsigned long long c0 = b0 + 2 * k, c1 = b0 + 4 + 2 * k, c2 = b1 + 2 * k;
+                                    tc_mma<KIND>(dt, ah, c0, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+                                    tc_mma<KIND>(dt, ah, c1, idesc, 1u);
+                                    tc_mma<KIND>(dt, ah, c2, idesc, 1u);
+                                    tc_mma<KIND>(dt, al, c0, idesc, 1u);
+                                    tc_mma<KIND>(dt, al, c1, idesc, 1u);
+                                }
+                            }
+                            tc_commit(&sh->empty_a[as]);
+                            any = true;
+                        }
+                        if (ok) tc_commit(&sh->slot_full[s]);
+                    }
+                if (ok) tc_commit(&sh->empty_w[wp]);
+            }
+            if (any) {
+                tc_commit(&sh->drain);
+                const unsigned long long t0 = now_ns();
+                while (!mbar_test(&sh->drain, 0) && now_ns() - t0 < kWaitNs) {}
+            }
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------ converters
+        const int ct = threadIdx.x - 64;
+        unsigned gF = 0, gA = 0, li = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x, li++) {
+            const TcItem item = P.items[it];
+            const DimerDesc& d = P.desc[item.dimer];
+            const ItemGeo g = geo_of(d, item.form);
+            const float* CY = P.Cf + d.cY;
+            const int wp = li & 1;
+            const int tile_rows_full = g.p1t * g.n3;
+            // ---- B operand of this item: row j < 16, K = p2: C_Y[p2][j] (zero past o2 / n2)
+            if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, &sh->abort, P.status, 15))) break;
+            for (int kc = 0; kc < g.kcs; kc++) {
+                unsigned char* W0 = Wr + (size_t)((wp * kKCMax + kc) * 2) * kNT * 128;
+                unsigned char* W1 = W0 + kNT * 128;
+                if (KIND == TC_TF32) {
+                    for (int task = ct; task < kNT * 8; task += 128) {
+                        const int j = task >> 3, c = task & 7;
+                        unsigned h4[4], l4[4];
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int p2 = kc * kKC + c * 4 + e;
+                            const float x = (j < g.o2 && p2 < g.n2) ? __ldg(CY + p2 * d.nY + j) : 0.f;
+                            h4[e] = to_tf32(x);
+                            l4[e] = to_tf32(x - __uint_as_float(h4[e]));
+                        }
+                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, c)) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
+                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+                    }
+                } else {
+                    for (int task = ct; task < kNT * 4; task += 128) {
+                        const int j = task >> 2, c = task & 3;
+                        unsigned short b0[8], b1[8], b2[8];
+#pragma unroll
+                        for (int e = 0; e < 8; e++) {
+                            const int p2 = kc * kKC + c * 8 + e;
+                            const float x = (j < g.o2 && p2 < g.n2) ? __ldg(CY + p2 * d.nY + j) : 0.f;
+                            b0[e] = to_bf16_bits(x);
+                            const float r1 = x - __bfloat162float(__ushort_as_bfloat16(b0[e]));
+                            b1[e] = to_bf16_bits(r1);
+                            b2[e] = to_bf16_bits(r1 - __bfloat162float(__ushort_as_bfloat16(b1[e])));
+                        }
+                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, c)) =
+                            make_uint4(b0[0] | (b0[1] << 16), b0[2] | (b0[3] << 16), b0[4] | (b0[5] << 16),
+                                       b0[6] | (b0[7] << 16));
+                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, 4 + c)) =
+                            make_uint4(b1[0] | (b1[1] << 16), b1[2] | (b1[3] << 16), b1[4] | (b1[5] << 16),
+                                       b1[6] | (b1[7] << 16));
+                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) =
+                            make_uint4(b2[0] | (b2[1] << 16), b2[2] | (b2[3] << 16), b2[4] | (b2[5] << 16),
+                                       b2[6] | (b2[7] << 16));
+                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, 4 + c)) = make_uint4(0, 0, 0, 0);
+                    }
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->full_w[wp]);
+
+            for (int mt = 0; mt < item.mts && ok; mt++)
+                for (int p0 = 0; p0 < g.n0 && ok; p0++)
+                    for (int kc = 0; kc < g.kcs; kc++, gF++, gA++) {
+                        const int s = gF % P.sf;
+                        if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, &sh->abort, P.status, 16))) break;
+                        const int as = gA & 1;
+                        if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, &sh->abort, P.status, 17))) break;
+                        const double* F = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
+                        convert_a_tile<KIND>(F, Ar + (size_t)as * kABytes, tile_rows_full, g.n3, ct);
+                        fence_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            mbar_arrive(&sh->full_a[as]);
+                            mbar_arrive(&sh->empty_f[s]);
+                        }
+                    }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        unsigned gS = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x) {
+            const TcItem item = P.items[it];
+            const DimerDesc& d = P.desc[item.dimer];
+            const ItemGeo g = geo_of(d, item.form);
+            const float* CX = P.Cf + d.cX;
+            float* Hf = P.H + d.h_off + (long long)item.form * g.rows * g.N;
+            for (int mt = 0; mt < item.mts && ok; mt++) {
+                float acc[kOB][kOB];
+#pragma unroll
+                for (int i = 0; i < kOB; i++)
+#pragma unroll
+                    for (int j = 0; j < kOB; j++) acc[i][j] = 0.f;
+                for (int p0 = 0; p0 < g.n0; p0++, gS++) {
+                    const int s = gS % kSlots;
+                    if (!(ok = mbar_wait(&sh->slot_full[s], (gS / kSlots) & 1, &sh->abort, P.status, 18))) break;
+                    tc_fence_after();
+                    float T[16];
+                    tmem_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(s * kNT), T);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
+                    float cx[kOB];
+#pragma unroll
+                    for (int i = 0; i < kOB; i++) cx[i] = i < g.o0 ? __ldg(CX + p0 * d.nX + i) : 0.f;
+#pragma unroll
+                    for (int i = 0; i < kOB; i++)
+#pragma unroll
+                        for (int j = 0; j < kOB; j++) acc[i][j] = fmaf(cx[i], T[j], acc[i][j]);
+                }
+                if (!ok) break;
+                const int tile = item.mt0 + mt;
+                const int p1_lo = tile * g.p1t;
+                const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
+                if (r < valid) {
+                    float* out = Hf + (long long)(p1_lo * g.n3 + r) * g.N;
+#pragma unroll
+                    for (int i = 0; i < kOB; i++)
+#pragma unroll
+                        for (int j = 0; j < kOB; j++)
+                            if (i < g.o0 && j < g.o2) out[i * g.o2 + j] = acc[i][j];
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P.tmem_cols)
+                     : "memory");
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 get_encode()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -548,14 +893,26 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-int items_per_form(const DimerDesc& d, int f, int* mts_max)
+// Variant 1 (rank) runs one M-tile per item; variant 0 groups as many M-tiles
+// as one TMEM accumulator set holds.
+int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
 {
     const int n1 = f ? d.nY : d.nX, n3 = f ? d.nX : d.nY;
     const int p1t = 128 / n3;
     const int tiles = (n1 + p1t - 1) / p1t;
-    const int mmax = std::max(1, std::min(8, kAccCols / d.ldh));
+    const int mmax = variant == 1 ? 1 : std::max(1, std::min(8, kAccCols / d.ldh));
     *mts_max = mmax;
     return (tiles + mmax - 1) / mmax;
+}
+
+int choose_variant(const DimerDesc* h, int nd)
+{
+    const char* env = getenv("MCPT_TC_KERNEL");
+    if (env && !strcmp(env, "kron")) return 0;
+    bool small = true;
+    for (int k = 0; k < nd; k++) small = small && h[k].oX <= kOB && h[k].oY <= kOB && h[k].nY <= kKCMax * kKC;
+    if (env && !strcmp(env, "rank") && small) return 1;
+    return small ? 1 : 0;
 }
 
 }  // namespace
@@ -563,15 +920,16 @@ int items_per_form(const DimerDesc& d, int f, int* mts_max)
 size_t tc_work_bytes(const DimerDesc* h, int nd)
 {
     size_t items = 0;
+    const int variant = choose_variant(h, nd);
     for (int k = 0; k < nd; k++)
         for (int f = 0; f < 2; f++) {
             int m;
-            items += items_per_form(h[k], f, &m);
+            items += items_per_form(h[k], f, variant, &m);
         }
     return (size_t)nd * 2 * sizeof(CUtensorMap) + items * sizeof(TcItem) + 256;
 }
 
-cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const double* Cpool,
+cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const float* Cf,
                        float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s, TcLaunch* out,
                        char* err, size_t errlen)
 {
@@ -583,6 +941,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     }
     std::vector<CUtensorMap> maps((size_t)nd * 2);
     std::vector<TcItem> items;
+    const int variant = choose_variant(h_desc, nd);
     int maxN = 16;
     unsigned max_box = 0;
     for (int k = 0; k < nd; k++) {
@@ -604,7 +963,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
             }
             max_box = std::max(max_box, (unsigned)(n3 * kKC * p1t * 8));
             int mmax;
-            const int nit = items_per_form(d, f, &mmax);
+            const int nit = items_per_form(d, f, variant, &mmax);
             const int tiles = (n1 + p1t - 1) / p1t;
             for (int q = 0; q < nit; q++) {
                 TcItem it;
@@ -647,14 +1006,17 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     P.n_items = (int)items.size();
     P.maps = w;
     P.desc = d_desc;
-    P.Cpool = Cpool;
+    P.Cf = Cf;
     P.H = H;
     P.status = d_status;
     P.kind = kind;
     P.f_stage_bytes = (max_box + 1023) & ~1023u;
     P.w_stage_bytes = (unsigned)(((size_t)maxN * 128 + 1023) & ~(size_t)1023);
-    P.tmem_cols = 2 * kAccCols;   // both accumulator sets at full width
-    const size_t fixed = 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)P.w_stage_bytes + sizeof(TcShared);
+    P.tmem_cols = 2 * kAccCols;   // both accumulator sets / all 32 slots
+    P.variant = variant;
+    const size_t fixed = variant == 1
+        ? 1024 + 2 * (size_t)kABytes + 2 * (size_t)kKCMax * 2 * kNT * 128 + sizeof(RankShared)
+        : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)P.w_stage_bytes + sizeof(TcShared);
     int sf = (int)(((size_t)max_smem - fixed) / P.f_stage_bytes);
     sf = std::min(sf, 8);
     if (sf < 2) {
@@ -674,7 +1036,7 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.n_items = L.n_items;
     P.maps = static_cast<const CUtensorMap*>(L.maps);
     P.desc = L.desc;
-    P.Cpool = L.Cpool;
+    P.Cf = L.Cf;
     P.H = L.H;
     P.status = L.status;
     P.sf = L.sf;
@@ -682,16 +1044,12 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.w_stage_bytes = L.w_stage_bytes;
     P.tmem_cols = L.tmem_cols;
     P.kind = L.kind;
-    cudaError_t e;
-    if (L.kind == TC_TF32) {
-        e = cudaFuncSetAttribute(k_half_tc<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-        if (e != cudaSuccess) return e;
-        k_half_tc<TC_TF32><<<L.grid, kThreadsTc, L.smem, s>>>(P);
-    } else {
-        e = cudaFuncSetAttribute(k_half_tc<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-        if (e != cudaSuccess) return e;
-        k_half_tc<TC_BF16X3><<<L.grid, kThreadsTc, L.smem, s>>>(P);
-    }
+    void (*fn)(const TcParams);
+    if (L.variant == 1) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32> : k_half_tc_rank<TC_BF16X3>;
+    else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    fn<<<L.grid, kThreadsTc, L.smem, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -305,3 +305,21 @@ def test_uneven_sizes_batch(prec):
     for k in range(len(ds)):
         assert abs(pd[k, 0] - E[k, 0]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
         assert abs(pd[k, 1] - E[k, 1]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
+
+
+@pytest.mark.parametrize("variant", ["rank", "kron"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_tensor_core_kernel_variants(lat8, prec, variant, monkeypatch):
+    """Both tcgen05 kernels (forced through MCPT_TC_KERNEL) against the oracle.
+    The rank-1 variant keeps each tensor-core sum to n2/8 steps; its mean
+    signed error over the lattice must stay well below the per-dimer bound."""
+    monkeypatch.setenv("MCPT_TC_KERNEL", variant)
+    w, mons, blocks, E = lat8
+    mj, mk, pd, tot = _run(prec, w, mons, blocks, range(w.n_dimers))
+    rel = (pd[:, 0] - E[:, 0]) / np.abs(E[:, 0])
+    print(f"{prec}/{variant}: mean signed rel err {rel.mean():.3e}, max |rel| {np.abs(rel).max():.3e}, "
+          f"lattice diff {tot[0] - E[:, 0].sum():.3e} Eh")
+    assert np.all(np.abs(rel) <= PER_DIMER[prec])
+    assert abs(tot[0] - E[:, 0].sum()) <= LATTICE[prec]
+    pos = float(np.mean(rel > 0))
+    print(f"{prec}/{variant}: fraction of dimers with positive error {pos:.2f}")
