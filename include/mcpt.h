@@ -164,6 +164,32 @@ int mcpt_num_dimers(mcpt_handle h);
  * error of a failed mcpt_create on this thread. */
 const char *mcpt_last_error(mcpt_handle h);
 
+/* One dimer's FP64 {E_J, E_K} without allocating any memory.  The paper has
+ * no counterpart: this exists for callers that must not allocate device
+ * memory -- code living inside another framework's memory pool or budget,
+ * hooks that are handed their buffers, paths that may not call cudaMalloc or
+ * cudaFree (which synchronise the device and can fail midway).  All
+ * arguments are DEVICE pointers owned by the caller, on the current device:
+ * A (nX,nX,nY,nY) then K (nX,nY,nY,nX) blocks as in MCPT_AO_BLOCKS (separate
+ * pointers), C_X (nX x nX), eps_X (nX), C_Y, eps_Y, and E2 (2 doubles,
+ * written {E_J, E_K}).  Work is enqueued on `stream` (cudaStream_t, NULL =
+ * legacy default stream); read E2 after synchronising it.
+ * Scratch: a fixed 8 MiB device array inside the library (every GPU that
+ * loads the library holds it until the process exits), so 2*nX*nY*nocc_X*
+ * nocc_Y must not exceed 1048576 doubles; nX, nY <= 96.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) and sets
+ * a kernel attribute; make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or different host threads) race and give wrong results; calls on
+ * one stream are ordered.  Nothing in the array needs to start at zero --
+ * every call overwrites all of the scratch it reads.
+ * Errors (message via mcpt_last_error(NULL)): EINVAL for NULL pointers, sizes
+ * outside the limits above; ECUDA if set-up or a launch fails. */
+mcpt_status mcpt_dimer_fp64_noalloc(const double *A, const double *K,
+                                    const double *C_X, const double *eps_X, int nX, int nocc_X,
+                                    const double *C_Y, const double *eps_Y, int nY, int nocc_Y,
+                                    double *E2, void *stream);
+
 /* Release the handle and every library-owned device buffer.  Borrowed
  * pointers are not touched.  NULL is a no-op. */
 void mcpt_destroy(mcpt_handle h);

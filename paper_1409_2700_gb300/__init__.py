@@ -28,7 +28,7 @@ MCPT_AO_FULL, MCPT_AO_BLOCKS = 0, 1
 # every symbol include/mcpt.h declares
 EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_set_precision",
            "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats", "mcpt_num_monomers",
-           "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy")
+           "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
 
 
 class McptError(RuntimeError):
@@ -81,6 +81,8 @@ def lib():
         L.mcpt_last_error.restype = ctypes.c_char_p
         L.mcpt_destroy.argtypes = [H]
         L.mcpt_destroy.restype = None
+        L.mcpt_dimer_fp64_noalloc.argtypes = [P, P, P, P, I, I, P, P, I, I, P, P]
+        L.mcpt_dimer_fp64_noalloc.restype = I
         _lib = L
     return _lib
 
@@ -164,6 +166,16 @@ def mcpt_last_error(h) -> str:
 
 def mcpt_destroy(h) -> None:
     lib().mcpt_destroy(h)
+
+
+def mcpt_dimer_fp64_noalloc(A, K, C_X, eps_X, nX, nocc_X, C_Y, eps_Y, nY, nocc_Y, E2, stream=None) -> None:
+    """One dimer's FP64 {E_J, E_K} into the device buffer E2, allocating
+    nothing (fixed 8 MiB scratch inside the library); all arrays are device
+    buffers (torch CUDA tensors or addresses).  See include/mcpt.h for the
+    limits and the rule that overlapping calls race."""
+    st = lib().mcpt_dimer_fp64_noalloc(_ptr(A), _ptr(K), _ptr(C_X), _ptr(eps_X), nX, nocc_X, _ptr(C_Y),
+                                       _ptr(eps_Y), nY, nocc_Y, _ptr(E2), stream)
+    _check(None, st)
 
 
 # ----------------------------------------------------------- convenience

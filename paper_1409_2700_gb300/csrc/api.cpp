@@ -240,6 +240,8 @@ mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY, int oX, int oY)
 
 }  // namespace
 
+void mcpt::set_thread_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 // =================================================================== C ABI
 extern "C" {
 

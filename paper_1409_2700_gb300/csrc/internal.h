@@ -72,6 +72,10 @@ cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStr
 cudaError_t launch_check_finite4(const double* x, const int dims[4], const long long st[3],
                                  int* flag, cudaStream_t s);
 
+// Record the calling thread's last error (read by mcpt_last_error(NULL)) for
+// entry points that have no handle.
+void set_thread_error(const char* msg);
+
 // ---- tensor-core first half (tcgen05) ----
 enum TcKind { TC_TF32 = 0, TC_BF16X3 = 1 };
 
