@@ -94,6 +94,7 @@ struct TcLaunch {
     unsigned f_stage_bytes, w_stage_bytes, tmem_cols;
     int kind;
     int variant;                // 0: Kronecker (p0,p2) GEMM, 1: p2 GEMM + FP32 rank-1 epilogue
+    int kcs_max;                // p2 chunks of 32 (largest n_Y of the launch)
     int grid;
     size_t smem;
 };

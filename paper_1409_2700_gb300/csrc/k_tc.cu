@@ -79,6 +79,7 @@ struct TcParams {
     unsigned int w_stage_bytes;    // bytes per W slot
     unsigned int tmem_cols;
     int kind;                      // TC_TF32 / TC_BF16X3
+    int kcs_max;                   // largest p2 chunk count of the launch (rank variant)
 };
 
 // ------------------------------------------------------------------ PTX
@@ -603,37 +604,117 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // own rounding, which is independent from element to element.  Needs
 // o_X, o_Y <= 8 (register accumulators) -- larger occupations use the
 // Kronecker kernel above.
-constexpr int kNT = 16;        // TMEM slot width = MMA N
-constexpr int kSlots = 32;     // 32 x 16 = 512 TMEM columns
-constexpr int kOB = 8;         // register accumulator block: o_X, o_Y <= 8
-constexpr int kKCMax = 4;      // p2 chunks: n2 <= 128
+constexpr int kNT = 16;           // TMEM slot width = MMA N
+constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns
+constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
+constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
+constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
+constexpr int kEpiWarp0 = 2 + kConvWarps;
+constexpr int kRankThreads = (kEpiWarp0 + 4) * 32;
+constexpr int kCxFloats = 128 * kOB;   // C_X occupied rows of one item (n0 <= 128)
 
 struct __align__(8) RankShared {
     unsigned long long full_f[8], empty_f[8];
     unsigned long long full_a[2], empty_a[2];
     unsigned long long full_w[2], empty_w[2];
+    unsigned long long cx_full[2], cx_empty[2];
     unsigned long long slot_full[kSlots], slot_empty[kSlots];
     unsigned long long drain;
     unsigned int tmem_base;
     volatile int abort;
 };
 
+// A converter thread's fixed share of every A tile of an item: row r of the
+// 128-row tile and where that row's integrals sit in the FP64 staging box.
+struct ConvRow {
+    int src;        // element offset of (p1l, p2 = 0, p3) in the box
+    unsigned dst;   // byte offset of row r's 128-byte line in the tile
+    int r7;         // swizzle phase of the row
+    bool valid;
+};
+
+__device__ __forceinline__ ConvRow conv_row(int r, int tile_rows_full, int n3)
+{
+    ConvRow c;
+    c.valid = r < tile_rows_full;
+    const int p1l = c.valid ? r / n3 : 0, p3 = c.valid ? r % n3 : 0;
+    c.src = p1l * kKC * n3 + p3;
+    c.dst = (unsigned)((r >> 3) * 1024 + (r & 7) * 128);
+    c.r7 = r & 7;
+    return c;
+}
+
+// Row r of one A tile, chunks c0, c0+2, ... (the two converter threads of a
+// row split the 128-byte line).  TF32: 4 chunks of 4 p2 from the high words
+// of the doubles; BF16x3: 2 chunks of 8 p2, hi in chunk c and lo in 4 + c.
 template <int KIND>
-__global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P)
+__device__ __forceinline__ void convert_row(const double* __restrict__ F, unsigned char* __restrict__ A,
+                                            const ConvRow& cr, int n3, int c0)
+{
+    if (KIND == TC_TF32) {
+        const unsigned* __restrict__ hw = reinterpret_cast<const unsigned*>(F + cr.src) + 1;
+        unsigned v[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const unsigned w = hw[2 * ((c0 + 2 * q) * 4 + e) * n3];
+                v[q][e] = cr.valid ? tf32_from_f64_hi(w) : 0u;
+            }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            *reinterpret_cast<uint4*>(A + cr.dst + (((c0 + 2 * q) ^ cr.r7) << 4)) =
+                make_uint4(v[q][0], v[q][1], v[q][2], v[q][3]);
+    } else {
+        const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
+        unsigned hv[2][4], lv[2][4];
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int c = c0 + 2 * q;
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                unsigned short hb[2], lb[2];
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                    const uint2 b = dw[(c * 8 + e + u) * n3];
+                    const float x = cr.valid ? f32_from_f64_bits(b.x, b.y) : 0.f;
+                    hb[u] = to_bf16_bits(x);
+                    lb[u] = to_bf16_bits(x - __bfloat162float(__ushort_as_bfloat16(hb[u])));
+                }
+                hv[q][e / 2] = hb[0] | ((unsigned)hb[1] << 16);
+                lv[q][e / 2] = lb[0] | ((unsigned)lb[1] << 16);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+            const int c = c0 + 2 * q;
+            *reinterpret_cast<uint4*>(A + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(hv[q][0], hv[q][1], hv[q][2], hv[q][3]);
+            *reinterpret_cast<uint4*>(A + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
+                make_uint4(lv[q][0], lv[q][1], lv[q][2], lv[q][3]);
+        }
+    }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams P)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
+    // [F ring][A ring x2][W: 2 parities x kcs_max x 2 planes x 2 KB][C_X rows x2][barriers]
     unsigned char* Fr = base;
     unsigned char* Ar = Fr + (size_t)P.sf * P.f_stage_bytes;
-    unsigned char* Wr = Ar + 2 * kABytes;   // [2 parities][kKCMax][2 planes][16 rows x 128 B]
-    RankShared* sh = reinterpret_cast<RankShared*>(Wr + 2 * kKCMax * 2 * kNT * 128);
+    unsigned char* Wr = Ar + 2 * kABytes;
+    const int wstride = P.kcs_max * 2 * kNT * 128;      // bytes per parity
+    float* cxs = reinterpret_cast<float*>(Wr + 2 * wstride);
+    RankShared* sh = reinterpret_cast<RankShared*>(cxs + 2 * kCxFloats);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < P.sf; s++) { mbar_init(&sh->full_f[s], 1); mbar_init(&sh->empty_f[s], 4); }
+        for (int s = 0; s < P.sf; s++) { mbar_init(&sh->full_f[s], 1); mbar_init(&sh->empty_f[s], kConvWarps); }
         for (int s = 0; s < 2; s++) {
-            mbar_init(&sh->full_a[s], 4); mbar_init(&sh->empty_a[s], 1);
-            mbar_init(&sh->full_w[s], 4); mbar_init(&sh->empty_w[s], 1);
+            mbar_init(&sh->full_a[s], kConvWarps); mbar_init(&sh->empty_a[s], 1);
+            mbar_init(&sh->full_w[s], kConvWarps); mbar_init(&sh->empty_w[s], 1);
+            mbar_init(&sh->cx_full[s], 128); mbar_init(&sh->cx_empty[s], 128);
         }
         for (int s = 0; s < kSlots; s++) { mbar_init(&sh->slot_full[s], 1); mbar_init(&sh->slot_empty[s], 4); }
         mbar_init(&sh->drain, 1);
@@ -650,6 +731,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = sh->tmem_base;
+    volatile int* abort = &sh->abort;
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
@@ -659,7 +741,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
             bool issued[8];
             for (int s = 0; s < 8; s++) issued[s] = false;
             bool ok = true;
-            for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x) {
+            for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x) {
                 const TcItem item = P.items[it];
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
                 const CUtensorMap* map = P.maps + 2 * item.dimer + item.form;
@@ -669,7 +751,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
                         for (int kc = 0; kc < g.kcs; kc++, gF++) {
                             const int s = gF % P.sf;
                             const unsigned ph = (gF / P.sf) & 1;
-                            if (!(ok = mbar_wait(&sh->empty_f[s], ph ^ 1, &sh->abort, P.status, 11))) break;
+                            if (!(ok = mbar_wait(&sh->empty_f[s], ph ^ 1, abort, P.status, 11))) break;
                             mbar_arrive_tx(&sh->full_f[s], box);
                             tma_load_4d(Fr + (size_t)s * P.f_stage_bytes, map, &sh->full_f[s], 0, kc * kKC,
                                         (item.mt0 + mt) * g.p1t, p0);
@@ -689,24 +771,25 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
             unsigned gA = 0, gS = 0, li = 0;
             bool any = false, ok = true;
             const unsigned idesc = make_idesc(KIND, kNT);
-            for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x, li++) {
+            for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
                 const TcItem item = P.items[it];
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
                 const int wp = li & 1;
-                if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, &sh->abort, P.status, 12))) break;
+                if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, abort, P.status, 12))) break;
                 for (int mt = 0; mt < item.mts && ok; mt++)
                     for (int p0 = 0; p0 < g.n0 && ok; p0++, gS++) {
                         const int s = gS % kSlots;
-                        if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / kSlots) & 1) ^ 1, &sh->abort, P.status, 13))) break;
+                        if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / kSlots) & 1) ^ 1, abort, P.status, 13))) break;
                         tc_fence_after();
                         const unsigned dt = tmem + (unsigned)(s * kNT);
                         for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
                             const int as = gA & 1;
-                            if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, &sh->abort, P.status, 14))) break;
+                            if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
                             tc_fence_after();
                             const unsigned long long adesc = sw128_desc(Ar + (size_t)as * kABytes);
-                            const unsigned long long b0 = sw128_desc(Wr + (size_t)((wp * kKCMax + kc) * 2) * kNT * 128);
-                            const unsigned long long b1 = sw128_desc(Wr + (size_t)((wp * kKCMax + kc) * 2 + 1) * kNT * 128);
+                            unsigned char* wk = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
+                            const unsigned long long b0 = sw128_desc(wk);
+                            const unsigned long long b1 = sw128_desc(wk + kNT * 128);
                             if (KIND == TC_TF32) {
                                 // C_Y = hi + lo (two TF32 planes): A (hi + lo)
 #pragma unroll
@@ -741,25 +824,26 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
                 while (!mbar_test(&sh->drain, 0) && now_ns() - t0 < kWaitNs) {}
             }
         }
-    } else if (warp < 6) {
+    } else if (warp < kEpiWarp0) {
         // ------------------------------------------------ converters
-        const int ct = threadIdx.x - 64;
+        const int ct = threadIdx.x - 64;        // 0 .. 32*kConvWarps-1
+        const int r = ct & 127, c0 = ct >> 7;   // tile row, first chunk
         unsigned gF = 0, gA = 0, li = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x, li++) {
+        for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
             const TcItem item = P.items[it];
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
             const float* CY = P.Cf + d.cY;
             const int wp = li & 1;
-            const int tile_rows_full = g.p1t * g.n3;
+            const ConvRow cr = conv_row(r, g.p1t * g.n3, g.n3);
             // ---- B operand of this item: row j < 16, K = p2: C_Y[p2][j] (zero past o2 / n2)
-            if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, &sh->abort, P.status, 15))) break;
+            if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, abort, P.status, 15))) break;
             for (int kc = 0; kc < g.kcs; kc++) {
-                unsigned char* W0 = Wr + (size_t)((wp * kKCMax + kc) * 2) * kNT * 128;
+                unsigned char* W0 = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                 unsigned char* W1 = W0 + kNT * 128;
                 if (KIND == TC_TF32) {
-                    for (int task = ct; task < kNT * 8; task += 128) {
+                    for (int task = ct; task < kNT * 8; task += 32 * kConvWarps) {
                         const int j = task >> 3, c = task & 7;
                         unsigned h4[4], l4[4];
 #pragma unroll
@@ -773,7 +857,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
                         *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
                     }
                 } else {
-                    for (int task = ct; task < kNT * 4; task += 128) {
+                    for (int task = ct; task < kNT * 4; task += 32 * kConvWarps) {
                         const int j = task >> 2, c = task & 3;
                         unsigned short b0[8], b1[8], b2[8];
 #pragma unroll
@@ -806,11 +890,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
                 for (int p0 = 0; p0 < g.n0 && ok; p0++)
                     for (int kc = 0; kc < g.kcs; kc++, gF++, gA++) {
                         const int s = gF % P.sf;
-                        if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, &sh->abort, P.status, 16))) break;
+                        if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16))) break;
                         const int as = gA & 1;
-                        if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, &sh->abort, P.status, 17))) break;
-                        const double* F = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
-                        convert_a_tile<KIND>(F, Ar + (size_t)as * kABytes, tile_rows_full, g.n3, ct);
+                        if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17))) break;
+                        convert_row<KIND>(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes),
+                                          Ar + (size_t)as * kABytes, cr, g.n3, c0);
                         fence_async_smem();
                         __syncwarp();
                         if (lane == 0) {
@@ -822,14 +906,25 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
     } else {
         // ------------------------------------------------ epilogue
         const int q = warp & 3;
-        const int r = q * 32 + lane;
-        unsigned gS = 0;
+        const int r = q * 32 + lane;                    // accumulator row = TMEM lane
+        const int e = (warp - kEpiWarp0) * 32 + lane;   // 0..127: C_X row this thread stages
+        unsigned gS = 0, li = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < P.n_items && ok && !sh->abort; it += gridDim.x) {
+        for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
             const TcItem item = P.items[it];
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
-            const float* CX = P.Cf + d.cX;
+            const int par = li & 1;
+            float* cx = cxs + par * kCxFloats;
+            // stage C_X's occupied columns, row p0 = e, for this item
+            if (!(ok = mbar_wait(&sh->cx_empty[par], ((li >> 1) & 1) ^ 1, abort, P.status, 19))) break;
+            if (e < g.n0) {
+                const float* CX = P.Cf + d.cX + e * d.nX;
+#pragma unroll
+                for (int i = 0; i < kOB; i++) cx[e * kOB + i] = i < g.o0 ? __ldg(CX + i) : 0.f;
+            }
+            mbar_arrive(&sh->cx_full[par]);
+            if (!(ok = mbar_wait(&sh->cx_full[par], (li >> 1) & 1, abort, P.status, 20))) break;
             float* Hf = P.H + d.h_off + (long long)item.form * g.rows * g.N;
             for (int mt = 0; mt < item.mts && ok; mt++) {
                 float acc[kOB][kOB];
@@ -839,20 +934,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
                     for (int j = 0; j < kOB; j++) acc[i][j] = 0.f;
                 for (int p0 = 0; p0 < g.n0; p0++, gS++) {
                     const int s = gS % kSlots;
-                    if (!(ok = mbar_wait(&sh->slot_full[s], (gS / kSlots) & 1, &sh->abort, P.status, 18))) break;
+                    if (!(ok = mbar_wait(&sh->slot_full[s], (gS / kSlots) & 1, abort, P.status, 18))) break;
                     tc_fence_after();
                     float T[16];
                     tmem_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(s * kNT), T);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
-                    float cx[kOB];
-#pragma unroll
-                    for (int i = 0; i < kOB; i++) cx[i] = i < g.o0 ? __ldg(CX + p0 * d.nX + i) : 0.f;
+                    const float4 ca = *reinterpret_cast<const float4*>(cx + p0 * kOB);
+                    const float4 cb = *reinterpret_cast<const float4*>(cx + p0 * kOB + 4);
+                    const float cv[kOB] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
 #pragma unroll
                     for (int i = 0; i < kOB; i++)
 #pragma unroll
-                        for (int j = 0; j < kOB; j++) acc[i][j] = fmaf(cx[i], T[j], acc[i][j]);
+                        for (int j = 0; j < kOB; j++) acc[i][j] = fmaf(cv[i], T[j], acc[i][j]);
                 }
                 if (!ok) break;
                 const int tile = item.mt0 + mt;
@@ -867,6 +962,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc_rank(const TcParams P
                             if (i < g.o0 && j < g.o2) out[i * g.o2 + j] = acc[i][j];
                 }
             }
+            mbar_arrive(&sh->cx_empty[par]);
         }
     }
 
@@ -1014,8 +1110,12 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     P.w_stage_bytes = (unsigned)(((size_t)maxN * 128 + 1023) & ~(size_t)1023);
     P.tmem_cols = 2 * kAccCols;   // both accumulator sets / all 32 slots
     P.variant = variant;
+    int kcs_max = 1;
+    for (int k = 0; k < nd; k++) kcs_max = std::max(kcs_max, (h_desc[k].nY + kKC - 1) / kKC);
+    P.kcs_max = kcs_max;
     const size_t fixed = variant == 1
-        ? 1024 + 2 * (size_t)kABytes + 2 * (size_t)kKCMax * 2 * kNT * 128 + sizeof(RankShared)
+        ? 1024 + 2 * (size_t)kABytes + 2 * (size_t)kcs_max * 2 * kNT * 128 + 2 * (size_t)kCxFloats * 4 +
+              sizeof(RankShared)
         : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)P.w_stage_bytes + sizeof(TcShared);
     int sf = (int)(((size_t)max_smem - fixed) / P.f_stage_bytes);
     sf = std::min(sf, 8);
@@ -1044,12 +1144,13 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.w_stage_bytes = L.w_stage_bytes;
     P.tmem_cols = L.tmem_cols;
     P.kind = L.kind;
+    P.kcs_max = L.kcs_max;
     void (*fn)(const TcParams);
     if (L.variant == 1) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32> : k_half_tc_rank<TC_BF16X3>;
     else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    fn<<<L.grid, kThreadsTc, L.smem, s>>>(P);
+    fn<<<L.grid, L.variant == 1 ? kRankThreads : kThreadsTc, L.smem, s>>>(P);
     return cudaGetLastError();
 }
 
