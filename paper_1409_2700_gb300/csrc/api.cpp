@@ -201,18 +201,14 @@ bool all_finite(const double* x, size_t n)
 
 bool is_tensor_form(mcpt_precision p) { return p == MCPT_TF32 || p == MCPT_BF16X3; }
 
-// Row stride of the first-half result for a dimer in a given form.
-int ldh_for(mcpt_precision p, int oX, int oY)
-{
-    const int pairs = oX * oY;
-    if (is_tensor_form(p)) return (pairs + 15) / 16 * 16;   // MMA N is a multiple of 16
-    return pairs;
-}
+// Occupied pairs padded to 16 (N of the Kronecker tensor-core GEMM).
+int npad_for(int oX, int oY) { return (oX * oY + 15) / 16 * 16; }
 
+// Bytes of the first-half result of one dimer (both forms, pair-major).
 size_t hbytes_for(mcpt_precision p, int nX, int nY, int oX, int oY)
 {
     const size_t elem = (p == MCPT_FP64) ? sizeof(double) : sizeof(float);
-    return 2 * (size_t)nX * nY * ldh_for(p, oX, oY) * elem;
+    return 2 * (size_t)nX * nY * oX * oY * elem;
 }
 
 mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY, int oX, int oY)
@@ -535,7 +531,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         dd.nX = mX.nao; dd.nY = mY.nao; dd.oX = mX.nocc; dd.oY = mY.nocc;
         dd.cX = mX.offC; dd.cY = mY.offC; dd.eX = mX.offE; dd.eY = mY.offE;
         dd.X = r.X; dd.Y = r.Y;
-        dd.ldh = ldh_for(prec, dd.oX, dd.oY);
+        dd.npad = npad_for(dd.oX, dd.oY);
         dd.slot = d;
         const size_t hb = hbytes_for(prec, dd.nX, dd.nY, dd.oX, dd.oY);
         const size_t elem = prec == MCPT_FP64 ? 8 : 4;

@@ -10,7 +10,8 @@
 //
 // The path has two halves:
 //   first half  ("transform", reads every AO byte once):
-//       H_f[(p1,p3)][(i,j)] = sum_{p0,p2} C_X[p0][i] C_Y[p2][j] E[p0][p1][p2][p3]
+//       H_f[(i,j)][(p1,p3)] = sum_{p0,p2} C_X[p0][i] C_Y[p2][j] E[p0][p1][p2][p3]
+//       (stored pair-major: one contiguous nX*nY slice per occupied pair)
 //   second half ("finish"):  (i a|j b) = sum_{nu,sig} C_X[nu][a] C_Y[sig][b] H_0[(nu,sig)][(i,j)]
 //                            (i b|j a) = sum_{lam,nu} C_Y[lam][b] C_X[nu][a] H_1[(lam,nu)][(i,j)]
 //       then D = 1/(e_i+e_j-e_a-e_b) and the two energy sums in FP64.
@@ -31,8 +32,9 @@ struct DimerDesc {
     int cX, cY;           // offsets (doubles) of C_X, C_Y in the coefficient pool
     int eX, eY;           // offsets (doubles) of eps_X, eps_Y in the energy pool
     int X, Y;             // monomer ids
-    long long h_off;      // first-half result: form f starts at h_off + f * nX*nY*ldh
-    int ldh;              // row stride of the first-half result (>= oX*oY)
+    long long h_off;      // first-half result H: element (form f, pair i*oY+j, row) at
+                          //   h_off + (f*oX*oY + i*oY + j) * nX*nY + row   (pair-major)
+    int npad;             // oX*oY padded to 16: N of the Kronecker tensor-core GEMM
     int slot;             // index of this dimer's {E_J, E_K} in the per-dimer output
 };
 

@@ -46,13 +46,13 @@ k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double
     const DimerDesc& d = dd[blockIdx.x];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
     const int vX = nX - oX, vY = nY - oY;
-    const int rows = nX * nY, ld = d.ldh;
+    const int rows = nX * nY, pairs = oX * oY;
     const T* CX = C + d.cX;
     const T* CY = C + d.cY;
     const double* eX = Epool + d.eX;
     const double* eY = Epool + d.eY;
     const T* H0 = H + d.h_off;
-    const T* H1 = H + d.h_off + (long long)rows * ld;
+    const T* H1 = H + d.h_off + (long long)pairs * rows;
 
     extern __shared__ __align__(16) unsigned char smraw[];
     T* S = reinterpret_cast<T*>(smraw);                 // [rows]
@@ -66,7 +66,7 @@ k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double
             const int col = i * oY + j;
             const double eij = eX[i] + eY[j];
             // ---- (i a|j b) from H_0
-            for (int k = tid; k < rows; k += kFinThreads) S[k] = H0[(long long)k * ld + col];
+            for (int k = tid; k < rows; k += kFinThreads) S[k] = H0[(long long)col * rows + k];
             __syncthreads();
             for (int k = tid; k < nX * vY; k += kFinThreads) {
                 const int nu = k / vY, b = k % vY;
@@ -84,7 +84,7 @@ k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double
             }
             __syncthreads();
             // ---- (i b|j a) from H_1
-            for (int k = tid; k < rows; k += kFinThreads) S[k] = H1[(long long)k * ld + col];
+            for (int k = tid; k < rows; k += kFinThreads) S[k] = H1[(long long)col * rows + k];
             __syncthreads();
             for (int k = tid; k < nY * vX; k += kFinThreads) {
                 const int lam = k / vX, a = k % vX;
@@ -122,11 +122,141 @@ k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double
     }
 }
 
+// ---------------------------------------------------------------------------
+// Monomers of at most 32 AO: one warp per occupied pair (i, j), one lane per
+// virtual orbital.  For pair (i, j):
+//   lane b:  tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]        (C_Y column b in registers)
+//            VA[a][b] = sum_nu C_X[nu][a] tm[nu]             (C_X rows broadcast from smem)
+//   lane a:  tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
+//            VK[b][a] = sum_lam C_Y[lam][b] tk[lam], and with VA[a][b] (transposed
+//            through smem) and D from the precomputed e_a + e_b the two FP64 sums.
+// The H slices are contiguous (pair-major), read with coalesced loads into a
+// zero-padded 32 x 32 tile.  Per-lane sums reduce in a fixed order.
+constexpr int kW32Warps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kW32Warps * 32)
+k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
+             const T* __restrict__ H, double* __restrict__ E2)
+{
+    const DimerDesc& d = dd[blockIdx.x];
+    const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
+    const int vX = nX - oX, vY = nY - oY;
+    const int rows = nX * nY, pairs = oX * oY;
+    const T* CX = C + d.cX;
+    const T* CY = C + d.cY;
+    const double* eX = Epool + d.eX;
+    const double* eY = Epool + d.eY;
+    const T* H0 = H + d.h_off;
+    const T* H1 = H + d.h_off + (long long)pairs * rows;
+
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* eab = reinterpret_cast<double*>(smraw);          // [32][32]: e_a + e_b
+    T* CXT = reinterpret_cast<T*>(eab + 32 * 32);             // [a][nu], zero padded
+    T* CYT = CXT + 32 * 32;                                   // [b][sig]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* S = CYT + 32 * 32 + warp * (32 * 32 + 32 * 33);        // [32][32] integral slice
+    T* VAs = S + 32 * 32;                                     // [a][b], stride 33
+
+    for (int k = threadIdx.x; k < 32 * 32; k += kW32Warps * 32) {
+        const int a = k >> 5, m = k & 31;
+        CXT[k] = (a < vX && m < nX) ? CX[m * nX + oX + a] : T(0);
+        CYT[k] = (a < vY && m < nY) ? CY[m * nY + oY + a] : T(0);
+        eab[k] = (a < vX && m < vY) ? eX[oX + a] + eY[oY + m] : 0.0;
+    }
+    __syncthreads();
+
+    double ej = 0.0, ek = 0.0;
+    for (int pr = warp; pr < pairs; pr += kW32Warps) {
+        const int i = pr / oY, j = pr % oY;
+        const double eij = eX[i] + eY[j];
+        // ---- (i a|j b): S[nu][sig] = H0 slice
+        const T* h0 = H0 + (long long)pr * rows;
+        for (int k = lane; k < 32 * 32; k += 32) {
+            const int r = k >> 5, c = k & 31;
+            S[k] = (r < nX && c < nY) ? h0[r * nY + c] : T(0);
+        }
+        __syncwarp();
+        {
+            T cy[32], tm[32];
+#pragma unroll
+            for (int m = 0; m < 32; m++) cy[m] = CYT[lane * 32 + m];
+#pragma unroll
+            for (int nu = 0; nu < 32; nu++) {
+                T acc = 0;
+#pragma unroll
+                for (int m = 0; m < 32; m++) acc = fma(S[nu * 32 + m], cy[m], acc);
+                tm[nu] = acc;
+            }
+#pragma unroll 4
+            for (int a = 0; a < 32; a++) {
+                T acc = 0;
+#pragma unroll
+                for (int nu = 0; nu < 32; nu++) acc = fma(CXT[a * 32 + nu], tm[nu], acc);
+                VAs[a * 33 + lane] = acc;
+            }
+        }
+        __syncwarp();
+        // ---- (i b|j a): S[lam][nu] = H1 slice
+        const T* h1 = H1 + (long long)pr * rows;
+        for (int k = lane; k < 32 * 32; k += 32) {
+            const int r = k >> 5, c = k & 31;
+            S[k] = (r < nY && c < nX) ? h1[r * nX + c] : T(0);
+        }
+        __syncwarp();
+        {
+            T cx[32], tk[32];
+#pragma unroll
+            for (int m = 0; m < 32; m++) cx[m] = CXT[lane * 32 + m];
+#pragma unroll
+            for (int lam = 0; lam < 32; lam++) {
+                T acc = 0;
+#pragma unroll
+                for (int m = 0; m < 32; m++) acc = fma(S[lam * 32 + m], cx[m], acc);
+                tk[lam] = acc;
+            }
+            const bool live = lane < vX;
+#pragma unroll 2
+            for (int b = 0; b < 32; b++) {
+                T vk = 0;
+#pragma unroll
+                for (int lam = 0; lam < 32; lam++) vk = fma(CYT[b * 32 + lam], tk[lam], vk);
+                if (live && b < vY) {
+                    const double va = to_f64(VAs[lane * 33 + b]);
+                    const double D = rcp_f64(eij - eab[lane * 32 + b]);
+                    ej = fma(va * va, D, ej);
+                    ek = fma(va * to_f64(vk), D, ek);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __shared__ double red[2][kW32Warps];
+    ej = warp_sum(ej);
+    ek = warp_sum(ek);
+    if (lane == 0) { red[0][warp] = ej; red[1][warp] = ek; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sj = 0.0, sk = 0.0;
+        for (int w = 0; w < kW32Warps; w++) { sj += red[0][w]; sk += red[1][w]; }
+        E2[2 * d.slot + 0] = 4.0 * sj;
+        E2[2 * d.slot + 1] = -2.0 * sk;
+    }
+}
+
 template <typename T>
 cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* C, const double* Epool,
                           const T* H, double* E2, cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
+    if (max_ao <= 32) {
+        const size_t smem = 32 * 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) +
+                            kW32Warps * (32 * 32 + 32 * 33) * sizeof(T);
+        cudaError_t e = cudaFuncSetAttribute(k_finish_w32<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_finish_w32<T><<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2);
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)3 * max_ao * max_ao * sizeof(T);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -148,7 +278,9 @@ constexpr int kRedThreads = 256;
 
 // Blocks [0, nbm): one thread per monomer sums half of each of its dimers'
 // terms in ascending dimer order.  Last block: lattice totals from a fixed
-// partition of the dimer list into kRedThreads contiguous chunks.
+// partition of the dimer list into kRedThreads contiguous chunks (Neumaier
+// within a chunk), merged by a fixed pairwise tree.  Long dependent FP64
+// chains are slow on GB300, so no thread walks more than a chunk.
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restrict__ mon,
          double* __restrict__ total)
@@ -178,16 +310,25 @@ k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restri
     }
     part[0][t] = sj; part[1][t] = cj; part[2][t] = sk; part[3][t] = ck;
     __syncthreads();
-    if (t == 0) {
-        double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
-        for (int w = 0; w < kRedThreads; w++) {
-            neumaier_add(s0, c0, part[0][w]);
-            c0 += part[1][w];
-            neumaier_add(s1, c1, part[2][w]);
-            c1 += part[3][w];
+    // pairwise tree over the chunk partials, fixed pairing: (sum, compensation)
+    // pairs are merged with Knuth's TwoSum so the rounding of each merge is kept
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (t < w) {
+#pragma unroll
+            for (int f = 0; f < 4; f += 2) {
+                const double a = part[f][t], b = part[f][t + w];
+                const double s = a + b;
+                const double bp = s - a;
+                const double err = (a - (s - bp)) + (b - bp);
+                part[f][t] = s;
+                part[f + 1][t] = part[f + 1][t] + part[f + 1][t + w] + err;
+            }
         }
-        total[0] = s0 + c0;
-        total[1] = s1 + c1;
+        __syncthreads();
+    }
+    if (t == 0) {
+        total[0] = part[0][0] + part[1][0];
+        total[1] = part[2][0] + part[3][0];
     }
 }
 

@@ -68,7 +68,7 @@ k_half_fp32c(const DimerDesc* __restrict__ dd, const float* __restrict__ Cf, flo
     const int p1 = active ? r / n3 : 0, p3 = active ? r % n3 : 0;
     const long long s0 = d.st[f][0], s1 = d.st[f][1], s2 = d.st[f][2];
     const double* __restrict__ Erow = d.E[f] + p1 * s1 + p3;
-    float* out = H + d.h_off + (long long)f * rows * d.ldh + (long long)r * d.ldh;
+    float* out = H + d.h_off + (long long)f * d.oX * d.oY * rows + r;   // pair-major
 
     for (int t0b = 0; t0b < o0; t0b += OB) {
         for (int t2b = 0; t2b < o2; t2b += OB) {
@@ -112,7 +112,7 @@ k_half_fp32c(const DimerDesc* __restrict__ dd, const float* __restrict__ Cf, flo
             for (int a = 0; a < OB; a++)
 #pragma unroll
                 for (int t = 0; t < OB; t++)
-                    if (t0b + a < o0 && t2b + t < o2) out[(t0b + a) * o2 + t2b + t] = acc[a][t].hi + acc[a][t].lo;
+                    if (t0b + a < o0 && t2b + t < o2) out[(long long)((t0b + a) * o2 + t2b + t) * rows] = acc[a][t].hi + acc[a][t].lo;
         }
     }
 }

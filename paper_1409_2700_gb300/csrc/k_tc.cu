@@ -232,7 +232,7 @@ struct ItemGeo {
     int p1t;          // p1 values per M-tile
     int kcs;          // p2 chunks
     int kblocks;      // n0 * kcs
-    int N;            // padded pair count (ldh)
+    int N;            // padded pair count (npad)
     int rows;         // n1 * n3
 };
 
@@ -248,7 +248,7 @@ __device__ __forceinline__ ItemGeo geo_of(const DimerDesc& d, int f)
     g.p1t = 128 / g.n3;
     g.kcs = (g.n2 + kKC - 1) / kKC;
     g.kblocks = g.n0 * g.kcs;
-    g.N = d.ldh;
+    g.N = d.npad;
     g.rows = g.n1 * g.n3;
     return g;
 }
@@ -553,20 +553,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
             const int b = li & 1;
             if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, &sh->abort, P.status, 8)) break;
             tc_fence_after();
-            float* Hf = P.H + d.h_off + (long long)item.form * g.rows * g.N;
+            const int npairs = g.o0 * g.o2;
+            float* Hf = P.H + d.h_off + (long long)item.form * npairs * g.rows;
             for (int mt = 0; mt < item.mts; mt++) {
                 const int tile = item.mt0 + mt;
                 const int p1_lo = tile * g.p1t;
                 const int p1_hi = min(g.n1, p1_lo + g.p1t);
                 const int valid = (p1_hi - p1_lo) * g.n3;
-                float* out = Hf + (long long)(p1_lo * g.n3 + r) * g.N;
+                float* out = Hf + p1_lo * g.n3 + r;
                 for (int c = 0; c < g.N; c += 16) {
                     float v[16];
                     tmem_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(b * kAccCols + mt * g.N + c), v);
                     if (r < valid) {
-                        float4* o4 = reinterpret_cast<float4*>(out + c);
 #pragma unroll
-                        for (int k = 0; k < 4; k++) o4[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                        for (int k = 0; k < 16; k++)
+                            if (c + k < npairs) out[(long long)(c + k) * g.rows] = v[k];
                     }
                 }
             }
@@ -925,7 +926,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             }
             mbar_arrive(&sh->cx_full[par]);
             if (!(ok = mbar_wait(&sh->cx_full[par], (li >> 1) & 1, abort, P.status, 20))) break;
-            float* Hf = P.H + d.h_off + (long long)item.form * g.rows * g.N;
+            float* Hf = P.H + d.h_off + (long long)item.form * g.o0 * g.o2 * g.rows;
             for (int mt = 0; mt < item.mts && ok; mt++) {
                 float acc[kOB][kOB];
 #pragma unroll
@@ -954,12 +955,12 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 const int p1_lo = tile * g.p1t;
                 const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
                 if (r < valid) {
-                    float* out = Hf + (long long)(p1_lo * g.n3 + r) * g.N;
+                    float* out = Hf + p1_lo * g.n3 + r;   // pair-major: coalesced over rows
 #pragma unroll
                     for (int i = 0; i < kOB; i++)
 #pragma unroll
                         for (int j = 0; j < kOB; j++)
-                            if (i < g.o0 && j < g.o2) out[i * g.o2 + j] = acc[i][j];
+                            if (i < g.o0 && j < g.o2) out[(long long)(i * g.o2 + j) * g.rows] = acc[i][j];
                 }
             }
             mbar_arrive(&sh->cx_empty[par]);
@@ -996,7 +997,7 @@ int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
     const int n1 = f ? d.nY : d.nX, n3 = f ? d.nX : d.nY;
     const int p1t = 128 / n3;
     const int tiles = (n1 + p1t - 1) / p1t;
-    const int mmax = variant == 1 ? 1 : std::max(1, std::min(8, kAccCols / d.ldh));
+    const int mmax = variant == 1 ? 1 : std::max(1, std::min(8, kAccCols / d.npad));
     *mts_max = mmax;
     return (tiles + mmax - 1) / mmax;
 }
@@ -1042,7 +1043,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     unsigned max_box = 0;
     for (int k = 0; k < nd; k++) {
         const DimerDesc& d = h_desc[k];
-        maxN = std::max(maxN, d.ldh);
+        maxN = std::max(maxN, d.npad);
         for (int f = 0; f < 2; f++) {
             const int n0 = d.nX, n1 = f ? d.nY : d.nX, n2 = d.nY, n3 = f ? d.nX : d.nY;
             const int p1t = 128 / n3;
