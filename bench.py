@@ -128,6 +128,13 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM traffic per dimer of the first-half kernel, from the ncu capture in
+# profiles/k_half_tc_rank_tf32_lattice-2x2x2.md (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over 28 dimers of 32 AO / 5 occupied,
+# scaled per dimer).  Only valid for that kernel, form and monomer size.
+TRAFFIC_PER_DIMER = {("tf32", 32, 5): (469.94e6 + 17.17e6) / 28}
+
+
 def host_sample(w, dimers):
     """Host inputs for the oracle (host generator)."""
     import synth  # noqa: F401
@@ -242,9 +249,13 @@ def our_arm(args, ws, rank, local):
                 "peak_kind": "nominal FP64 rate"}
     else:
         achieved = per_launch_bytes / (transform_ms / st.waves * 1e-3) / 1e9
+        tpd = TRAFFIC_PER_DIMER.get((args.precision, w.nao[0], w.nocc[0]))
+        uniform = len(set(w.nao)) == 1 and len(set(w.nocc)) == 1
+        traffic = tpd * w.n_dimers / st.waves if (tpd and uniform) else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "k_half_tc" if args.precision in ("tf32", "bf16x3") else "k_half_fp32c",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": ("k_half_tc_rank" if max(w.nocc) <= 8 else "k_half_tc")
+                if args.precision in ("tf32", "bf16x3") else "k_half_fp32c",
                 "peak_kind": peak_kind}
 
     line = {

@@ -52,15 +52,19 @@ __device__ __forceinline__ double f64_from_f32(float f)
 }
 
 // 1/x in FP64 for |x| in a normal FP32 range: FP32 reciprocal seed (relative
-// error ~2^-23) and two Newton-Raphson steps r <- r + r(1 - x r), each
-// squaring the error (2^-46, then below FP64 rounding).
+// error ~2^-23) and STEPS Newton-Raphson steps r <- r + r(1 - x r), each
+// squaring the error: one step leaves ~2^-46 (1.4e-14), two reach FP64
+// rounding.
+template <int STEPS>
 __device__ __forceinline__ double rcp_f64(double x)
 {
     double r = f64_from_f32(__frcp_rn(f32_from_f64(x)));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+#pragma unroll
+    for (int k = 0; k < STEPS; k++) {
+        const double e = fma(-x, r, 1.0);
+        r = fma(r, e, r);
+    }
+    return r;
 }
 
 }  // namespace mcpt

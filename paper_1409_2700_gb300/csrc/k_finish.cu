@@ -9,9 +9,11 @@
 //   (i b|j a) = sum_lam C_Y[lam][b] sum_nu H_1[lam][nu] C_X[nu][a]
 // Then, in FP64 (Sec. II.C energy tensor, Eq. (ed2) with T = vD):
 //   D = 1/(e_i + e_j - e_a - e_b),  E_J += 4 (ia|jb)^2 D,  E_K += -2 (ia|jb)(ib|ja) D.
-// GB300's FP64 unit is small, so D is an FP32 reciprocal refined by two
-// Newton steps in FP64 (convert.h) rather than a full FP64 division, and the
-// FP32 -> FP64 widening of the mixed forms' integrals runs on integer pipes.
+// GB300's FP64 unit is small, so D is an FP32 reciprocal refined by Newton
+// steps in FP64 (convert.h) rather than a full FP64 division -- two for the
+// FP64 form (full FP64 accuracy), one for the mixed forms (relative error
+// ~1.4e-14, far below their transform error) -- and the FP32 -> FP64 widening
+// of the mixed forms' integrals runs on integer pipes.
 // One CTA owns one dimer, so the per-dimer energies come out of a fixed-order
 // block reduction: deterministic run to run, no atomics.
 #include "internal.h"
@@ -101,7 +103,7 @@ k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double
                 for (int lam = 0; lam < nY; lam++) acc = fma(__ldg(CY + lam * nY + oY + b), Tm[lam * vX + a], acc);
                 const double va = to_f64(VA[k]);
                 const double vk = to_f64(acc);
-                const double D = rcp_f64(eij - (eX[oX + a] + eY[oY + b]));
+                const double D = rcp_f64<sizeof(T) == 8 ? 2 : 1>(eij - (eX[oX + a] + eY[oY + b]));
                 ej = fma(va * va, D, ej);
                 ek = fma(va * vk, D, ek);
             }
@@ -223,7 +225,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 for (int lam = 0; lam < 32; lam++) vk = fma(CYT[b * 32 + lam], tk[lam], vk);
                 if (live && b < vY) {
                     const double va = to_f64(VAs[lane * 33 + b]);
-                    const double D = rcp_f64(eij - eab[lane * 32 + b]);
+                    const double D = rcp_f64<sizeof(T) == 8 ? 2 : 1>(eij - eab[lane * 32 + b]);
                     ej = fma(va * va, D, ej);
                     ek = fma(va * to_f64(vk), D, ek);
                 }
