@@ -194,6 +194,29 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
+// Batched TMEM access for the accumulators that live in TMEM: loads without
+// the wait (issue several, then one tcgen05.wait::ld) and stores.
+__device__ __forceinline__ void tmem_ld16_nowait(unsigned taddr, unsigned (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // K-major operand with SWIZZLE_128B: 8-row x 128-byte atoms stacked along the
 // row dimension (stride 1024 B); the 16-byte chunk c of row r sits at chunk
 // position c ^ (r % 8).  Matrix-descriptor fields: start address >> 4,
@@ -607,17 +630,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // it is split into two TF32 planes (hi + lo, two MMAs per step) or three
 // BF16 pieces (c0 + c1 + c2; A_hi(c0+c1+c2) + A_lo(c0+c1), five MMAs), which
 // represents it to about FP32 accuracy.  Only the integrals keep the form's
-// own rounding, which is independent from element to element.  Needs
-// o_X, o_Y <= 8 (register accumulators) -- larger occupations use the
-// Kronecker kernel above.
+// own rounding, which is independent from element to element.
+// BIG = false: the rank-1 accumulators live in registers (o_X, o_Y <= 8),
+// T slots use all 512 TMEM columns.  BIG = true (o_X, o_Y <= 16): the
+// accumulators live in TMEM columns 256-511 (row r = lane r, column
+// 256 + 16 i + j) and the epilogue updates them four occupied i at a time
+// (tcgen05.ld, FFMA, tcgen05.st); the T ring shrinks to 16 slots.
 constexpr int kNT = 16;           // TMEM slot width = MMA N
-constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns
+constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns (16 slots when BIG)
 constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
 constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
 constexpr int kEpiWarp0 = 2 + kConvWarps;
 constexpr int kRankThreads = (kEpiWarp0 + 4) * 32;
-constexpr int kCxFloats = 128 * kOB;   // C_X occupied rows of one item (n0 <= 128)
+constexpr int kOBig = 16;         // TMEM accumulators: o_X, o_Y <= 16
+constexpr int kCxFloats = 128 * kOBig; // C_X occupied rows of one item (n0 <= 128)
 
 struct __align__(8) RankShared {
     unsigned long long full_f[8], empty_f[8];
@@ -701,9 +728,11 @@ __device__ __forceinline__ void convert_row(const double* __restrict__ F, unsign
     }
 }
 
-template <int KIND>
+template <int KIND, bool BIG>
 __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams P)
 {
+    constexpr int NS = BIG ? 16 : kSlots;   // T slots in the ring
+    constexpr int CXW = BIG ? kOBig : kOB;  // staged C_X occupied columns per row
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
     // [F ring][A ring x2][W: 2 parities x kcs_max x 2 planes x 2 KB][C_X rows x2][barriers]
@@ -784,8 +813,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, abort, P.status, 12))) break;
                 for (int mt = 0; mt < item.mts && ok; mt++)
                     for (int p0 = 0; p0 < g.n0 && ok; p0++, gS++) {
-                        const int s = gS % kSlots;
-                        if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / kSlots) & 1) ^ 1, abort, P.status, 13))) break;
+                        const int s = gS % NS;
+                        if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13))) break;
                         tc_fence_after();
                         const unsigned dt = tmem + (unsigned)(s * kNT);
                         for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
@@ -927,45 +956,106 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             if (e < g.n0) {
                 const float* CX = P.Cf + d.cX + e * d.nX;
 #pragma unroll
-                for (int i = 0; i < kOB; i++) cx[e * kOB + i] = i < g.o0 ? __ldg(CX + i) : 0.f;
+                for (int i = 0; i < CXW; i++) cx[e * CXW + i] = i < g.o0 ? __ldg(CX + i) : 0.f;
             }
             mbar_arrive(&sh->cx_full[par]);
             if (!(ok = mbar_wait(&sh->cx_full[par], (li >> 1) & 1, abort, P.status, 20))) break;
             float* Hf = P.H + d.h_off + (long long)item.form * g.o0 * g.o2 * g.rows;
+            const unsigned lanebase = tmem + ((unsigned)(q * 32) << 16);
             for (int mt = 0; mt < item.mts && ok; mt++) {
-                float acc[kOB][kOB];
-#pragma unroll
-                for (int i = 0; i < kOB; i++)
-#pragma unroll
-                    for (int j = 0; j < kOB; j++) acc[i][j] = 0.f;
-                for (int p0 = 0; p0 < g.n0; p0++, gS++) {
-                    const int s = gS % kSlots;
-                    if (!(ok = mbar_wait(&sh->slot_full[s], (gS / kSlots) & 1, abort, P.status, 18))) break;
-                    tc_fence_after();
-                    float T[16];
-                    tmem_ld16(tmem + ((unsigned)(q * 32) << 16) + (unsigned)(s * kNT), T);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
-                    const float4 ca = *reinterpret_cast<const float4*>(cx + p0 * kOB);
-                    const float4 cb = *reinterpret_cast<const float4*>(cx + p0 * kOB + 4);
-                    const float cv[kOB] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+                const int p1_lo = (item.mt0 + mt) * g.p1t;
+                if constexpr (!BIG) {
+                    float acc[kOB][kOB];
 #pragma unroll
                     for (int i = 0; i < kOB; i++)
 #pragma unroll
-                        for (int j = 0; j < kOB; j++) acc[i][j] = fmaf(cv[i], T[j], acc[i][j]);
-                }
-                if (!ok) break;
-                const int tile = item.mt0 + mt;
-                const int p1_lo = tile * g.p1t;
-                const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
-                if (r < valid) {
+                        for (int j = 0; j < kOB; j++) acc[i][j] = 0.f;
+                    for (int p0 = 0; p0 < g.n0; p0++, gS++) {
+                        const int s = gS % NS;
+                        if (!(ok = mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, P.status, 18))) break;
+                        tc_fence_after();
+                        float T[16];
+                        tmem_ld16(lanebase + (unsigned)(s * kNT), T);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
+                        const float4 ca = *reinterpret_cast<const float4*>(cx + p0 * kOB);
+                        const float4 cb = *reinterpret_cast<const float4*>(cx + p0 * kOB + 4);
+                        const float cv[kOB] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
+#pragma unroll
+                        for (int i = 0; i < kOB; i++)
+#pragma unroll
+                            for (int j = 0; j < kOB; j++) acc[i][j] = fmaf(cv[i], T[j], acc[i][j]);
+                    }
+                    if (!ok) break;
+                    const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
                     float* out = Hf + p1_lo * g.n3 + r;   // pair-major: coalesced over rows
+                    if (r < valid) {
+                        // pair (i, j) of this row lives at out + (i*o2 + j) * rows
+                        const size_t step = (size_t)g.rows;
+                        float* q = out;
 #pragma unroll
-                    for (int i = 0; i < kOB; i++)
+                        for (int i = 0; i < kOB; i++) {
+                            if (i < g.o0) {
 #pragma unroll
-                        for (int j = 0; j < kOB; j++)
-                            if (i < g.o0 && j < g.o2) out[(long long)(i * g.o2 + j) * g.rows] = acc[i][j];
+                                for (int j = 0; j < kOB; j++)
+                                    if (j < g.o2) { *q = acc[i][j]; q += step; }
+                            }
+                        }
+                    }
+                } else {
+                    const unsigned accbase = lanebase + 256u;
+                    const int nchunk = (g.o0 + 3) >> 2;
+                    for (int p0 = 0; p0 < g.n0; p0++, gS++) {
+                        const int s = gS % NS;
+                        if (!(ok = mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, P.status, 18))) break;
+                        tc_fence_after();
+                        float T[16];
+                        tmem_ld16(lanebase + (unsigned)(s * kNT), T);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
+                        const float* cp = cx + p0 * kOBig;
+#pragma unroll 1
+                        for (int ic = 0; ic < nchunk; ic++) {
+                            unsigned a[4][16];
+                            if (p0 > 0) {
+#pragma unroll
+                                for (int u = 0; u < 4; u++) tmem_ld16_nowait(accbase + (unsigned)((ic * 4 + u) * 16), a[u]);
+                                tmem_wait_ld();
+                            } else {
+#pragma unroll
+                                for (int u = 0; u < 4; u++)
+#pragma unroll
+                                    for (int j = 0; j < 16; j++) a[u][j] = 0u;
+                            }
+                            const float4 c4 = *reinterpret_cast<const float4*>(cp + ic * 4);
+                            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                            for (int u = 0; u < 4; u++)
+#pragma unroll
+                                for (int j = 0; j < 16; j++)
+                                    a[u][j] = __float_as_uint(fmaf(cv[u], T[j], __uint_as_float(a[u][j])));
+#pragma unroll
+                            for (int u = 0; u < 4; u++) tmem_st16(accbase + (unsigned)((ic * 4 + u) * 16), a[u]);
+                        }
+                        tmem_wait_st();   // this p0's updates land before the next one reads them
+                    }
+                    if (!ok) break;
+                    const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
+                    float* out = Hf + p1_lo * g.n3 + r;
+                    const size_t step = (size_t)g.rows;
+                    float* q = out;
+                    for (int i = 0; i < g.o0; i++) {
+                        float v[16];
+                        tmem_ld16(accbase + (unsigned)(i * 16), v);
+#pragma unroll
+                        for (int j = 0; j < 16; j++)
+                            if (j < g.o2) {
+                                if (r < valid) *q = v[j];
+                                q += step;
+                            }
+                    }
                 }
             }
             mbar_arrive(&sh->cx_empty[par]);
@@ -1002,19 +1092,28 @@ int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
     const int n1 = f ? d.nY : d.nX, n3 = f ? d.nX : d.nY;
     const int p1t = 128 / n3;
     const int tiles = (n1 + p1t - 1) / p1t;
-    const int mmax = variant == 1 ? 1 : std::max(1, std::min(8, kAccCols / d.npad));
+    const int mmax = variant >= 1 ? 1 : std::max(1, std::min(8, kAccCols / d.npad));
     *mts_max = mmax;
     return (tiles + mmax - 1) / mmax;
 }
 
+// 1: rank kernel, register accumulators (occupations <= 8); 2: rank kernel,
+// TMEM accumulators (<= 16); 0: Kronecker kernel (anything else the
+// tensor-core forms accept).  MCPT_TC_KERNEL=kron|rank|rankbig forces a
+// kernel where the sizes allow it.
 int choose_variant(const DimerDesc* h, int nd)
 {
+    int omax = 0, nymax = 0;
+    for (int k = 0; k < nd; k++) {
+        omax = std::max(omax, std::max(h[k].oX, h[k].oY));
+        nymax = std::max(nymax, h[k].nY);
+    }
+    const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
     const char* env = getenv("MCPT_TC_KERNEL");
     if (env && !strcmp(env, "kron")) return 0;
-    bool small = true;
-    for (int k = 0; k < nd; k++) small = small && h[k].oX <= kOB && h[k].oY <= kOB && h[k].nY <= kKCMax * kKC;
-    if (env && !strcmp(env, "rank") && small) return 1;
-    return small ? 1 : 0;
+    if (env && !strcmp(env, "rankbig") && fits_rank) return 2;
+    if (!fits_rank) return 0;
+    return omax <= kOB ? 1 : 2;
 }
 
 }  // namespace
@@ -1119,7 +1218,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     int kcs_max = 1;
     for (int k = 0; k < nd; k++) kcs_max = std::max(kcs_max, (h_desc[k].nY + kKC - 1) / kKC);
     P.kcs_max = kcs_max;
-    const size_t fixed = variant == 1
+    const size_t fixed = variant >= 1
         ? 1024 + 2 * (size_t)kABytes + 2 * (size_t)kcs_max * 2 * kNT * 128 + 2 * (size_t)kCxFloats * 4 +
               sizeof(RankShared)
         : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)P.w_stage_bytes + sizeof(TcShared);
@@ -1152,11 +1251,12 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.kind = L.kind;
     P.kcs_max = L.kcs_max;
     void (*fn)(const TcParams);
-    if (L.variant == 1) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32> : k_half_tc_rank<TC_BF16X3>;
+    if (L.variant == 1) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32, false> : k_half_tc_rank<TC_BF16X3, false>;
+    else if (L.variant == 2) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32, true> : k_half_tc_rank<TC_BF16X3, true>;
     else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    fn<<<L.grid, L.variant == 1 ? kRankThreads : kThreadsTc, L.smem, s>>>(P);
+    fn<<<L.grid, L.variant >= 1 ? kRankThreads : kThreadsTc, L.smem, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -191,6 +191,21 @@ def eri_blocks(B, nX: int, s: float):
     return np.ascontiguousarray(s * A), np.ascontiguousarray(s * K)
 
 
+def eri_blocks_direct(B, nX: int, s: float):
+    """The same two blocks straight from factor products, for dimers too large
+    for the packed-pair route (equal to ``eri_blocks`` up to FP64 rounding;
+    not bitwise 8-fold symmetric)."""
+    naux, n, _ = B.shape
+    nY = n - nX
+    bxx = B[:, :nX, :nX].reshape(naux, -1)
+    byy = B[:, nX:, nX:].reshape(naux, -1)
+    bxy = B[:, :nX, nX:].reshape(naux, -1)
+    byx = B[:, nX:, :nX].reshape(naux, -1)
+    A = (s * (bxx.T @ byy)).reshape(nX, nX, nY, nY)
+    K = (s * (bxy.T @ byx)).reshape(nX, nY, nY, nX)
+    return np.ascontiguousarray(A), np.ascontiguousarray(K)
+
+
 def extract_blocks(G, nX: int):
     """A and K blocks cut out of a full tensor (layout conversion only)."""
     A = G[:nX, :nX, nX:, nX:]

@@ -307,7 +307,7 @@ def test_uneven_sizes_batch(prec):
         assert abs(pd[k, 1] - E[k, 1]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
 
 
-@pytest.mark.parametrize("variant", ["rank", "kron"])
+@pytest.mark.parametrize("variant", ["rank", "rankbig", "kron"])
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
 def test_tensor_core_kernel_variants(lat8, prec, variant, monkeypatch):
     """Both tcgen05 kernels (forced through MCPT_TC_KERNEL) against the oracle.
@@ -323,3 +323,35 @@ def test_tensor_core_kernel_variants(lat8, prec, variant, monkeypatch):
     assert abs(tot[0] - E[:, 0].sum()) <= LATTICE[prec]
     pos = float(np.mean(rel > 0))
     print(f"{prec}/{variant}: fraction of dimers with positive error {pos:.2f}")
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_uneven_large_occupations(prec):
+    """Dimers of 56-96 AO (occupations 9-16) from the uneven workload: the
+    tensor-core forms take the rank kernel with TMEM accumulators, the second
+    half the general (n > 32) path; one launch covers the mixed sizes."""
+    w = synth.workload("uneven-4096")
+    ds = [k for k in range(400) if 56 <= w.nao[2 * k] <= 80 and 56 <= w.nao[2 * k + 1] <= 80][:3]
+    assert len(ds) == 3
+    items, blocks = [], {}
+    for d in ds:
+        X, Y = w.pairs[d]
+        mX, mY = w.monomer(X), w.monomer(Y)
+        B = w.factors(d)
+        blocks[d] = synth.eri_blocks_direct(B, w.nao[X], synth.scale_for_distance(w.R[d]))
+        items.append((*blocks[d], mX.C, mX.eps, mY.C, mY.eps, mX.nocc, mY.nocc))
+    E = oracle.dimers_parallel(items)
+    with M.Context(precision=prec) as ctx:
+        for k, d in enumerate(ds):
+            X, Y = w.pairs[d]
+            mX, mY = w.monomer(X), w.monomer(Y)
+            ctx.add_monomer(mX.C, mX.eps, mX.nocc)
+            ctx.add_monomer(mY.C, mY.eps, mY.nocc)
+            A, K = blocks[d]
+            ctx.add_dimer(2 * k, 2 * k + 1, np.concatenate([A.ravel(), K.ravel()]))
+        ctx.run()
+        pd = ctx.energies()[2]
+    for k in range(len(ds)):
+        print(prec, ds[k], w.nao[2 * ds[k]], w.nao[2 * ds[k] + 1], pd[k], E[k])
+        assert abs(pd[k, 0] - E[k, 0]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
+        assert abs(pd[k, 1] - E[k, 1]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
