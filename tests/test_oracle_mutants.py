@@ -1,0 +1,107 @@
+"""Planted mistakes in the oracle must be caught by its pins (CPU only).
+
+Each mutant is a copy of oracle/oracle.c with one plausible mistake -- a
+wrong index or axis, a transposed operand, a dropped term, a wrong factor or
+sign -- compiled in a temporary directory and loaded in a subprocess, where
+a compact set of the pins runs against it.  The unmodified source passes all
+of them.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "virtual index starts at 0": (
+        "CX, nX, oX, nX - oX,    /* nu  -> a */\n                      CY, nY, 0, oY,          /* lam -> j */",
+        "CX, nX, 0, nX - oX,     /* nu  -> a */\n                      CY, nY, 0, oY,          /* lam -> j */"),
+    "exchange axes swapped": (
+        "CY, nY, oY, nY - oY,    /* lam -> b */\n                      CY, nY, 0, oY,          /* sig -> j */",
+        "CY, nY, 0, oY,          /* lam -> b */\n                      CY, nY, oY, nY - oY,    /* sig -> j */"),
+    "factor 4 -> 2": ("ej += 4.0 * v * v * D;", "ej += 2.0 * v * v * D;"),
+    "denominator sign": ("1.0 / (epsX[i] + epsY[j] - epsX[oX + a] - epsY[oY + b])",
+                         "1.0 / (epsX[i] - epsY[j] - epsX[oX + a] - epsY[oY + b])"),
+    "exchange integral dropped": ("ek += -2.0 * v * w * D;", "ek += -2.0 * v * v * D;"),
+    "brute force lam/sig swapped": ("CY[la * nY + j] * CY[si * nY + oY + b]", "CY[si * nY + j] * CY[la * nY + oY + b]"),
+    "compensation dropped": ("    return s + c;\n}", "    return s;\n}"),
+    "whole term to each monomer": ("double v = 0.5 * E2[2 * d + f];", "double v = E2[2 * d + f];"),
+}
+
+CHECKS = r'''
+import sys, numpy as np
+sys.path.insert(0, ROOT)
+import oracle, synth
+oracle._SRC, oracle._LIB, oracle._lib = SRCFILE, LIBFILE, None
+fails = []
+def check(name, ok):
+    if not ok: fails.append(name)
+rng = np.random.default_rng(2)
+nX, nY, oX, oY = 5, 4, 2, 1
+A = rng.standard_normal((nX, nX, nY, nY)); K = rng.standard_normal((nX, nY, nY, nX))
+CX = rng.standard_normal((nX, nX)); CY = rng.standard_normal((nY, nY))
+V, Vb = oracle.transform_J(A, CX, CY, oX, oY), oracle.bruteforce_J(A, CX, CY, oX, oY)
+W, Wb = oracle.transform_K(K, CX, CY, oX, oY), oracle.bruteforce_K(K, CX, CY, oX, oY)
+Ve = np.einsum("mnls,mi,na,lj,sb->iajb", A, CX[:, :oX], CX[:, oX:], CY[:, :oY], CY[:, oY:])
+check("bruteforce J", np.abs(V - Vb).max() <= 1e-13 * np.abs(Vb).max())
+check("bruteforce K", np.abs(W - Wb).max() <= 1e-13 * np.abs(Wb).max())
+check("einsum J", np.abs(Vb - Ve).max() <= 1e-12 * np.abs(Ve).max())
+# hand-derived 2+2 dimer
+CXh = np.array([[0.6, -0.8], [0.8, 0.6]]); CYh = np.eye(2)
+Ah = np.full((2, 2, 2, 2), 100.0); Ah[:, :, 0, 1] = [[1, 2], [3, 4]]
+Kh = np.full((2, 2, 2, 2), -50.0); Kh[:, 1, 0, :] = [[2, 0], [1, -1]]
+EJ, EK = oracle.dimer(Ah, Kh, CXh, np.array([-1.0, 2.0]), CYh, np.array([-0.5, 1.5]), 1, 1)
+check("hand E_J", abs(EJ + 0.04608) < 1e-14)
+check("hand E_K", abs(EK + 0.19968) < 1e-14)
+# rank-1 closed form
+z = rng.standard_normal(13); B = np.outer(z, z)[None]
+mX, mY = synth.monomer(10, 7, 2), synth.monomer(11, 6, 2)
+s = 0.3
+Ar, Kr = synth.eri_blocks(B, 7, s)
+EJ, EK = oracle.dimer(Ar, Kr, mX.C, mX.eps, mY.C, mY.eps, 2, 2)
+xi, yj = mX.C.T @ z[:7], mY.C.T @ z[7:]
+ref = sum(4 * s * s * xi[i] ** 2 * xi[a] ** 2 * yj[j] ** 2 * yj[b] ** 2 /
+          (mX.eps[i] + mY.eps[j] - mX.eps[a] - mY.eps[b])
+          for i in range(2) for a in range(2, 7) for j in range(2) for b in range(2, 6))
+check("rank-1 E_J", abs(EJ - ref) <= 1e-13 * abs(ref))
+check("rank-1 E_K", abs(EK + 0.5 * EJ) <= 1e-13 * abs(EJ))
+# accumulation
+E2 = np.array([[1e16, 1.0], [1.0, 2.0], [-1e16, 3.0], [1.0, 4.0]])
+mon, tot = oracle.accumulate(E2, np.array([0, 0, 1, 2]), np.array([1, 2, 2, 3]), 4)
+check("Neumaier total", tot[0] == 2.0)
+check("split conserves total", mon[:, 1].sum() == tot[1])
+print("FAILS:" + ",".join(fails))
+'''
+
+
+def _run_checks(src_text):
+    with tempfile.TemporaryDirectory() as tmp:
+        src = os.path.join(tmp, "oracle.c")
+        lib = os.path.join(tmp, "liboracle.so")
+        with open(src, "w") as f:
+            f.write(src_text)
+        code = f"ROOT = {ROOT!r}\nSRCFILE = {src!r}\nLIBFILE = {lib!r}\n" + CHECKS
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+        if r.returncode != 0:
+            return None, r.stderr[-500:]   # a crash also counts as caught
+        line = [l for l in r.stdout.splitlines() if l.startswith("FAILS:")][0]
+        fails = [x for x in line[len("FAILS:"):].split(",") if x]
+        return fails, ""
+
+
+def test_unmodified_oracle_passes_every_check():
+    fails, err = _run_checks(open(SRC).read())
+    assert fails == [], (fails, err)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for '{name}' not found exactly once"
+    fails, err = _run_checks(text.replace(old, new))
+    assert fails is None or len(fails) > 0, f"mutant '{name}' passed every pin"
