@@ -288,6 +288,24 @@ def our_arm(args, ws, rank, local):
                             "max_dimer_K": float(np.max(np.abs(pd[:, 1] - Eo[:, 1]))),
                             "reference": "FP64 oracle, stored per-dimer values"}
 
+    # ---- the same runs replayed as a captured CUDA graph (the library's default
+    # when per-phase timing is off); reported beside the eagerly timed value
+    gctx = make_ctx(args.precision, False)
+    for _ in range(args.warmup):
+        gctx.run()
+    gctx.energies()
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        g0.record(stream)
+        for _ in range(args.steps):
+            gctx.run()
+        g1.record(stream)
+    torch.cuda.synchronize()
+    gms = g0.elapsed_time(g1) / args.steps
+    line["graph"] = {"value": w.n_dimers / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms}
+    gctx.close()
+
     if not args.no_extras and rank == 0:
         # ---- the plain FP64 GPU form on the same resident inputs
         if args.precision != "fp64":

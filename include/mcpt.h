@@ -78,9 +78,13 @@ typedef struct {
     const char *tune_cache;   /* path of the tile-choice cache, or NULL for none */
     int timing;               /* 1: record CUDA events per phase of mcpt_run (see mcpt_run_stats) */
     size_t mem_cap_bytes;     /* cap on library-owned device memory (0 = no cap) */
+    int graphs;               /* 1: with timing = 0, replay each run as a CUDA graph captured on the
+                                 first run of a plan (the plan = dimer set, range and precision);
+                                 runs on a stream that is itself being captured are launched directly */
 } mcpt_options;
 
-/* Defaults: device 0, own stream, MCPT_FP64, validate 1, 1 GiB waves, no cache, no timing. */
+/* Defaults: device 0, own stream, MCPT_FP64, validate 1, 1 GiB waves, no cache, no timing,
+ * graphs 1, no memory cap. */
 void mcpt_default_options(mcpt_options *opt);
 
 /* Create a handle.  opt may be NULL (defaults).  *out is NULL on failure.

@@ -40,7 +40,7 @@ class McptError(RuntimeError):
 class mcpt_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("validate", ctypes.c_int), ("wave_bytes", ctypes.c_size_t), ("tune_cache", ctypes.c_char_p),
-                ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t)]
+                ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int)]
 
 
 class mcpt_run_stats(ctypes.Structure):
@@ -184,7 +184,7 @@ class Context:
     ``torch.cuda.current_stream().cuda_stream``) or None for a library stream."""
 
     def __init__(self, precision="fp64", device=0, stream=None, validate=True, wave_bytes=0, timing=False,
-                 mem_cap_bytes=0):
+                 mem_cap_bytes=0, graphs=True):
         o = mcpt_default_options()
         o.device = device
         o.stream = stream
@@ -193,6 +193,7 @@ class Context:
         o.wave_bytes = wave_bytes
         o.timing = int(bool(timing))
         o.mem_cap_bytes = mem_cap_bytes
+        o.graphs = int(bool(graphs))
         self.h = mcpt_create(o)
 
     def add_monomer(self, C, eps, nocc):

@@ -54,6 +54,7 @@ struct mcpt_ctx {
     size_t wave_bytes = (size_t)1 << 30;
     std::string tune_cache;
     int timing = 0;
+    int graphs = 1;
     size_t mem_cap = 0;
     size_t mem_used = 0;
 
@@ -98,6 +99,8 @@ struct mcpt_ctx {
         int first = 0, count = 0;
         std::vector<Wave> waves;
         double alg_bytes = 0, alg_flops = 0, alg_flops_half = 0;
+        cudaGraphExec_t graph = nullptr;   // the plan's launch sequence, captured on first use
+        int graph_launches = 0;
     } plan;
     RunEvents rev;
     mcpt_run_stats stats{};
@@ -253,6 +256,7 @@ void mcpt_default_options(mcpt_options* o)
     o->tune_cache = nullptr;
     o->timing = 0;
     o->mem_cap_bytes = 0;
+    o->graphs = 1;
 }
 
 mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
@@ -289,6 +293,7 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     h->wave_bytes = o.wave_bytes ? o.wave_bytes : ((size_t)1 << 30);
     h->tune_cache = o.tune_cache ? o.tune_cache : "";
     h->timing = o.timing;
+    h->graphs = o.graphs;
     h->mem_cap = o.mem_cap_bytes;
     if (o.stream) {
         h->stream = static_cast<cudaStream_t>(o.stream);
@@ -511,6 +516,10 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
     auto& P = h->plan;
     P.valid = false;
     P.waves.clear();
+    if (P.graph) {
+        cudaGraphExecDestroy(P.graph);
+        P.graph = nullptr;
+    }
 
     h->hDesc.resize(count);
     std::vector<std::pair<int, int>> waves;   // [begin, end) into hDesc
@@ -603,37 +612,19 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
     return MCPT_OK;
 }
 
-static mcpt_status run_impl(mcpt_handle h, int first, int count)
+// The launch sequence of one run of the current plan on the handle's stream
+// (no host synchronisation, no allocation): status reset, then per wave the
+// first half and the second half, then the per-monomer reduction.  With `ev`
+// (timing), CUDA events are recorded around the phases.
+static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev, int* launches_out)
 {
-    CK(h, cudaSetDevice(h->device));
-    auto& P = h->plan;
-    if (!P.valid || P.first != first || P.count != count || P.prec != h->prec) {
-        mcpt_status st = build_plan(h, first, count);
-        if (st) return st;
-    }
+    const auto& P = h->plan;
     const int D = (int)h->dims.size();
     const int N = (int)h->mons.size();
     const mcpt_precision prec = h->prec;
-    CK(h, cudaMemsetAsync(h->dFlag + 1, 0, sizeof(int), h->stream));
-
-    RunEvents& re = h->rev;
     const size_t W = P.waves.size();
-    const size_t nev = 2 + 2 * W;
-    std::vector<cudaEvent_t> ev;
-    if (h->timing) {
-        while (ev.size() < nev) {
-            if (!re.pool.empty()) {
-                ev.push_back(re.pool.back());
-                re.pool.pop_back();
-            } else {
-                cudaEvent_t e;
-                CK(h, cudaEventCreate(&e));
-                ev.push_back(e);
-            }
-        }
-        CK(h, cudaEventRecord(ev[0], h->stream));
-    }
-
+    CK(h, cudaMemsetAsync(h->dFlag + 1, 0, sizeof(int), h->stream));
+    if (ev) CK(h, cudaEventRecord((*ev)[0], h->stream));
     int launches = 0;
     for (size_t w = 0; w < W; w++) {
         const auto& wv = P.waves[w];
@@ -651,7 +642,7 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
             break;
         }
         launches++;
-        if (h->timing) CK(h, cudaEventRecord(ev[1 + 2 * w], h->stream));
+        if (ev) CK(h, cudaEventRecord((*ev)[1 + 2 * w], h->stream));
         if (prec == MCPT_FP64)
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
                                      h->stream));
@@ -659,14 +650,66 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
             CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dCf, h->dE, static_cast<const float*>(h->dH), h->dE2,
                                      h->stream));
         launches++;
-        if (h->timing) CK(h, cudaEventRecord(ev[2 + 2 * w], h->stream));
+        if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
     }
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
     CK(h, launch_reduce(h->dE2, D, L, h->dMon, h->dTot, h->stream));
     launches++;
+    if (ev) CK(h, cudaEventRecord((*ev)[2 * W + 1], h->stream));
+    *launches_out = launches;
+    return MCPT_OK;
+}
+
+static mcpt_status run_impl(mcpt_handle h, int first, int count)
+{
+    CK(h, cudaSetDevice(h->device));
+    auto& P = h->plan;
+    if (!P.valid || P.first != first || P.count != count || P.prec != h->prec) {
+        mcpt_status st = build_plan(h, first, count);
+        if (st) return st;
+    }
+    RunEvents& re = h->rev;
+    const size_t W = P.waves.size();
+    int launches = 0;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(h, cudaStreamIsCapturing(h->stream, &cap));
     if (h->timing) {
-        CK(h, cudaEventRecord(ev[nev - 1], h->stream));
+        std::vector<cudaEvent_t> ev;
+        while (ev.size() < 2 + 2 * W) {
+            if (!re.pool.empty()) {
+                ev.push_back(re.pool.back());
+                re.pool.pop_back();
+            } else {
+                cudaEvent_t e;
+                CK(h, cudaEventCreate(&e));
+                ev.push_back(e);
+            }
+        }
+        mcpt_status st = enqueue_run(h, &ev, &launches);
         re.pending.push_back(std::move(ev));
+        if (st) return st;
+    } else if (h->graphs && cap == cudaStreamCaptureStatusNone) {
+        // replay the plan's launches as one CUDA graph (captured on first use)
+        if (!P.graph) {
+            CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+            mcpt_status st = enqueue_run(h, nullptr, &launches);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+            if (st) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            CK(h, e);
+            e = cudaGraphInstantiate(&P.graph, g, 0);
+            cudaGraphDestroy(g);
+            CK(h, e);
+            P.graph_launches = launches;
+        }
+        CK(h, cudaGraphLaunch(P.graph, h->stream));
+        launches = P.graph_launches;
+    } else {
+        mcpt_status st = enqueue_run(h, nullptr, &launches);
+        if (st) return st;
     }
 
     for (int k = 0; k < count; k++) h->dims[first + k].computed = true;
@@ -762,6 +805,7 @@ void mcpt_destroy(mcpt_handle h)
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->plan.graph) cudaGraphExecDestroy(h->plan.graph);
     for (void* p : h->owned) cudaFree(p);
     cudaFree(h->dC);
     cudaFree(h->dCf);

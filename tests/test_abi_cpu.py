@@ -61,3 +61,4 @@ def test_default_options(libpath):
     import paper_1409_2700_gb300 as M
     o = M.mcpt_default_options()
     assert o.precision == M.MCPT_FP64 and o.validate == 1 and o.wave_bytes == 1 << 30 and o.stream is None
+    assert o.graphs == 1 and o.timing == 0 and o.mem_cap_bytes == 0

@@ -355,3 +355,24 @@ def test_uneven_large_occupations(prec):
         print(prec, ds[k], w.nao[2 * ds[k]], w.nao[2 * ds[k] + 1], pd[k], E[k])
         assert abs(pd[k, 0] - E[k, 0]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
         assert abs(pd[k, 1] - E[k, 1]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_graph_replay_matches_eager(lat8, prec):
+    """Runs replayed as a captured CUDA graph give bitwise the eager results,
+    replay after replay."""
+    w, mons, blocks, E = lat8
+    out = {}
+    for graphs in (False, True):
+        with M.Context(precision=prec, graphs=graphs) as ctx:
+            load_context(ctx, w, mons, blocks, range(w.n_dimers))
+            res = []
+            for _ in range(3):
+                ctx.run()
+                res.append(ctx.energies())
+            for r in res[1:]:
+                for x, y in zip(res[0], r):
+                    assert np.array_equal(x, y)
+            out[graphs] = res[0]
+    for x, y in zip(out[False], out[True]):
+        assert np.array_equal(x, y)
