@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=192, help="dimers in the oracle's timed sample")
     p.add_argument("--no-extras", action="store_true", help="skip e2e, CPU baseline and the FP64 comparison")
+    p.add_argument("--max-dimers", type=int, default=0,
+                   help="keep only the first N dimers of the workload (smaller cases for profiling)")
     return p.parse_args()
 
 
@@ -162,7 +164,14 @@ def reference_arm(args, ws, rank):
     w = synth.workload(args.workload)
     oracle.build()
     ds = sample_dimers(w, min(args.cpu_sample, 96))   # host generation of the sample stays bounded
-    items = host_sample(w, ds)
+    keep, nbytes = [], 0
+    for d in ds:                                      # and so does its host memory (4 GB)
+        X, Y = w.pairs[d]
+        nbytes += 16 * w.nao[X] ** 2 * w.nao[Y] ** 2
+        if keep and nbytes > (4 << 30):
+            break
+        keep.append(d)
+    items = host_sample(w, keep)
     for _ in range(max(0, min(args.warmup, 1))):
         oracle.dimers_parallel(items[:8])
     times = []
@@ -196,6 +205,8 @@ def our_arm(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     w = synth.workload(args.workload)
+    if args.max_dimers:
+        w.pairs, w.R = w.pairs[:args.max_dimers], w.R[:args.max_dimers]
     # inputs: every dimer's [A | K] blocks resident in HBM (generation untimed)
     buf, offs = synth.device.workload_blocks(w)
     torch.cuda.synchronize()
@@ -278,7 +289,7 @@ def our_arm(args, ws, rank, local):
     sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
     try:
         import make_lattice_oracle as golden
-        g = golden.load(args.workload)
+        g = None if args.max_dimers else golden.load(args.workload)
     except Exception:
         g = None
     if g is not None:
@@ -391,11 +402,101 @@ def our_arm(args, ws, rank, local):
         print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ streamed workloads
+# Workloads whose integral blocks exceed device memory: every pass regenerates
+# each wave's blocks on the device (untimed) and runs the wave; the step time
+# is the device time of the waves' runs (CUDA events around each run).
+STREAMED = {"lattice-10x10x10-cheb2", "uneven-4096", "lattice-7x7x7-cheb1-ao128"}
+WAVE_BUDGET = 96 << 30
+
+
+def streamed_arm(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1409_2700_gb300 as M
+    import synth
+    import synth.device
+    from paper_1409_2700_gb300.stream import Streamed
+
+    torch.cuda.set_device(local)
+    w = synth.workload(args.workload)
+    stream = torch.cuda.Stream()
+    ctx = M.Context(precision=args.precision, device=local, stream=stream.cuda_stream, validate=False,
+                    timing=True, graphs=False)
+    for X in range(w.n_monomers):
+        m = w.monomer(X)
+        ctx.add_monomer(m.C, m.eps, m.nocc)
+    alg_bytes = float(sum(2 * 8 * w.nao[X] ** 2 * w.nao[Y] ** 2 for X, Y in w.pairs))
+    with torch.cuda.stream(stream):
+        st = Streamed(ctx, w.pairs, w.nao, WAVE_BUDGET)
+        synth.device.fill_views(w, st.views(0))
+        for _ in range(max(args.warmup, 3)):      # warm-up runs of the first wave
+            st.run(0)
+        stream.synchronize()
+        ctx.stats()
+        ev = []
+        t_gen = 0.0
+        with Clocks(local) as clk:
+            for _ in range(args.steps):
+                for k in range(len(st)):
+                    t0 = time.perf_counter()
+                    if not (args.steps == 1 and k == 0):
+                        synth.device.fill_views(w, st.views(k))
+                    stream.synchronize()
+                    t_gen += time.perf_counter() - t0
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st.run(k)
+                    e1.record(stream)
+                    ev.append((e0, e1))
+                stream.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    ms = max_over_ranks(ws, ms)
+    stt = ctx.stats()
+    mj, mk, pd, tot = ctx.energies()
+    ms_step = ms / args.steps
+    peaks, peak_kind = measured_peaks()
+    first_half_ms = stt.ms[0] / args.steps
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": None, "peak": 1.25, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": "k_half_fp64", "peak_kind": "nominal FP64 rate"}
+    else:
+        achieved = alg_bytes / (first_half_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3") else "k_half_fp32c",
+                "peak_kind": peak_kind, "note": "all first-half launches of a pass (one or more per wave)"}
+    line = {
+        "metric": METRIC, "value": ws * w.n_dimers / (ms_step * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": args.workload, "n_dimers": w.n_dimers, "n_monomers": w.n_monomers,
+                   "nao": sorted(set(w.nao)), "nocc": sorted(set(w.nocc)), "precision": args.precision,
+                   "inputs_gb": round(alg_bytes / 1e9, 1), "waves": len(st),
+                   "timed": "device time of the waves' runs; on-device generation of each wave untimed",
+                   "l2": "inputs larger than L2"},
+        "phase_ms_per_step": {"first_half": first_half_ms, "finish": stt.ms[1] / args.steps,
+                              "reduce": stt.ms[2] / args.steps},
+        "generation_s_per_step": t_gen / args.steps,
+        "roofline": roof,
+        "gpu_launches": stt.launches,
+        "clocks": clk.summary(),
+        "lattice_E": {"J": tot[0], "K": tot[1]},
+    }
+    del st
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init()
     if args.impl == "reference":
         reference_arm(args, ws, rank)
+    elif args.workload in STREAMED:
+        streamed_arm(args, ws, rank, local)
     else:
         our_arm(args, ws, rank, local)
     if ws > 1:

@@ -60,7 +60,9 @@ typedef enum {
 typedef enum {
     MCPT_FP64 = 0,    /* FP64 everywhere (CUDA-core DFMA) */
     MCPT_TF32 = 1,    /* AO integrals and C rounded to TF32 (round-to-nearest), tcgen05 MMA, FP32 accumulate */
-    MCPT_BF16X3 = 2,  /* hi/lo BF16 split of both operands, 3 tcgen05 MMAs per product, FP32 accumulate */
+    MCPT_BF16X3 = 2,  /* both operands as three BF16 digits of a fixed-point value relative to each
+                         vector's largest exponent (rank kernel, n_Y <= 96): 6 tcgen05 MMAs per step whose
+                         FP32 sums are exact integers; elsewhere a hi/lo BF16 split */
     MCPT_FP32C = 3    /* FP32 FMA with error-free TwoProduct/TwoSum compensation (Ogita-Rump-Oishi) */
 } mcpt_precision;
 
@@ -75,7 +77,9 @@ typedef struct {
     mcpt_precision precision; /* see above */
     int validate;             /* 1: reject non-finite C / eps / integrals (adds a pass over inputs) */
     size_t wave_bytes;        /* cap on per-run device scratch; dimers run in waves under it (0 = 1 GiB) */
-    const char *tune_cache;   /* path of the tile-choice cache, or NULL for none */
+    const char *tune_cache;   /* path of the autotuner's cache, or NULL: with a path, each tensor-core
+                                 wave's launch choices (kernel variant, staging depth, grid) are timed on
+                                 the first plan of its shape signature and kept in that text file */
     int timing;               /* 1: record CUDA events per phase of mcpt_run (see mcpt_run_stats) */
     size_t mem_cap_bytes;     /* cap on library-owned device memory (0 = no cap) */
     int graphs;               /* 1: with timing = 0, replay each run as a CUDA graph captured on the

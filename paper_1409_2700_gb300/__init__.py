@@ -184,8 +184,10 @@ class Context:
     ``torch.cuda.current_stream().cuda_stream``) or None for a library stream."""
 
     def __init__(self, precision="fp64", device=0, stream=None, validate=True, wave_bytes=0, timing=False,
-                 mem_cap_bytes=0, graphs=True):
+                 mem_cap_bytes=0, graphs=True, tune_cache=None):
         o = mcpt_default_options()
+        if tune_cache is not None:
+            o.tune_cache = os.fsencode(tune_cache)
         o.device = device
         o.stream = stream
         o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -194,6 +196,8 @@ class Context:
         o.timing = int(bool(timing))
         o.mem_cap_bytes = mem_cap_bytes
         o.graphs = int(bool(graphs))
+        self.validate = bool(validate)
+        self.stream = stream
         self.h = mcpt_create(o)
 
     def add_monomer(self, C, eps, nocc):

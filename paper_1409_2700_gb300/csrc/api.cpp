@@ -12,7 +12,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <set>
+#include <sstream>
 #include <string>
 #include <utility>
 #include <vector>
@@ -53,6 +56,8 @@ struct mcpt_ctx {
     int validate = 1;
     size_t wave_bytes = (size_t)1 << 30;
     std::string tune_cache;
+    bool tune_loaded = false;
+    std::map<std::string, TcTune> tuned;   // launch choices by wave signature
     int timing = 0;
     int graphs = 1;
     size_t mem_cap = 0;
@@ -78,6 +83,10 @@ struct mcpt_ctx {
     size_t capH = 0;
     void* dWork = nullptr;
     size_t capWork = 0;
+    void* dFin = nullptr;            // second-half tasks of waves above 32 AO (+ first-task indices)
+    size_t capFin = 0;
+    double* dPart = nullptr;         // their FP64 partial sums
+    size_t capPart = 0;
     double* dE2 = nullptr;
     size_t capE2 = 0;
     double* dMon = nullptr;
@@ -92,6 +101,9 @@ struct mcpt_ctx {
     struct Wave {
         int b, nd, max_rows, max_occ, max_ao;
         TcLaunch tc;
+        size_t fin_off;              // byte offset of the wave's tasks in dFin
+        int ntasks;                  // 0: one CTA per dimer (<= 32 AO)
+        size_t part_off;             // first partial (pairs of doubles) in dPart
     };
     struct Plan {
         bool valid = false;
@@ -508,6 +520,94 @@ static mcpt_status upload_static(mcpt_handle h)
 // Host work of a run that does not change between runs of the same dimer set:
 // descriptors, wave split under the scratch cap, scratch buffers, and (for
 // the tensor-core forms) tensor maps and ordered work items, all uploaded.
+// ------------------------------------------------------------------ autotuner
+// With options.tune_cache set, the launch choices of each tensor-core wave
+// (kernel variant, staging depth, grid) are measured once per wave signature
+// -- precision, device, and the multiset of dimer shapes (nX, nY, oX, oY) --
+// and kept as one text line per signature in that file:
+//   <key> <variant+1> <stages> <grid> <ms>
+// Later plans with the same signature reuse the line without timing.
+static std::string tune_key(mcpt_ctx* h, mcpt_precision prec, const DimerDesc* d, int nd)
+{
+    std::map<std::vector<int>, int> sig;
+    for (int k = 0; k < nd; k++) sig[{d[k].nX, d[k].nY, d[k].oX, d[k].oY}]++;
+    unsigned long long f = 1469598103934665603ull;        // FNV-1a over the signature
+    auto mix = [&](long long v) {
+        for (int b = 0; b < 8; b++) {
+            f ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+            f *= 1099511628211ull;
+        }
+    };
+    for (auto& kv : sig) {
+        for (int v : kv.first) mix(v);
+        mix(kv.second);
+    }
+    cudaDeviceProp prop;
+    std::string dev = "gpu";
+    if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess) dev = prop.name;
+    for (auto& c : dev)
+        if (c == ' ') c = '_';
+    char buf[160];
+    snprintf(buf, sizeof buf, "%s:%s:%d:%016llx", prec == MCPT_TF32 ? "tf32" : "bf16x3", dev.c_str(), nd, f);
+    return buf;
+}
+
+static void tune_load(mcpt_ctx* h)
+{
+    if (h->tune_loaded) return;
+    h->tune_loaded = true;
+    std::ifstream in(h->tune_cache);
+    std::string line;
+    while (std::getline(in, line)) {
+        std::istringstream ls(line);
+        std::string key;
+        TcTune t{};
+        double ms = 0;
+        if (ls >> key >> t.variant1 >> t.sf >> t.grid >> ms) h->tuned[key] = t;
+    }
+}
+
+// Time every candidate launch of wave `wv` on the handle's stream (one
+// warm-up launch, then three timed ones) and return the fastest.
+static mcpt_status tune_wave(mcpt_handle h, TcKind kind, const mcpt_ctx::Wave& wv, void* work, size_t work_bytes,
+                             TcTune* best, float* best_ms)
+{
+    TcTune cand[16];
+    const int n = tc_candidates(kind, h->hDesc.data() + wv.b, wv.nd, cand, 16);
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    *best_ms = 1e30f;
+    *best = TcTune{};
+    for (int c = 0; c < n; c++) {
+        TcLaunch L{};
+        char err[256] = {0};
+        if (tc_prepare(kind, h->hDesc.data() + wv.b, h->dDesc + wv.b, wv.nd, h->dCf, static_cast<float*>(h->dH),
+                       work, work_bytes, h->dFlag + 1, h->stream, &cand[c], &L, err, sizeof err) != cudaSuccess)
+            continue;
+        cudaError_t e = tc_launch(L, h->stream);
+        e = e ? e : cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; r++) e = tc_launch(L, h->stream);
+        e = e ? e : cudaEventRecord(e1, h->stream);
+        e = e ? e : cudaEventSynchronize(e1);
+        float ms = 0;
+        e = e ? e : cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(h, MCPT_ECUDA, "autotuner: %s", cudaGetErrorString(e));
+        }
+        if (ms < *best_ms) {
+            *best_ms = ms;
+            *best = cand[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(h, cudaMemsetAsync(h->dFlag + 1, 0, sizeof(int), h->stream));
+    return MCPT_OK;
+}
+
 static mcpt_status build_plan(mcpt_handle h, int first, int count)
 {
     const int D = (int)h->dims.size();
@@ -573,16 +673,51 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         size_t total = 0;
         for (auto& w : waves) {
             work_off.push_back(total);
-            total += (tc_work_bytes(h->hDesc.data() + w.first, w.second - w.first) + 255) & ~(size_t)255;
+            total += (tc_work_bytes(prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3, h->hDesc.data() + w.first, w.second - w.first) + 255) & ~(size_t)255;
         }
         if ((st = ensure(h, &h->dWork, &h->capWork, total))) return st;
     }
     CK(h, cudaMemcpyAsync(h->dDesc, h->hDesc.data(), count * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
 
+    // second-half tasks of the waves with monomers above 32 AO: [tasks][first-task index per dimer]
+    std::vector<unsigned char> fin_host;
+    std::vector<size_t> fin_off(waves.size(), 0), part_off(waves.size(), 0);
+    std::vector<int> ntasks(waves.size(), 0);
+    size_t parts = 0;
+    for (size_t w = 0; w < waves.size(); w++) {
+        const int b = waves[w].first, nd = waves[w].second - b;
+        int max_ao = 0;
+        for (int k = b; k < b + nd; k++) max_ao = std::max(max_ao, std::max(h->hDesc[k].nX, h->hDesc[k].nY));
+        if (max_ao <= 32) continue;
+        std::vector<FinTask> t;
+        finish_tasks(h->hDesc.data() + b, nd, 1 << 22, &t);
+        std::vector<int> first(nd);
+        for (size_t q = 0; q < t.size(); q++)
+            if (t[q].pr0 == 0) first[t[q].dimer] = (int)q;
+        fin_host.resize((fin_host.size() + 255) & ~(size_t)255);
+        fin_off[w] = fin_host.size();
+        const size_t tb = t.size() * sizeof(FinTask), fb = first.size() * sizeof(int);
+        fin_host.resize(fin_host.size() + tb + fb);
+        std::memcpy(fin_host.data() + fin_off[w], t.data(), tb);
+        std::memcpy(fin_host.data() + fin_off[w] + tb, first.data(), fb);
+        ntasks[w] = (int)t.size();
+        part_off[w] = parts;
+        parts += t.size();
+    }
+    if (!fin_host.empty()) {
+        if ((st = ensure(h, &h->dFin, &h->capFin, fin_host.size()))) return st;
+        if ((st = ensure(h, &h->dPart, &h->capPart, parts * 2 * sizeof(double)))) return st;
+        CK(h, cudaMemcpyAsync(h->dFin, fin_host.data(), fin_host.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));   // fin_host is pageable and goes out of scope
+    }
+
     for (size_t w = 0; w < waves.size(); w++) {
         mcpt_ctx::Wave wv{};
         wv.b = waves[w].first;
         wv.nd = waves[w].second - wv.b;
+        wv.fin_off = fin_off[w];
+        wv.ntasks = ntasks[w];
+        wv.part_off = part_off[w];
         for (int k = wv.b; k < wv.b + wv.nd; k++) {
             const DimerDesc& dd = h->hDesc[k];
             wv.max_rows = std::max(wv.max_rows, dd.nX * dd.nY);
@@ -592,10 +727,30 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         if (is_tensor_form(prec)) {
             char tcerr[256] = {0};
             const size_t end = (w + 1 < work_off.size()) ? work_off[w + 1] : h->capWork;
-            cudaError_t e = tc_prepare(prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3, h->hDesc.data() + wv.b,
-                                       h->dDesc + wv.b, wv.nd, h->dCf, static_cast<float*>(h->dH),
-                                       static_cast<char*>(h->dWork) + work_off[w], end - work_off[w], h->dFlag + 1,
-                                       h->stream, &wv.tc, tcerr, sizeof tcerr);
+            const TcKind kind = prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3;
+            void* work = static_cast<char*>(h->dWork) + work_off[w];
+            TcTune tune{};
+            bool tuned = false;
+            if (!h->tune_cache.empty()) {
+                tune_load(h);
+                const std::string key = tune_key(h, prec, h->hDesc.data() + wv.b, wv.nd);
+                auto it = h->tuned.find(key);
+                if (it != h->tuned.end()) {
+                    tune = it->second;
+                } else {
+                    float ms = 0;
+                    mcpt_status st2 = tune_wave(h, kind, wv, work, end - work_off[w], &tune, &ms);
+                    if (st2) return st2;
+                    h->tuned[key] = tune;
+                    std::ofstream out(h->tune_cache, std::ios::app);
+                    out << key << ' ' << tune.variant1 << ' ' << tune.sf << ' ' << tune.grid << ' ' << ms / 3
+                        << '\n';
+                }
+                tuned = tune.variant1 != 0;
+            }
+            cudaError_t e = tc_prepare(kind, h->hDesc.data() + wv.b, h->dDesc + wv.b, wv.nd, h->dCf,
+                                       static_cast<float*>(h->dH), work, end - work_off[w], h->dFlag + 1,
+                                       h->stream, tuned ? &tune : nullptr, &wv.tc, tcerr, sizeof tcerr);
             if (e != cudaSuccess)
                 return fail(h, MCPT_ECUDA, "tensor-core plan: %s (%s)", cudaGetErrorString(e), tcerr);
         }
@@ -643,13 +798,16 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
         }
         launches++;
         if (ev) CK(h, cudaEventRecord((*ev)[1 + 2 * w], h->stream));
+        const FinTask* tasks =
+            wv.ntasks ? reinterpret_cast<const FinTask*>(static_cast<const char*>(h->dFin) + wv.fin_off) : nullptr;
+        double* part = wv.ntasks ? h->dPart + 2 * wv.part_off : nullptr;
         if (prec == MCPT_FP64)
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
-                                     h->stream));
+                                     tasks, wv.ntasks, part, h->stream));
         else
             CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dCf, h->dE, static_cast<const float*>(h->dH), h->dE2,
-                                     h->stream));
-        launches++;
+                                     tasks, wv.ntasks, part, h->stream));
+        launches += wv.ntasks ? 2 : 1;
         if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
     }
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
@@ -813,6 +971,8 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dDesc);
     cudaFree(h->dH);
     cudaFree(h->dWork);
+    cudaFree(h->dFin);
+    cudaFree(h->dPart);
     cudaFree(h->dE2);
     cudaFree(h->dMon);
     cudaFree(h->dLists);

@@ -51,20 +51,31 @@ __device__ __forceinline__ double f64_from_f32(float f)
     return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
 }
 
-// 1/x in FP64 for |x| in a normal FP32 range: FP32 reciprocal seed (relative
-// error ~2^-23) and STEPS Newton-Raphson steps r <- r + r(1 - x r), each
-// squaring the error: one step leaves ~2^-46 (1.4e-14), two reach FP64
-// rounding.
-template <int STEPS>
-__device__ __forceinline__ double rcp_f64(double x)
+// FP32 reciprocal seed of an FP64 value, widened back to FP64: conversions on
+// the integer pipes, rcp.approx.ftz.f32 on the special-function unit.  For |x|
+// in a normal FP32 range its relative error is below 2^-22 (rounding x to
+// FP32 plus the approximate reciprocal).
+__device__ __forceinline__ double rcp_seed_f64(double x)
 {
-    double r = f64_from_f32(__frcp_rn(f32_from_f64(x)));
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(f32_from_f64(x)));
+    return f64_from_f32(r);
+}
+
+// v / x in FP64 by Newton-Raphson on the reciprocal, r <- r + r(1 - x r),
+// from the FP32 seed; each step squares the relative error.  The last step is
+// folded into the product: with e = 1 - x r, v/x ~= (v r) + (v r) e, so STEPS
+// steps cost 2 STEPS + 1 FP64 operations.  One step leaves ~2^-44 (6e-14),
+// two reach FP64 rounding.
+template <int STEPS>
+__device__ __forceinline__ double div_newton(double v, double x)
+{
+    double r = rcp_seed_f64(x);
 #pragma unroll
-    for (int k = 0; k < STEPS; k++) {
-        const double e = fma(-x, r, 1.0);
-        r = fma(r, e, r);
-    }
-    return r;
+    for (int k = 0; k + 1 < STEPS; k++) r = fma(r, fma(-x, r, 1.0), r);
+    const double e = fma(-x, r, 1.0);
+    const double t = v * r;
+    return fma(t, e, t);
 }
 
 }  // namespace mcpt

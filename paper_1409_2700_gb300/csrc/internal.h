@@ -17,6 +17,8 @@
 //       then D = 1/(e_i+e_j-e_a-e_b) and the two energy sums in FP64.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <stdint.h>
 
 namespace mcpt {
@@ -56,13 +58,27 @@ cudaError_t launch_half_fp64(const DimerDesc* d_desc, int nd, int max_rows, int 
 cudaError_t launch_half_fp32c(const DimerDesc* d_desc, int nd, int max_rows, int max_occ,
                               const float* Cf, float* H, cudaStream_t s);
 
+// Second half of monomers above 32 AO: one CTA per task = a range of one
+// dimer's occupied pairs; the tasks of a dimer are consecutive.
+struct FinTask {
+    int dimer;            // descriptor index within the wave
+    int pr0, pr1;         // pairs [pr0, pr1) (pair = i*oY + j)
+    int first;            // index of the dimer's first task
+    int ntasks;           // tasks of the dimer
+};
+// Split each dimer's pairs into tasks of about `pairs_per_task`.
+void finish_tasks(const DimerDesc* h_desc, int nd, int pairs_per_task, std::vector<FinTask>* out);
+
 // Second half + denominators + energies.  H is double (FP64 form) or float.
+// Waves whose monomers all have <= 32 AO run one CTA per dimer; larger ones
+// run the tasks (`tasks`, device array of `ntasks`) and sum each dimer's
+// task partials (`part`, 2 doubles per task) in task order.
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
                                const double* Cpool, const double* Epool, const double* H,
-                               double* E2, cudaStream_t s);
+                               double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s);
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
                                const float* Cf, const double* Epool, const float* H,
-                               double* E2, cudaStream_t s);
+                               double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s);
 
 // Per-monomer halves and the compensated lattice total.
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists,
@@ -101,13 +117,27 @@ struct TcLaunch {
     size_t smem;
 };
 
+// Launch choices of one tensor-core launch (0 in a field = the default):
+// kernel variant + 1 (1 Kronecker, 2 rank with register accumulators, 3 rank
+// with TMEM accumulators), FP64 staging depth, CTAs.
+struct TcTune {
+    int variant1;
+    int sf;
+    int grid;
+};
+
 // Bytes of device work space (tensor maps + items) the dimers need.
-size_t tc_work_bytes(const DimerDesc* h_desc, int nd);
+size_t tc_work_bytes(TcKind kind, const DimerDesc* h_desc, int nd);
+// The launch choices worth timing for these dimers (at most `max`): the
+// exact kernels that accept them (the Kronecker kernel only where no rank
+// kernel does), a few staging depths, and two grid sizes.
+int tc_candidates(TcKind kind, const DimerDesc* h_desc, int nd, TcTune* out, int max);
 // Encode tensor maps, order work items (longest first), upload them to
-// d_work, and fill *out.  Synchronous w.r.t. the host buffers.
+// d_work, and fill *out.  Synchronous w.r.t. the host buffers.  `tune`
+// (may be NULL) overrides the default launch choices.
 cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const float* Cf,
-                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s, TcLaunch* out,
-                       char* err, size_t errlen);
+                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s,
+                       const TcTune* tune, TcLaunch* out, char* err, size_t errlen);
 cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s);
 
 }  // namespace mcpt

@@ -9,20 +9,24 @@
 //   (i b|j a) = sum_lam C_Y[lam][b] sum_nu H_1[lam][nu] C_X[nu][a]
 // Then, in FP64 (Sec. II.C energy tensor, Eq. (ed2) with T = vD):
 //   D = 1/(e_i + e_j - e_a - e_b),  E_J += 4 (ia|jb)^2 D,  E_K += -2 (ia|jb)(ib|ja) D.
-// GB300's FP64 unit is small, so D is an FP32 reciprocal refined by Newton
-// steps in FP64 (convert.h) rather than a full FP64 division -- two for the
-// FP64 form (full FP64 accuracy), one for the mixed forms (relative error
-// ~1.4e-14, far below their transform error) -- and the FP32 -> FP64 widening
-// of the mixed forms' integrals runs on integer pipes.
-// One CTA owns one dimer, so the per-dimer energies come out of a fixed-order
-// block reduction: deterministic run to run, no atomics.
+// GB300's FP64 unit is small and bounds this kernel, so each term costs as
+// few FP64 operations as possible: v D comes from an FP32 reciprocal seed
+// refined by Newton steps in FP64 with the last step folded into the product
+// (convert.h) -- two steps for the FP64 form (full FP64 accuracy), one for the
+// mixed forms (relative error ~6e-14, far below their transform error) -- then
+// E_J and E_K take one FMA each, and the FP32 -> FP64 widening of the mixed
+// forms' integrals runs on integer pipes.
+// Monomers of at most 32 AO: one CTA per dimer, one warp per occupied pair.
+// Larger ones: register-tiled GEMMs, one CTA per range of a dimer's pairs,
+// the ranges' partial sums added per dimer in range order.  Every sum has a
+// fixed order: the energies are deterministic run to run, with no atomics.
 #include "internal.h"
 #include "convert.h"
 
+#include <algorithm>
+
 namespace mcpt {
 namespace {
-
-constexpr int kFinThreads = 256;
 
 __device__ __forceinline__ double warp_sum(double v)
 {
@@ -31,120 +35,59 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Newton steps of the denominator: full FP64 accuracy for the FP64 form.
+template <typename T> constexpr int kSteps = sizeof(T) == 8 ? 2 : 1;
+
 __device__ __forceinline__ double to_f64(double x) { return x; }
 __device__ __forceinline__ double to_f64(float x) { return f64_from_f32(x); }   // integer pipes
 
-// T: arithmetic type of the second half (double for the FP64 form, float for
-// the mixed forms) -- also the type of the coefficient pool C and of H.
-// Per occupied pair (i, j):
-//   TmA[nu][b] = sum_sig H0[nu][sig] C_Y[sig][b];   VA[a][b] = sum_nu C_X[nu][a] TmA[nu][b]
-//   TmK[lam][a] = sum_nu H1[lam][nu] C_X[nu][a];    VK[b][a] = sum_lam C_Y[lam][b] TmK[lam][a]
-// then one FP64 denominator per (a, b) feeds both energy sums.
+// ---------------------------------------------------------------------------
+// Monomers of at most 32 AO: one warp per occupied pair (i, j).
+//   lane b:  tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]         (C_Y column b in registers)
+//            VA[a][b] = sum_nu C_X[nu][a] tm[nu]              (C_X rows broadcast from smem)
+//   lane a:  tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
+//            VK[a][b] = sum_lam C_Y[lam][b] tk[lam]
+// Both land in shared memory as [a][b] tiles, and the FP64 part then walks the
+// v_X v_Y terms packed 32 to a warp instruction (no idle lanes when v is not a
+// multiple of 32; the FP64 pipe is the bound).  The H slices are contiguous
+// (pair-major), read with coalesced loads into a zero-padded 32 x 32 tile.
+// Per-lane sums reduce in a fixed order.
+constexpr int kW32Warps = 4;
+constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33)
+
 template <typename T>
-__global__ void __launch_bounds__(kFinThreads)
-k_finish(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
-         const T* __restrict__ H, double* __restrict__ E2)
+constexpr size_t w32_smem_bytes()
 {
-    const DimerDesc& d = dd[blockIdx.x];
-    const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
-    const int vX = nX - oX, vY = nY - oY;
-    const int rows = nX * nY, pairs = oX * oY;
-    const T* CX = C + d.cX;
-    const T* CY = C + d.cY;
-    const double* eX = Epool + d.eX;
-    const double* eY = Epool + d.eY;
-    const T* H0 = H + d.h_off;
-    const T* H1 = H + d.h_off + (long long)pairs * rows;
-
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* S = reinterpret_cast<T*>(smraw);                 // [rows]
-    T* Tm = S + rows;                                   // [max(nX*vY, nY*vX)]
-    T* VA = Tm + (nX * vY > nY * vX ? nX * vY : nY * vX);  // [vX][vY]
-
-    double ej = 0.0, ek = 0.0;
-    const int tid = threadIdx.x;
-    for (int i = 0; i < oX; i++) {
-        for (int j = 0; j < oY; j++) {
-            const int col = i * oY + j;
-            const double eij = eX[i] + eY[j];
-            // ---- (i a|j b) from H_0
-            for (int k = tid; k < rows; k += kFinThreads) S[k] = H0[(long long)col * rows + k];
-            __syncthreads();
-            for (int k = tid; k < nX * vY; k += kFinThreads) {
-                const int nu = k / vY, b = k % vY;
-                const T* s = S + nu * nY;
-                T acc = 0;
-                for (int sg = 0; sg < nY; sg++) acc = fma(s[sg], __ldg(CY + sg * nY + oY + b), acc);
-                Tm[k] = acc;
-            }
-            __syncthreads();
-            for (int k = tid; k < vX * vY; k += kFinThreads) {
-                const int a = k / vY, b = k % vY;
-                T acc = 0;
-                for (int nu = 0; nu < nX; nu++) acc = fma(__ldg(CX + nu * nX + oX + a), Tm[nu * vY + b], acc);
-                VA[k] = acc;
-            }
-            __syncthreads();
-            // ---- (i b|j a) from H_1
-            for (int k = tid; k < rows; k += kFinThreads) S[k] = H1[(long long)col * rows + k];
-            __syncthreads();
-            for (int k = tid; k < nY * vX; k += kFinThreads) {
-                const int lam = k / vX, a = k % vX;
-                const T* s = S + lam * nX;
-                T acc = 0;
-                for (int nu = 0; nu < nX; nu++) acc = fma(s[nu], __ldg(CX + nu * nX + oX + a), acc);
-                Tm[k] = acc;
-            }
-            __syncthreads();
-            // ---- energies: one denominator per (a, b)
-            for (int k = tid; k < vX * vY; k += kFinThreads) {
-                const int a = k / vY, b = k % vY;
-                T acc = 0;
-                for (int lam = 0; lam < nY; lam++) acc = fma(__ldg(CY + lam * nY + oY + b), Tm[lam * vX + a], acc);
-                const double va = to_f64(VA[k]);
-                const double vk = to_f64(acc);
-                const double D = rcp_f64<sizeof(T) == 8 ? 2 : 1>(eij - (eX[oX + a] + eY[oY + b]));
-                ej = fma(va * va, D, ej);
-                ek = fma(va * vk, D, ek);
-            }
-            __syncthreads();
-        }
-    }
-    // fixed-order block reduction
-    __shared__ double red[2][kFinThreads / 32];
-    ej = warp_sum(ej);
-    ek = warp_sum(ek);
-    if ((tid & 31) == 0) { red[0][tid >> 5] = ej; red[1][tid >> 5] = ek; }
-    __syncthreads();
-    if (tid == 0) {
-        double sj = 0.0, sk = 0.0;
-        for (int w = 0; w < kFinThreads / 32; w++) { sj += red[0][w]; sk += red[1][w]; }
-        E2[2 * d.slot + 0] = 4.0 * sj;
-        E2[2 * d.slot + 1] = -2.0 * sk;
-    }
+    return 32 * 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
 }
 
-// ---------------------------------------------------------------------------
-// Monomers of at most 32 AO: one warp per occupied pair (i, j), one lane per
-// virtual orbital.  For pair (i, j):
-//   lane b:  tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]        (C_Y column b in registers)
-//            VA[a][b] = sum_nu C_X[nu][a] tm[nu]             (C_X rows broadcast from smem)
-//   lane a:  tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
-//            VK[b][a] = sum_lam C_Y[lam][b] tk[lam], and with VA[a][b] (transposed
-//            through smem) and D from the precomputed e_a + e_b the two FP64 sums.
-// The H slices are contiguous (pair-major), read with coalesced loads into a
-// zero-padded 32 x 32 tile.  Per-lane sums reduce in a fixed order.
-constexpr int kW32Warps = 4;
+// One warp copies an nr x nc (<= 32 x 32) row-major slice into a zero-padded
+// 32 x 32 tile: lane c loads column c of every row, all 32 loads issued before
+// the first store, so the slice costs one memory round trip, not 32.
+template <typename T>
+__device__ __forceinline__ void load_slice(T* S, const T* __restrict__ h, int nr, int nc, int lane)
+{
+    T v[32];
+    const T* p = h + lane;                  // one running address, not 32
+    const bool col = lane < nc;
+#pragma unroll
+    for (int r = 0; r < 32; r++) {
+        v[r] = (r < nr && col) ? *p : T(0);
+        p += nc;
+    }
+#pragma unroll
+    for (int r = 0; r < 32; r++) S[r * 32 + lane] = v[r];
+}
 
 template <typename T>
-__global__ void __launch_bounds__(kW32Warps * 32)
+__global__ void __launch_bounds__(kW32Warps * 32, 4)
 k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
              const T* __restrict__ H, double* __restrict__ E2)
 {
     const DimerDesc& d = dd[blockIdx.x];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
     const int vX = nX - oX, vY = nY - oY;
-    const int rows = nX * nY, pairs = oX * oY;
+    const int rows = nX * nY, pairs = oX * oY, nab = vX * vY;
     const T* CX = C + d.cX;
     const T* CY = C + d.cY;
     const double* eX = Epool + d.eX;
@@ -153,31 +96,44 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     const T* H1 = H + d.h_off + (long long)pairs * rows;
 
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* eab = reinterpret_cast<double*>(smraw);          // [32][32]: e_a + e_b
+    double* eab = reinterpret_cast<double*>(smraw);          // [a][b] (stride 32): e_a + e_b
     T* CXT = reinterpret_cast<T*>(eab + 32 * 32);             // [a][nu], zero padded
     T* CYT = CXT + 32 * 32;                                   // [b][sig]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* S = CYT + 32 * 32 + warp * (32 * 32 + 32 * 33);        // [32][32] integral slice
-    T* VAs = S + 32 * 32;                                     // [a][b], stride 33
+    T* S = CYT + 32 * 32 + warp * (2 * kW32Slab);             // integral slice [32][32], then VK [a][b]
+    T* VA = S + kW32Slab;                                     // [a][b], stride 33
 
-    for (int k = threadIdx.x; k < 32 * 32; k += kW32Warps * 32) {
-        const int a = k >> 5, m = k & 31;
-        CXT[k] = (a < vX && m < nX) ? CX[m * nX + oX + a] : T(0);
-        CYT[k] = (a < vY && m < nY) ? CY[m * nY + oY + a] : T(0);
-        eab[k] = (a < vX && m < vY) ? eX[oX + a] + eY[oY + m] : 0.0;
+    {
+        // all loads first (independent, in flight together), then the stores
+        constexpr int kPer = 32 * 32 / (kW32Warps * 32);
+        T cxv[kPer], cyv[kPer];
+        double ev[kPer];
+#pragma unroll
+        for (int t = 0; t < kPer; t++) {
+            const int k = threadIdx.x + t * kW32Warps * 32;
+            const int a = k >> 5, m = k & 31;
+            cxv[t] = (a < vX && m < nX) ? CX[m * nX + oX + a] : T(0);
+            cyv[t] = (a < vY && m < nY) ? CY[m * nY + oY + a] : T(0);
+            ev[t] = (a < vX && m < vY) ? eX[oX + a] + eY[oY + m] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < kPer; t++) {
+            const int k = threadIdx.x + t * kW32Warps * 32;
+            CXT[k] = cxv[t];
+            CYT[k] = cyv[t];
+            eab[k] = ev[t];
+        }
     }
     __syncthreads();
 
+    // this lane's first packed (a, b) term and the step of 32 terms
+    const int lane0_a = lane / vY, lane0_b = lane % vY, step_q = 32 / vY, step_r = 32 % vY;
     double ej = 0.0, ek = 0.0;
     for (int pr = warp; pr < pairs; pr += kW32Warps) {
         const int i = pr / oY, j = pr % oY;
         const double eij = eX[i] + eY[j];
-        // ---- (i a|j b): S[nu][sig] = H0 slice
-        const T* h0 = H0 + (long long)pr * rows;
-        for (int k = lane; k < 32 * 32; k += 32) {
-            const int r = k >> 5, c = k & 31;
-            S[k] = (r < nX && c < nY) ? h0[r * nY + c] : T(0);
-        }
+        // ---- (i a|j b): S[nu][sig] = H0 slice; lane b
+        load_slice(S, H0 + (long long)pr * rows, nX, nY, lane);
         __syncwarp();
         {
             T cy[32], tm[32];
@@ -195,16 +151,14 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 T acc = 0;
 #pragma unroll
                 for (int nu = 0; nu < 32; nu++) acc = fma(CXT[a * 32 + nu], tm[nu], acc);
-                VAs[a * 33 + lane] = acc;
+                VA[a * 33 + lane] = acc;
             }
         }
         __syncwarp();
-        // ---- (i b|j a): S[lam][nu] = H1 slice
-        const T* h1 = H1 + (long long)pr * rows;
-        for (int k = lane; k < 32 * 32; k += 32) {
-            const int r = k >> 5, c = k & 31;
-            S[k] = (r < nY && c < nX) ? h1[r * nX + c] : T(0);
-        }
+        // ---- (i b|j a): S[lam][nu] = H1 slice; lane a.  The barrier keeps the
+        // slice's loads from being hoisted above the VA work (register pressure).
+        asm volatile("" ::: "memory");
+        load_slice(S, H1 + (long long)pr * rows, nY, nX, lane);
         __syncwarp();
         {
             T cx[32], tk[32];
@@ -217,18 +171,31 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 for (int m = 0; m < 32; m++) acc = fma(S[lam * 32 + m], cx[m], acc);
                 tk[lam] = acc;
             }
-            const bool live = lane < vX;
-#pragma unroll 2
-            for (int b = 0; b < 32; b++) {
-                T vk = 0;
+            __syncwarp();                        // S is overwritten with VK below
+#pragma unroll 1
+            for (int b = 0; b < vY; b++) {
+                T v0 = 0, v1 = 0;                    // two chains of 16
 #pragma unroll
-                for (int lam = 0; lam < 32; lam++) vk = fma(CYT[b * 32 + lam], tk[lam], vk);
-                if (live && b < vY) {
-                    const double va = to_f64(VAs[lane * 33 + b]);
-                    const double D = rcp_f64<sizeof(T) == 8 ? 2 : 1>(eij - eab[lane * 32 + b]);
-                    ej = fma(va * va, D, ej);
-                    ek = fma(va * to_f64(vk), D, ek);
+                for (int lam = 0; lam < 32; lam += 2) {
+                    v0 = fma(CYT[b * 32 + lam], tk[lam], v0);
+                    v1 = fma(CYT[b * 32 + lam + 1], tk[lam + 1], v1);
                 }
+                S[lane * 33 + b] = v0 + v1;
+            }
+        }
+        __syncwarp();
+        // ---- FP64 denominators and energy sums over the packed (a, b) terms:
+        // lane l takes terms l, l + 32, ...; (a, b) advance by (q, r), 32 = q vY + r
+        {
+            int a = lane0_a, b = lane0_b;
+            for (int idx = lane; idx < nab; idx += 32) {
+                const double va = to_f64(VA[a * 33 + b]);
+                const double t = div_newton<kSteps<T>>(va, eij - eab[a * 32 + b]);   // v D
+                ej = fma(t, va, ej);
+                ek = fma(t, to_f64(S[a * 33 + b]), ek);
+                b += step_r;
+                a += step_q;
+                if (b >= vY) { b -= vY; a++; }
             }
         }
         __syncwarp();
@@ -246,24 +213,222 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     }
 }
 
+// ---------------------------------------------------------------------------
+// Monomers above 32 AO: the virtual quarter transformations of one occupied
+// pair are four small GEMMs,
+//   Tm  [nu][b]  = sum_sig H0[nu][sig]  C_Y[sig][oY+b]      (nX x vY, K = nY)
+//   TmK [lam][a] = sum_nu  H1[lam][nu]  C_X[nu][oX+a]       (nY x vX, K = nX)
+//   VA  [a][b]   = sum_nu  C_X[nu][oX+a] Tm[nu][b]          (vX x vY, K = nX)
+//   VKT [a][b]   = sum_lam TmK[lam][a]  C_Y[lam][oY+b]      (vX x vY, K = nY)
+// run by 256 threads as a 16 x 16 grid, each thread accumulating an 8 x TN
+// block of outputs (rows ty + 16 i, columns tx + 16 j) in registers: per K
+// step 8 + TN loads feed 8 TN FMAs.  H slices and Tm/TmK live in shared
+// memory, the C columns are read through L1.  VA and VKT share the thread
+// mapping, so each thread meets its own (a, b) terms for the FP64 epilogue
+// (VA goes through shared memory to free its registers).  One CTA runs a
+// range of pairs of one dimer; its FP64 partial sums are written per task and
+// added in task order by k_finish_sum.
+constexpr int kTThreads = 256;
+
+template <typename T>
+__host__ __device__ constexpr int tiled_tn() { return sizeof(T) == 8 ? 4 : 8; }   // FP64 keeps 32 accumulators
+
+template <typename T>
+size_t tiled_smem_bytes(int max_ao)
+{
+    const size_t n = (size_t)max_ao;
+    return (n * n + 2 * n * n) * sizeof(T) + 2 * n * sizeof(double) + 64;
+}
+
+// acc[i][j] = sum_k A(ty + 16 i, k) B(k, n0 + tx + 16 j) over rows < M, columns < N.
+template <typename T, int TN, typename FA, typename FB>
+__device__ __forceinline__ void mm_tile(T (&acc)[8][TN], int M, int N, int K, int n0, int ty, int tx, FA A, FB B)
+{
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+#pragma unroll
+        for (int j = 0; j < TN; j++) acc[i][j] = T(0);
+    bool mok[8], nok[TN];
+#pragma unroll
+    for (int i = 0; i < 8; i++) mok[i] = ty + 16 * i < M;
+#pragma unroll
+    for (int j = 0; j < TN; j++) nok[j] = n0 + tx + 16 * j < N;
+#pragma unroll 2
+    for (int k = 0; k < K; k++) {
+        T a[8], b[TN];
+#pragma unroll
+        for (int i = 0; i < 8; i++) a[i] = mok[i] ? A(ty + 16 * i, k) : T(0);
+#pragma unroll
+        for (int j = 0; j < TN; j++) b[j] = nok[j] ? B(k, n0 + tx + 16 * j) : T(0);
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+#pragma unroll
+            for (int j = 0; j < TN; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void copy_slice(T* S, const T* __restrict__ src, int n, int tid)
+{
+    for (int k0 = 0; k0 < n; k0 += 4 * kTThreads) {
+        T v[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int k = k0 + t * kTThreads + tid;
+            v[t] = k < n ? src[k] : T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int k = k0 + t * kTThreads + tid;
+            if (k < n) S[k] = v[t];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTThreads)
+k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tasks, const T* __restrict__ C,
+               const double* __restrict__ Epool, const T* __restrict__ H, double* __restrict__ part)
+{
+    constexpr int TN = tiled_tn<T>();
+    const FinTask tk = tasks[blockIdx.x];
+    const DimerDesc& d = dd[tk.dimer];
+    const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
+    const int vX = nX - oX, vY = nY - oY;
+    const int rows = nX * nY, pairs = oX * oY;
+    const T* __restrict__ CX = C + d.cX;
+    const T* __restrict__ CY = C + d.cY;
+    const double* eX = Epool + d.eX;
+    const double* eY = Epool + d.eY;
+    const T* H0 = H + d.h_off;
+    const T* H1 = H + d.h_off + (long long)pairs * rows;
+
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double* eXv = reinterpret_cast<double*>(smraw);           // [vX]
+    double* eYv = eXv + nX;                                   // [vY]
+    T* S = reinterpret_cast<T*>(eYv + nY);                    // H slice [rows], then VA [vX][vY]
+    T* Tm = S + rows;                                         // [nX][vY]
+    T* TmK = Tm + nX * vY;                                    // [nY][vX]
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    for (int k = tid; k < vX; k += kTThreads) eXv[k] = eX[oX + k];
+    for (int k = tid; k < vY; k += kTThreads) eYv[k] = eY[oY + k];
+
+    double ej = 0.0, ek = 0.0;
+    for (int pr = tk.pr0; pr < tk.pr1; pr++) {
+        const int i = pr / oY, j = pr % oY;
+        const double eij = eX[i] + eY[j];
+        T acc[8][TN];
+        // ---- Tm = H0 C_Y(virtual)
+        copy_slice(S, H0 + (long long)pr * rows, rows, tid);
+        __syncthreads();
+        for (int n0 = 0; n0 < vY; n0 += 16 * TN) {
+            mm_tile<T, TN>(acc, nX, vY, nY, n0, ty, tx, [&](int m, int k) { return S[m * nY + k]; },
+                           [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int b = 0; b < TN; b++) {
+                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
+                    if (m < nX && n < vY) Tm[m * vY + n] = acc[a][b];
+                }
+        }
+        __syncthreads();
+        // ---- TmK = H1 C_X(virtual)
+        copy_slice(S, H1 + (long long)pr * rows, rows, tid);
+        __syncthreads();
+        for (int n0 = 0; n0 < vX; n0 += 16 * TN) {
+            mm_tile<T, TN>(acc, nY, vX, nX, n0, ty, tx, [&](int m, int k) { return S[m * nX + k]; },
+                           [&](int k, int n) { return __ldg(CX + k * nX + oX + n); });
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int b = 0; b < TN; b++) {
+                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
+                    if (m < nY && n < vX) TmK[m * vX + n] = acc[a][b];
+                }
+        }
+        __syncthreads();
+        // ---- VA, VKT and the FP64 epilogue, one column band at a time
+        for (int n0 = 0; n0 < vY; n0 += 16 * TN) {
+            mm_tile<T, TN>(acc, vX, vY, nX, n0, ty, tx, [&](int m, int k) { return __ldg(CX + k * nX + oX + m); },
+                           [&](int k, int n) { return Tm[k * vY + n]; });
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int b = 0; b < TN; b++) {
+                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
+                    if (m < vX && n < vY) S[m * vY + n] = acc[a][b];   // own elements only
+                }
+            mm_tile<T, TN>(acc, vX, vY, nY, n0, ty, tx, [&](int m, int k) { return TmK[k * vX + m]; },
+                           [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int b = 0; b < TN; b++) {
+                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
+                    if (m < vX && n < vY) {
+                        const double va = to_f64(S[m * vY + n]);
+                        const double t = div_newton<kSteps<T>>(va, eij - (eXv[m] + eYv[n]));   // v D
+                        ej = fma(t, va, ej);
+                        ek = fma(t, to_f64(acc[a][b]), ek);
+                    }
+                }
+        }
+        __syncthreads();
+    }
+    // fixed-order block reduction
+    __shared__ double red[2][kTThreads / 32];
+    ej = warp_sum(ej);
+    ek = warp_sum(ek);
+    if ((tid & 31) == 0) { red[0][tid >> 5] = ej; red[1][tid >> 5] = ek; }
+    __syncthreads();
+    if (tid == 0) {
+        double sj = 0.0, sk = 0.0;
+        for (int w = 0; w < kTThreads / 32; w++) { sj += red[0][w]; sk += red[1][w]; }
+        part[2 * blockIdx.x + 0] = sj;
+        part[2 * blockIdx.x + 1] = sk;
+    }
+}
+
+// Per dimer: its task partials in task order -> {4 sum, -2 sum}.
+__global__ void k_finish_sum(const DimerDesc* __restrict__ dd, int nd, const FinTask* __restrict__ tasks,
+                             const int* __restrict__ first_task, const double* __restrict__ part,
+                             double* __restrict__ E2)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nd) return;
+    const FinTask t0 = tasks[first_task[k]];
+    double sj = 0.0, sk = 0.0;
+    for (int t = t0.first; t < t0.first + t0.ntasks; t++) {
+        sj += part[2 * t];
+        sk += part[2 * t + 1];
+    }
+    E2[2 * dd[k].slot + 0] = 4.0 * sj;
+    E2[2 * dd[k].slot + 1] = -2.0 * sk;
+}
+
 template <typename T>
 cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* C, const double* Epool,
-                          const T* H, double* E2, cudaStream_t s)
+                          const T* H, double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
     if (max_ao <= 32) {
-        const size_t smem = 32 * 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) +
-                            kW32Warps * (32 * 32 + 32 * 33) * sizeof(T);
+        const size_t smem = w32_smem_bytes<T>();
         cudaError_t e = cudaFuncSetAttribute(k_finish_w32<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         k_finish_w32<T><<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2);
         return cudaGetLastError();
     }
-    const size_t smem = (size_t)3 * max_ao * max_ao * sizeof(T);
+    if (!tasks || ntasks <= 0 || !part) return cudaErrorInvalidValue;
+    const size_t smem = tiled_smem_bytes<T>(max_ao);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_finish<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_finish_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_finish<T><<<nd, kFinThreads, smem, s>>>(d_desc, C, Epool, H, E2);
+    k_finish_tiled<T><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the dimers' first-task indices follow the task array
+    const int* first = reinterpret_cast<const int*>(tasks + ntasks);
+    k_finish_sum<<<(nd + 127) / 128, 128, 0, s>>>(d_desc, nd, tasks, first, part, E2);
     return cudaGetLastError();
 }
 
@@ -363,15 +528,32 @@ __global__ void k_check_finite4(const double* __restrict__ x, int d0, int d1, in
 }  // namespace
 
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
-                               const double* Epool, const double* H, double* E2, cudaStream_t s)
+                               const double* Epool, const double* H, double* E2, const FinTask* tasks,
+                               int ntasks, double* part, cudaStream_t s)
 {
-    return launch_finish<double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, s);
+    return launch_finish<double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, s);
 }
 
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const float* Cf,
-                               const double* Epool, const float* H, double* E2, cudaStream_t s)
+                               const double* Epool, const float* H, double* E2, const FinTask* tasks,
+                               int ntasks, double* part, cudaStream_t s)
 {
-    return launch_finish<float>(d_desc, nd, max_ao, Cf, Epool, H, E2, s);
+    return launch_finish<float>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, s);
+}
+
+void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinTask>* out)
+{
+    out->clear();
+    for (int k = 0; k < nd; k++) {
+        const long long nX = h[k].nX, nY = h[k].nY, vX = nX - h[k].oX, vY = nY - h[k].oY;
+        const int pairs = h[k].oX * h[k].oY;
+        const long long per_pair = 2 * (nX * nY * vY + vX * vY * nX);   // FMAs of one pair, both forms
+        const int ppt = (int)std::max<long long>(1, std::min<long long>(pairs, fma_per_task / std::max(1LL, per_pair)));
+        const int ntasks = (pairs + ppt - 1) / ppt;
+        const int first = (int)out->size();
+        for (int t = 0; t < ntasks; t++)
+            out->push_back(FinTask{k, t * ppt, std::min(pairs, (t + 1) * ppt), first, ntasks});
+    }
 }
 
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists, double* mon, double* total,

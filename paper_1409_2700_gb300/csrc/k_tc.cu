@@ -627,10 +627,25 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // split keeps each tensor-core sum short.  The B operand (C_Y's occupied
 // columns) is constant per work item and reused for every p0 and row, so its
 // rounding error would act as a slightly wrong orbital and bias the energy:
-// it is split into two TF32 planes (hi + lo, two MMAs per step) or three
-// BF16 pieces (c0 + c1 + c2; A_hi(c0+c1+c2) + A_lo(c0+c1), five MMAs), which
-// represents it to about FP32 accuracy.  Only the integrals keep the form's
-// own rounding, which is independent from element to element.
+// it is split into two TF32 planes (hi + lo, two MMAs per step), which
+// represents it to about FP32 accuracy; the integrals keep TF32's rounding,
+// independent from element to element.
+// BF16x3 goes further and makes every tensor-core sum exact.  Each operand
+// vector is held in 32-bit fixed point relative to its largest power of two:
+// an integral row (p1,p3) of one p0 over all p2, x ~ 2^(e-31) N_x, and a C_Y
+// column j, c ~ 2^(f-31) N_c, |N| <= 2^32, cut into four balanced base-256
+// digits N = d0 2^24 + d1 2^16 + d2 2^8 + d3 (|d0| <= 256, the others <= 128,
+// each exact in BF16).  The digits come from the FP32 value by round-to-
+// nearest-even FMAs (FP32 pipe), so every integral keeps its 24 FP32 bits
+// unless it lies more than 2^8 below its row's largest.  The four levels
+//     L0 = A0.B0, L1 = A0.B1 + A1.B0, L2 = A0.B2 + A1.B1 + A2.B0,
+//     L3 = A0.B3 + A1.B2 + A2.B1 + A3.B0
+// (ten MMAs per K step, into four 16-column TMEM slots) are sums of at most
+// 4 n2 integer products, each below 2^16: for n2 <= 128 every partial sum is
+// an integer below 2^24, so the tensor core adds them without rounding.  The
+// epilogue forms T = 2^(e+f-14) (L0 + 2^-8 L1 + 2^-16 L2 + 2^-24 L3) in FP32
+// with round-to-nearest; the dropped digit products lie below 2^-31 of the
+// vectors' largest terms.
 // BIG = false: the rank-1 accumulators live in registers (o_X, o_Y <= 8),
 // T slots use all 512 TMEM columns.  BIG = true (o_X, o_Y <= 16): the
 // accumulators live in TMEM columns 256-511 (row r = lane r, column
@@ -638,6 +653,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // (tcgen05.ld, FFMA, tcgen05.st); the T ring shrinks to 16 slots.
 constexpr int kNT = 16;           // TMEM slot width = MMA N
 constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns (16 slots when BIG)
+constexpr int kFxUnits = 8;       // BF16x3: 4-slot p0 units in 512 columns (4 when BIG)
+constexpr int kFxMaxKcs = 3;      // BF16x3 rank kernel: n2 <= 96 (all p2 of a p0 staged at once)
 constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
 constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
@@ -652,10 +669,73 @@ struct __align__(8) RankShared {
     unsigned long long full_w[2], empty_w[2];
     unsigned long long cx_full[2], cx_empty[2];
     unsigned long long slot_full[kSlots], slot_empty[kSlots];
+    unsigned long long exp_full[kFxUnits];   // BF16x3: unit scales written
+    unsigned long long colx_full[2];         // BF16x3: column exponent partials written
     unsigned long long drain;
     unsigned int tmem_base;
     volatile int abort;
 };
+
+// TMEM columns of one p0 unit and units in the ring.
+template <int KIND, bool BIG>
+__host__ __device__ constexpr int unit_cols() { return KIND == TC_BF16X3 ? 4 * kNT : kNT; }
+template <int KIND, bool BIG>
+__host__ __device__ constexpr int n_units() { return (BIG ? 256 : 512) / unit_cols<KIND, BIG>(); }
+// Shared bytes of the A ring (two slots; BF16x3 uses two tiles per slot) and
+// of the BF16x3 unit scales (row scales 128 + column scales 16 per unit).
+__host__ __device__ constexpr size_t a_ring_bytes(int kind) { return 2 * (size_t)kABytes * (kind == TC_BF16X3 ? 2 : 1); }
+__host__ __device__ constexpr size_t fx_scale_bytes(int kind)
+{
+    return kind == TC_BF16X3 ? kFxUnits * (128 + kNT) * 4 + 2 * 16 * kNT * 4 : 0;
+}
+
+// ---- BF16x3 fixed-point digits
+// Round-to-nearest-even integer of |v| < 2^22 by the FP32 magic constant
+// 1.5 * 2^23 (one FMA with the scale, one subtraction).
+__device__ __forceinline__ float rint_scaled(float v, float scale)
+{
+    return fmaf(v, scale, 12582912.0f) - 12582912.0f;
+}
+// Balanced base-256 digits of y (|y| <= 2^32, an FP32 value scaled to the
+// vector's fixed point): y ~ d0 2^24 + d1 2^16 + d2 2^8 + d3, the last digit
+// rounded to nearest; every remainder is exact (FMA of a digit multiple).
+__device__ __forceinline__ void digits4(float y, float (&d)[4])
+{
+    d[0] = rint_scaled(y, 0x1p-24f);
+    y = fmaf(-d[0], 16777216.0f, y);
+    d[1] = rint_scaled(y, 0x1p-16f);
+    y = fmaf(-d[1], 65536.0f, y);
+    d[2] = rint_scaled(y, 0x1p-8f);
+    y = fmaf(-d[2], 256.0f, y);
+    d[3] = rint_scaled(y, 1.0f);
+}
+// Two BF16 digits (exact: integers of at most 9 bits) packed low | high.
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
+{
+    return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+// Scale 2^(31 - e) that brings a vector whose largest binary exponent field
+// is emax (FP64: e = emax - 1023) to 32-bit fixed point; 0 below 2^-96.
+__device__ __forceinline__ float fx_scale_f64(int emax)
+{
+    return (emax >= 927 && emax <= 1180) ? __uint_as_float((unsigned)(1181 - emax) << 23) : 0.f;
+}
+// The same for an FP32 vector (f = fmax - 127).
+__device__ __forceinline__ float fx_scale_f32(int fmax)
+{
+    return (fmax >= 31 && fmax <= 254) ? __uint_as_float((unsigned)(285 - fmax) << 23) : 0.f;
+}
+// 2^(e - 7) with e = emax - 1023, the row's share of the product scale
+// (0 where the row's digits are zero).
+__device__ __forceinline__ float row_scale(int emax)
+{
+    return emax >= 927 ? __uint_as_float((unsigned)(emax - 903) << 23) : 0.f;
+}
+// 2^(f - 7) with f = fmax - 127.
+__device__ __forceinline__ float col_scale(int fmax)
+{
+    return fmax >= 31 ? __uint_as_float((unsigned)(fmax - 7) << 23) : 0.f;
+}
 
 // A converter thread's fixed share of every A tile of an item: row r of the
 // 128-row tile and where that row's integrals sit in the FP64 staging box.
@@ -728,20 +808,107 @@ __device__ __forceinline__ void convert_row(const double* __restrict__ F, unsign
     }
 }
 
+// T[(p1,p3) = this lane's row][j] of one p0 unit.  TF32: the slot itself.
+// BF16x3: the three digit levels combined in FP32 (round to nearest), times
+// the row scale and column scale 2^(e-7) 2^(f-7).
+template <int KIND>
+__device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[16], const float* srow, const float* scol)
+{
+    if constexpr (KIND == TC_TF32) {
+        tmem_ld16(taddr, T);
+    } else {
+        // two rounds of two slots keep 32 registers in flight (the register
+        // accumulators stay live): ((L3/256 + L2)/256 + L1)/256 + L0
+        unsigned a[16], b[16];
+        tmem_ld16_nowait(taddr + 3 * kNT, a);
+        tmem_ld16_nowait(taddr + 2 * kNT, b);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; j++) T[j] = fmaf(__uint_as_float(a[j]), 0x1p-8f, __uint_as_float(b[j]));
+        tmem_ld16_nowait(taddr + kNT, a);
+        tmem_ld16_nowait(taddr, b);
+        tmem_wait_ld();
+        const float sr = *srow;
+#pragma unroll
+        for (int j = 0; j < 16; j++)
+            T[j] = fmaf(fmaf(T[j], 0x1p-8f, __uint_as_float(a[j])), 0x1p-8f, __uint_as_float(b[j])) * (sr * scol[j]);
+    }
+}
+
+// BF16x3: largest binary exponent field of row r over the chunks of one p0
+// (the staged boxes hold the row's p2 = 32 kc + 0..31; out-of-range p2 read
+// 0).  The two threads of a row (lanes l and l ^ 16) scan their own chunks
+// c0 and c0 + 2 and exchange.
+__device__ __forceinline__ int row_emax(const unsigned char* Fr, unsigned f_stage_bytes, int sf, unsigned g0,
+                                        int kcs, const ConvRow& cr, int n3, int c0)
+{
+    int emax = 0;
+    for (int kc = 0; kc < kcs; kc++) {
+        const unsigned* hw = reinterpret_cast<const unsigned*>(
+                                 reinterpret_cast<const double*>(Fr + (size_t)((g0 + kc) % sf) * f_stage_bytes) +
+                                 cr.src) + 1;
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+            for (int e = 0; e < 8; e++)
+                emax = max(emax, (int)((hw[2 * ((c0 + 2 * q) * 8 + e) * n3] >> 20) & 0x7FFu));
+    }
+    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 16));
+    return cr.valid ? emax : 0;
+}
+
+// BF16x3: row r of one chunk as four digit planes, chunks c0 and c0 + 2 of
+// 8 p2 each: tile 1 holds [d0 | d1] (bytes 0-63 / 64-127), tile 2 [d2 | d3].
+__device__ __forceinline__ void convert_row_fx(const double* __restrict__ F, unsigned char* __restrict__ A1,
+                                               unsigned char* __restrict__ A2, const ConvRow& cr, int n3, int c0,
+                                               float scale)
+{
+    const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int c = c0 + 2 * q;
+        unsigned w[4][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float d[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const uint2 b = dw[(c * 8 + e + u) * n3];
+                digits4(cr.valid ? f32_from_f64_bits(b.x, b.y) * scale : 0.f, d[u]);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(d[0][k], d[1][k]);
+        }
+        *reinterpret_cast<uint4*>(A1 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+        *reinterpret_cast<uint4*>(A1 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
+            make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+        *reinterpret_cast<uint4*>(A2 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+        *reinterpret_cast<uint4*>(A2 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
+            make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
+    }
+}
+
 template <int KIND, bool BIG>
 __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams P)
 {
-    constexpr int NS = BIG ? 16 : kSlots;   // T slots in the ring
-    constexpr int CXW = BIG ? kOBig : kOB;  // staged C_X occupied columns per row
+    constexpr bool FX = KIND == TC_BF16X3;          // fixed-point digit planes
+    constexpr int UC = unit_cols<KIND, BIG>();      // TMEM columns per p0 unit
+    constexpr int NS = n_units<KIND, BIG>();        // p0 units in the ring
+    constexpr int CXW = BIG ? kOBig : kOB;          // staged C_X occupied columns per row
+    constexpr size_t ASLOT = a_ring_bytes(KIND) / 2;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
     // [F ring][A ring x2][W: 2 parities x kcs_max x 2 planes x 2 KB][C_X rows x2][barriers]
     unsigned char* Fr = base;
     unsigned char* Ar = Fr + (size_t)P.sf * P.f_stage_bytes;
-    unsigned char* Wr = Ar + 2 * kABytes;
+    unsigned char* Wr = Ar + a_ring_bytes(KIND);
     const int wstride = P.kcs_max * 2 * kNT * 128;      // bytes per parity
     float* cxs = reinterpret_cast<float*>(Wr + 2 * wstride);
-    RankShared* sh = reinterpret_cast<RankShared*>(cxs + 2 * kCxFloats);
+    float* exps = cxs + 2 * kCxFloats;                  // BF16x3: [unit][128 rows] row scales
+    float* scu = exps + kFxUnits * 128;                 //          [unit][16 columns] column scales
+    int* colx = reinterpret_cast<int*>(scu + kFxUnits * kNT);   // [parity][16 parts][16 columns] exponents
+    RankShared* sh = reinterpret_cast<RankShared*>(reinterpret_cast<unsigned char*>(cxs + 2 * kCxFloats) +
+                                                   fx_scale_bytes(KIND));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -752,6 +919,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             mbar_init(&sh->cx_full[s], 128); mbar_init(&sh->cx_empty[s], 128);
         }
         for (int s = 0; s < kSlots; s++) { mbar_init(&sh->slot_full[s], 1); mbar_init(&sh->slot_empty[s], 4); }
+        for (int s = 0; s < kFxUnits; s++) mbar_init(&sh->exp_full[s], kConvWarps);
+        for (int s = 0; s < 2; s++) mbar_init(&sh->colx_full[s], kConvWarps);
         mbar_init(&sh->drain, 1);
         sh->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -816,12 +985,12 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         const int s = gS % NS;
                         if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13))) break;
                         tc_fence_after();
-                        const unsigned dt = tmem + (unsigned)(s * kNT);
+                        const unsigned dt = tmem + (unsigned)(s * UC);
                         for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
                             const int as = gA & 1;
                             if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
                             tc_fence_after();
-                            const unsigned long long adesc = sw128_desc(Ar + (size_t)as * kABytes);
+                            const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
                             unsigned char* wk = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                             const unsigned long long b0 = sw128_desc(wk);
                             const unsigned long long b1 = sw128_desc(wk + kNT * 128);
@@ -833,17 +1002,23 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                     tc_mma<KIND>(dt, adesc + 2 * k, b1 + 2 * k, idesc, 1u);
                                 }
                             } else {
-                                // A = hi + lo (bytes 0-63 / 64-127 of each row); C_Y = c0 + c1 + c2
-                                // (plane 0 = [c0 | c1], plane 1 = [c2 | 0]): A_hi (c0+c1+c2) + A_lo (c0+c1)
+                                // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3]; B plane 0 =
+                                // [d0 | d1], plane 1 = [d2 | d3].  Level l (slot l) takes the products
+                                // A_u B_(l-u): one, two, three and four MMAs.
+                                const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
 #pragma unroll
                                 for (int k = 0; k < 2; k++) {
-                                    const unsigned long long ah = adesc + 2 * k, al = adesc + 4 + 2 * k;
-                                    const unsigned long long c0 = b0 + 2 * k, c1 = b0 + 4 + 2 * k, c2 = b1 + 2 * k;
-                                    tc_mma<KIND>(dt, ah, c0, idesc, (kc > 0 || k > 0) ? 1u : 0u);
-                                    tc_mma<KIND>(dt, ah, c1, idesc, 1u);
-                                    tc_mma<KIND>(dt, ah, c2, idesc, 1u);
-                                    tc_mma<KIND>(dt, al, c0, idesc, 1u);
-                                    tc_mma<KIND>(dt, al, c1, idesc, 1u);
+                                    const unsigned acc = (kc > 0 || k > 0) ? 1u : 0u;
+                                    const unsigned long long A[4] = {adesc + 2 * k, adesc + 4 + 2 * k, a2 + 2 * k,
+                                                                     a2 + 4 + 2 * k};
+                                    const unsigned long long B[4] = {b0 + 2 * k, b0 + 4 + 2 * k, b1 + 2 * k,
+                                                                     b1 + 4 + 2 * k};
+#pragma unroll
+                                    for (int l = 0; l < 4; l++)
+#pragma unroll
+                                        for (int u = 0; u <= l; u++)
+                                            tc_mma<KIND>(dt + (unsigned)(l * kNT), A[u], B[l - u], idesc,
+                                                         u == 0 ? acc : 1u);
                                 }
                             }
                             tc_commit(&sh->empty_a[as]);
@@ -862,8 +1037,10 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
     } else if (warp < kEpiWarp0) {
         // ------------------------------------------------ converters
         const int ct = threadIdx.x - 64;        // 0 .. 32*kConvWarps-1
-        const int r = ct & 127, c0 = ct >> 7;   // tile row, first chunk
-        unsigned gF = 0, gA = 0, li = 0;
+        // tile row and first chunk; BF16x3 keeps both threads of a row in one warp
+        const int r = FX ? (((ct >> 5) << 4) | (lane & 15)) : (ct & 127);
+        const int c0 = FX ? (lane >> 4) : (ct >> 7);
+        unsigned gF = 0, gA = 0, gU = 0, li = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
             const TcItem item = P.items[it];
@@ -874,6 +1051,29 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             const ConvRow cr = conv_row(r, g.p1t * g.n3, g.n3);
             // ---- B operand of this item: row j < 16, K = p2: C_Y[p2][j] (zero past o2 / n2)
             if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, abort, P.status, 15))) break;
+            float sc_mine = 0.f;                 // BF16x3: column scale of column ct (< 16)
+            int* cx_part = colx + wp * 16 * kNT;
+            if constexpr (FX) {
+                // largest exponent field of each occupied C_Y column: 16 parts x 16
+                // columns, each part a strided eighth of the rows, then combined
+                const int j = ct & 15, part = ct >> 4;
+                int fm = 0;
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const int p2 = part + 16 * t;
+                    if (j < g.o2 && p2 < g.n2)
+                        fm = max(fm, (int)((__float_as_uint(__ldg(CY + p2 * d.nY + j)) >> 23) & 0xFFu));
+                }
+                cx_part[part * kNT + j] = fm;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->colx_full[wp]);
+                if (!(ok = mbar_wait(&sh->colx_full[wp], (li >> 1) & 1, abort, P.status, 24))) break;
+                if (ct < kNT) {
+                    int m = 0;
+                    for (int q = 0; q < 16; q++) m = max(m, cx_part[q * kNT + ct]);
+                    sc_mine = col_scale(m);
+                }
+            }
             for (int kc = 0; kc < g.kcs; kc++) {
                 unsigned char* W0 = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                 unsigned char* W1 = W0 + kNT * 128;
@@ -892,28 +1092,31 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
                     }
                 } else {
+                    // C_Y column j in fixed point relative to its largest exponent, four digits
                     for (int task = ct; task < kNT * 4; task += 32 * kConvWarps) {
                         const int j = task >> 2, c = task & 3;
-                        unsigned short b0[8], b1[8], b2[8];
+                        int fmax = 0;
+                        for (int q = 0; q < 16; q++) fmax = max(fmax, cx_part[q * kNT + j]);
+                        const float scale = fx_scale_f32(fmax);
+                        unsigned w[4][4];
 #pragma unroll
-                        for (int e = 0; e < 8; e++) {
-                            const int p2 = kc * kKC + c * 8 + e;
-                            const float x = (j < g.o2 && p2 < g.n2) ? __ldg(CY + p2 * d.nY + j) : 0.f;
-                            b0[e] = to_bf16_bits(x);
-                            const float r1 = x - __bfloat162float(__ushort_as_bfloat16(b0[e]));
-                            b1[e] = to_bf16_bits(r1);
-                            b2[e] = to_bf16_bits(r1 - __bfloat162float(__ushort_as_bfloat16(b1[e])));
+                        for (int e = 0; e < 8; e += 2) {
+                            float dg[2][4];
+#pragma unroll
+                            for (int u = 0; u < 2; u++) {
+                                const int p2 = kc * kKC + c * 8 + e + u;
+                                const float x = (j < g.o2 && p2 < g.n2) ? __ldg(CY + p2 * d.nY + j) : 0.f;
+                                digits4(x * scale, dg[u]);
+                            }
+#pragma unroll
+                            for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(dg[0][k], dg[1][k]);
                         }
-                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, c)) =
-                            make_uint4(b0[0] | (b0[1] << 16), b0[2] | (b0[3] << 16), b0[4] | (b0[5] << 16),
-                                       b0[6] | (b0[7] << 16));
+                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, c)) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
                         *reinterpret_cast<uint4*>(W0 + sw128_off(j, 4 + c)) =
-                            make_uint4(b1[0] | (b1[1] << 16), b1[2] | (b1[3] << 16), b1[4] | (b1[5] << 16),
-                                       b1[6] | (b1[7] << 16));
-                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) =
-                            make_uint4(b2[0] | (b2[1] << 16), b2[2] | (b2[3] << 16), b2[4] | (b2[5] << 16),
-                                       b2[6] | (b2[7] << 16));
-                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, 4 + c)) = make_uint4(0, 0, 0, 0);
+                            make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, 4 + c)) =
+                            make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
                     }
                 }
             }
@@ -922,21 +1125,56 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             if (lane == 0) mbar_arrive(&sh->full_w[wp]);
 
             for (int mt = 0; mt < item.mts && ok; mt++)
-                for (int p0 = 0; p0 < g.n0 && ok; p0++)
-                    for (int kc = 0; kc < g.kcs; kc++, gF++, gA++) {
-                        const int s = gF % P.sf;
-                        if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16))) break;
-                        const int as = gA & 1;
-                        if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17))) break;
-                        convert_row<KIND>(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes),
-                                          Ar + (size_t)as * kABytes, cr, g.n3, c0);
-                        fence_async_smem();
-                        __syncwarp();
-                        if (lane == 0) {
-                            mbar_arrive(&sh->full_a[as]);
-                            mbar_arrive(&sh->empty_f[s]);
+                for (int p0 = 0; p0 < g.n0 && ok; p0++) {
+                    if constexpr (!FX) {
+                        for (int kc = 0; kc < g.kcs; kc++, gF++, gA++) {
+                            const int s = gF % P.sf;
+                            if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16))) break;
+                            const int as = gA & 1;
+                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
+                                break;
+                            convert_row<KIND>(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes),
+                                              Ar + (size_t)as * ASLOT, cr, g.n3, c0);
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                mbar_arrive(&sh->full_a[as]);
+                                mbar_arrive(&sh->empty_f[s]);
+                            }
                         }
+                    } else {
+                        // every p2 chunk of this p0 staged (the ring holds >= kcs boxes), then the
+                        // row's exponent, its scale for the epilogue, and the digit planes
+                        for (int kc = 0; kc < g.kcs && ok; kc++)
+                            ok = mbar_wait(&sh->full_f[(gF + kc) % P.sf], ((gF + kc) / P.sf) & 1, abort, P.status, 16);
+                        if (!ok) break;
+                        const int emax = row_emax(Fr, P.f_stage_bytes, P.sf, gF, g.kcs, cr, g.n3, c0);
+                        const float xscale = fx_scale_f64(emax);
+                        const int su = gU % NS;
+                        if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22))) break;
+                        if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
+                        if (ct < kNT) scu[su * kNT + ct] = sc_mine;
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sh->exp_full[su]);
+                        for (int kc = 0; kc < g.kcs; kc++, gA++) {
+                            const int s = (gF + kc) % P.sf;
+                            const int as = gA & 1;
+                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
+                                break;
+                            unsigned char* At = Ar + (size_t)as * ASLOT;
+                            convert_row_fx(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes), At,
+                                           At + kABytes, cr, g.n3, c0, xscale);
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                mbar_arrive(&sh->full_a[as]);
+                                mbar_arrive(&sh->empty_f[s]);
+                            }
+                        }
+                        gF += g.kcs;
+                        gU++;
                     }
+                }
         }
     } else {
         // ------------------------------------------------ epilogue
@@ -973,9 +1211,10 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                     for (int p0 = 0; p0 < g.n0; p0++, gS++) {
                         const int s = gS % NS;
                         if (!(ok = mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, P.status, 18))) break;
+                        if (FX && !(ok = mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, P.status, 23))) break;
                         tc_fence_after();
                         float T[16];
-                        tmem_ld16(lanebase + (unsigned)(s * kNT), T);
+                        unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT);
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
@@ -1009,9 +1248,10 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                     for (int p0 = 0; p0 < g.n0; p0++, gS++) {
                         const int s = gS % NS;
                         if (!(ok = mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, P.status, 18))) break;
+                        if (FX && !(ok = mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, P.status, 23))) break;
                         tc_fence_after();
                         float T[16];
-                        tmem_ld16(lanebase + (unsigned)(s * kNT), T);
+                        unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT);
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
@@ -1099,16 +1339,18 @@ int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
 
 // 1: rank kernel, register accumulators (occupations <= 8); 2: rank kernel,
 // TMEM accumulators (<= 16); 0: Kronecker kernel (anything else the
-// tensor-core forms accept).  MCPT_TC_KERNEL=kron|rank|rankbig forces a
+// tensor-core forms accept; BF16x3 also when n_Y > 96, since its rank kernel
+// stages all p2 of a p0 at once).  MCPT_TC_KERNEL=kron|rank|rankbig forces a
 // kernel where the sizes allow it.
-int choose_variant(const DimerDesc* h, int nd)
+int choose_variant(TcKind kind, const DimerDesc* h, int nd)
 {
     int omax = 0, nymax = 0;
     for (int k = 0; k < nd; k++) {
         omax = std::max(omax, std::max(h[k].oX, h[k].oY));
         nymax = std::max(nymax, h[k].nY);
     }
-    const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
+    const int kcs_cap = kind == TC_BF16X3 ? kFxMaxKcs : kKCMax;
+    const bool fits_rank = nymax <= kcs_cap * kKC && omax <= kOBig;
     const char* env = getenv("MCPT_TC_KERNEL");
     if (env && !strcmp(env, "kron")) return 0;
     if (env && !strcmp(env, "rankbig") && fits_rank) return 2;
@@ -1118,10 +1360,10 @@ int choose_variant(const DimerDesc* h, int nd)
 
 }  // namespace
 
-size_t tc_work_bytes(const DimerDesc* h, int nd)
+size_t tc_work_bytes(TcKind kind, const DimerDesc* h, int nd)
 {
     size_t items = 0;
-    const int variant = choose_variant(h, nd);
+    const int variant = choose_variant(kind, h, nd);
     for (int k = 0; k < nd; k++)
         for (int f = 0; f < 2; f++) {
             int m;
@@ -1130,9 +1372,72 @@ size_t tc_work_bytes(const DimerDesc* h, int nd)
     return (size_t)nd * 2 * sizeof(CUtensorMap) + items * sizeof(TcItem) + 256;
 }
 
+// Shared-memory bytes of a launch apart from its staging ring, and the
+// deepest ring that fits.
+static size_t fixed_smem(TcKind kind, int variant, int kcs_max, unsigned w_stage_bytes)
+{
+    return variant >= 1 ? 1024 + a_ring_bytes(kind) + 2 * (size_t)kcs_max * 2 * kNT * 128 +
+                              2 * (size_t)kCxFloats * 4 + fx_scale_bytes(kind) + sizeof(RankShared)
+                        : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)w_stage_bytes + sizeof(TcShared);
+}
+
+static void launch_shape(const DimerDesc* h, int nd, int* kcs_max, unsigned* f_stage, unsigned* w_stage)
+{
+    int maxN = 16, kc = 1;
+    unsigned box = 0;
+    for (int k = 0; k < nd; k++) {
+        maxN = std::max(maxN, h[k].npad);
+        kc = std::max(kc, (h[k].nY + kKC - 1) / kKC);
+        for (int f = 0; f < 2; f++) {
+            const int n3 = f ? h[k].nX : h[k].nY;
+            box = std::max(box, (unsigned)(n3 * kKC * (128 / n3) * 8));
+        }
+    }
+    *kcs_max = kc;
+    *f_stage = (box + 1023) & ~1023u;
+    *w_stage = (unsigned)(((size_t)maxN * 128 + 1023) & ~(size_t)1023);
+}
+
+int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
+{
+    int omax = 0, nymax = 0;
+    for (int k = 0; k < nd; k++) {
+        omax = std::max(omax, std::max(h[k].oX, h[k].oY));
+        nymax = std::max(nymax, h[k].nY);
+    }
+    const int kcs_cap = kind == TC_BF16X3 ? kFxMaxKcs : kKCMax;
+    std::vector<int> vars;
+    if (nymax <= kcs_cap * kKC && omax <= kOBig) {
+        if (omax <= kOB) vars.push_back(1);
+        vars.push_back(2);
+    } else {
+        vars.push_back(0);
+    }
+    int dev = 0, nsm = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int kcs_max;
+    unsigned fs, ws;
+    launch_shape(h, nd, &kcs_max, &fs, &ws);
+    int n = 0;
+    for (int v : vars) {
+        const int sf_max = std::min(8, (int)(((size_t)max_smem - fixed_smem(kind, v, kcs_max, ws)) / fs));
+        const int sf_min = (v >= 1 && kind == TC_BF16X3) ? std::max(2, kcs_max) : 2;
+        if (sf_max < sf_min) continue;
+        int sfs[3] = {sf_min, (sf_min + sf_max) / 2, sf_max};
+        for (int a = 0; a < 3; a++) {
+            if (a > 0 && sfs[a] == sfs[a - 1]) continue;
+            for (int gdiv = 0; gdiv < 2; gdiv++)
+                if (n < max) out[n++] = TcTune{v + 1, sfs[a], gdiv ? nsm - nsm / 4 : nsm};
+        }
+    }
+    return n;
+}
+
 cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const float* Cf,
-                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s, TcLaunch* out,
-                       char* err, size_t errlen)
+                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s,
+                       const TcTune* tune, TcLaunch* out, char* err, size_t errlen)
 {
     if (nd <= 0) return cudaSuccess;
     auto encode = get_encode();
@@ -1142,7 +1447,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     }
     std::vector<CUtensorMap> maps((size_t)nd * 2);
     std::vector<TcItem> items;
-    const int variant = choose_variant(h_desc, nd);
+    const int variant = (tune && tune->variant1) ? tune->variant1 - 1 : choose_variant(kind, h_desc, nd);
     int maxN = 16;
     unsigned max_box = 0;
     for (int k = 0; k < nd; k++) {
@@ -1218,19 +1523,19 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     int kcs_max = 1;
     for (int k = 0; k < nd; k++) kcs_max = std::max(kcs_max, (h_desc[k].nY + kKC - 1) / kKC);
     P.kcs_max = kcs_max;
-    const size_t fixed = variant >= 1
-        ? 1024 + 2 * (size_t)kABytes + 2 * (size_t)kcs_max * 2 * kNT * 128 + 2 * (size_t)kCxFloats * 4 +
-              sizeof(RankShared)
-        : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)P.w_stage_bytes + sizeof(TcShared);
+    const size_t fixed = fixed_smem(kind, variant, kcs_max, P.w_stage_bytes);
     int sf = (int)(((size_t)max_smem - fixed) / P.f_stage_bytes);
     sf = std::min(sf, 8);
-    if (sf < 2) {
-        snprintf(err, errlen, "not enough shared memory for the staging ring");
+    if (tune && tune->sf) sf = std::min(sf, tune->sf);
+    // the BF16x3 rank kernel holds every p2 box of a p0 at once
+    const int sf_min = (variant >= 1 && kind == TC_BF16X3) ? std::max(2, kcs_max) : 2;
+    if (sf < sf_min) {
+        snprintf(err, errlen, "not enough shared memory for the staging ring (%d < %d stages)", sf, sf_min);
         return cudaErrorInvalidConfiguration;
     }
     P.sf = sf;
     P.smem = fixed + (size_t)sf * P.f_stage_bytes;
-    P.grid = std::min<int>((int)items.size(), nsm);
+    P.grid = std::min<int>((int)items.size(), (tune && tune->grid) ? std::min(tune->grid, nsm) : nsm);
     return cudaSuccess;
 }
 

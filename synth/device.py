@@ -84,3 +84,13 @@ def workload_blocks(w: synth.Workload, dimers=None, device="cuda"):
         B = factors(X, Y, w.nao[X], w.nao[Y], seed=w.seed, device=device)
         blocks_into(B, w.nao[X], synth.scale_for_distance(w.R[d]), buf[offs[k]:offs[k] + sizes[k]])
     return buf, offs
+
+
+def fill_views(w: synth.Workload, views, device="cuda"):
+    """Producer for streamed runs: write each view's [A | K] blocks (objects
+    with ``dimer`` and ``out``) from the dimer's seeded factors."""
+    for v in views:
+        X, Y = w.pairs[v.dimer]
+        B = factors(X, Y, w.nao[X], w.nao[Y], seed=w.seed, device=device)
+        blocks_into(B, w.nao[X], synth.scale_for_distance(w.R[v.dimer]), v.out)
+        del B

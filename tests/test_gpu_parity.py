@@ -376,3 +376,28 @@ def test_graph_replay_matches_eager(lat8, prec):
             out[graphs] = res[0]
     for x, y in zip(out[False], out[True]):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_autotuner_cache(lat8, prec, tmp_path):
+    """With a tune cache the first plan times every candidate launch of its
+    wave and writes one line for the wave's shape signature; a second context
+    reuses the line without timing; energies stay within the form's
+    tolerance whatever launch won."""
+    w, mons, blocks, E = lat8
+    cache = tmp_path / "tune.txt"
+    res = []
+    for _ in range(2):
+        with M.Context(precision=prec, tune_cache=str(cache)) as ctx:
+            load_context(ctx, w, mons, blocks, range(w.n_dimers))
+            ctx.run()
+            res.append(ctx.energies())
+        lines = cache.read_text().splitlines()
+        assert len(lines) == 1, lines
+    key, variant1, sf, grid, ms = lines[0].split()
+    assert key.startswith(prec + ":") and int(variant1) in (1, 2, 3) and int(sf) >= 2 and int(grid) >= 1
+    print(f"{prec}: tuned {lines[0]}")
+    for mj, mk, pd, tot in res:
+        assert np.all(np.abs(pd[:, 0] - E[:, 0]) <= PER_DIMER[prec] * np.abs(E[:, 0]))
+        assert abs(tot[0] - E[:, 0].sum()) <= LATTICE[prec]
+    assert np.array_equal(res[0][2], res[1][2])

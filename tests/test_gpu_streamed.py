@@ -1,0 +1,144 @@
+"""Full-size workloads whose integrals do not fit on the device at once,
+streamed in waves of device-generated blocks through the C ABI (marked gpu).
+
+Outputs the oracle can compute one at a time are checked directly: a seeded
+sample of dimers (always including the first and the last, and every size
+class present) against the oracle's factor route (O(n^3 naux) per dimer; it
+agrees with the four-index oracle to 1e-12 relative).  The rest is checked
+through properties that hold at any size: every E_J is finite and negative
+(D < 0), the per-monomer halves are the oracle's accumulation of the GPU's
+own per-dimer terms, and the lattice totals of two forms agree within the
+mixed form's lattice tolerance.
+
+Inputs: the device generator and the host generator draw the same Philox
+streams; the blocks differ by FP64 rounding only (matrix-product order,
+Box-Muller's transcendental functions), far below every tolerance here.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+M = pytest.importorskip("paper_1409_2700_gb300")
+torch = pytest.importorskip("torch")
+
+from paper_1409_2700_gb300.stream import Streamed  # noqa: E402
+
+# per-dimer relative tolerance against the factor route (the fp64 bound adds
+# the factor route's own 1e-12 and the generators' FP64 rounding)
+PER_DIMER = {"fp64": 1e-11, "fp32c": 2e-6, "bf16x3": 2e-4, "tf32": 1e-2}
+BUDGET = 96 << 30      # bytes of device integral blocks per wave
+
+
+def _factor_route_oracle(w, d):
+    X, Y = w.pairs[d]
+    mX, mY = w.monomer(X), w.monomer(Y)
+    V, W = oracle.factor_route(w.factors(d), synth.scale_for_distance(w.R[d]), mX.C, mY.C, mX.nocc, mY.nocc)
+    return np.array(oracle.energy_from_mo(V, W, mX.eps, mY.eps, mX.nocc, mY.nocc))
+
+
+def _sample(w, k, seed):
+    rng = np.random.default_rng(seed)
+    pick = set(rng.choice(w.n_dimers, size=min(k, w.n_dimers), replace=False).tolist())
+    pick |= {0, w.n_dimers - 1}
+    seen = {}
+    for d, (X, Y) in enumerate(w.pairs):        # one dimer of every size pair
+        seen.setdefault((w.nao[X], w.nao[Y]), d)
+    if len(seen) <= 4 * k:
+        pick |= set(seen.values())
+    return sorted(pick)
+
+
+def _streamed(w, precs, dimers=None):
+    """Run `precs` over the workload (or the listed dimers, renumbered) in
+    waves; returns {prec: (mon_J, mon_K, per_dimer, total)} and the pairs."""
+    import synth.device as sd
+    s = torch.cuda.Stream()                     # one stream: fill, then run, wave after wave
+    ds = list(range(w.n_dimers)) if dimers is None else list(dimers)
+    pairs = [w.pairs[d] for d in ds]
+    ctxs = {p: M.Context(precision=p, validate=False, stream=s.cuda_stream, graphs=False) for p in precs}
+    try:
+        for X in range(w.n_monomers):
+            m = w.monomer(X)
+            for c in ctxs.values():
+                c.add_monomer(m.C, m.eps, m.nocc)
+        view = synth.Workload(w.name, w.nao, w.nocc, pairs, [w.R[d] for d in ds], w.seed)
+        with torch.cuda.stream(s):
+            st = Streamed(list(ctxs.values()), pairs, w.nao, BUDGET)
+            for k in range(len(st)):
+                sd.fill_views(view, st.views(k))
+                st.run(k)
+            out = {p: c.energies() for p, c in ctxs.items()}
+            s.synchronize()
+            del st
+        return out, pairs
+    finally:
+        for c in ctxs.values():
+            c.close()
+
+
+def _check_sample(w, res, pairs, sample, idx_of):
+    ref = {d: _factor_route_oracle(w, d) for d in sample}
+    for prec, (_, _, pd, _) in res.items():
+        worst = 0.0
+        for d in sample:
+            g = pd[idx_of[d]]
+            scale = abs(ref[d][0])
+            err = max(abs(g[0] - ref[d][0]), abs(g[1] - ref[d][1])) / scale
+            worst = max(worst, err)
+            assert err <= PER_DIMER[prec], (prec, d, g, ref[d])
+        print(f"{w.name} {prec}: {len(sample)} sampled dimers, max rel err {worst:.2e}")
+
+
+def _check_invariants(res, pairs, nmon):
+    X = [p[0] for p in pairs]
+    Y = [p[1] for p in pairs]
+    for prec, (mj, mk, pd, tot) in res.items():
+        assert np.all(np.isfinite(pd))
+        assert np.all(pd[:, 0] < 0), prec
+        omon, otot = oracle.accumulate(pd, X, Y, nmon)
+        assert np.allclose(mj, omon[:, 0], rtol=1e-12, atol=1e-300), prec
+        assert np.allclose(mk, omon[:, 1], rtol=1e-12, atol=1e-300), prec
+        assert abs(tot[0] - otot[0]) <= 1e-13 * abs(otot[0]), prec
+        assert abs(tot[1] - otot[1]) <= 1e-12 * abs(otot[0]), prec
+
+
+def test_lattice_10x10x10_cheb2_streamed():
+    """1000 monomers, 42,092 dimers (706 GB of blocks): TF32 and FP64 forms."""
+    w = synth.workload("lattice-10x10x10-cheb2")
+    res, pairs = _streamed(w, ["tf32", "fp64"])
+    sample = _sample(w, 24, seed=11)
+    _check_sample(w, res, pairs, sample, {d: d for d in range(w.n_dimers)})
+    _check_invariants(res, pairs, w.n_monomers)
+    dJ = res["tf32"][3][0] - res["fp64"][3][0]
+    dK = res["tf32"][3][1] - res["fp64"][3][1]
+    print(f"lattice E_J fp64 {res['fp64'][3][0]:.12e}  tf32 - fp64: J {dJ:.3e} K {dK:.3e} Eh")
+    assert abs(dJ) <= 1e-5 and abs(dK) <= 1e-5
+
+
+def test_uneven_4096_streamed():
+    """8192 monomers of 16..96 AO, 4096 dimers (934 GB of blocks): BF16x3
+    (the batched form) and FP64."""
+    w = synth.workload("uneven-4096")
+    res, pairs = _streamed(w, ["bf16x3", "fp64"])
+    sample = _sample(w, 12, seed=12)
+    _check_sample(w, res, pairs, sample, {d: d for d in range(w.n_dimers)})
+    _check_invariants(res, pairs, w.n_monomers)
+    dJ = res["bf16x3"][3][0] - res["fp64"][3][0]
+    dK = res["bf16x3"][3][1] - res["fp64"][3][1]
+    print(f"lattice E_J fp64 {res['fp64'][3][0]:.12e}  bf16x3 - fp64: J {dJ:.3e} K {dK:.3e} Eh")
+    assert abs(dJ) <= 1e-6 and abs(dK) <= 1e-6
+
+
+def test_ao128_subset():
+    """343 monomers of 128 AO / 20 occupied: a seeded 16-dimer subset (4.3 GB
+    of blocks per dimer) in the compensated FP32 form."""
+    w = synth.workload("lattice-7x7x7-cheb1-ao128")
+    rng = np.random.default_rng(13)
+    subset = sorted(rng.choice(w.n_dimers, size=16, replace=False).tolist())
+    res, pairs = _streamed(w, ["fp32c"], dimers=subset)
+    _check_sample(w, res, pairs, subset, {d: k for k, d in enumerate(subset)})
+    _check_invariants(res, pairs, w.n_monomers)
