@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip e2e, CPU baseline and the FP64 comparison")
     p.add_argument("--max-dimers", type=int, default=0,
                    help="keep only the first N dimers of the workload (smaller cases for profiling)")
+    p.add_argument("--alias-blocks", action="store_true",
+                   help="profiling aid: every dimer reads dimer 0's integral blocks, so the second half runs "
+                        "the full dimer grid with a device footprint of one dimer (energies are not the workload's)")
     return p.parse_args()
 
 
@@ -208,7 +211,11 @@ def our_arm(args, ws, rank, local):
     if args.max_dimers:
         w.pairs, w.R = w.pairs[:args.max_dimers], w.R[:args.max_dimers]
     # inputs: every dimer's [A | K] blocks resident in HBM (generation untimed)
-    buf, offs = synth.device.workload_blocks(w)
+    if args.alias_blocks:
+        buf, offs0 = synth.device.workload_blocks(w, dimers=[0])
+        offs = [offs0[0]] * w.n_dimers
+    else:
+        buf, offs = synth.device.workload_blocks(w)
     torch.cuda.synchronize()
     mons = [w.monomer(X) for X in range(w.n_monomers)]
 
@@ -289,7 +296,7 @@ def our_arm(args, ws, rank, local):
     sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
     try:
         import make_lattice_oracle as golden
-        g = None if args.max_dimers else golden.load(args.workload)
+        g = None if (args.max_dimers or args.alias_blocks) else golden.load(args.workload)
     except Exception:
         g = None
     if g is not None:

@@ -46,12 +46,12 @@ __device__ __forceinline__ double to_f64(float x) { return f64_from_f32(x); }   
 //   lane b:  tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]         (C_Y column b in registers)
 //            VA[a][b] = sum_nu C_X[nu][a] tm[nu]              (C_X rows broadcast from smem)
 //   lane a:  tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
-//            VK[a][b] = sum_lam C_Y[lam][b] tk[lam]
-// Both land in shared memory as [a][b] tiles, and the FP64 part then walks the
-// v_X v_Y terms packed 32 to a warp instruction (no idle lanes when v is not a
-// multiple of 32; the FP64 pipe is the bound).  The H slices are contiguous
-// (pair-major), read with coalesced loads into a zero-padded 32 x 32 tile.
-// Per-lane sums reduce in a fixed order.
+//            for each b: VK = sum_lam C_Y[lam][b] tk[lam], then with VA[a][b] and
+//            the FP64 denominator the two energy terms of (a, b)
+// Two slice buffers per warp swap roles every pair and are filled by cp.async
+// one step ahead: H1 of this pair streams in during the H0 work, H0 of the
+// next pair during the H1 work, so the warp rarely waits on memory.  VA
+// takes the place of H0 in its buffer.  Per-lane sums reduce in a fixed order.
 constexpr int kW32Warps = 4;
 constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33)
 
@@ -61,22 +61,34 @@ constexpr size_t w32_smem_bytes()
     return 32 * 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
 }
 
-// One warp copies an nr x nc (<= 32 x 32) row-major slice into a zero-padded
-// 32 x 32 tile: lane c loads column c of every row, all 32 loads issued before
-// the first store, so the slice costs one memory round trip, not 32.
+// One warp starts the asynchronous copy of an nr x nc (<= 32 x 32) row-major
+// slice into a zero-padded 32 x 32 tile (lane c copies column c of every
+// row; padding is written as zeros by the copy itself) and commits it as one
+// group of this lane's cp.async operations.
 template <typename T>
-__device__ __forceinline__ void load_slice(T* S, const T* __restrict__ h, int nr, int nc, int lane)
+__device__ __forceinline__ void prefetch_slice(T* S, const T* __restrict__ h, int nr, int nc, int lane)
 {
-    T v[32];
-    const T* p = h + lane;                  // one running address, not 32
+    const T* p = h + lane;
     const bool col = lane < nc;
-#pragma unroll
+    const unsigned dst0 = (unsigned)__cvta_generic_to_shared(S + lane);
+#pragma unroll 4
     for (int r = 0; r < 32; r++) {
-        v[r] = (r < nr && col) ? *p : T(0);
+        const bool ok = r < nr && col;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(dst0 + (unsigned)(r * 32 * sizeof(T))),
+                     "l"(ok ? p : h), "n"(sizeof(T)), "r"(ok ? (int)sizeof(T) : 0)
+                     : "memory");
         p += nc;
     }
-#pragma unroll
-    for (int r = 0; r < 32; r++) S[r * 32 + lane] = v[r];
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Wait until at most N of this lane's copy groups are in flight, then make
+// the whole warp's copies visible to the warp.
+template <int N>
+__device__ __forceinline__ void slice_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    __syncwarp();
 }
 
 template <typename T>
@@ -87,7 +99,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     const DimerDesc& d = dd[blockIdx.x];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
     const int vX = nX - oX, vY = nY - oY;
-    const int rows = nX * nY, pairs = oX * oY, nab = vX * vY;
+    const int rows = nX * nY, pairs = oX * oY;
     const T* CX = C + d.cX;
     const T* CY = C + d.cY;
     const double* eX = Epool + d.eX;
@@ -100,9 +112,13 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     T* CXT = reinterpret_cast<T*>(eab + 32 * 32);             // [a][nu], zero padded
     T* CYT = CXT + 32 * 32;                                   // [b][sig]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* S = CYT + 32 * 32 + warp * (2 * kW32Slab);             // integral slice [32][32], then VK [a][b]
-    T* VA = S + kW32Slab;                                     // [a][b], stride 33
+    T* const buf = CYT + 32 * 32 + warp * (2 * kW32Slab);     // two slice buffers of kW32Slab
 
+    // the warp's first pair streams in while the block stages C and the energies
+    if (warp < pairs) {
+        prefetch_slice(buf, H0 + (long long)warp * rows, nX, nY, lane);
+        prefetch_slice(buf + kW32Slab, H1 + (long long)warp * rows, nY, nX, lane);
+    }
     {
         // all loads first (independent, in flight together), then the stores
         constexpr int kPer = 32 * 32 / (kW32Warps * 32);
@@ -126,15 +142,17 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     }
     __syncthreads();
 
-    // this lane's first packed (a, b) term and the step of 32 terms
-    const int lane0_a = lane / vY, lane0_b = lane % vY, step_q = 32 / vY, step_r = 32 % vY;
+    const bool live = lane < vX;
     double ej = 0.0, ek = 0.0;
-    for (int pr = warp; pr < pairs; pr += kW32Warps) {
+    int x = 0;                                   // buffer holding this pair's H0
+    for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
         const int i = pr / oY, j = pr % oY;
         const double eij = eX[i] + eY[j];
-        // ---- (i a|j b): S[nu][sig] = H0 slice; lane b
-        load_slice(S, H0 + (long long)pr * rows, nX, nY, lane);
-        __syncwarp();
+        const int nx = pr + kW32Warps;           // next pair of this warp
+        T* SX = x ? buf + kW32Slab : buf;        // H0, then VA [a][b] (stride 33)
+        T* SY = x ? buf : buf + kW32Slab;        // H1, then the next pair's H0
+        // ---- (i a|j b): SX[nu][sig] = H0 slice; lane b
+        slice_wait<1>();
         {
             T cy[32], tm[32];
 #pragma unroll
@@ -143,23 +161,20 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             for (int nu = 0; nu < 32; nu++) {
                 T acc = 0;
 #pragma unroll
-                for (int m = 0; m < 32; m++) acc = fma(S[nu * 32 + m], cy[m], acc);
+                for (int m = 0; m < 32; m++) acc = fma(SX[nu * 32 + m], cy[m], acc);
                 tm[nu] = acc;
             }
+            __syncwarp();                        // H0 consumed: VA takes its place
 #pragma unroll 4
             for (int a = 0; a < 32; a++) {
                 T acc = 0;
 #pragma unroll
                 for (int nu = 0; nu < 32; nu++) acc = fma(CXT[a * 32 + nu], tm[nu], acc);
-                VA[a * 33 + lane] = acc;
+                SX[a * 33 + lane] = acc;
             }
         }
-        __syncwarp();
-        // ---- (i b|j a): S[lam][nu] = H1 slice; lane a.  The barrier keeps the
-        // slice's loads from being hoisted above the VA work (register pressure).
-        asm volatile("" ::: "memory");
-        load_slice(S, H1 + (long long)pr * rows, nY, nX, lane);
-        __syncwarp();
+        // ---- (i b|j a): SY[lam][nu] = H1 slice; lane a
+        slice_wait<0>();
         {
             T cx[32], tk[32];
 #pragma unroll
@@ -168,37 +183,30 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             for (int lam = 0; lam < 32; lam++) {
                 T acc = 0;
 #pragma unroll
-                for (int m = 0; m < 32; m++) acc = fma(S[lam * 32 + m], cx[m], acc);
+                for (int m = 0; m < 32; m++) acc = fma(SY[lam * 32 + m], cx[m], acc);
                 tk[lam] = acc;
             }
-            __syncwarp();                        // S is overwritten with VK below
+            __syncwarp();                        // H1 consumed: the next pair's H0 streams into SY
+            if (nx < pairs) prefetch_slice(SY, H0 + (long long)nx * rows, nX, nY, lane);
+            // ---- FP64 denominators and energy sums, lane a over b
 #pragma unroll 1
             for (int b = 0; b < vY; b++) {
-                T v0 = 0, v1 = 0;                    // two chains of 16
+                T v0 = 0, v1 = 0;                // two chains of 16
 #pragma unroll
                 for (int lam = 0; lam < 32; lam += 2) {
                     v0 = fma(CYT[b * 32 + lam], tk[lam], v0);
                     v1 = fma(CYT[b * 32 + lam + 1], tk[lam + 1], v1);
                 }
-                S[lane * 33 + b] = v0 + v1;
+                if (live) {
+                    const double va = to_f64(SX[lane * 33 + b]);
+                    const double t = div_newton<kSteps<T>>(va, eij - eab[lane * 32 + b]);   // v D
+                    ej = fma(t, va, ej);
+                    ek = fma(t, to_f64(v0 + v1), ek);
+                }
             }
         }
-        __syncwarp();
-        // ---- FP64 denominators and energy sums over the packed (a, b) terms:
-        // lane l takes terms l, l + 32, ...; (a, b) advance by (q, r), 32 = q vY + r
-        {
-            int a = lane0_a, b = lane0_b;
-            for (int idx = lane; idx < nab; idx += 32) {
-                const double va = to_f64(VA[a * 33 + b]);
-                const double t = div_newton<kSteps<T>>(va, eij - eab[a * 32 + b]);   // v D
-                ej = fma(t, va, ej);
-                ek = fma(t, to_f64(S[a * 33 + b]), ek);
-                b += step_r;
-                a += step_q;
-                if (b >= vY) { b -= vY; a++; }
-            }
-        }
-        __syncwarp();
+        __syncwarp();                            // VA consumed: the next pair's H1 streams into SX
+        if (nx < pairs) prefetch_slice(SX, H1 + (long long)nx * rows, nY, nX, lane);
     }
     __shared__ double red[2][kW32Warps];
     ej = warp_sum(ej);

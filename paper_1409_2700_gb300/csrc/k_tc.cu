@@ -640,7 +640,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // unless it lies more than 2^8 below its row's largest.  The four levels
 //     L0 = A0.B0, L1 = A0.B1 + A1.B0, L2 = A0.B2 + A1.B1 + A2.B0,
 //     L3 = A0.B3 + A1.B2 + A2.B1 + A3.B0
-// (ten MMAs per K step, into four 16-column TMEM slots) are sums of at most
+// (four MMAs per K step: A_u times the stacked digit planes B_0..B_(3-u) of
+// C_Y, N = 64, 48, 32, 16, landing in the four 16-column TMEM slots of levels
+// u..3) are sums of at most
 // 4 n2 integer products, each below 2^16: for n2 <= 128 every partial sum is
 // an integer below 2^24, so the tensor core adds them without rounding.  The
 // epilogue forms T = 2^(e+f-14) (L0 + 2^-8 L1 + 2^-16 L2 + 2^-24 L3) in FP32
@@ -661,7 +663,9 @@ constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
 constexpr int kEpiWarp0 = 2 + kConvWarps;
 constexpr int kRankThreads = (kEpiWarp0 + 4) * 32;
 constexpr int kOBig = 16;         // TMEM accumulators: o_X, o_Y <= 16
-constexpr int kCxFloats = 128 * kOBig; // C_X occupied rows of one item (n0 <= 128)
+// C_X occupied rows of one item (n0 <= 128), per parity: the register
+// accumulator kernel stages kOB columns, the TMEM one kOBig.
+__host__ __device__ constexpr int cx_floats(bool big) { return 128 * (big ? kOBig : kOB); }
 
 struct __align__(8) RankShared {
     unsigned long long full_f[8], empty_f[8];
@@ -684,6 +688,14 @@ __host__ __device__ constexpr int n_units() { return (BIG ? 256 : 512) / unit_co
 // Shared bytes of the A ring (two slots; BF16x3 uses two tiles per slot) and
 // of the BF16x3 unit scales (row scales 128 + column scales 16 per unit).
 __host__ __device__ constexpr size_t a_ring_bytes(int kind) { return 2 * (size_t)kABytes * (kind == TC_BF16X3 ? 2 : 1); }
+// Bytes of one parity of the B operand (C_Y's occupied columns) for an item
+// of kcs_max p2 chunks.  TF32: per chunk two 16-row planes (hi, lo).  BF16x3:
+// per pair of chunks one 64-row tile, row 16 v + j = digit v of column j,
+// chunk kc in bytes 64 (kc % 2) .. +63 of the row.
+__host__ __device__ constexpr size_t w_stride_bytes(int kind, int kcs_max)
+{
+    return kind == TC_BF16X3 ? (size_t)((kcs_max + 1) / 2) * 64 * 128 : (size_t)kcs_max * 2 * kNT * 128;
+}
 __host__ __device__ constexpr size_t fx_scale_bytes(int kind)
 {
     return kind == TC_BF16X3 ? kFxUnits * (128 + kNT) * 4 + 2 * 16 * kNT * 4 : 0;
@@ -714,11 +726,29 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
 {
     return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
 }
-// Scale 2^(31 - e) that brings a vector whose largest binary exponent field
-// is emax (FP64: e = emax - 1023) to 32-bit fixed point; 0 below 2^-96.
-__device__ __forceinline__ float fx_scale_f64(int emax)
+// An FP64 row element scaled to the row's 32-bit fixed point, y = x 2^(31-e)
+// with e = emax - 1023, as FP32 (mantissa rounded half away from zero),
+// built from the bit fields on the integer pipes: the double's exponent and
+// leading 23 mantissa bits shifted into FP32 position, the exponent offset
+// 158 - emax added modulo 2^9 (exact, the result lies in [1, 158]), the sign
+// put back.  Elements below 2^-157 of the row's largest (and every element of
+// a row marked invalid) become 0.
+struct FxRow {
+    unsigned add;   // (158 - emax) << 23, modulo 2^32
+    unsigned thr;   // |hi| below this flushes to 0
+};
+__device__ __forceinline__ FxRow fx_row(int emax, bool valid)
 {
-    return (emax >= 927 && emax <= 1180) ? __uint_as_float((unsigned)(1181 - emax) << 23) : 0.f;
+    FxRow f;
+    f.add = (unsigned)((158 - emax) & 511) << 23;
+    f.thr = valid ? (unsigned)max(1, emax - 157) << 20 : 0xFFFFFFFFu;
+    return f;
+}
+__device__ __forceinline__ float fx_y(unsigned lo, unsigned hi, FxRow f)
+{
+    unsigned w = __funnelshift_l(lo, hi, 3) + f.add + ((lo >> 28) & 1u);
+    w = (w & 0x7FFFFFFFu) | (hi & 0x80000000u);
+    return (hi & 0x7FFFFFFFu) < f.thr ? 0.f : __uint_as_float(w);
 }
 // The same for an FP32 vector (f = fmax - 127).
 __device__ __forceinline__ float fx_scale_f32(int fmax)
@@ -861,7 +891,7 @@ __device__ __forceinline__ int row_emax(const unsigned char* Fr, unsigned f_stag
 // 8 p2 each: tile 1 holds [d0 | d1] (bytes 0-63 / 64-127), tile 2 [d2 | d3].
 __device__ __forceinline__ void convert_row_fx(const double* __restrict__ F, unsigned char* __restrict__ A1,
                                                unsigned char* __restrict__ A2, const ConvRow& cr, int n3, int c0,
-                                               float scale)
+                                               FxRow fr)
 {
     const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
 #pragma unroll
@@ -874,7 +904,7 @@ __device__ __forceinline__ void convert_row_fx(const double* __restrict__ F, uns
 #pragma unroll
             for (int u = 0; u < 2; u++) {
                 const uint2 b = dw[(c * 8 + e + u) * n3];
-                digits4(cr.valid ? f32_from_f64_bits(b.x, b.y) * scale : 0.f, d[u]);
+                digits4(fx_y(b.x, b.y, fr), d[u]);
             }
 #pragma unroll
             for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(d[0][k], d[1][k]);
@@ -902,12 +932,13 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
     unsigned char* Fr = base;
     unsigned char* Ar = Fr + (size_t)P.sf * P.f_stage_bytes;
     unsigned char* Wr = Ar + a_ring_bytes(KIND);
-    const int wstride = P.kcs_max * 2 * kNT * 128;      // bytes per parity
+    const int wstride = (int)w_stride_bytes(KIND, P.kcs_max);   // bytes per parity
     float* cxs = reinterpret_cast<float*>(Wr + 2 * wstride);
-    float* exps = cxs + 2 * kCxFloats;                  // BF16x3: [unit][128 rows] row scales
+    constexpr int CXF = cx_floats(BIG);
+    float* exps = cxs + 2 * CXF;                        // BF16x3: [unit][128 rows] row scales
     float* scu = exps + kFxUnits * 128;                 //          [unit][16 columns] column scales
     int* colx = reinterpret_cast<int*>(scu + kFxUnits * kNT);   // [parity][16 parts][16 columns] exponents
-    RankShared* sh = reinterpret_cast<RankShared*>(reinterpret_cast<unsigned char*>(cxs + 2 * kCxFloats) +
+    RankShared* sh = reinterpret_cast<RankShared*>(reinterpret_cast<unsigned char*>(cxs + 2 * CXF) +
                                                    fx_scale_bytes(KIND));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -975,6 +1006,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             unsigned gA = 0, gS = 0, li = 0;
             bool any = false, ok = true;
             const unsigned idesc = make_idesc(KIND, kNT);
+            const unsigned idesc_fx[4] = {make_idesc(KIND, 4 * kNT), make_idesc(KIND, 3 * kNT),
+                                          make_idesc(KIND, 2 * kNT), make_idesc(KIND, kNT)};
             for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
                 const TcItem item = P.items[it];
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
@@ -991,7 +1024,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                             if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
                             tc_fence_after();
                             const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
-                            unsigned char* wk = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
+                            unsigned char* wk = FX ? Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128
+                                                   : Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                             const unsigned long long b0 = sw128_desc(wk);
                             const unsigned long long b1 = sw128_desc(wk + kNT * 128);
                             if (KIND == TC_TF32) {
@@ -1002,23 +1036,18 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                     tc_mma<KIND>(dt, adesc + 2 * k, b1 + 2 * k, idesc, 1u);
                                 }
                             } else {
-                                // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3]; B plane 0 =
-                                // [d0 | d1], plane 1 = [d2 | d3].  Level l (slot l) takes the products
-                                // A_u B_(l-u): one, two, three and four MMAs.
+                                // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3]; the B tile
+                                // stacks C_Y's digits B0..B3 as rows 0-63.  A_u x [B0..B(3-u)] lands
+                                // A_u B_v in the slot of level u + v; A0's MMA opens all four slots.
                                 const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
+                                const unsigned long long bk = b0 + (unsigned long long)((kc & 1) * 4);
 #pragma unroll
                                 for (int k = 0; k < 2; k++) {
                                     const unsigned acc = (kc > 0 || k > 0) ? 1u : 0u;
-                                    const unsigned long long A[4] = {adesc + 2 * k, adesc + 4 + 2 * k, a2 + 2 * k,
-                                                                     a2 + 4 + 2 * k};
-                                    const unsigned long long B[4] = {b0 + 2 * k, b0 + 4 + 2 * k, b1 + 2 * k,
-                                                                     b1 + 4 + 2 * k};
-#pragma unroll
-                                    for (int l = 0; l < 4; l++)
-#pragma unroll
-                                        for (int u = 0; u <= l; u++)
-                                            tc_mma<KIND>(dt + (unsigned)(l * kNT), A[u], B[l - u], idesc,
-                                                         u == 0 ? acc : 1u);
+                                    tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[0], acc);
+                                    tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[1], 1u);
+                                    tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
+                                    tc_mma<KIND>(dt + 3 * kNT, a2 + 4 + 2 * k, bk + 2 * k, idesc_fx[3], 1u);
                                 }
                             }
                             tc_commit(&sh->empty_a[as]);
@@ -1075,7 +1104,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 }
             }
             for (int kc = 0; kc < g.kcs; kc++) {
-                unsigned char* W0 = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
+                unsigned char* W0 = FX ? Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128
+                                       : Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                 unsigned char* W1 = W0 + kNT * 128;
                 if (KIND == TC_TF32) {
                     for (int task = ct; task < kNT * 8; task += 32 * kConvWarps) {
@@ -1111,12 +1141,10 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
 #pragma unroll
                             for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(dg[0][k], dg[1][k]);
                         }
-                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, c)) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
-                        *reinterpret_cast<uint4*>(W0 + sw128_off(j, 4 + c)) =
-                            make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
-                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
-                        *reinterpret_cast<uint4*>(W1 + sw128_off(j, 4 + c)) =
-                            make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
+#pragma unroll
+                        for (int v = 0; v < 4; v++)
+                            *reinterpret_cast<uint4*>(W0 + sw128_off(v * kNT + j, (kc & 1) * 4 + c)) =
+                                make_uint4(w[v][0], w[v][1], w[v][2], w[v][3]);
                     }
                 }
             }
@@ -1149,7 +1177,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                             ok = mbar_wait(&sh->full_f[(gF + kc) % P.sf], ((gF + kc) / P.sf) & 1, abort, P.status, 16);
                         if (!ok) break;
                         const int emax = row_emax(Fr, P.f_stage_bytes, P.sf, gF, g.kcs, cr, g.n3, c0);
-                        const float xscale = fx_scale_f64(emax);
+                        const FxRow xrow = fx_row(emax, cr.valid);
                         const int su = gU % NS;
                         if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22))) break;
                         if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
@@ -1163,7 +1191,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                 break;
                             unsigned char* At = Ar + (size_t)as * ASLOT;
                             convert_row_fx(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes), At,
-                                           At + kABytes, cr, g.n3, c0, xscale);
+                                           At + kABytes, cr, g.n3, c0, xrow);
                             fence_async_smem();
                             __syncwarp();
                             if (lane == 0) {
@@ -1188,7 +1216,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
             const int par = li & 1;
-            float* cx = cxs + par * kCxFloats;
+            float* cx = cxs + par * CXF;
             // stage C_X's occupied columns, row p0 = e, for this item
             if (!(ok = mbar_wait(&sh->cx_empty[par], ((li >> 1) & 1) ^ 1, abort, P.status, 19))) break;
             if (e < g.n0) {
@@ -1376,8 +1404,8 @@ size_t tc_work_bytes(TcKind kind, const DimerDesc* h, int nd)
 // deepest ring that fits.
 static size_t fixed_smem(TcKind kind, int variant, int kcs_max, unsigned w_stage_bytes)
 {
-    return variant >= 1 ? 1024 + a_ring_bytes(kind) + 2 * (size_t)kcs_max * 2 * kNT * 128 +
-                              2 * (size_t)kCxFloats * 4 + fx_scale_bytes(kind) + sizeof(RankShared)
+    return variant >= 1 ? 1024 + a_ring_bytes(kind) + 2 * w_stride_bytes(kind, kcs_max) +
+                              2 * (size_t)cx_floats(variant == 2) * 4 + fx_scale_bytes(kind) + sizeof(RankShared)
                         : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)w_stage_bytes + sizeof(TcShared);
 }
 
