@@ -228,18 +228,16 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 //   TmK [lam][a] = sum_nu  H1[lam][nu]  C_X[nu][oX+a]       (nY x vX, K = nX)
 //   VA  [a][b]   = sum_nu  C_X[nu][oX+a] Tm[nu][b]          (vX x vY, K = nX)
 //   VKT [a][b]   = sum_lam TmK[lam][a]  C_Y[lam][oY+b]      (vX x vY, K = nY)
-// run by 256 threads as a 16 x 16 grid, each thread accumulating an 8 x TN
-// block of outputs (rows ty + 16 i, columns tx + 16 j) in registers: per K
-// step 8 + TN loads feed 8 TN FMAs.  H slices and Tm/TmK live in shared
-// memory, the C columns are read through L1.  VA and VKT share the thread
-// mapping, so each thread meets its own (a, b) terms for the FP64 epilogue
-// (VA goes through shared memory to free its registers).  One CTA runs a
-// range of pairs of one dimer; its FP64 partial sums are written per task and
-// added in task order by k_finish_sum.
+// Each GEMM's M x N outputs are cut into 8 x 4 blocks dealt round-robin to the
+// 256 threads, so small and ragged shapes keep the threads on useful work;
+// a thread accumulates its block in registers (per K step 12 loads feed 32
+// FMAs).  H slices and Tm/TmK live in shared memory, the C columns are read
+// through L1.  VA and VKT use the same blocks, so each thread meets its own
+// (a, b) terms for the FP64 epilogue (VA goes through shared memory to free
+// its registers).  One CTA runs a range of pairs of one dimer; its FP64
+// partial sums are written per task and added in task order by k_finish_sum.
 constexpr int kTThreads = 256;
-
-template <typename T>
-__host__ __device__ constexpr int tiled_tn() { return sizeof(T) == 8 ? 4 : 8; }   // FP64 keeps 32 accumulators
+constexpr int kTM = 8, kTN = 4;
 
 template <typename T>
 size_t tiled_smem_bytes(int max_ao)
@@ -248,30 +246,30 @@ size_t tiled_smem_bytes(int max_ao)
     return (n * n + 2 * n * n) * sizeof(T) + 2 * n * sizeof(double) + 64;
 }
 
-// acc[i][j] = sum_k A(ty + 16 i, k) B(k, n0 + tx + 16 j) over rows < M, columns < N.
-template <typename T, int TN, typename FA, typename FB>
-__device__ __forceinline__ void mm_tile(T (&acc)[8][TN], int M, int N, int K, int n0, int ty, int tx, FA A, FB B)
+// acc[i][j] = sum_k A(m0 + i, k) B(k, n0 + j) over rows < M, columns < N.
+template <typename T, typename FA, typename FB>
+__device__ __forceinline__ void mm_block(T (&acc)[kTM][kTN], int m0, int n0, int M, int N, int K, FA A, FB B)
 {
 #pragma unroll
-    for (int i = 0; i < 8; i++)
+    for (int i = 0; i < kTM; i++)
 #pragma unroll
-        for (int j = 0; j < TN; j++) acc[i][j] = T(0);
-    bool mok[8], nok[TN];
+        for (int j = 0; j < kTN; j++) acc[i][j] = T(0);
+    bool mok[kTM], nok[kTN];
 #pragma unroll
-    for (int i = 0; i < 8; i++) mok[i] = ty + 16 * i < M;
+    for (int i = 0; i < kTM; i++) mok[i] = m0 + i < M;
 #pragma unroll
-    for (int j = 0; j < TN; j++) nok[j] = n0 + tx + 16 * j < N;
+    for (int j = 0; j < kTN; j++) nok[j] = n0 + j < N;
 #pragma unroll 2
     for (int k = 0; k < K; k++) {
-        T a[8], b[TN];
+        T a[kTM], b[kTN];
 #pragma unroll
-        for (int i = 0; i < 8; i++) a[i] = mok[i] ? A(ty + 16 * i, k) : T(0);
+        for (int i = 0; i < kTM; i++) a[i] = mok[i] ? A(m0 + i, k) : T(0);
 #pragma unroll
-        for (int j = 0; j < TN; j++) b[j] = nok[j] ? B(k, n0 + tx + 16 * j) : T(0);
+        for (int j = 0; j < kTN; j++) b[j] = nok[j] ? B(k, n0 + j) : T(0);
 #pragma unroll
-        for (int i = 0; i < 8; i++)
+        for (int i = 0; i < kTM; i++)
 #pragma unroll
-            for (int j = 0; j < TN; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < kTN; j++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
 }
 
@@ -298,7 +296,6 @@ __global__ void __launch_bounds__(kTThreads)
 k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tasks, const T* __restrict__ C,
                const double* __restrict__ Epool, const T* __restrict__ H, double* __restrict__ part)
 {
-    constexpr int TN = tiled_tn<T>();
     const FinTask tk = tasks[blockIdx.x];
     const DimerDesc& d = dd[tk.dimer];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
@@ -317,63 +314,65 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     T* S = reinterpret_cast<T*>(eYv + nY);                    // H slice [rows], then VA [vX][vY]
     T* Tm = S + rows;                                         // [nX][vY]
     T* TmK = Tm + nX * vY;                                    // [nY][vX]
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int tid = threadIdx.x;
     for (int k = tid; k < vX; k += kTThreads) eXv[k] = eX[oX + k];
     for (int k = tid; k < vY; k += kTThreads) eYv[k] = eY[oY + k];
+    // 8 x 4 output blocks of each GEMM shape
+    const int bn_vY = (vY + kTN - 1) / kTN, bn_vX = (vX + kTN - 1) / kTN;
+    const int nb1 = ((nX + kTM - 1) / kTM) * bn_vY;          // Tm
+    const int nb3 = ((nY + kTM - 1) / kTM) * bn_vX;          // TmK
+    const int nb2 = ((vX + kTM - 1) / kTM) * bn_vY;          // VA, VKT
 
     double ej = 0.0, ek = 0.0;
     for (int pr = tk.pr0; pr < tk.pr1; pr++) {
         const int i = pr / oY, j = pr % oY;
         const double eij = eX[i] + eY[j];
-        T acc[8][TN];
+        T acc[kTM][kTN];
         // ---- Tm = H0 C_Y(virtual)
         copy_slice(S, H0 + (long long)pr * rows, rows, tid);
         __syncthreads();
-        for (int n0 = 0; n0 < vY; n0 += 16 * TN) {
-            mm_tile<T, TN>(acc, nX, vY, nY, n0, ty, tx, [&](int m, int k) { return S[m * nY + k]; },
-                           [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
+        for (int blk = tid; blk < nb1; blk += kTThreads) {
+            const int m0 = (blk / bn_vY) * kTM, n0 = (blk % bn_vY) * kTN;
+            mm_block<T>(acc, m0, n0, nX, vY, nY, [&](int m, int k) { return S[m * nY + k]; },
+                        [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
 #pragma unroll
-            for (int a = 0; a < 8; a++)
+            for (int a = 0; a < kTM; a++)
 #pragma unroll
-                for (int b = 0; b < TN; b++) {
-                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
-                    if (m < nX && n < vY) Tm[m * vY + n] = acc[a][b];
-                }
+                for (int b = 0; b < kTN; b++)
+                    if (m0 + a < nX && n0 + b < vY) Tm[(m0 + a) * vY + n0 + b] = acc[a][b];
         }
         __syncthreads();
         // ---- TmK = H1 C_X(virtual)
         copy_slice(S, H1 + (long long)pr * rows, rows, tid);
         __syncthreads();
-        for (int n0 = 0; n0 < vX; n0 += 16 * TN) {
-            mm_tile<T, TN>(acc, nY, vX, nX, n0, ty, tx, [&](int m, int k) { return S[m * nX + k]; },
-                           [&](int k, int n) { return __ldg(CX + k * nX + oX + n); });
+        for (int blk = tid; blk < nb3; blk += kTThreads) {
+            const int m0 = (blk / bn_vX) * kTM, n0 = (blk % bn_vX) * kTN;
+            mm_block<T>(acc, m0, n0, nY, vX, nX, [&](int m, int k) { return S[m * nX + k]; },
+                        [&](int k, int n) { return __ldg(CX + k * nX + oX + n); });
 #pragma unroll
-            for (int a = 0; a < 8; a++)
+            for (int a = 0; a < kTM; a++)
 #pragma unroll
-                for (int b = 0; b < TN; b++) {
-                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
-                    if (m < nY && n < vX) TmK[m * vX + n] = acc[a][b];
-                }
+                for (int b = 0; b < kTN; b++)
+                    if (m0 + a < nY && n0 + b < vX) TmK[(m0 + a) * vX + n0 + b] = acc[a][b];
         }
         __syncthreads();
-        // ---- VA, VKT and the FP64 epilogue, one column band at a time
-        for (int n0 = 0; n0 < vY; n0 += 16 * TN) {
-            mm_tile<T, TN>(acc, vX, vY, nX, n0, ty, tx, [&](int m, int k) { return __ldg(CX + k * nX + oX + m); },
-                           [&](int k, int n) { return Tm[k * vY + n]; });
+        // ---- VA, VKT and the FP64 epilogue, block by block
+        for (int blk = tid; blk < nb2; blk += kTThreads) {
+            const int m0 = (blk / bn_vY) * kTM, n0 = (blk % bn_vY) * kTN;
+            mm_block<T>(acc, m0, n0, vX, vY, nX, [&](int m, int k) { return __ldg(CX + k * nX + oX + m); },
+                        [&](int k, int n) { return Tm[k * vY + n]; });
 #pragma unroll
-            for (int a = 0; a < 8; a++)
+            for (int a = 0; a < kTM; a++)
 #pragma unroll
-                for (int b = 0; b < TN; b++) {
-                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
-                    if (m < vX && n < vY) S[m * vY + n] = acc[a][b];   // own elements only
-                }
-            mm_tile<T, TN>(acc, vX, vY, nY, n0, ty, tx, [&](int m, int k) { return TmK[k * vX + m]; },
-                           [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
+                for (int b = 0; b < kTN; b++)
+                    if (m0 + a < vX && n0 + b < vY) S[(m0 + a) * vY + n0 + b] = acc[a][b];   // own elements only
+            mm_block<T>(acc, m0, n0, vX, vY, nY, [&](int m, int k) { return TmK[k * vX + m]; },
+                        [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
 #pragma unroll
-            for (int a = 0; a < 8; a++)
+            for (int a = 0; a < kTM; a++)
 #pragma unroll
-                for (int b = 0; b < TN; b++) {
-                    const int m = ty + 16 * a, n = n0 + tx + 16 * b;
+                for (int b = 0; b < kTN; b++) {
+                    const int m = m0 + a, n = n0 + b;
                     if (m < vX && n < vY) {
                         const double va = to_f64(S[m * vY + n]);
                         const double t = div_newton<kSteps<T>>(va, eij - (eXv[m] + eYv[n]));   // v D

@@ -887,6 +887,48 @@ __device__ __forceinline__ int row_emax(const unsigned char* Fr, unsigned f_stag
     return cr.valid ? emax : 0;
 }
 
+// BF16x3, all p2 in one box (n2 <= 32): the thread's 16 values are loaded
+// once; the row's largest magnitude is their bitwise maximum (|x| orders like
+// its bit pattern), combined with the partner lane; then the digit planes as
+// in convert_row_fx.  Returns the row's exponent field.
+__device__ __forceinline__ int convert_row_fx1(const double* __restrict__ F, unsigned char* __restrict__ A1,
+                                               unsigned char* __restrict__ A2, const ConvRow& cr, int n3, int c0)
+{
+    const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
+    uint2 v[2][8];
+    unsigned m = 0;
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            v[q][e] = dw[((c0 + 2 * q) * 8 + e) * n3];
+            m = max(m, v[q][e].y & 0x7FFFFFFFu);
+        }
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    const int emax = cr.valid ? (int)(m >> 20) : 0;
+    const FxRow fr = fx_row(emax, cr.valid);
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int c = c0 + 2 * q;
+        unsigned w[4][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float d[2][4];
+#pragma unroll
+            for (int u = 0; u < 2; u++) digits4(fx_y(v[q][e + u].x, v[q][e + u].y, fr), d[u]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(d[0][k], d[1][k]);
+        }
+        *reinterpret_cast<uint4*>(A1 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
+        *reinterpret_cast<uint4*>(A1 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
+            make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
+        *reinterpret_cast<uint4*>(A2 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
+        *reinterpret_cast<uint4*>(A2 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
+            make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
+    }
+    return emax;
+}
+
 // BF16x3: row r of one chunk as four digit planes, chunks c0 and c0 + 2 of
 // 8 p2 each: tile 1 holds [d0 | d1] (bytes 0-63 / 64-127), tile 2 [d2 | d3].
 __device__ __forceinline__ void convert_row_fx(const double* __restrict__ F, unsigned char* __restrict__ A1,
@@ -1176,9 +1218,36 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         for (int kc = 0; kc < g.kcs && ok; kc++)
                             ok = mbar_wait(&sh->full_f[(gF + kc) % P.sf], ((gF + kc) / P.sf) & 1, abort, P.status, 16);
                         if (!ok) break;
+                        const int su = gU % NS;
+                        if (g.kcs == 1) {
+                            // one box holds the row: fused load, maximum and digits
+                            const int s = gF % P.sf;
+                            const int as = gA & 1;
+                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
+                                break;
+                            unsigned char* At = Ar + (size_t)as * ASLOT;
+                            const int emax = convert_row_fx1(
+                                reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes), At, At + kABytes, cr,
+                                g.n3, c0);
+                            fence_async_smem();
+                            __syncwarp();
+                            if (lane == 0) {
+                                mbar_arrive(&sh->full_a[as]);
+                                mbar_arrive(&sh->empty_f[s]);
+                            }
+                            gA++;
+                            if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22)))
+                                break;
+                            if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
+                            if (ct < kNT) scu[su * kNT + ct] = sc_mine;
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&sh->exp_full[su]);
+                            gF += 1;
+                            gU++;
+                            continue;
+                        }
                         const int emax = row_emax(Fr, P.f_stage_bytes, P.sf, gF, g.kcs, cr, g.n3, c0);
                         const FxRow xrow = fx_row(emax, cr.valid);
-                        const int su = gU % NS;
                         if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22))) break;
                         if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
                         if (ct < kNT) scu[su * kNT + ct] = sc_mine;
