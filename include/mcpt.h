@@ -100,7 +100,7 @@ mcpt_status mcpt_create(mcpt_handle *out, const mcpt_options *opt);
  *    monomer Hartree-Fock solution of Sec. III's program flow, step 1);
  * eps: host pointer to nao FP64 orbital energies (occupied first).
  * Both are copied before the call returns.
- * Errors: EINVAL if nao < 2 or nao > 256, nocc not in [1, nao-1], a pointer
+ * Errors: EINVAL if nao < 2 or nao > 128, nocc not in [1, nao-1], a pointer
  * is NULL, or (validate) a value is not finite; ESTATE after mcpt_destroy. */
 mcpt_status mcpt_add_monomer(mcpt_handle h, const double *C, const double *eps,
                              int nao, int nocc, int *id_out);
@@ -126,7 +126,9 @@ mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p);
  * stream.  Asynchronous: returns once the work is enqueued.  Re-running
  * recomputes everything.
  * Errors: ESTATE (no dimers), EUNSUPPORTED (precision cannot handle a dimer's
- * sizes: tensor-core forms need even nX, nY <= 128 and nocc_X*nocc_Y <= 256),
+ * sizes: tensor-core forms need even nX, nY <= 128, the FP64 form nX, nY <= 96;
+ * tensor-core dimers with more than 16 occupied orbitals on a monomer run as
+ * blocks of at most 16 x 16 occupied pairs, each reading the integrals),
  * ENOMEM, ECUDA, ETIMEOUT. */
 mcpt_status mcpt_run(mcpt_handle h);
 

@@ -83,6 +83,8 @@ struct mcpt_ctx {
     size_t capH = 0;
     void* dWork = nullptr;
     size_t capWork = 0;
+    int* dFold = nullptr;            // split dimers: (dimer, first block slot, blocks)
+    size_t capFold = 0;
     void* dFin = nullptr;            // second-half tasks of waves above 32 AO (+ first-task indices)
     size_t capFin = 0;
     double* dPart = nullptr;         // their FP64 partial sums
@@ -111,6 +113,7 @@ struct mcpt_ctx {
         int first = 0, count = 0;
         std::vector<Wave> waves;
         double alg_bytes = 0, alg_flops = 0, alg_flops_half = 0;
+        int nfold = 0;                     // split dimers whose block results are folded
         cudaGraphExec_t graph = nullptr;   // the plan's launch sequence, captured on first use
         int graph_launches = 0;
     } plan;
@@ -241,9 +244,6 @@ mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY, int oX, int oY)
             return fail(h, MCPT_EUNSUPPORTED,
                         "dimer %d: tensor-core forms need even AO counts <= %d (got %d, %d)", d,
                         kMaxAOTensor, nX, nY);
-        if (oX * oY > kMaxPairsTensor)
-            return fail(h, MCPT_EUNSUPPORTED, "dimer %d: tensor-core forms need nocc_X*nocc_Y <= %d", d,
-                        kMaxPairsTensor);
         return MCPT_OK;
     }
     return fail(h, MCPT_EINVAL, "unknown precision");
@@ -621,8 +621,10 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         P.graph = nullptr;
     }
 
-    h->hDesc.resize(count);
+    h->hDesc.clear();
     std::vector<std::pair<int, int>> waves;   // [begin, end) into hDesc
+    std::vector<int> fold;                    // split dimers: (dimer, first block slot, blocks)
+    int nblk_extra = 0;                       // result slots of blocks past the D dimers
     size_t wave_h = 0, max_wave_h = 0;
     int wbeg = 0;
     double alg_bytes = 0.0, alg_flops = 0.0, alg_flops_half = 0.0;
@@ -633,39 +635,77 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         const MonomerRec& mY = h->mons[r.Y];
         mcpt_status st = check_supported(h, d, mX.nao, mY.nao, mX.nocc, mY.nocc);
         if (st) return st;
-        DimerDesc& dd = h->hDesc[k];
-        dd.E[0] = r.E[0];
-        dd.E[1] = r.E[1];
-        std::memcpy(dd.st, r.st, sizeof dd.st);
-        dd.nX = mX.nao; dd.nY = mY.nao; dd.oX = mX.nocc; dd.oY = mY.nocc;
-        dd.cX = mX.offC; dd.cY = mY.offC; dd.eX = mX.offE; dd.eY = mY.offE;
-        dd.X = r.X; dd.Y = r.Y;
-        dd.npad = npad_for(dd.oX, dd.oY);
-        dd.slot = d;
-        const size_t hb = hbytes_for(prec, dd.nX, dd.nY, dd.oX, dd.oY);
-        const size_t elem = prec == MCPT_FP64 ? 8 : 4;
-        if (k > wbeg && (wave_h + hb > h->wave_bytes || k - wbeg >= 65535)) {
-            waves.emplace_back(wbeg, k);
-            max_wave_h = std::max(max_wave_h, wave_h);
-            wbeg = k;
-            wave_h = 0;
+        DimerDesc base{};
+        base.E[0] = r.E[0];
+        base.E[1] = r.E[1];
+        std::memcpy(base.st, r.st, sizeof base.st);
+        base.nX = mX.nao; base.nY = mY.nao;
+        base.cXv = mX.offC + mX.nocc; base.cYv = mY.offC + mY.nocc;
+        base.eXv = mX.offE + mX.nocc; base.eYv = mY.offE + mY.nocc;
+        base.vX = mX.nao - mX.nocc; base.vY = mY.nao - mY.nocc;
+        base.X = r.X; base.Y = r.Y;
+        // tensor-core work items hold at most kMaxOccTensor occupied orbitals per
+        // monomer: larger occupations run as near-equal blocks of (i, j)
+        const int bx = is_tensor_form(prec) ? (mX.nocc + kMaxOccTensor - 1) / kMaxOccTensor : 1;
+        const int by = is_tensor_form(prec) ? (mY.nocc + kMaxOccTensor - 1) / kMaxOccTensor : 1;
+        if (bx * by > 1) {
+            fold.insert(fold.end(), {d, D + nblk_extra, bx * by});
         }
-        dd.h_off = (long long)(wave_h / elem);
-        wave_h += hb;
-        const double nx = dd.nX, ny = dd.nY, ox = dd.oX, oy = dd.oY, vx = nx - ox, vy = ny - oy;
+        for (int ib = 0; ib < bx; ib++)
+            for (int jb = 0; jb < by; jb++) {
+                DimerDesc dd = base;
+                const int i0 = ib * mX.nocc / bx, i1 = (ib + 1) * mX.nocc / bx;
+                const int j0 = jb * mY.nocc / by, j1 = (jb + 1) * mY.nocc / by;
+                dd.oX = i1 - i0; dd.oY = j1 - j0;
+                dd.cX = mX.offC + i0; dd.cY = mY.offC + j0;
+                dd.eX = mX.offE + i0; dd.eY = mY.offE + j0;
+                dd.npad = npad_for(dd.oX, dd.oY);
+                dd.slot = bx * by > 1 ? D + nblk_extra++ : d;
+                const size_t hb = hbytes_for(prec, dd.nX, dd.nY, dd.oX, dd.oY);
+                const size_t elem = prec == MCPT_FP64 ? 8 : 4;
+                const int kk = (int)h->hDesc.size();
+                if (kk > wbeg && (wave_h + hb > h->wave_bytes || kk - wbeg >= 65535)) {
+                    waves.emplace_back(wbeg, kk);
+                    max_wave_h = std::max(max_wave_h, wave_h);
+                    wbeg = kk;
+                    wave_h = 0;
+                }
+                dd.h_off = (long long)(wave_h / elem);
+                wave_h += hb;
+                h->hDesc.push_back(dd);
+            }
+        const double nx = mX.nao, ny = mY.nao, ox = mX.nocc, oy = mY.nocc, vx = nx - ox, vy = ny - oy;
         alg_bytes += 2.0 * nx * nx * ny * ny * 8.0;
         alg_flops += 2.0 * 2.0 * (nx * nx * ny * ny * oy + ox * nx * nx * ny * oy + ox * nx * oy * ny * vy +
                                   ox * vx * oy * vy * nx);
         alg_flops_half += 2.0 * 2.0 * (nx * nx * ny * ny * oy + ox * nx * nx * ny * oy);
     }
-    waves.emplace_back(wbeg, count);
+    const int ndesc = (int)h->hDesc.size();
+    waves.emplace_back(wbeg, ndesc);
     max_wave_h = std::max(max_wave_h, wave_h);
 
     mcpt_status st = upload_static(h);
     if (st) return st;
-    if ((st = ensure(h, &h->dDesc, &h->capDesc, count * sizeof(DimerDesc)))) return st;
+    if ((st = ensure(h, &h->dDesc, &h->capDesc, ndesc * sizeof(DimerDesc)))) return st;
     if ((st = ensure(h, &h->dH, &h->capH, max_wave_h))) return st;
-    if ((st = ensure(h, &h->dE2, &h->capE2, (size_t)2 * D * sizeof(double)))) return st;
+    if (!fold.empty() && (st = ensure(h, &h->dFold, &h->capFold, fold.size() * sizeof(int)))) return st;
+    // per-dimer results, then the results of split dimers' blocks (kept across
+    // plans: a larger array copies the dimers' results over)
+    const size_t e2_bytes = (size_t)2 * (D + nblk_extra) * sizeof(double);
+    if (h->capE2 < e2_bytes) {
+        double* old = h->dE2;
+        const size_t old_cap = h->capE2;
+        void* q = nullptr;
+        if ((st = dev_alloc(h, &q, e2_bytes))) return st;
+        if (old) {
+            CK(h, cudaMemcpyAsync(q, old, std::min(old_cap, (size_t)2 * D * sizeof(double)), cudaMemcpyDeviceToDevice,
+                                  h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            dev_free(h, old, old_cap);
+        }
+        h->dE2 = static_cast<double*>(q);
+        h->capE2 = e2_bytes;
+    }
     if ((st = ensure(h, &h->dMon, &h->capMon, (size_t)2 * N * sizeof(double) + 2 * sizeof(double)))) return st;
     h->dTot = h->dMon + 2 * N;
     std::vector<size_t> work_off;
@@ -677,7 +717,10 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         }
         if ((st = ensure(h, &h->dWork, &h->capWork, total))) return st;
     }
-    CK(h, cudaMemcpyAsync(h->dDesc, h->hDesc.data(), count * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->dDesc, h->hDesc.data(), ndesc * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
+    if (!fold.empty())
+        CK(h, cudaMemcpyAsync(h->dFold, fold.data(), fold.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    P.nfold = (int)fold.size() / 3;
 
     // second-half tasks of the waves with monomers above 32 AO: [tasks][first-task index per dimer]
     std::vector<unsigned char> fin_host;
@@ -809,6 +852,10 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
                                      tasks, wv.ntasks, part, h->stream));
         launches += wv.ntasks ? 2 : 1;
         if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
+    }
+    if (P.nfold) {
+        CK(h, launch_fold(h->dFold, P.nfold, h->dE2, h->stream));
+        launches++;
     }
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
     CK(h, launch_reduce(h->dE2, D, L, h->dMon, h->dTot, h->stream));
@@ -972,6 +1019,7 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dH);
     cudaFree(h->dWork);
     cudaFree(h->dFin);
+    cudaFree(h->dFold);
     cudaFree(h->dPart);
     cudaFree(h->dE2);
     cudaFree(h->dMon);

@@ -25,19 +25,26 @@ namespace mcpt {
 
 constexpr int kMaxAO = 256;          // any form (FP64 / FP32C)
 constexpr int kMaxAOTensor = 128;    // tensor-core forms
-constexpr int kMaxPairsTensor = 256; // nocc_X * nocc_Y for tensor-core forms
+constexpr int kMaxOccTensor = 16;    // occupied orbitals per monomer in one tensor-core work item
 
 struct DimerDesc {
     const double* E[2];   // block base of form 0 (A) and form 1 (K)
     long long st[2][3];   // element strides of axes p0, p1, p2 (axis p3 is contiguous)
-    int nX, nY, oX, oY;
-    int cX, cY;           // offsets (doubles) of C_X, C_Y in the coefficient pool
-    int eX, eY;           // offsets (doubles) of eps_X, eps_Y in the energy pool
+    int nX, nY, oX, oY;   // AO counts; occupied orbitals of this descriptor's block
+    int cX, cY;           // pool offsets of the block's first occupied column of C_X, C_Y
+    int eX, eY;           // pool offsets of the block's first occupied eps_X, eps_Y
+    int cXv, cYv;         // pool offsets of the first virtual column of C_X, C_Y
+    int eXv, eYv;         // pool offsets of the first virtual eps_X, eps_Y
+    int vX, vY;           // virtual orbital counts
+    // A dimer whose occupations exceed what one tensor-core work item holds
+    // runs as several descriptors, one per block of occupied orbitals (i, j);
+    // each covers all virtual orbitals, and their terms are added per dimer.
     int X, Y;             // monomer ids
     long long h_off;      // first-half result H: element (form f, pair i*oY+j, row) at
                           //   h_off + (f*oX*oY + i*oY + j) * nX*nY + row   (pair-major)
     int npad;             // oX*oY padded to 16: N of the Kronecker tensor-core GEMM
-    int slot;             // index of this dimer's {E_J, E_K} in the per-dimer output
+    int slot;             // index of this descriptor's {E_J, E_K} in the per-dimer output
+                          // (blocks of a split dimer: entries past the dimers, folded)
 };
 
 // Per-monomer accumulation lists: dimers touching monomer m are
@@ -79,6 +86,10 @@ cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
                                const float* Cf, const double* Epool, const float* H,
                                double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s);
+
+// Split dimers: E2[dimer] = sum, in block order, of E2[first .. first+n) for
+// each (dimer, first, n) triple of `fold` (device, 3 ints each).
+cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s);
 
 // Per-monomer halves and the compensated lattice total.
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists,

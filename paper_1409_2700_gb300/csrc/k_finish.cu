@@ -58,7 +58,7 @@ constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33
 template <typename T>
 constexpr size_t w32_smem_bytes()
 {
-    return 32 * 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
+    return 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
 }
 
 // One warp starts the asynchronous copy of an nr x nc (<= 32 x 32) row-major
@@ -98,18 +98,18 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 {
     const DimerDesc& d = dd[blockIdx.x];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
-    const int vX = nX - oX, vY = nY - oY;
+    const int vX = d.vX, vY = d.vY;
     const int rows = nX * nY, pairs = oX * oY;
-    const T* CX = C + d.cX;
-    const T* CY = C + d.cY;
-    const double* eX = Epool + d.eX;
+    const T* CXv = C + d.cXv;                 // virtual columns
+    const T* CYv = C + d.cYv;
+    const double* eX = Epool + d.eX;          // occupied energies of this block
     const double* eY = Epool + d.eY;
     const T* H0 = H + d.h_off;
     const T* H1 = H + d.h_off + (long long)pairs * rows;
 
     extern __shared__ __align__(16) unsigned char smraw[];
-    double* eab = reinterpret_cast<double*>(smraw);          // [a][b] (stride 32): e_a + e_b
-    T* CXT = reinterpret_cast<T*>(eab + 32 * 32);             // [a][nu], zero padded
+    double* eYv = reinterpret_cast<double*>(smraw);          // [b]: e_b (read as a broadcast)
+    T* CXT = reinterpret_cast<T*>(eYv + 32);                  // [a][nu], zero padded
     T* CYT = CXT + 32 * 32;                                   // [b][sig]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* const buf = CYT + 32 * 32 + warp * (2 * kW32Slab);     // two slice buffers of kW32Slab
@@ -123,31 +123,30 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
         // all loads first (independent, in flight together), then the stores
         constexpr int kPer = 32 * 32 / (kW32Warps * 32);
         T cxv[kPer], cyv[kPer];
-        double ev[kPer];
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
             const int k = threadIdx.x + t * kW32Warps * 32;
             const int a = k >> 5, m = k & 31;
-            cxv[t] = (a < vX && m < nX) ? CX[m * nX + oX + a] : T(0);
-            cyv[t] = (a < vY && m < nY) ? CY[m * nY + oY + a] : T(0);
-            ev[t] = (a < vX && m < vY) ? eX[oX + a] + eY[oY + m] : 0.0;
+            cxv[t] = (a < vX && m < nX) ? CXv[m * nX + a] : T(0);
+            cyv[t] = (a < vY && m < nY) ? CYv[m * nY + a] : T(0);
         }
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
             const int k = threadIdx.x + t * kW32Warps * 32;
             CXT[k] = cxv[t];
             CYT[k] = cyv[t];
-            eab[k] = ev[t];
         }
+        if (threadIdx.x < 32) eYv[threadIdx.x] = threadIdx.x < vY ? Epool[d.eYv + threadIdx.x] : 0.0;
     }
     __syncthreads();
 
     const bool live = lane < vX;
+    const double ea = live ? Epool[d.eXv + lane] : 0.0;   // this lane's virtual orbital a
     double ej = 0.0, ek = 0.0;
     int x = 0;                                   // buffer holding this pair's H0
     for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
         const int i = pr / oY, j = pr % oY;
-        const double eij = eX[i] + eY[j];
+        const double eija = (eX[i] + eY[j]) - ea;  // e_i + e_j - e_a of this lane
         const int nx = pr + kW32Warps;           // next pair of this warp
         T* SX = x ? buf + kW32Slab : buf;        // H0, then VA [a][b] (stride 33)
         T* SY = x ? buf : buf + kW32Slab;        // H1, then the next pair's H0
@@ -199,7 +198,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 }
                 if (live) {
                     const double va = to_f64(SX[lane * 33 + b]);
-                    const double t = div_newton<kSteps<T>>(va, eij - eab[lane * 32 + b]);   // v D
+                    const double t = div_newton<kSteps<T>>(va, eija - eYv[b]);   // v D
                     ej = fma(t, va, ej);
                     ek = fma(t, to_f64(v0 + v1), ek);
                 }
@@ -299,11 +298,11 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     const FinTask tk = tasks[blockIdx.x];
     const DimerDesc& d = dd[tk.dimer];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
-    const int vX = nX - oX, vY = nY - oY;
+    const int vX = d.vX, vY = d.vY;
     const int rows = nX * nY, pairs = oX * oY;
-    const T* __restrict__ CX = C + d.cX;
-    const T* __restrict__ CY = C + d.cY;
-    const double* eX = Epool + d.eX;
+    const T* __restrict__ CXv = C + d.cXv;    // virtual columns
+    const T* __restrict__ CYv = C + d.cYv;
+    const double* eX = Epool + d.eX;          // occupied energies of this block
     const double* eY = Epool + d.eY;
     const T* H0 = H + d.h_off;
     const T* H1 = H + d.h_off + (long long)pairs * rows;
@@ -315,8 +314,8 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     T* Tm = S + rows;                                         // [nX][vY]
     T* TmK = Tm + nX * vY;                                    // [nY][vX]
     const int tid = threadIdx.x;
-    for (int k = tid; k < vX; k += kTThreads) eXv[k] = eX[oX + k];
-    for (int k = tid; k < vY; k += kTThreads) eYv[k] = eY[oY + k];
+    for (int k = tid; k < vX; k += kTThreads) eXv[k] = Epool[d.eXv + k];
+    for (int k = tid; k < vY; k += kTThreads) eYv[k] = Epool[d.eYv + k];
     // 8 x 4 output blocks of each GEMM shape
     const int bn_vY = (vY + kTN - 1) / kTN, bn_vX = (vX + kTN - 1) / kTN;
     const int nb1 = ((nX + kTM - 1) / kTM) * bn_vY;          // Tm
@@ -334,7 +333,7 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
         for (int blk = tid; blk < nb1; blk += kTThreads) {
             const int m0 = (blk / bn_vY) * kTM, n0 = (blk % bn_vY) * kTN;
             mm_block<T>(acc, m0, n0, nX, vY, nY, [&](int m, int k) { return S[m * nY + k]; },
-                        [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
+                        [&](int k, int n) { return __ldg(CYv + k * nY + n); });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
 #pragma unroll
@@ -348,7 +347,7 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
         for (int blk = tid; blk < nb3; blk += kTThreads) {
             const int m0 = (blk / bn_vX) * kTM, n0 = (blk % bn_vX) * kTN;
             mm_block<T>(acc, m0, n0, nY, vX, nX, [&](int m, int k) { return S[m * nX + k]; },
-                        [&](int k, int n) { return __ldg(CX + k * nX + oX + n); });
+                        [&](int k, int n) { return __ldg(CXv + k * nX + n); });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
 #pragma unroll
@@ -359,7 +358,7 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
         // ---- VA, VKT and the FP64 epilogue, block by block
         for (int blk = tid; blk < nb2; blk += kTThreads) {
             const int m0 = (blk / bn_vY) * kTM, n0 = (blk % bn_vY) * kTN;
-            mm_block<T>(acc, m0, n0, vX, vY, nX, [&](int m, int k) { return __ldg(CX + k * nX + oX + m); },
+            mm_block<T>(acc, m0, n0, vX, vY, nX, [&](int m, int k) { return __ldg(CXv + k * nX + m); },
                         [&](int k, int n) { return Tm[k * vY + n]; });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
@@ -367,7 +366,7 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
                 for (int b = 0; b < kTN; b++)
                     if (m0 + a < vX && n0 + b < vY) S[(m0 + a) * vY + n0 + b] = acc[a][b];   // own elements only
             mm_block<T>(acc, m0, n0, vX, vY, nY, [&](int m, int k) { return TmK[k * vX + m]; },
-                        [&](int k, int n) { return __ldg(CY + k * nY + oY + n); });
+                        [&](int k, int n) { return __ldg(CYv + k * nY + n); });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
 #pragma unroll
@@ -437,6 +436,21 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     const int* first = reinterpret_cast<const int*>(tasks + ntasks);
     k_finish_sum<<<(nd + 127) / 128, 128, 0, s>>>(d_desc, nd, tasks, first, part, E2);
     return cudaGetLastError();
+}
+
+// Split dimers: the blocks' terms added in block order.
+__global__ void k_fold(const int* __restrict__ fold, int nfold, double* __restrict__ E2)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nfold) return;
+    const int d = fold[3 * f], first = fold[3 * f + 1], n = fold[3 * f + 2];
+    double sj = 0.0, sk = 0.0;
+    for (int b = 0; b < n; b++) {
+        sj += E2[2 * (first + b)];
+        sk += E2[2 * (first + b) + 1];
+    }
+    E2[2 * d] = sj;
+    E2[2 * d + 1] = sk;
 }
 
 // ------------------------------------------------------------ reduction
@@ -552,7 +566,7 @@ void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinT
 {
     out->clear();
     for (int k = 0; k < nd; k++) {
-        const long long nX = h[k].nX, nY = h[k].nY, vX = nX - h[k].oX, vY = nY - h[k].oY;
+        const long long nX = h[k].nX, nY = h[k].nY, vX = h[k].vX, vY = h[k].vY;
         const int pairs = h[k].oX * h[k].oY;
         const long long per_pair = 2 * (nX * nY * vY + vX * vY * nX);   // FMAs of one pair, both forms
         const int ppt = (int)std::max<long long>(1, std::min<long long>(pairs, fma_per_task / std::max(1LL, per_pair)));
@@ -561,6 +575,13 @@ void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinT
         for (int t = 0; t < ntasks; t++)
             out->push_back(FinTask{k, t * ppt, std::min(pairs, (t + 1) * ppt), first, ntasks});
     }
+}
+
+cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s)
+{
+    if (nfold <= 0) return cudaSuccess;
+    k_fold<<<(nfold + 127) / 128, 128, 0, s>>>(fold, nfold, E2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists, double* mon, double* total,

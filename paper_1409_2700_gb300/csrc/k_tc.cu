@@ -656,7 +656,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 constexpr int kNT = 16;           // TMEM slot width = MMA N
 constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns (16 slots when BIG)
 constexpr int kFxUnits = 8;       // BF16x3: 4-slot p0 units in 512 columns (4 when BIG)
-constexpr int kFxMaxKcs = 3;      // BF16x3 rank kernel: n2 <= 96 (all p2 of a p0 staged at once)
 constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
 constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
@@ -838,59 +837,39 @@ __device__ __forceinline__ void convert_row(const double* __restrict__ F, unsign
     }
 }
 
-// T[(p1,p3) = this lane's row][j] of one p0 unit.  TF32: the slot itself.
-// BF16x3: the three digit levels combined in FP32 (round to nearest), times
-// the row scale and column scale 2^(e-7) 2^(f-7).
+// T[(p1,p3) = this lane's row][j] of one unit, written to T (add = false) or
+// added to it.  TF32: the slot itself.  BF16x3: the four digit levels
+// combined in FP32 (round to nearest), ((L3/256 + L2)/256 + L1)/256 + L0, one
+// level at a time (16 registers in flight), times the row and column scales.
 template <int KIND>
-__device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[16], const float* srow, const float* scol)
+__device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[16], const float* srow, const float* scol, bool add)
 {
     if constexpr (KIND == TC_TF32) {
         tmem_ld16(taddr, T);
     } else {
-        // two rounds of two slots keep 32 registers in flight (the register
-        // accumulators stay live): ((L3/256 + L2)/256 + L1)/256 + L0
-        unsigned a[16], b[16];
-        tmem_ld16_nowait(taddr + 3 * kNT, a);
-        tmem_ld16_nowait(taddr + 2 * kNT, b);
-        tmem_wait_ld();
+        float v[16], w[16];
+        tmem_ld16(taddr + 3 * kNT, v);
 #pragma unroll
-        for (int j = 0; j < 16; j++) T[j] = fmaf(__uint_as_float(a[j]), 0x1p-8f, __uint_as_float(b[j]));
-        tmem_ld16_nowait(taddr + kNT, a);
-        tmem_ld16_nowait(taddr, b);
-        tmem_wait_ld();
+        for (int l = 2; l >= 0; l--) {
+            tmem_ld16(taddr + (unsigned)(l * kNT), w);
+#pragma unroll
+            for (int j = 0; j < 16; j++) v[j] = fmaf(v[j], 0x1p-8f, w[j]);
+        }
         const float sr = *srow;
 #pragma unroll
-        for (int j = 0; j < 16; j++)
-            T[j] = fmaf(fmaf(T[j], 0x1p-8f, __uint_as_float(a[j])), 0x1p-8f, __uint_as_float(b[j])) * (sr * scol[j]);
+        for (int j = 0; j < 16; j++) {
+            const float x = v[j] * (sr * scol[j]);
+            T[j] = add ? T[j] + x : x;
+        }
     }
 }
 
-// BF16x3: largest binary exponent field of row r over the chunks of one p0
-// (the staged boxes hold the row's p2 = 32 kc + 0..31; out-of-range p2 read
-// 0).  The two threads of a row (lanes l and l ^ 16) scan their own chunks
-// c0 and c0 + 2 and exchange.
-__device__ __forceinline__ int row_emax(const unsigned char* Fr, unsigned f_stage_bytes, int sf, unsigned g0,
-                                        int kcs, const ConvRow& cr, int n3, int c0)
-{
-    int emax = 0;
-    for (int kc = 0; kc < kcs; kc++) {
-        const unsigned* hw = reinterpret_cast<const unsigned*>(
-                                 reinterpret_cast<const double*>(Fr + (size_t)((g0 + kc) % sf) * f_stage_bytes) +
-                                 cr.src) + 1;
-#pragma unroll
-        for (int q = 0; q < 2; q++)
-#pragma unroll
-            for (int e = 0; e < 8; e++)
-                emax = max(emax, (int)((hw[2 * ((c0 + 2 * q) * 8 + e) * n3] >> 20) & 0x7FFu));
-    }
-    emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 16));
-    return cr.valid ? emax : 0;
-}
-
-// BF16x3, all p2 in one box (n2 <= 32): the thread's 16 values are loaded
-// once; the row's largest magnitude is their bitwise maximum (|x| orders like
-// its bit pattern), combined with the partner lane; then the digit planes as
-// in convert_row_fx.  Returns the row's exponent field.
+// BF16x3: row r of one staged box (one p2 chunk of one p0) as four digit
+// planes, chunks c0 and c0 + 2 of 8 p2 each: tile 1 holds [d0 | d1] (bytes
+// 0-63 / 64-127), tile 2 [d2 | d3].  The thread's 16 values are loaded once;
+// the row's largest magnitude over the chunk is their bitwise maximum (|x|
+// orders like its bit pattern) combined with the partner lane (l ^ 16), which
+// fixes the chunk's fixed point.  Returns the row's exponent field.
 __device__ __forceinline__ int convert_row_fx1(const double* __restrict__ F, unsigned char* __restrict__ A1,
                                                unsigned char* __restrict__ A2, const ConvRow& cr, int n3, int c0)
 {
@@ -929,35 +908,26 @@ __device__ __forceinline__ int convert_row_fx1(const double* __restrict__ F, uns
     return emax;
 }
 
-// BF16x3: row r of one chunk as four digit planes, chunks c0 and c0 + 2 of
-// 8 p2 each: tile 1 holds [d0 | d1] (bytes 0-63 / 64-127), tile 2 [d2 | d3].
-__device__ __forceinline__ void convert_row_fx(const double* __restrict__ F, unsigned char* __restrict__ A1,
-                                               unsigned char* __restrict__ A2, const ConvRow& cr, int n3, int c0,
-                                               FxRow fr)
+// T[row][j] of one p0 for this lane's row: TF32 reads the p0's unit; BF16x3
+// adds the units of the p2 chunks in chunk order (FP32, round to nearest).
+// Frees each unit's slot after reading it.  False on timeout/abort.
+template <int KIND, int NS, int UC>
+__device__ __forceinline__ bool load_p0_T(float (&T)[16], RankShared* sh, unsigned& gS, int kcs, unsigned lanebase,
+                                          const float* exps, const float* scu, int r, int lane, volatile int* abort,
+                                          int* status)
 {
-    const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
-#pragma unroll
-    for (int q = 0; q < 2; q++) {
-        const int c = c0 + 2 * q;
-        unsigned w[4][4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            float d[2][4];
-#pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const uint2 b = dw[(c * 8 + e + u) * n3];
-                digits4(fx_y(b.x, b.y, fr), d[u]);
-            }
-#pragma unroll
-            for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(d[0][k], d[1][k]);
-        }
-        *reinterpret_cast<uint4*>(A1 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
-        *reinterpret_cast<uint4*>(A1 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
-            make_uint4(w[1][0], w[1][1], w[1][2], w[1][3]);
-        *reinterpret_cast<uint4*>(A2 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[2][0], w[2][1], w[2][2], w[2][3]);
-        *reinterpret_cast<uint4*>(A2 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
-            make_uint4(w[3][0], w[3][1], w[3][2], w[3][3]);
+    const int nunits = KIND == TC_BF16X3 ? kcs : 1;
+    for (int u = 0; u < nunits; u++, gS++) {
+        const int s = gS % NS;
+        if (!mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, status, 18)) return false;
+        if (KIND == TC_BF16X3 && !mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, status, 23)) return false;
+        tc_fence_after();
+        unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT, u > 0);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
     }
+    return true;
 }
 
 template <int KIND, bool BIG>
@@ -1056,46 +1026,64 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 const int wp = li & 1;
                 if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, abort, P.status, 12))) break;
                 for (int mt = 0; mt < item.mts && ok; mt++)
-                    for (int p0 = 0; p0 < g.n0 && ok; p0++, gS++) {
-                        const int s = gS % NS;
-                        if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13))) break;
-                        tc_fence_after();
-                        const unsigned dt = tmem + (unsigned)(s * UC);
-                        for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
-                            const int as = gA & 1;
-                            if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
+                    for (int p0 = 0; p0 < g.n0 && ok; p0++) {
+                        if constexpr (!FX) {
+                            // one unit per p0: the tensor core accumulates over the p2 chunks
+                            const int s = gS % NS;
+                            if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13)))
+                                break;
                             tc_fence_after();
-                            const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
-                            unsigned char* wk = FX ? Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128
-                                                   : Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
-                            const unsigned long long b0 = sw128_desc(wk);
-                            const unsigned long long b1 = sw128_desc(wk + kNT * 128);
-                            if (KIND == TC_TF32) {
+                            const unsigned dt = tmem + (unsigned)(s * UC);
+                            for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
+                                const int as = gA & 1;
+                                if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
+                                tc_fence_after();
+                                const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
+                                unsigned char* wk = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
+                                const unsigned long long b0 = sw128_desc(wk);
+                                const unsigned long long b1 = sw128_desc(wk + kNT * 128);
                                 // C_Y = hi + lo (two TF32 planes): A (hi + lo)
 #pragma unroll
                                 for (int k = 0; k < 4; k++) {
                                     tc_mma<KIND>(dt, adesc + 2 * k, b0 + 2 * k, idesc, (kc > 0 || k > 0) ? 1u : 0u);
                                     tc_mma<KIND>(dt, adesc + 2 * k, b1 + 2 * k, idesc, 1u);
                                 }
-                            } else {
+                                tc_commit(&sh->empty_a[as]);
+                                any = true;
+                            }
+                            if (ok) tc_commit(&sh->slot_full[s]);
+                            gS++;
+                        } else {
+                            // one unit per (p0, p2 chunk): each chunk has its own fixed point
+                            for (int kc = 0; kc < g.kcs && ok; kc++, gA++, gS++) {
+                                const int s = gS % NS;
+                                if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13)))
+                                    break;
+                                const int as = gA & 1;
+                                if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
+                                tc_fence_after();
+                                const unsigned dt = tmem + (unsigned)(s * UC);
                                 // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3]; the B tile
                                 // stacks C_Y's digits B0..B3 as rows 0-63.  A_u x [B0..B(3-u)] lands
                                 // A_u B_v in the slot of level u + v; A0's MMA opens all four slots.
+                                const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
                                 const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
-                                const unsigned long long bk = b0 + (unsigned long long)((kc & 1) * 4);
+                                const unsigned long long bk =
+                                    sw128_desc(Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128) +
+                                    (unsigned long long)((kc & 1) * 4);
 #pragma unroll
                                 for (int k = 0; k < 2; k++) {
-                                    const unsigned acc = (kc > 0 || k > 0) ? 1u : 0u;
+                                    const unsigned acc = k > 0 ? 1u : 0u;
                                     tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[0], acc);
                                     tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[1], 1u);
                                     tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
                                     tc_mma<KIND>(dt + 3 * kNT, a2 + 4 + 2 * k, bk + 2 * k, idesc_fx[3], 1u);
                                 }
+                                tc_commit(&sh->empty_a[as]);
+                                any = true;
+                                tc_commit(&sh->slot_full[s]);
                             }
-                            tc_commit(&sh->empty_a[as]);
-                            any = true;
                         }
-                        if (ok) tc_commit(&sh->slot_full[s]);
                     }
                 if (ok) tc_commit(&sh->empty_w[wp]);
             }
@@ -1213,15 +1201,11 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                             }
                         }
                     } else {
-                        // every p2 chunk of this p0 staged (the ring holds >= kcs boxes), then the
-                        // row's exponent, its scale for the epilogue, and the digit planes
-                        for (int kc = 0; kc < g.kcs && ok; kc++)
-                            ok = mbar_wait(&sh->full_f[(gF + kc) % P.sf], ((gF + kc) / P.sf) & 1, abort, P.status, 16);
-                        if (!ok) break;
-                        const int su = gU % NS;
-                        if (g.kcs == 1) {
-                            // one box holds the row: fused load, maximum and digits
+                        // one unit per p2 chunk: fused load, row maximum and digit planes,
+                        // then the unit's row and column scales for the epilogue
+                        for (int kc = 0; kc < g.kcs && ok; kc++, gF++, gA++, gU++) {
                             const int s = gF % P.sf;
+                            if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16))) break;
                             const int as = gA & 1;
                             if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
                                 break;
@@ -1235,41 +1219,14 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                 mbar_arrive(&sh->full_a[as]);
                                 mbar_arrive(&sh->empty_f[s]);
                             }
-                            gA++;
+                            const int su = gU % NS;
                             if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22)))
                                 break;
                             if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
                             if (ct < kNT) scu[su * kNT + ct] = sc_mine;
                             __syncwarp();
                             if (lane == 0) mbar_arrive(&sh->exp_full[su]);
-                            gF += 1;
-                            gU++;
-                            continue;
                         }
-                        const int emax = row_emax(Fr, P.f_stage_bytes, P.sf, gF, g.kcs, cr, g.n3, c0);
-                        const FxRow xrow = fx_row(emax, cr.valid);
-                        if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22))) break;
-                        if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
-                        if (ct < kNT) scu[su * kNT + ct] = sc_mine;
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh->exp_full[su]);
-                        for (int kc = 0; kc < g.kcs; kc++, gA++) {
-                            const int s = (gF + kc) % P.sf;
-                            const int as = gA & 1;
-                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
-                                break;
-                            unsigned char* At = Ar + (size_t)as * ASLOT;
-                            convert_row_fx(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes), At,
-                                           At + kABytes, cr, g.n3, c0, xrow);
-                            fence_async_smem();
-                            __syncwarp();
-                            if (lane == 0) {
-                                mbar_arrive(&sh->full_a[as]);
-                                mbar_arrive(&sh->empty_f[s]);
-                            }
-                        }
-                        gF += g.kcs;
-                        gU++;
                     }
                 }
         }
@@ -1305,16 +1262,11 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                     for (int i = 0; i < kOB; i++)
 #pragma unroll
                         for (int j = 0; j < kOB; j++) acc[i][j] = 0.f;
-                    for (int p0 = 0; p0 < g.n0; p0++, gS++) {
-                        const int s = gS % NS;
-                        if (!(ok = mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, P.status, 18))) break;
-                        if (FX && !(ok = mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, P.status, 23))) break;
-                        tc_fence_after();
+                    for (int p0 = 0; p0 < g.n0; p0++) {
                         float T[16];
-                        unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT);
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
+                        if (!(ok = load_p0_T<KIND, NS, UC>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane, abort,
+                                                            P.status)))
+                            break;
                         const float4 ca = *reinterpret_cast<const float4*>(cx + p0 * kOB);
                         const float4 cb = *reinterpret_cast<const float4*>(cx + p0 * kOB + 4);
                         const float cv[kOB] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
@@ -1342,16 +1294,11 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 } else {
                     const unsigned accbase = lanebase + 256u;
                     const int nchunk = (g.o0 + 3) >> 2;
-                    for (int p0 = 0; p0 < g.n0; p0++, gS++) {
-                        const int s = gS % NS;
-                        if (!(ok = mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, P.status, 18))) break;
-                        if (FX && !(ok = mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, P.status, 23))) break;
-                        tc_fence_after();
+                    for (int p0 = 0; p0 < g.n0; p0++) {
                         float T[16];
-                        unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT);
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
+                        if (!(ok = load_p0_T<KIND, NS, UC>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane, abort,
+                                                            P.status)))
+                            break;
                         const float* cp = cx + p0 * kOBig;
 #pragma unroll 1
                         for (int ic = 0; ic < nchunk; ic++) {
@@ -1436,8 +1383,7 @@ int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
 
 // 1: rank kernel, register accumulators (occupations <= 8); 2: rank kernel,
 // TMEM accumulators (<= 16); 0: Kronecker kernel (anything else the
-// tensor-core forms accept; BF16x3 also when n_Y > 96, since its rank kernel
-// stages all p2 of a p0 at once).  MCPT_TC_KERNEL=kron|rank|rankbig forces a
+// tensor-core forms accept).  MCPT_TC_KERNEL=kron|rank|rankbig forces a
 // kernel where the sizes allow it.
 int choose_variant(TcKind kind, const DimerDesc* h, int nd)
 {
@@ -1446,8 +1392,7 @@ int choose_variant(TcKind kind, const DimerDesc* h, int nd)
         omax = std::max(omax, std::max(h[k].oX, h[k].oY));
         nymax = std::max(nymax, h[k].nY);
     }
-    const int kcs_cap = kind == TC_BF16X3 ? kFxMaxKcs : kKCMax;
-    const bool fits_rank = nymax <= kcs_cap * kKC && omax <= kOBig;
+    const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
     const char* env = getenv("MCPT_TC_KERNEL");
     if (env && !strcmp(env, "kron")) return 0;
     if (env && !strcmp(env, "rankbig") && fits_rank) return 2;
@@ -1502,9 +1447,8 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
         omax = std::max(omax, std::max(h[k].oX, h[k].oY));
         nymax = std::max(nymax, h[k].nY);
     }
-    const int kcs_cap = kind == TC_BF16X3 ? kFxMaxKcs : kKCMax;
     std::vector<int> vars;
-    if (nymax <= kcs_cap * kKC && omax <= kOBig) {
+    if (nymax <= kKCMax * kKC && omax <= kOBig) {
         if (omax <= kOB) vars.push_back(1);
         vars.push_back(2);
     } else {
@@ -1520,7 +1464,7 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
     int n = 0;
     for (int v : vars) {
         const int sf_max = std::min(8, (int)(((size_t)max_smem - fixed_smem(kind, v, kcs_max, ws)) / fs));
-        const int sf_min = (v >= 1 && kind == TC_BF16X3) ? std::max(2, kcs_max) : 2;
+        const int sf_min = 2;
         if (sf_max < sf_min) continue;
         int sfs[3] = {sf_min, (sf_min + sf_max) / 2, sf_max};
         for (int a = 0; a < 3; a++) {
@@ -1624,8 +1568,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     int sf = (int)(((size_t)max_smem - fixed) / P.f_stage_bytes);
     sf = std::min(sf, 8);
     if (tune && tune->sf) sf = std::min(sf, tune->sf);
-    // the BF16x3 rank kernel holds every p2 box of a p0 at once
-    const int sf_min = (variant >= 1 && kind == TC_BF16X3) ? std::max(2, kcs_max) : 2;
+    const int sf_min = 2;
     if (sf < sf_min) {
         snprintf(err, errlen, "not enough shared memory for the staging ring (%d < %d stages)", sf, sf_min);
         return cudaErrorInvalidConfiguration;

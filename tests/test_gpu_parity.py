@@ -70,6 +70,9 @@ def test_nonsymmetric_random_blocks(prec):
     cases = [(6, 10, 2, 3), (14, 8, 3, 1), (32, 32, 5, 5), (40, 24, 7, 4)]
     if prec in ("fp64", "fp32c"):
         cases += [(5, 7, 2, 3), (9, 3, 1, 2)]
+    if prec != "fp64":
+        # up to four 32-p2 chunks per p0 (ragged last chunk), 128-AO rows
+        cases += [(16, 128, 3, 16), (24, 100, 4, 12), (128, 16, 16, 3)]
     for nX, nY, oX, oY in cases:
         A, K, CX, eX, CY, eY = rand_dimer(rng, nX, nY, oX, oY)
         ref = oracle.dimer(A, K, CX, eX, CY, eY, oX, oY)
@@ -401,3 +404,27 @@ def test_autotuner_cache(lat8, prec, tmp_path):
         assert np.all(np.abs(pd[:, 0] - E[:, 0]) <= PER_DIMER[prec] * np.abs(E[:, 0]))
         assert abs(tot[0] - E[:, 0].sum()) <= LATTICE[prec]
     assert np.array_equal(res[0][2], res[1][2])
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3"])
+def test_occupations_above_16_run_as_blocks(prec):
+    """More than 16 occupied orbitals on a monomer: the tensor-core forms run
+    the dimer as blocks of at most 16 x 16 occupied pairs (each over all
+    virtual orbitals) and add the blocks' terms; the result is the whole
+    dimer's, on non-symmetric random integrals."""
+    rng = np.random.default_rng(17)
+    for nX, nY, oX, oY in [(40, 36, 20, 18), (24, 34, 17, 3), (18, 40, 2, 33)]:
+        A, K, CX, eX, CY, eY = rand_dimer(rng, nX, nY, oX, oY)
+        ref = oracle.dimer(A, K, CX, eX, CY, eY, oX, oY)
+        with M.Context(precision=prec) as ctx:
+            ctx.add_monomer(CX, eX, oX)
+            ctx.add_monomer(CY, eY, oY)
+            ctx.add_dimer(0, 1, np.concatenate([A.ravel(), K.ravel()]), M.MCPT_AO_BLOCKS)
+            ctx.run()
+            _, _, pd, tot = ctx.energies()
+        s = abs(ref[0])
+        print(f"{prec} {nX}x{nY} occ {oX}x{oY}: rel err J {abs(pd[0, 0] - ref[0]) / s:.2e} K {abs(pd[0, 1] - ref[1]) / s:.2e}")
+        assert abs(pd[0, 0] - ref[0]) <= PER_DIMER[prec] * s
+        assert abs(pd[0, 1] - ref[1]) <= PER_DIMER[prec] * s
+        assert tot[0] == pd[0, 0]
+

@@ -135,10 +135,11 @@ def test_uneven_4096_streamed():
 
 def test_ao128_subset():
     """343 monomers of 128 AO / 20 occupied: a seeded 16-dimer subset (4.3 GB
-    of blocks per dimer) in the compensated FP32 form."""
+    of blocks per dimer) in the compensated FP32 and BF16x3 forms (the latter
+    as 2 x 2 blocks of 10 x 10 occupied pairs)."""
     w = synth.workload("lattice-7x7x7-cheb1-ao128")
     rng = np.random.default_rng(13)
     subset = sorted(rng.choice(w.n_dimers, size=16, replace=False).tolist())
-    res, pairs = _streamed(w, ["fp32c"], dimers=subset)
+    res, pairs = _streamed(w, ["fp32c", "bf16x3"], dimers=subset)
     _check_sample(w, res, pairs, subset, {d: k for k, d in enumerate(subset)})
     _check_invariants(res, pairs, w.n_monomers)
