@@ -118,6 +118,29 @@ mcpt_status mcpt_add_monomer(mcpt_handle h, const double *C, const double *eps,
 mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double *ao_eri,
                            mcpt_ao_layout layout, int on_device, int *id_out);
 
+/* Flags of mcpt_update_dimer. */
+enum { MCPT_UPDATE_ASYNC = 1 };
+
+/* Replace the AO integrals of registered dimer `id` for later runs (same
+ * monomers, same sizes), e.g. the next geometry of a sequence of lattices.
+ * ao_eri: FP64 in `layout` for the dimer's stored order (X < Y as registered;
+ *   no relabelling).
+ * on_device = 0: host pointer.  The integrals go into the dimer's library
+ *   storage (allocated on its first host update if it had been given on the
+ *   device), copied before the call returns; with MCPT_UPDATE_ASYNC and the
+ *   BLOCKS layout the copy is only enqueued on the handle's stream, and the
+ *   host buffer must stay valid and unmodified until the next mcpt_run has
+ *   completed (mcpt_energies returns) -- with pinned host memory the copies of
+ *   many dimers then overlap and run at the link's bandwidth.
+ * on_device = 1: device pointer, BORROWED as in mcpt_add_dimer.
+ * The dimer counts as not computed until the next run that covers it.  The
+ * run plan (and its CUDA graph) is kept when the integrals' device addresses
+ * do not change (host updates into existing storage).
+ * Errors: EINVAL (unknown id, NULL, bad layout, unknown flags, non-finite with
+ *   validate=1, on_device=1 with host memory), ENOMEM, ECUDA. */
+mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double *ao_eri, mcpt_ao_layout layout,
+                              int on_device, int flags);
+
 /* Switch the transformation arithmetic for later runs (no re-upload). */
 mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p);
 

@@ -24,9 +24,11 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "
 MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C = range(4)
 PRECISIONS = {"fp64": MCPT_FP64, "tf32": MCPT_TF32, "bf16x3": MCPT_BF16X3, "fp32c": MCPT_FP32C}
 MCPT_AO_FULL, MCPT_AO_BLOCKS = 0, 1
+MCPT_UPDATE_ASYNC = 1
 
 # every symbol include/mcpt.h declares
-EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_set_precision",
+EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer",
+           "mcpt_set_precision",
            "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats", "mcpt_num_monomers",
            "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
 
@@ -65,12 +67,13 @@ def lib():
         L.mcpt_create.argtypes = [ctypes.POINTER(H), ctypes.POINTER(mcpt_options)]
         L.mcpt_add_monomer.argtypes = [H, P, P, I, I, ctypes.POINTER(I)]
         L.mcpt_add_dimer.argtypes = [H, I, I, P, I, I, ctypes.POINTER(I)]
+        L.mcpt_update_dimer.argtypes = [H, I, P, I, I, I]
         L.mcpt_set_precision.argtypes = [H, I]
         L.mcpt_run.argtypes = [H]
         L.mcpt_run_range.argtypes = [H, I, I]
         L.mcpt_energies.argtypes = [H, P, P, P, P]
         L.mcpt_collect_stats.argtypes = [H, ctypes.POINTER(mcpt_run_stats)]
-        for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_set_precision", "mcpt_run",
+        for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer", "mcpt_set_precision", "mcpt_run",
                   "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats"):
             getattr(L, f).restype = I
         L.mcpt_num_monomers.argtypes = [H]
@@ -123,6 +126,12 @@ def mcpt_add_monomer(h, C, eps, nao: int, nocc: int) -> int:
     out = ctypes.c_int()
     _check(h, lib().mcpt_add_monomer(h, _ptr(C), _ptr(eps), nao, nocc, ctypes.byref(out)))
     return out.value
+
+
+def mcpt_update_dimer(h, dimer: int, ao_eri, layout: int, on_device: int, flags: int = 0) -> None:
+    if isinstance(ao_eri, np.ndarray):
+        ao_eri = np.ascontiguousarray(ao_eri, dtype=np.float64)
+    _check(h, lib().mcpt_update_dimer(h, dimer, _ptr(ao_eri), layout, on_device, flags))
 
 
 def mcpt_add_dimer(h, X: int, Y: int, ao_eri, layout: int, on_device: int) -> int:
@@ -208,6 +217,14 @@ class Context:
         if on_device is None:
             on_device = 0 if isinstance(ao_eri, np.ndarray) else 1
         return mcpt_add_dimer(self.h, X, Y, ao_eri, layout, on_device)
+
+    def update_dimer(self, dimer, ao_eri, layout=MCPT_AO_BLOCKS, on_device=None, asynchronous=False):
+        """New integrals for a registered dimer (stored order X < Y).  With
+        asynchronous=True a host buffer is copied on the handle's stream and
+        must stay unchanged until the next run completes."""
+        if on_device is None:
+            on_device = 0 if isinstance(ao_eri, np.ndarray) else 1
+        mcpt_update_dimer(self.h, dimer, ao_eri, layout, on_device, MCPT_UPDATE_ASYNC if asynchronous else 0)
 
     def set_precision(self, p):
         mcpt_set_precision(self.h, PRECISIONS[p] if isinstance(p, str) else int(p))

@@ -36,6 +36,7 @@ struct DimerRec {
     const double* E[2];
     long long st[2][3];
     bool computed;
+    double* owned;        // library storage of host-given integrals (nullptr: never had any)
 };
 
 // Events of the timed runs since the last mcpt_collect_stats: per run
@@ -349,35 +350,20 @@ mcpt_status mcpt_add_monomer(mcpt_handle h, const double* C, const double* eps, 
     return MCPT_OK;
 }
 
-mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_ao_layout layout, int on_device,
-                           int* id_out)
+// Point record r (monomers X, Y in the caller's order; r.X < r.Y) at the
+// dimer's integrals: device data in place (borrowed), host data copied into
+// `storage` (2 nX^2 nY^2 doubles of library memory) or into new arena memory.
+static mcpt_status make_record(mcpt_handle h, int X, int Y, const double* ao, mcpt_ao_layout layout, int on_device,
+                               double* storage, bool async, DimerRec& r, const char* who)
 {
-    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_add_dimer: NULL handle");
-    const int N = (int)h->mons.size();
-    if (X < 0 || X >= N || Y < 0 || Y >= N)
-        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: unknown monomer id (%d, %d) of %d", X, Y, N);
-    if (X == Y) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: X == Y == %d", X);
-    if (!ao) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: ao_eri is NULL");
-    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS)
-        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: bad layout %d", (int)layout);
-    if (on_device && X > Y)
-        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: device integrals must be given with X < Y");
-    const std::pair<int, int> key(std::min(X, Y), std::max(X, Y));
-    if (h->pairs.count(key)) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: duplicate dimer (%d, %d)", X, Y);
-    CK(h, cudaSetDevice(h->device));
-
     const int nX = h->mons[X].nao, nY = h->mons[Y].nao, n = nX + nY;
     const size_t blk = (size_t)nX * nX * nY * nY;
-    DimerRec r{};
-    r.X = key.first;
-    r.Y = key.second;
-    r.computed = false;
     if (on_device) {
         cudaPointerAttributes pa;
         cudaError_t e = cudaPointerGetAttributes(&pa, ao);
         if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != h->device) {
             cudaGetLastError();
-            return fail(h, MCPT_EINVAL, "mcpt_add_dimer: on_device=1 but ao_eri is not device memory of device %d",
+            return fail(h, MCPT_EINVAL, "%s: on_device=1 but ao_eri is not device memory of device %d", who,
                         h->device);
         }
         const long long n1 = n, n2 = n1 * n, n3 = n2 * n;
@@ -400,7 +386,7 @@ mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_a
             int flag = 0;
             CK(h, cudaMemcpyAsync(&flag, h->dFlag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
-            if (flag) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: non-finite integral");
+            if (flag) return fail(h, MCPT_EINVAL, "%s: non-finite integral", who);
         }
     } else {
         // Host integrals: keep only the two blocks the term reads.  With X > Y
@@ -451,23 +437,78 @@ mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_a
             src = tmp.data();
         }
         if (h->validate && !all_finite(src, 2 * blk))
-            return fail(h, MCPT_EINVAL, "mcpt_add_dimer: non-finite integral");
-        void* dst = nullptr;
-        mcpt_status st = arena_alloc(h, 2 * blk * sizeof(double), &dst);
-        if (st) return st;
+            return fail(h, MCPT_EINVAL, "%s: non-finite integral", who);
+        void* dst = storage;
+        if (!dst) {
+            mcpt_status st = arena_alloc(h, 2 * blk * sizeof(double), &dst);
+            if (st) return st;
+        }
         CK(h, cudaMemcpyAsync(dst, src, 2 * blk * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        CK(h, cudaStreamSynchronize(h->stream));   // the caller may free its buffer on return
+        // the caller may free its buffer on return, unless it asked for an
+        // asynchronous copy of its own (unrelabelled) blocks
+        if (!(async && src == ao)) CK(h, cudaStreamSynchronize(h->stream));
         const double* b = static_cast<const double*>(dst);
+        r.owned = static_cast<double*>(dst);
         r.E[0] = b;
         r.st[0][0] = (long long)fX * fY * fY; r.st[0][1] = (long long)fY * fY; r.st[0][2] = fY;
         r.E[1] = b + blk;
         r.st[1][0] = (long long)fY * fY * fX; r.st[1][1] = (long long)fY * fX; r.st[1][2] = fX;
     }
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_ao_layout layout, int on_device,
+                           int* id_out)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_add_dimer: NULL handle");
+    const int N = (int)h->mons.size();
+    if (X < 0 || X >= N || Y < 0 || Y >= N)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: unknown monomer id (%d, %d) of %d", X, Y, N);
+    if (X == Y) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: X == Y == %d", X);
+    if (!ao) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: ao_eri is NULL");
+    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: bad layout %d", (int)layout);
+    if (on_device && X > Y)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer: device integrals must be given with X < Y");
+    const std::pair<int, int> key(std::min(X, Y), std::max(X, Y));
+    if (h->pairs.count(key)) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: duplicate dimer (%d, %d)", X, Y);
+    CK(h, cudaSetDevice(h->device));
+    DimerRec r{};
+    r.X = key.first;
+    r.Y = key.second;
+    r.computed = false;
+    mcpt_status st = make_record(h, X, Y, ao, layout, on_device, nullptr, false, r, "mcpt_add_dimer");
+    if (st) return st;
     h->dims.push_back(r);
     h->pairs.insert(key);
     h->plan.valid = false;
     h->lists_dirty = true;
     if (id_out) *id_out = (int)h->dims.size() - 1;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double* ao, mcpt_ao_layout layout, int on_device,
+                              int flags)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_update_dimer: NULL handle");
+    if (id < 0 || id >= (int)h->dims.size())
+        return fail(h, MCPT_EINVAL, "mcpt_update_dimer: unknown dimer id %d of %zu", id, h->dims.size());
+    if (!ao) return fail(h, MCPT_EINVAL, "mcpt_update_dimer: ao_eri is NULL");
+    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS)
+        return fail(h, MCPT_EINVAL, "mcpt_update_dimer: bad layout %d", (int)layout);
+    if (flags & ~MCPT_UPDATE_ASYNC) return fail(h, MCPT_EINVAL, "mcpt_update_dimer: unknown flags 0x%x", flags);
+    CK(h, cudaSetDevice(h->device));
+    const DimerRec& old = h->dims[id];
+    DimerRec r = old;
+    r.computed = false;
+    // host data reuses the dimer's library storage when it has some
+    mcpt_status st = make_record(h, old.X, old.Y, ao, layout, on_device, on_device ? nullptr : old.owned,
+                                 (flags & MCPT_UPDATE_ASYNC) != 0, r, "mcpt_update_dimer");
+    if (st) return st;
+    if (on_device) r.owned = old.owned;     // keep the storage for a later host update
+    if (r.E[0] != old.E[0] || r.E[1] != old.E[1] || std::memcmp(r.st, old.st, sizeof r.st))
+        h->plan.valid = false;              // the tensor maps name the old addresses
+    h->dims[id] = r;
     return MCPT_OK;
 }
 

@@ -293,13 +293,14 @@ __device__ __forceinline__ void copy_slice(T* S, const T* __restrict__ src, int 
 template <typename T>
 __global__ void __launch_bounds__(kTThreads)
 k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tasks, const T* __restrict__ C,
-               const double* __restrict__ Epool, const T* __restrict__ H, double* __restrict__ part)
+               const double* __restrict__ Epool, const T* __restrict__ H, double* __restrict__ part,
+               int smem_elems)
 {
     const FinTask tk = tasks[blockIdx.x];
     const DimerDesc& d = dd[tk.dimer];
-    const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
+    const int nX = d.nX, nY = d.nY, oY = d.oY;
     const int vX = d.vX, vY = d.vY;
-    const int rows = nX * nY, pairs = oX * oY;
+    const int rows = nX * nY, pairs = d.oX * oY;
     const T* __restrict__ CXv = C + d.cXv;    // virtual columns
     const T* __restrict__ CYv = C + d.cYv;
     const double* eX = Epool + d.eX;          // occupied energies of this block
@@ -310,62 +311,78 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     extern __shared__ __align__(16) unsigned char smraw[];
     double* eXv = reinterpret_cast<double*>(smraw);           // [vX]
     double* eYv = eXv + nX;                                   // [vY]
-    T* S = reinterpret_cast<T*>(eYv + nY);                    // H slice [rows], then VA [vX][vY]
-    T* Tm = S + rows;                                         // [nX][vY]
-    T* TmK = Tm + nX * vY;                                    // [nY][vX]
+    T* base = reinterpret_cast<T*>(eYv + nY);
+    // a group of np pairs runs each phase together (one barrier per phase for
+    // the group): as many as the launch's shared memory holds
+    const int per_pair = rows + nX * vY + nY * vX;
+    const int gmax = max(1, min(tk.pr1 - tk.pr0, smem_elems / per_pair));
+    T* S = base;                                              // H slices [np][rows], then VA [np][vX][vY]
+    T* Tm = S + gmax * rows;                                  // [np][nX][vY]
+    T* TmK = Tm + gmax * nX * vY;                             // [np][nY][vX]
     const int tid = threadIdx.x;
     for (int k = tid; k < vX; k += kTThreads) eXv[k] = Epool[d.eXv + k];
     for (int k = tid; k < vY; k += kTThreads) eYv[k] = Epool[d.eYv + k];
-    // 8 x 4 output blocks of each GEMM shape
+    // 8 x 4 output blocks of each GEMM shape, per pair
     const int bn_vY = (vY + kTN - 1) / kTN, bn_vX = (vX + kTN - 1) / kTN;
     const int nb1 = ((nX + kTM - 1) / kTM) * bn_vY;          // Tm
     const int nb3 = ((nY + kTM - 1) / kTM) * bn_vX;          // TmK
     const int nb2 = ((vX + kTM - 1) / kTM) * bn_vY;          // VA, VKT
 
     double ej = 0.0, ek = 0.0;
-    for (int pr = tk.pr0; pr < tk.pr1; pr++) {
-        const int i = pr / oY, j = pr % oY;
-        const double eij = eX[i] + eY[j];
+    for (int g0 = tk.pr0; g0 < tk.pr1; g0 += gmax) {
+        const int np = min(gmax, tk.pr1 - g0);
         T acc[kTM][kTN];
-        // ---- Tm = H0 C_Y(virtual)
-        copy_slice(S, H0 + (long long)pr * rows, rows, tid);
+        // ---- Tm = H0 C_Y(virtual), every pair of the group
+        copy_slice(S, H0 + (long long)g0 * rows, np * rows, tid);
         __syncthreads();
-        for (int blk = tid; blk < nb1; blk += kTThreads) {
-            const int m0 = (blk / bn_vY) * kTM, n0 = (blk % bn_vY) * kTN;
-            mm_block<T>(acc, m0, n0, nX, vY, nY, [&](int m, int k) { return S[m * nY + k]; },
+        for (int blk = tid; blk < np * nb1; blk += kTThreads) {
+            const int p = blk / nb1, q = blk - p * nb1;
+            const int m0 = (q / bn_vY) * kTM, n0 = (q % bn_vY) * kTN;
+            const T* Sp = S + p * rows;
+            T* Tp = Tm + p * nX * vY;
+            mm_block<T>(acc, m0, n0, nX, vY, nY, [&](int m, int k) { return Sp[m * nY + k]; },
                         [&](int k, int n) { return __ldg(CYv + k * nY + n); });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
 #pragma unroll
                 for (int b = 0; b < kTN; b++)
-                    if (m0 + a < nX && n0 + b < vY) Tm[(m0 + a) * vY + n0 + b] = acc[a][b];
+                    if (m0 + a < nX && n0 + b < vY) Tp[(m0 + a) * vY + n0 + b] = acc[a][b];
         }
         __syncthreads();
         // ---- TmK = H1 C_X(virtual)
-        copy_slice(S, H1 + (long long)pr * rows, rows, tid);
+        copy_slice(S, H1 + (long long)g0 * rows, np * rows, tid);
         __syncthreads();
-        for (int blk = tid; blk < nb3; blk += kTThreads) {
-            const int m0 = (blk / bn_vX) * kTM, n0 = (blk % bn_vX) * kTN;
-            mm_block<T>(acc, m0, n0, nY, vX, nX, [&](int m, int k) { return S[m * nX + k]; },
+        for (int blk = tid; blk < np * nb3; blk += kTThreads) {
+            const int p = blk / nb3, q = blk - p * nb3;
+            const int m0 = (q / bn_vX) * kTM, n0 = (q % bn_vX) * kTN;
+            const T* Sp = S + p * rows;
+            T* Kp = TmK + p * nY * vX;
+            mm_block<T>(acc, m0, n0, nY, vX, nX, [&](int m, int k) { return Sp[m * nX + k]; },
                         [&](int k, int n) { return __ldg(CXv + k * nX + n); });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
 #pragma unroll
                 for (int b = 0; b < kTN; b++)
-                    if (m0 + a < nY && n0 + b < vX) TmK[(m0 + a) * vX + n0 + b] = acc[a][b];
+                    if (m0 + a < nY && n0 + b < vX) Kp[(m0 + a) * vX + n0 + b] = acc[a][b];
         }
         __syncthreads();
         // ---- VA, VKT and the FP64 epilogue, block by block
-        for (int blk = tid; blk < nb2; blk += kTThreads) {
-            const int m0 = (blk / bn_vY) * kTM, n0 = (blk % bn_vY) * kTN;
+        for (int blk = tid; blk < np * nb2; blk += kTThreads) {
+            const int p = blk / nb2, q = blk - p * nb2;
+            const int m0 = (q / bn_vY) * kTM, n0 = (q % bn_vY) * kTN;
+            const int pr = g0 + p, i = pr / oY, j = pr - i * oY;
+            const double eij = eX[i] + eY[j];
+            const T* Tp = Tm + p * nX * vY;
+            const T* Kp = TmK + p * nY * vX;
+            T* Vp = S + p * rows;                                 // VA of pair p (own elements)
             mm_block<T>(acc, m0, n0, vX, vY, nX, [&](int m, int k) { return __ldg(CXv + k * nX + m); },
-                        [&](int k, int n) { return Tm[k * vY + n]; });
+                        [&](int k, int n) { return Tp[k * vY + n]; });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
 #pragma unroll
                 for (int b = 0; b < kTN; b++)
-                    if (m0 + a < vX && n0 + b < vY) S[(m0 + a) * vY + n0 + b] = acc[a][b];   // own elements only
-            mm_block<T>(acc, m0, n0, vX, vY, nY, [&](int m, int k) { return TmK[k * vX + m]; },
+                    if (m0 + a < vX && n0 + b < vY) Vp[(m0 + a) * vY + n0 + b] = acc[a][b];
+            mm_block<T>(acc, m0, n0, vX, vY, nY, [&](int m, int k) { return Kp[k * vX + m]; },
                         [&](int k, int n) { return __ldg(CYv + k * nY + n); });
 #pragma unroll
             for (int a = 0; a < kTM; a++)
@@ -373,7 +390,7 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
                 for (int b = 0; b < kTN; b++) {
                     const int m = m0 + a, n = n0 + b;
                     if (m < vX && n < vY) {
-                        const double va = to_f64(S[m * vY + n]);
+                        const double va = to_f64(Vp[m * vY + n]);
                         const double t = div_newton<kSteps<T>>(va, eij - (eXv[m] + eYv[n]));   // v D
                         ej = fma(t, va, ej);
                         ek = fma(t, to_f64(acc[a][b]), ek);
@@ -430,7 +447,8 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_finish_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_finish_tiled<T><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part);
+    const int smem_elems = (int)((smem - 2 * max_ao * sizeof(double) - 64) / sizeof(T));
+    k_finish_tiled<T><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part, smem_elems);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the dimers' first-task indices follow the task array
     const int* first = reinterpret_cast<const int*>(tasks + ntasks);
