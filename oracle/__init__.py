@@ -14,6 +14,8 @@ Functions and the passages they follow (Byrd et al., MCPT I):
                   E_K = -2 sum (ia|jb)(ib|ja) D (exchange completion)
   dimer         the two transforms plus the energies for one dimer
   accumulate    half-and-half per-monomer split, Neumaier lattice total
+  coupling_add  dimer -> monomer doubles coupling of Eq. (tm2) (the c, k sum
+                over the neighbour) at the first-order dimer amplitude T = vD
 
 Parity unpinned: the half/half per-monomer split (only its sum is pinned) and
 the inclusion and scale of E_K (a reading of the paper, pinned only by the
@@ -72,6 +74,8 @@ def lib():
             ip = ctypes.POINTER(I)
             L.oracle_dimers.argtypes = [I, pp, pp, pp, pp, pp, pp, ip, ip, ip, ip, _dp]
             L.oracle_dimers.restype = I
+            L.oracle_coupling_add.argtypes = [_dp, _dp, _dp, I, I, I, I, _dp, _dp]
+            L.oracle_coupling_add.restype = None
             L.oracle_max_threads.argtypes = []
             L.oracle_max_threads.restype = I
             _lib = L
@@ -151,6 +155,35 @@ def factor_route(B, s, CX, CY, oX, oY):
     if lib().oracle_factor_route(_p(B), B.shape[0], float(s), _p(CX), _p(CY), nX, nY, oX, oY, _p(V), _p(W)):
         raise MemoryError("oracle_factor_route")
     return V, W
+
+
+def coupling_add(V, epsX, epsY, oX, oY, RX, RY):
+    """Add one dimer's coupling to R_X ((oX vX)^2) and R_Y ((oY vY)^2), in place.
+    V: (ia|jb) as [oX][vX][oY][vY] (transform_J's layout)."""
+    V, epsX, epsY = _f64(V), _f64(epsX), _f64(epsY)
+    for R in (RX, RY):
+        assert R.dtype == np.float64 and R.flags.c_contiguous
+    nX, nY = epsX.shape[0], epsY.shape[0]
+    lib().oracle_coupling_add(_p(V), _p(epsX), _p(epsY), nX, nY, oX, oY, _p(RX), _p(RY))
+
+
+def coupling_lattice(w, dimers=None, blocks=None):
+    """R_X of every monomer of workload w over the listed dimers (default all),
+    from host inputs: {X: R_X}.  `blocks` may hold precomputed {d: (A, K)}."""
+    ds = range(w.n_dimers) if dimers is None else dimers
+    mons, R = {}, {}
+    for d in ds:
+        X, Y = w.pairs[d]
+        for m in (X, Y):
+            if m not in mons:
+                mons[m] = w.monomer(m)
+                n, o = w.nao[m], w.nocc[m]
+                R[m] = np.zeros(((o * (n - o)), (o * (n - o))))
+        mX, mY = mons[X], mons[Y]
+        A = blocks[d][0] if blocks is not None else w.blocks(d)[0]
+        V = transform_J(A, mX.C, mY.C, mX.nocc, mY.nocc)
+        coupling_add(V, mX.eps, mY.eps, mX.nocc, mY.nocc, R[X], R[Y])
+    return R
 
 
 def accumulate(E2, X, Y, nmon):

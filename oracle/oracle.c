@@ -141,6 +141,46 @@ void oracle_energy_from_mo(const double *V, const double *W,
     *EK = ek;
 }
 
+/* Dimer -> monomer doubles coupling of Eq. (tm2) (the sum over c, k of the
+ * neighbour Y) for this dimer, at the first-order dimer amplitude
+ * T^{ac}_{ik} = v^{ac}_{ik} D^{ik}_{ac} (the same T as the energy above):
+ *   R_X[(i,a)][(i1,a1)] += sum_{k,c} ( v^{a1 k}_{i1 c} T^{ac}_{ik} + v^{ak}_{ic} T^{a1 c}_{i1 k} )
+ * with v^{ak}_{ic} = (i a|k c) = V[i][a][k][c] (i, a of X; k, c of Y), and the
+ * same with the roles of X and Y exchanged for R_Y[(j,b)][(j1,b1)].  R_X is
+ * (oX vX) x (oX vX) row-major, R_Y (oY vY) x (oY vY). */
+void oracle_coupling_add(const double *V, const double *epsX, const double *epsY,
+                         int nX, int nY, int oX, int oY, double *RX, double *RY)
+{
+    int vX = nX - oX, vY = nY - oY;
+    size_t mX = (size_t)oX * vX, mY = (size_t)oY * vY;
+    double *T = malloc(mX * mY * sizeof(double));
+    if (!T) return;
+    for (int i = 0; i < oX; i++)
+    for (int a = 0; a < vX; a++)
+    for (int k = 0; k < oY; k++)
+    for (int c = 0; c < vY; c++) {
+        size_t e = ((size_t)i * vX + a) * mY + (size_t)k * vY + c;
+        T[e] = V[e] / (epsX[i] + epsY[k] - epsX[oX + a] - epsY[oY + c]);
+    }
+    /* X's matrix: (i,a) x (i1,a1), summed over the pairs (k,c) of Y */
+    for (size_t p = 0; p < mX; p++)
+    for (size_t q = 0; q < mX; q++) {
+        double s = 0.0;
+        for (size_t r = 0; r < mY; r++)
+            s += V[q * mY + r] * T[p * mY + r] + V[p * mY + r] * T[q * mY + r];
+        RX[p * mX + q] += s;
+    }
+    /* Y's matrix: (j,b) x (j1,b1), summed over the pairs (i,a) of X */
+    for (size_t p = 0; p < mY; p++)
+    for (size_t q = 0; q < mY; q++) {
+        double s = 0.0;
+        for (size_t r = 0; r < mX; r++)
+            s += V[r * mY + q] * T[r * mY + p] + V[r * mY + p] * T[r * mY + q];
+        RY[p * mY + q] += s;
+    }
+    free(T);
+}
+
 /* One dimer term {E_J, E_K} from the two AO blocks.  Returns 0 on success. */
 int oracle_dimer(const double *A, const double *K,
                  const double *CX, const double *epsX,

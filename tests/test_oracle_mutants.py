@@ -30,6 +30,10 @@ MUTANTS = {
     "brute force lam/sig swapped": ("CY[la * nY + j] * CY[si * nY + oY + b]", "CY[si * nY + j] * CY[la * nY + oY + b]"),
     "compensation dropped": ("    return s + c;\n}", "    return s;\n}"),
     "whole term to each monomer": ("double v = 0.5 * E2[2 * d + f];", "double v = E2[2 * d + f];"),
+    "coupling pairs T with the wrong row": ("s += V[q * mY + r] * T[p * mY + r] + V[p * mY + r] * T[q * mY + r];",
+                                            "s += V[q * mY + r] * T[p * mY + r] + V[p * mY + r] * T[p * mY + r];"),
+    "coupling without the denominator": ("T[e] = V[e] / (epsX[i] + epsY[k] - epsX[oX + a] - epsY[oY + c]);",
+                                         "T[e] = V[e];"),
 }
 
 CHECKS = r'''
@@ -74,6 +78,20 @@ E2 = np.array([[1e16, 1.0], [1.0, 2.0], [-1e16, 3.0], [1.0, 4.0]])
 mon, tot = oracle.accumulate(E2, np.array([0, 0, 1, 2]), np.array([1, 2, 2, 3]), 4)
 check("Neumaier total", tot[0] == 2.0)
 check("split conserves total", mon[:, 1].sum() == tot[1])
+# coupling of Eq. (tm2): rank-1 closed form with degenerate energies, and symmetry
+eo, ev = -0.8, 1.1
+eXd = np.array([eo] * 2 + [ev] * 5); eYd = np.array([eo] * 2 + [ev] * 4)
+Vr = oracle.transform_J(Ar, mX.C, mY.C, 2, 2)
+RX = np.zeros((10, 10)); RY = np.zeros((8, 8))
+oracle.coupling_add(Vr, eXd, eYd, 2, 2, RX, RY)
+Dd = 1.0 / (2 * eo - 2 * ev)
+u = np.outer(xi[:2], xi[2:]).ravel()
+refR = 2 * Dd * s * s * np.sum(yj[:2] ** 2) * np.sum(yj[2:] ** 2) * np.outer(u, u)
+check("coupling rank-1", np.max(np.abs(RX - refR)) <= 1e-13 * np.max(np.abs(refR)))
+V2 = rng.standard_normal((2, 3, 1, 3)); e2X = np.array([-1.0, -0.7, 0.4, 0.9, 2.0]); e2Y = np.array([-0.6, 0.5, 1.2, 2.5])
+R2X = np.zeros((6, 6)); R2Y = np.zeros((3, 3))
+oracle.coupling_add(V2, e2X, e2Y, 2, 1, R2X, R2Y)
+check("coupling symmetric", np.array_equal(R2X, R2X.T) and np.array_equal(R2Y, R2Y.T))
 print("FAILS:" + ",".join(fails))
 '''
 

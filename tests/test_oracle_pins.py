@@ -12,6 +12,7 @@ import pytest
 import oracle
 import synth
 from conftest import read_golden
+from helpers import rand_dimer
 
 RNG_SEED = 1409
 
@@ -295,3 +296,88 @@ def test_lattice_monomer_sum_equals_total():
     assert abs(mon[:, 1].sum() - tot[1]) <= 1e-15 * abs(tot[0]) * 8
     for k, it in enumerate(items):
         assert tuple(E[k]) == oracle.dimer(*it)
+
+
+# ---------------------------------------------------------------- coupling (Eq. tm2)
+def _rand_mo(rng, nX, nY, oX, oY):
+    vX, vY = nX - oX, nY - oY
+    V = rng.standard_normal((oX, vX, oY, vY))
+    eX = np.concatenate([np.sort(rng.uniform(-1.5, -0.5, oX)), np.sort(rng.uniform(0.2, 3.0, vX))])
+    eY = np.concatenate([np.sort(rng.uniform(-1.5, -0.5, oY)), np.sort(rng.uniform(0.2, 3.0, vY))])
+    return V, eX, eY
+
+
+def test_coupling_literal_sum_and_symmetry():
+    """The coupling summed literally over (i, a, i1, a1, k, c) as Eq. (tm2)
+    writes it (v^{a1 k}_{i1 c} T^{ac}_{ik} + v^{ak}_{ic} T^{a1 c}_{i1 k}), for
+    both monomers of a dimer; R is symmetric."""
+    rng = np.random.default_rng(21)
+    nX, nY, oX, oY = 5, 4, 2, 1
+    V, eX, eY = _rand_mo(rng, nX, nY, oX, oY)
+    vX, vY = nX - oX, nY - oY
+    RX = np.zeros((oX * vX, oX * vX))
+    RY = np.zeros((oY * vY, oY * vY))
+    oracle.coupling_add(V, eX, eY, oX, oY, RX, RY)
+
+    def T(i, a, k, c):
+        return V[i, a, k, c] / (eX[i] + eY[k] - eX[oX + a] - eY[oY + c])
+
+    for i in range(oX):
+        for a in range(vX):
+            for i1 in range(oX):
+                for a1 in range(vX):
+                    s = sum(V[i1, a1, k, c] * T(i, a, k, c) + V[i, a, k, c] * T(i1, a1, k, c)
+                            for k in range(oY) for c in range(vY))
+                    assert abs(RX[i * vX + a, i1 * vX + a1] - s) <= 1e-13 * (1 + abs(s))
+    for j in range(oY):
+        for b in range(vY):
+            for j1 in range(oY):
+                for b1 in range(vY):
+                    s = sum(V[i, a, j1, b1] * T(i, a, j, b) + V[i, a, j, b] * T(i, a, j1, b1)
+                            for i in range(oX) for a in range(vX))
+                    assert abs(RY[j * vY + b, j1 * vY + b1] - s) <= 1e-13 * (1 + abs(s))
+    assert np.array_equal(RX, RX.T) and np.array_equal(RY, RY.T)
+
+
+def test_coupling_trace_is_half_the_dimer_energy():
+    """tr R_X = 2 sum v^2 D = E_J / 2, and the same for R_Y: ties the coupling
+    to the energy of Eq. (ed2) computed by the independent energy routine."""
+    rng = np.random.default_rng(22)
+    for nX, nY, oX, oY in [(7, 6, 2, 3), (9, 5, 4, 1)]:
+        A, K, CX, eX, CY, eY = rand_dimer(rng, nX, nY, oX, oY)
+        V = oracle.transform_J(A, CX, CY, oX, oY)
+        W = oracle.transform_K(K, CX, CY, oX, oY)
+        EJ, _ = oracle.energy_from_mo(V, W, eX, eY, oX, oY)
+        RX = np.zeros((oX * (nX - oX),) * 2)
+        RY = np.zeros((oY * (nY - oY),) * 2)
+        oracle.coupling_add(V, eX, eY, oX, oY, RX, RY)
+        assert abs(np.trace(RX) - EJ / 2) <= 1e-13 * abs(EJ)
+        assert abs(np.trace(RY) - EJ / 2) <= 1e-13 * abs(EJ)
+
+
+def test_coupling_rank1_closed_form():
+    """Rank-1 separable integrals (naux = 1, B = z z^T) with degenerate
+    orbital energies: (ia|jb) = s x_i x_a y_j y_b and D is one constant, so
+    R_X = 2 D s^2 (sum_j y_j^2)(sum_b y_b^2) (x_i x_a)(x_i1 x_a1)."""
+    nX, nY, oX, oY = 7, 6, 2, 2
+    rng = np.random.default_rng(23)
+    z = rng.standard_normal(nX + nY)
+    s = 0.3
+    A, K = synth.eri_blocks(np.outer(z, z)[None], nX, s)
+    CX = np.linalg.qr(rng.standard_normal((nX, nX)))[0]
+    CY = np.linalg.qr(rng.standard_normal((nY, nY)))[0]
+    eo, ev = -0.8, 1.1
+    eX = np.array([eo] * oX + [ev] * (nX - oX))
+    eY = np.array([eo] * oY + [ev] * (nY - oY))
+    V = oracle.transform_J(A, CX, CY, oX, oY)
+    RX = np.zeros((oX * (nX - oX),) * 2)
+    RY = np.zeros((oY * (nY - oY),) * 2)
+    oracle.coupling_add(V, eX, eY, oX, oY, RX, RY)
+    x, y = CX.T @ z[:nX], CY.T @ z[nX:]
+    D = 1.0 / (2 * eo - 2 * ev)
+    u = np.outer(x[:oX], x[oX:]).ravel()
+    ref = 2 * D * s * s * np.sum(y[:oY] ** 2) * np.sum(y[oY:] ** 2) * np.outer(u, u)
+    assert np.max(np.abs(RX - ref)) <= 1e-13 * np.max(np.abs(ref))
+    w_ = np.outer(y[:oY], y[oY:]).ravel()
+    refY = 2 * D * s * s * np.sum(x[:oX] ** 2) * np.sum(x[oX:] ** 2) * np.outer(w_, w_)
+    assert np.max(np.abs(RY - refY)) <= 1e-13 * np.max(np.abs(refY))
