@@ -223,8 +223,9 @@ def our_arm(args, ws, rank, local):
 
     stream = torch.cuda.Stream()
 
-    def make_ctx(prec, timing):
-        ctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing)
+    def make_ctx(prec, timing, coupling=False):
+        ctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing,
+                        coupling=coupling)
         for m in mons:
             ctx.add_monomer(m.C, m.eps, m.nocc)
         base = buf.data_ptr()
@@ -326,6 +327,34 @@ def our_arm(args, ws, rank, local):
     gctx.close()
 
     if not args.no_extras and rank == 0:
+        # ---- the dimer -> monomer doubles coupling of Eq. (tm2) at first order on
+        # the same inputs: the same runs with coupling on, the difference timed
+        cc = make_ctx(args.precision, False, coupling=True)
+        cc.run()
+        cmj = cc.energies()[0]
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            c0.record(stream)
+            for _ in range(args.steps):
+                cc.run()
+            c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        cflops = 0.0
+        for X, Y in w.pairs:
+            mX = w.nocc[X] * (w.nao[X] - w.nocc[X])
+            mY = w.nocc[Y] * (w.nao[Y] - w.nocc[Y])
+            cflops += 2 * 2 * (mX * mX * mY + mY * mY * mX)
+        trace_err = max(abs(np.trace(cc.coupling(X, w.nao[X], w.nocc[X])) - cmj[X]) / abs(cmj[X])
+                        for X in range(w.n_monomers))
+        line["coupling"] = {"ms_per_step": cms, "extra_ms_per_step": cms - gms,
+                            "tflops": cflops / ((cms - gms) * 1e-3) / 1e12 if cms > gms else None,
+                            "alg_gflop_per_step": cflops / 1e9,
+                            "max_rel_trace_minus_monomer_EJ": trace_err,
+                            "what": "R_X = sum_Y (T V^t + V T^t) of Eq. (tm2) at T = vD, every monomer"}
+        cc.close()
+
         # ---- the plain FP64 GPU form on the same resident inputs
         if args.precision != "fp64":
             c64 = make_ctx("fp64", True)

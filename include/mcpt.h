@@ -85,6 +85,10 @@ typedef struct {
     int graphs;               /* 1: with timing = 0, replay each run as a CUDA graph captured on the
                                  first run of a plan (the plan = dimer set, range and precision);
                                  runs on a stream that is itself being captured are launched directly */
+    int coupling;             /* 1: mcpt_run also forms each monomer's dimer -> monomer doubles
+                                 coupling R_X of Eq. (tm2) at first order (see mcpt_coupling); the
+                                 dimers' (ia|jb) and T = vD stay on the device (2 o_X v_X o_Y v_Y
+                                 elements each) */
 } mcpt_options;
 
 /* Defaults: device 0, own stream, MCPT_FP64, validate 1, 1 GiB waves, no cache, no timing,
@@ -168,11 +172,25 @@ mcpt_status mcpt_run_range(mcpt_handle h, int first, int count);
 mcpt_status mcpt_energies(mcpt_handle h, double *per_monomer_J, double *per_monomer_K,
                           double *per_dimer, double *total);
 
-/* Per-phase timing and launch counts of every run since the previous call
+/* Dimer -> monomer doubles coupling of Eq. (tm2) (the sum over the
+ * neighbours' occupied k and virtual c), evaluated at the first-order dimer
+ * amplitudes T^{ab}_{ij} = (ia|jb) D^{ij}_{ab} of the last mcpt_run:
+ *   R_X[(i,a)][(i1,a1)] = sum_{Y, k, c} (i1 a1|k c) T^{ac}_{ik} + (i a|k c) T^{a1 c}_{i1 k}
+ * over every registered dimer containing X (i, i1 occupied and a, a1 virtual
+ * orbitals of X).  R: caller's buffer of (o_X v_X)^2 doubles, row-major,
+ * index i * v_X + a; symmetric.  Waits for the handle's stream.
+ * Arithmetic: the form's (FP32 for the mixed forms, FP64 for the FP64 form),
+ * summed over dimers in ascending order.
+ * Errors: EINVAL (unknown X, NULL), ESTATE (options.coupling = 0, or no
+ *   mcpt_run of every dimer since the integrals last changed), ECUDA. */
+mcpt_status mcpt_coupling(mcpt_handle h, int X, double *R);
+
+/* Per-phase timing and launch counts of every run since the previous call/* Per-phase timing and launch counts of every run since the previous call
  * (timing requires options.timing = 1; CUDA events are recorded on the
  * handle's stream around each phase, and this call waits for the stream).
  * ms[0] = first half (the AO-reading transform kernel), ms[1] = finish
- * (second half + denominators + energies), ms[2] = per-monomer reduction,
+ * (second half + denominators + energies), ms[2] = per-monomer reduction
+ * (and the coupling, when enabled),
  * ms[3] = whole run: each summed over the `runs` collected runs;
  * launches = kernels those runs launched; waves = waves per run;
  * alg_bytes = algorithmic AO bytes read per run (2 nX^2 nY^2 x 8 B per dimer);

@@ -29,7 +29,7 @@ MCPT_UPDATE_ASYNC = 1
 # every symbol include/mcpt.h declares
 EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer",
            "mcpt_set_precision",
-           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats", "mcpt_num_monomers",
+           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_collect_stats", "mcpt_num_monomers",
            "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
 
 
@@ -42,7 +42,8 @@ class McptError(RuntimeError):
 class mcpt_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("validate", ctypes.c_int), ("wave_bytes", ctypes.c_size_t), ("tune_cache", ctypes.c_char_p),
-                ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int),
+                ("coupling", ctypes.c_int)]
 
 
 class mcpt_run_stats(ctypes.Structure):
@@ -72,9 +73,10 @@ def lib():
         L.mcpt_run.argtypes = [H]
         L.mcpt_run_range.argtypes = [H, I, I]
         L.mcpt_energies.argtypes = [H, P, P, P, P]
+        L.mcpt_coupling.argtypes = [H, I, P]
         L.mcpt_collect_stats.argtypes = [H, ctypes.POINTER(mcpt_run_stats)]
         for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer", "mcpt_set_precision", "mcpt_run",
-                  "mcpt_run_range", "mcpt_energies", "mcpt_collect_stats"):
+                  "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_collect_stats"):
             getattr(L, f).restype = I
         L.mcpt_num_monomers.argtypes = [H]
         L.mcpt_num_monomers.restype = I
@@ -163,6 +165,12 @@ def mcpt_energies(h):
     return mj, mk, pd, tot
 
 
+def mcpt_coupling(h, X: int, dim: int) -> np.ndarray:
+    R = np.empty((dim, dim))
+    _check(h, lib().mcpt_coupling(h, X, _ptr(R)))
+    return R
+
+
 def mcpt_collect_stats(h) -> mcpt_run_stats:
     s = mcpt_run_stats()
     _check(h, lib().mcpt_collect_stats(h, ctypes.byref(s)))
@@ -193,7 +201,7 @@ class Context:
     ``torch.cuda.current_stream().cuda_stream``) or None for a library stream."""
 
     def __init__(self, precision="fp64", device=0, stream=None, validate=True, wave_bytes=0, timing=False,
-                 mem_cap_bytes=0, graphs=True, tune_cache=None):
+                 mem_cap_bytes=0, graphs=True, tune_cache=None, coupling=False):
         o = mcpt_default_options()
         if tune_cache is not None:
             o.tune_cache = os.fsencode(tune_cache)
@@ -205,6 +213,7 @@ class Context:
         o.timing = int(bool(timing))
         o.mem_cap_bytes = mem_cap_bytes
         o.graphs = int(bool(graphs))
+        o.coupling = int(bool(coupling))
         self.validate = bool(validate)
         self.stream = stream
         self.h = mcpt_create(o)
@@ -237,6 +246,11 @@ class Context:
 
     def energies(self):
         return mcpt_energies(self.h)
+
+    def coupling(self, X, nao, nocc):
+        """R_X of Eq. (tm2)'s dimer coupling, (nocc (nao - nocc))^2, after a run
+        of a context created with coupling=True."""
+        return mcpt_coupling(self.h, X, nocc * (nao - nocc))
 
     def stats(self):
         """Timing and launch counts of the runs since the previous call."""

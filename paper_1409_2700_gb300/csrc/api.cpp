@@ -61,6 +61,7 @@ struct mcpt_ctx {
     std::map<std::string, TcTune> tuned;   // launch choices by wave signature
     int timing = 0;
     int graphs = 1;
+    int coupling = 0;
     size_t mem_cap = 0;
     size_t mem_used = 0;
 
@@ -84,6 +85,14 @@ struct mcpt_ctx {
     size_t capH = 0;
     void* dWork = nullptr;
     size_t capWork = 0;
+    void* dVT = nullptr;             // coupling: every dimer's (ia|jb) and T = vD
+    size_t capVT = 0;
+    void* dCoup = nullptr;           // coupling tables: tiles, per-dimer info, monomer sizes, R offsets
+    size_t capCoup = 0;
+    double* dR = nullptr;            // coupling matrices R_X, per monomer
+    size_t capR = 0;
+    std::vector<long long> r_off;    // host copy of the R offsets
+    bool coupled = false;            // R holds the coupling of the current integrals
     int* dFold = nullptr;            // split dimers: (dimer, first block slot, blocks)
     size_t capFold = 0;
     void* dFin = nullptr;            // second-half tasks of waves above 32 AO (+ first-task indices)
@@ -115,6 +124,9 @@ struct mcpt_ctx {
         std::vector<Wave> waves;
         double alg_bytes = 0, alg_flops = 0, alg_flops_half = 0;
         int nfold = 0;                     // split dimers whose block results are folded
+        bool coupling = false;             // the plan stores (ia|jb), T and forms R
+        int ntiles = 0;                    // coupling output tiles
+        size_t off_tiles = 0, off_dims = 0, off_mdim = 0, off_roff = 0;   // into dCoup
         cudaGraphExec_t graph = nullptr;   // the plan's launch sequence, captured on first use
         int graph_launches = 0;
     } plan;
@@ -270,6 +282,7 @@ void mcpt_default_options(mcpt_options* o)
     o->timing = 0;
     o->mem_cap_bytes = 0;
     o->graphs = 1;
+    o->coupling = 0;
 }
 
 mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
@@ -307,6 +320,7 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     h->tune_cache = o.tune_cache ? o.tune_cache : "";
     h->timing = o.timing;
     h->graphs = o.graphs;
+    h->coupling = o.coupling;
     h->mem_cap = o.mem_cap_bytes;
     if (o.stream) {
         h->stream = static_cast<cudaStream_t>(o.stream);
@@ -481,6 +495,7 @@ mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_a
     if (st) return st;
     h->dims.push_back(r);
     h->pairs.insert(key);
+    h->coupled = false;
     h->plan.valid = false;
     h->lists_dirty = true;
     if (id_out) *id_out = (int)h->dims.size() - 1;
@@ -509,6 +524,7 @@ mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double* ao, mcpt_ao_l
     if (r.E[0] != old.E[0] || r.E[1] != old.E[1] || std::memcmp(r.st, old.st, sizeof r.st))
         h->plan.valid = false;              // the tensor maps name the old addresses
     h->dims[id] = r;
+    h->coupled = false;
     return MCPT_OK;
 }
 
@@ -663,6 +679,9 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
     }
 
     h->hDesc.clear();
+    // the coupling needs every dimer's amplitudes at once: full runs only
+    const bool coupled_plan = h->coupling && first == 0 && count == D;
+    long long vt_total = 0;
     std::vector<std::pair<int, int>> waves;   // [begin, end) into hDesc
     std::vector<int> fold;                    // split dimers: (dimer, first block slot, blocks)
     int nblk_extra = 0;                       // result slots of blocks past the D dimers
@@ -685,6 +704,12 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         base.eXv = mX.offE + mX.nocc; base.eYv = mY.offE + mY.nocc;
         base.vX = mX.nao - mX.nocc; base.vY = mY.nao - mY.nocc;
         base.X = r.X; base.Y = r.Y;
+        base.oXt = mX.nocc; base.oYt = mY.nocc;
+        base.vt_off = -1;
+        if (coupled_plan) {
+            base.vt_off = vt_total;
+            vt_total += 2LL * mX.nocc * (mX.nao - mX.nocc) * mY.nocc * (mY.nao - mY.nocc);
+        }
         // tensor-core work items hold at most kMaxOccTensor occupied orbitals per
         // monomer: larger occupations run as near-equal blocks of (i, j)
         const int bx = is_tensor_form(prec) ? (mX.nocc + kMaxOccTensor - 1) / kMaxOccTensor : 1;
@@ -698,6 +723,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
                 const int i0 = ib * mX.nocc / bx, i1 = (ib + 1) * mX.nocc / bx;
                 const int j0 = jb * mY.nocc / by, j1 = (jb + 1) * mY.nocc / by;
                 dd.oX = i1 - i0; dd.oY = j1 - j0;
+                dd.iX0 = i0; dd.jY0 = j0;
                 dd.cX = mX.offC + i0; dd.cY = mY.offC + j0;
                 dd.eX = mX.offE + i0; dd.eY = mY.offE + j0;
                 dd.npad = npad_for(dd.oX, dd.oY);
@@ -757,6 +783,51 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
             total += (tc_work_bytes(prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3, h->hDesc.data() + w.first, w.second - w.first) + 255) & ~(size_t)255;
         }
         if ((st = ensure(h, &h->dWork, &h->capWork, total))) return st;
+    }
+    P.coupling = coupled_plan;
+    P.ntiles = 0;
+    if (coupled_plan) {
+        const size_t elem = prec == MCPT_FP64 ? sizeof(double) : sizeof(float);
+        if ((st = ensure(h, &h->dVT, &h->capVT, (size_t)vt_total * elem))) return st;
+        // tables: output tiles, per-dimer info, monomer sizes o v, R offsets
+        std::vector<CoupTile> tiles;
+        std::vector<CoupDim> cds(D);
+        std::vector<int> mdim(N);
+        h->r_off.assign(N, 0);
+        long long roff = 0;
+        for (int m = 0; m < N; m++) {
+            const int mm = h->mons[m].nocc * (h->mons[m].nao - h->mons[m].nocc);
+            mdim[m] = mm;
+            h->r_off[m] = roff;
+            roff += (long long)mm * mm;
+            for (int p0 = 0; p0 < mm; p0 += 64)
+                for (int q0 = 0; q0 < mm; q0 += 64) tiles.push_back(CoupTile{m, p0, q0});
+        }
+        long long vt = 0;
+        for (int d = 0; d < D; d++) {
+            const MonomerRec& mX = h->mons[h->dims[d].X];
+            const MonomerRec& mY = h->mons[h->dims[d].Y];
+            cds[d] = CoupDim{h->dims[d].X, h->dims[d].Y, mX.nocc * (mX.nao - mX.nocc), mY.nocc * (mY.nao - mY.nocc),
+                             vt};
+            vt += 2LL * cds[d].mX * cds[d].mY;
+        }
+        std::vector<unsigned char> tab;
+        auto put = [&](const void* src, size_t bytes) {
+            tab.resize((tab.size() + 15) & ~(size_t)15);
+            const size_t off = tab.size();
+            tab.resize(off + bytes);
+            std::memcpy(tab.data() + off, src, bytes);
+            return off;
+        };
+        P.off_tiles = put(tiles.data(), tiles.size() * sizeof(CoupTile));
+        P.off_dims = put(cds.data(), cds.size() * sizeof(CoupDim));
+        P.off_mdim = put(mdim.data(), mdim.size() * sizeof(int));
+        P.off_roff = put(h->r_off.data(), h->r_off.size() * sizeof(long long));
+        P.ntiles = (int)tiles.size();
+        if ((st = ensure(h, &h->dCoup, &h->capCoup, tab.size()))) return st;
+        if ((st = ensure(h, &h->dR, &h->capR, (size_t)roff * sizeof(double)))) return st;
+        CK(h, cudaMemcpyAsync(h->dCoup, tab.data(), tab.size(), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));   // tab is pageable and goes out of scope
     }
     CK(h, cudaMemcpyAsync(h->dDesc, h->hDesc.data(), ndesc * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
     if (!fold.empty())
@@ -887,10 +958,12 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
         double* part = wv.ntasks ? h->dPart + 2 * wv.part_off : nullptr;
         if (prec == MCPT_FP64)
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
-                                     tasks, wv.ntasks, part, h->stream));
+                                     tasks, wv.ntasks, part, P.coupling ? static_cast<double*>(h->dVT) : nullptr,
+                                     h->stream));
         else
             CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dCf, h->dE, static_cast<const float*>(h->dH), h->dE2,
-                                     tasks, wv.ntasks, part, h->stream));
+                                     tasks, wv.ntasks, part, P.coupling ? static_cast<float*>(h->dVT) : nullptr,
+                                     h->stream));
         launches += wv.ntasks ? 2 : 1;
         if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
     }
@@ -900,6 +973,20 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
     }
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
     CK(h, launch_reduce(h->dE2, D, L, h->dMon, h->dTot, h->stream));
+    if (P.coupling) {
+        const char* tab = static_cast<const char*>(h->dCoup);
+        const CoupTile* tiles = reinterpret_cast<const CoupTile*>(tab + P.off_tiles);
+        const CoupDim* cds = reinterpret_cast<const CoupDim*>(tab + P.off_dims);
+        const int* mdim = reinterpret_cast<const int*>(tab + P.off_mdim);
+        const long long* roff = reinterpret_cast<const long long*>(tab + P.off_roff);
+        if (prec == MCPT_FP64)
+            CK(h, launch_coupling_fp64(tiles, P.ntiles, cds, L, mdim, roff, static_cast<const double*>(h->dVT), h->dR,
+                                       h->stream));
+        else
+            CK(h, launch_coupling_fp32(tiles, P.ntiles, cds, L, mdim, roff, static_cast<const float*>(h->dVT), h->dR,
+                                       h->stream));
+        launches++;
+    }
     launches++;
     if (ev) CK(h, cudaEventRecord((*ev)[2 * W + 1], h->stream));
     *launches_out = launches;
@@ -966,6 +1053,7 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
     h->stats.alg_flops = P.alg_flops;
     h->stats.alg_flops_half = P.alg_flops_half;
     h->ran = true;
+    h->coupled = P.coupling;
     return MCPT_OK;
 }
 
@@ -1004,6 +1092,25 @@ mcpt_status mcpt_energies(mcpt_handle h, double* mon_J, double* mon_K, double* p
     if (mon_K) CK(h, cudaMemcpy(mon_K, h->dMon + N, N * sizeof(double), cudaMemcpyDeviceToHost));
     if (per_dimer) CK(h, cudaMemcpy(per_dimer, h->dE2, 2 * (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
     if (total) CK(h, cudaMemcpy(total, h->dTot, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_coupling(mcpt_handle h, int X, double* R)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_coupling: NULL handle");
+    if (X < 0 || X >= (int)h->mons.size())
+        return fail(h, MCPT_EINVAL, "mcpt_coupling: unknown monomer %d of %zu", X, h->mons.size());
+    if (!R) return fail(h, MCPT_EINVAL, "mcpt_coupling: R is NULL");
+    if (!h->coupling) return fail(h, MCPT_ESTATE, "mcpt_coupling: the context was created with coupling = 0");
+    if (!h->coupled)
+        return fail(h, MCPT_ESTATE, "mcpt_coupling: no mcpt_run of every dimer since the integrals last changed");
+    CK(h, cudaSetDevice(h->device));
+    const size_t mm = (size_t)h->mons[X].nocc * (h->mons[X].nao - h->mons[X].nocc);
+    CK(h, cudaStreamSynchronize(h->stream));
+    int status = 0;
+    CK(h, cudaMemcpy(&status, h->dFlag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) return fail(h, MCPT_ETIMEOUT, "mcpt_coupling: a device-side wait gave up (status 0x%x)", status);
+    CK(h, cudaMemcpy(R, h->dR + h->r_off[X], mm * mm * sizeof(double), cudaMemcpyDeviceToHost));
     return MCPT_OK;
 }
 
@@ -1061,6 +1168,9 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dWork);
     cudaFree(h->dFin);
     cudaFree(h->dFold);
+    cudaFree(h->dVT);
+    cudaFree(h->dCoup);
+    cudaFree(h->dR);
     cudaFree(h->dPart);
     cudaFree(h->dE2);
     cudaFree(h->dMon);

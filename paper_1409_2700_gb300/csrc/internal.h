@@ -36,6 +36,10 @@ struct DimerDesc {
     int cXv, cYv;         // pool offsets of the first virtual column of C_X, C_Y
     int eXv, eYv;         // pool offsets of the first virtual eps_X, eps_Y
     int vX, vY;           // virtual orbital counts
+    int iX0, jY0;         // first occupied orbital of this block within the monomer
+    int oXt, oYt;         // the monomers' occupied counts
+    long long vt_off;     // coupling storage of the dimer (-1: none): (ia|jb) then T = vD, each
+                          //   [(j,b)][(i,a)] of (oYt vY) x (oXt vX) elements
     // A dimer whose occupations exceed what one tensor-core work item holds
     // runs as several descriptors, one per block of occupied orbitals (i, j);
     // each covers all virtual orbitals, and their terms are added per dimer.
@@ -80,12 +84,37 @@ void finish_tasks(const DimerDesc* h_desc, int nd, int pairs_per_task, std::vect
 // Waves whose monomers all have <= 32 AO run one CTA per dimer; larger ones
 // run the tasks (`tasks`, device array of `ntasks`) and sum each dimer's
 // task partials (`part`, 2 doubles per task) in task order.
+// With VT non-null, descriptors with vt_off >= 0 also store their (ia|jb)
+// and T = vD for the coupling.
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
                                const double* Cpool, const double* Epool, const double* H,
-                               double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s);
+                               double* E2, const FinTask* tasks, int ntasks, double* part, double* VT,
+                               cudaStream_t s);
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
                                const float* Cf, const double* Epool, const float* H,
-                               double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s);
+                               double* E2, const FinTask* tasks, int ntasks, double* part, float* VT,
+                               cudaStream_t s);
+
+// Dimer -> monomer doubles coupling of Eq. (tm2) at first order.
+struct CoupDim {
+    int X, Y;             // monomer ids
+    int mX, mY;           // oX vX and oY vY
+    long long vt_off;     // (ia|jb) at vt_off, T at vt_off + mX*mY, both [(j,b)][(i,a)]
+};
+struct CoupTile {
+    int mon;              // monomer
+    int p0, q0;           // output tile origin in R_mon
+};
+// R_mon = sum over the monomer's dimers (ascending) of T V^T + V T^T (X side)
+// or the transposed contractions (Y side); one CTA per 64 x 64 output tile.
+// dims: every dimer; lists: the per-monomer dimer lists; R: per monomer at
+// r_off[mon], (o v)^2 doubles row-major.  T = float or double storage.
+cudaError_t launch_coupling_fp32(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists,
+                                 const int* mdim, const long long* r_off, const float* VT, double* R,
+                                 cudaStream_t s);
+cudaError_t launch_coupling_fp64(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists,
+                                 const int* mdim, const long long* r_off, const double* VT, double* R,
+                                 cudaStream_t s);
 
 // Split dimers: E2[dimer] = sum, in block order, of E2[first .. first+n) for
 // each (dimer, first, n) triple of `fold` (device, 3 ints each).

@@ -39,6 +39,10 @@ __device__ __forceinline__ double warp_sum(double v)
 template <typename T> constexpr int kSteps = sizeof(T) == 8 ? 2 : 1;
 
 __device__ __forceinline__ double to_f64(double x) { return x; }
+// FP64 to the storage type (FP32 through the integer pipes)
+template <typename T> __device__ __forceinline__ T narrow(double x);
+template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <> __device__ __forceinline__ float narrow<float>(double x) { return f32_from_f64(x); }
 __device__ __forceinline__ double to_f64(float x) { return f64_from_f32(x); }   // integer pipes
 
 // ---------------------------------------------------------------------------
@@ -94,7 +98,7 @@ __device__ __forceinline__ void slice_wait()
 template <typename T>
 __global__ void __launch_bounds__(kW32Warps * 32, 4)
 k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
-             const T* __restrict__ H, double* __restrict__ E2)
+             const T* __restrict__ H, double* __restrict__ E2, T* __restrict__ VT)
 {
     const DimerDesc& d = dd[blockIdx.x];
     const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
@@ -142,6 +146,10 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 
     const bool live = lane < vX;
     const double ea = live ? Epool[d.eXv + lane] : 0.0;   // this lane's virtual orbital a
+    // coupling storage: (ia|jb) and T = vD as [(j,b)][(i,a)] over the whole dimer
+    const bool store = VT != nullptr && d.vt_off >= 0;
+    const long long mXc = (long long)d.oXt * vX, mYc = (long long)d.oYt * vY;
+    T* const Vst = store ? VT + d.vt_off : nullptr;
     double ej = 0.0, ek = 0.0;
     int x = 0;                                   // buffer holding this pair's H0
     for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
@@ -197,10 +205,16 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                     v1 = fma(CYT[b * 32 + lam + 1], tk[lam + 1], v1);
                 }
                 if (live) {
-                    const double va = to_f64(SX[lane * 33 + b]);
+                    const T vab = SX[lane * 33 + b];
+                    const double va = to_f64(vab);
                     const double t = div_newton<kSteps<T>>(va, eija - eYv[b]);   // v D
                     ej = fma(t, va, ej);
                     ek = fma(t, to_f64(v0 + v1), ek);
+                    if (store) {
+                        const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
+                        Vst[e] = vab;
+                        Vst[mXc * mYc + e] = narrow<T>(t);
+                    }
                 }
             }
         }
@@ -291,10 +305,10 @@ __device__ __forceinline__ void copy_slice(T* S, const T* __restrict__ src, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTThreads)
+__global__ void __launch_bounds__(kTThreads, 2)
 k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tasks, const T* __restrict__ C,
                const double* __restrict__ Epool, const T* __restrict__ H, double* __restrict__ part,
-               int smem_elems)
+               int smem_elems, T* __restrict__ VT)
 {
     const FinTask tk = tasks[blockIdx.x];
     const DimerDesc& d = dd[tk.dimer];
@@ -328,6 +342,9 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     const int nb3 = ((nY + kTM - 1) / kTM) * bn_vX;          // TmK
     const int nb2 = ((vX + kTM - 1) / kTM) * bn_vY;          // VA, VKT
 
+    const bool store = VT != nullptr && d.vt_off >= 0;
+    const long long mXc = (long long)d.oXt * vX, mYc = (long long)d.oYt * vY;
+    T* const Vst = store ? VT + d.vt_off : nullptr;
     double ej = 0.0, ek = 0.0;
     for (int g0 = tk.pr0; g0 < tk.pr1; g0 += gmax) {
         const int np = min(gmax, tk.pr1 - g0);
@@ -390,10 +407,17 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
                 for (int b = 0; b < kTN; b++) {
                     const int m = m0 + a, n = n0 + b;
                     if (m < vX && n < vY) {
-                        const double va = to_f64(Vp[m * vY + n]);
+                        const T vab = Vp[m * vY + n];
+                        const double va = to_f64(vab);
                         const double t = div_newton<kSteps<T>>(va, eij - (eXv[m] + eYv[n]));   // v D
                         ej = fma(t, va, ej);
                         ek = fma(t, to_f64(acc[a][b]), ek);
+                        if (store) {
+                            const long long e =
+                                ((long long)(d.jY0 + j) * vY + n) * mXc + (long long)(d.iX0 + i) * vX + m;
+                            Vst[e] = vab;
+                            Vst[mXc * mYc + e] = narrow<T>(t);
+                        }
                     }
                 }
         }
@@ -432,14 +456,15 @@ __global__ void k_finish_sum(const DimerDesc* __restrict__ dd, int nd, const Fin
 
 template <typename T>
 cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* C, const double* Epool,
-                          const T* H, double* E2, const FinTask* tasks, int ntasks, double* part, cudaStream_t s)
+                          const T* H, double* E2, const FinTask* tasks, int ntasks, double* part, T* VT,
+                          cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
     if (max_ao <= 32) {
         const size_t smem = w32_smem_bytes<T>();
         cudaError_t e = cudaFuncSetAttribute(k_finish_w32<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_finish_w32<T><<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2);
+        k_finish_w32<T><<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
         return cudaGetLastError();
     }
     if (!tasks || ntasks <= 0 || !part) return cudaErrorInvalidValue;
@@ -448,7 +473,7 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     cudaError_t e = cudaFuncSetAttribute(k_finish_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int smem_elems = (int)((smem - 2 * max_ao * sizeof(double) - 64) / sizeof(T));
-    k_finish_tiled<T><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part, smem_elems);
+    k_finish_tiled<T><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part, smem_elems, VT);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the dimers' first-task indices follow the task array
     const int* first = reinterpret_cast<const int*>(tasks + ntasks);
@@ -568,16 +593,16 @@ __global__ void k_check_finite4(const double* __restrict__ x, int d0, int d1, in
 
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
                                const double* Epool, const double* H, double* E2, const FinTask* tasks,
-                               int ntasks, double* part, cudaStream_t s)
+                               int ntasks, double* part, double* VT, cudaStream_t s)
 {
-    return launch_finish<double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, s);
+    return launch_finish<double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, VT, s);
 }
 
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const float* Cf,
                                const double* Epool, const float* H, double* E2, const FinTask* tasks,
-                               int ntasks, double* part, cudaStream_t s)
+                               int ntasks, double* part, float* VT, cudaStream_t s)
 {
-    return launch_finish<float>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, s);
+    return launch_finish<float>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s);
 }
 
 void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinTask>* out)
