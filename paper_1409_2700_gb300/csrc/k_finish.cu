@@ -95,7 +95,9 @@ __device__ __forceinline__ void slice_wait()
     __syncwarp();
 }
 
-template <typename T>
+// STORE: also write the dimer's (ia|jb) and T for the coupling (a separate
+// instantiation keeps the plain path's registers).
+template <typename T, bool STORE>
 __global__ void __launch_bounds__(kW32Warps * 32, 4)
 k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
              const T* __restrict__ H, double* __restrict__ E2, T* __restrict__ VT)
@@ -147,7 +149,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     const bool live = lane < vX;
     const double ea = live ? Epool[d.eXv + lane] : 0.0;   // this lane's virtual orbital a
     // coupling storage: (ia|jb) and T = vD as [(j,b)][(i,a)] over the whole dimer
-    const bool store = VT != nullptr && d.vt_off >= 0;
+    const bool store = STORE && d.vt_off >= 0;
     const long long mXc = (long long)d.oXt * vX, mYc = (long long)d.oYt * vY;
     T* const Vst = store ? VT + d.vt_off : nullptr;
     double ej = 0.0, ek = 0.0;
@@ -462,9 +464,10 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     if (nd <= 0) return cudaSuccess;
     if (max_ao <= 32) {
         const size_t smem = w32_smem_bytes<T>();
-        cudaError_t e = cudaFuncSetAttribute(k_finish_w32<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto fn = VT ? k_finish_w32<T, true> : k_finish_w32<T, false>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_finish_w32<T><<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
+        fn<<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
         return cudaGetLastError();
     }
     if (!tasks || ntasks <= 0 || !part) return cudaErrorInvalidValue;

@@ -720,6 +720,24 @@ __device__ __forceinline__ void digits4(float y, float (&d)[4])
     y = fmaf(-d[2], 256.0f, y);
     d[3] = rint_scaled(y, 1.0f);
 }
+// digits4 for two values at once with the packed FP32 instructions of sm_100+
+// (one issue per pair of lanes' values): the same operations, elementwise.
+__device__ __forceinline__ float2 rint_scaled2(float2 v, float scale)
+{
+    const float2 m = make_float2(12582912.0f, 12582912.0f);
+    return __fadd2_rn(__ffma2_rn(v, make_float2(scale, scale), m), make_float2(-12582912.0f, -12582912.0f));
+}
+__device__ __forceinline__ void digits4x2(float2 y, float2 (&d)[4])
+{
+    d[0] = rint_scaled2(y, 0x1p-24f);
+    y = __ffma2_rn(d[0], make_float2(-16777216.0f, -16777216.0f), y);
+    d[1] = rint_scaled2(y, 0x1p-16f);
+    y = __ffma2_rn(d[1], make_float2(-65536.0f, -65536.0f), y);
+    d[2] = rint_scaled2(y, 0x1p-8f);
+    y = __ffma2_rn(d[2], make_float2(-256.0f, -256.0f), y);
+    d[3] = rint_scaled2(y, 1.0f);
+}
+
 // Two BF16 digits (exact: integers of at most 9 bits) packed low | high.
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi)
 {
@@ -892,11 +910,10 @@ __device__ __forceinline__ int convert_row_fx1(const double* __restrict__ F, uns
         unsigned w[4][4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            float d[2][4];
+            float2 d[4];
+            digits4x2(make_float2(fx_y(v[q][e].x, v[q][e].y, fr), fx_y(v[q][e + 1].x, v[q][e + 1].y, fr)), d);
 #pragma unroll
-            for (int u = 0; u < 2; u++) digits4(fx_y(v[q][e + u].x, v[q][e + u].y, fr), d[u]);
-#pragma unroll
-            for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(d[0][k], d[1][k]);
+            for (int k = 0; k < 4; k++) w[k][e / 2] = pack_bf16(d[k].x, d[k].y);
         }
         *reinterpret_cast<uint4*>(A1 + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w[0][0], w[0][1], w[0][2], w[0][3]);
         *reinterpret_cast<uint4*>(A1 + cr.dst + (((4 + c) ^ cr.r7) << 4)) =
