@@ -125,7 +125,7 @@ struct mcpt_ctx {
         double alg_bytes = 0, alg_flops = 0, alg_flops_half = 0;
         int nfold = 0;                     // split dimers whose block results are folded
         bool coupling = false;             // the plan stores (ia|jb), T and forms R
-        int ntiles = 0;                    // coupling output tiles
+        int ntile[3] = {0, 0, 0};          // coupling output tiles of edge 64, 48, 32
         size_t off_tiles = 0, off_dims = 0, off_mdim = 0, off_roff = 0;   // into dCoup
         cudaGraphExec_t graph = nullptr;   // the plan's launch sequence, captured on first use
         int graph_launches = 0;
@@ -785,31 +785,54 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         if ((st = ensure(h, &h->dWork, &h->capWork, total))) return st;
     }
     P.coupling = coupled_plan;
-    P.ntiles = 0;
+    P.ntile[0] = P.ntile[1] = P.ntile[2] = 0;
     if (coupled_plan) {
         const size_t elem = prec == MCPT_FP64 ? sizeof(double) : sizeof(float);
         if ((st = ensure(h, &h->dVT, &h->capVT, (size_t)vt_total * elem))) return st;
         // tables: output tiles, per-dimer info, monomer sizes o v, R offsets
-        std::vector<CoupTile> tiles;
         std::vector<CoupDim> cds(D);
         std::vector<int> mdim(N);
+        std::vector<long long> rows(N, 0);          // rows each monomer's tiles sum over
         h->r_off.assign(N, 0);
         long long roff = 0;
         for (int m = 0; m < N; m++) {
-            const int mm = h->mons[m].nocc * (h->mons[m].nao - h->mons[m].nocc);
-            mdim[m] = mm;
+            mdim[m] = h->mons[m].nocc * (h->mons[m].nao - h->mons[m].nocc);
             h->r_off[m] = roff;
-            roff += (long long)mm * mm;
-            for (int p0 = 0; p0 < mm; p0 += 64)
-                for (int q0 = 0; q0 < mm; q0 += 64) tiles.push_back(CoupTile{m, p0, q0});
+            roff += (long long)mdim[m] * mdim[m];
         }
         long long vt = 0;
         for (int d = 0; d < D; d++) {
-            const MonomerRec& mX = h->mons[h->dims[d].X];
-            const MonomerRec& mY = h->mons[h->dims[d].Y];
-            cds[d] = CoupDim{h->dims[d].X, h->dims[d].Y, mX.nocc * (mX.nao - mX.nocc), mY.nocc * (mY.nao - mY.nocc),
-                             vt};
+            const int X = h->dims[d].X, Y = h->dims[d].Y;
+            cds[d] = CoupDim{X, Y, mdim[X], mdim[Y], vt};
             vt += 2LL * cds[d].mX * cds[d].mY;
+            rows[X] += mdim[Y];
+            rows[Y] += mdim[X];
+        }
+        // per monomer the tile edge with the least padded upper-triangle work,
+        // smaller edges weighted for their extra staging per FMA; within an
+        // edge the monomers with the longest sums start first
+        static const int kEdge[3] = {64, 48, 32};
+        std::vector<int> cls(N), order(N);
+        for (int m = 0; m < N; m++) {
+            double best = 0;
+            for (int c = 0; c < 3; c++) {
+                const double nt = (mdim[m] + kEdge[c] - 1) / kEdge[c];
+                const double cost = nt * (nt + 1) / 2 * kEdge[c] * kEdge[c] * (1.0 + 16.0 / kEdge[c]);
+                if (c == 0 || cost < best) { best = cost; cls[m] = c; }
+            }
+            order[m] = m;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return rows[a] > rows[b]; });
+        std::vector<CoupTile> tiles;
+        for (int c = 0; c < 3; c++) {
+            const size_t before = tiles.size();
+            for (int m : order) {
+                if (cls[m] != c || mdim[m] == 0) continue;    // a monomer with no dimers gets R = 0
+                const int e = kEdge[c];
+                for (int p0 = 0; p0 < mdim[m]; p0 += e)
+                    for (int q0 = p0; q0 < mdim[m]; q0 += e) tiles.push_back(CoupTile{m, p0, q0});
+            }
+            P.ntile[c] = (int)(tiles.size() - before);
         }
         std::vector<unsigned char> tab;
         auto put = [&](const void* src, size_t bytes) {
@@ -823,7 +846,6 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         P.off_dims = put(cds.data(), cds.size() * sizeof(CoupDim));
         P.off_mdim = put(mdim.data(), mdim.size() * sizeof(int));
         P.off_roff = put(h->r_off.data(), h->r_off.size() * sizeof(long long));
-        P.ntiles = (int)tiles.size();
         if ((st = ensure(h, &h->dCoup, &h->capCoup, tab.size()))) return st;
         if ((st = ensure(h, &h->dR, &h->capR, (size_t)roff * sizeof(double)))) return st;
         CK(h, cudaMemcpyAsync(h->dCoup, tab.data(), tab.size(), cudaMemcpyHostToDevice, h->stream));
@@ -980,12 +1002,12 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
         const int* mdim = reinterpret_cast<const int*>(tab + P.off_mdim);
         const long long* roff = reinterpret_cast<const long long*>(tab + P.off_roff);
         if (prec == MCPT_FP64)
-            CK(h, launch_coupling_fp64(tiles, P.ntiles, cds, L, mdim, roff, static_cast<const double*>(h->dVT), h->dR,
+            CK(h, launch_coupling_fp64(tiles, P.ntile, cds, L, mdim, roff, static_cast<const double*>(h->dVT), h->dR,
                                        h->stream));
         else
-            CK(h, launch_coupling_fp32(tiles, P.ntiles, cds, L, mdim, roff, static_cast<const float*>(h->dVT), h->dR,
+            CK(h, launch_coupling_fp32(tiles, P.ntile, cds, L, mdim, roff, static_cast<const float*>(h->dVT), h->dR,
                                        h->stream));
-        launches++;
+        launches += (P.ntile[0] > 0) + (P.ntile[1] > 0) + (P.ntile[2] > 0);
     }
     launches++;
     if (ev) CK(h, cudaEventRecord((*ev)[2 * W + 1], h->stream));

@@ -106,13 +106,15 @@ struct CoupTile {
     int p0, q0;           // output tile origin in R_mon
 };
 // R_mon = sum over the monomer's dimers (ascending) of T V^T + V T^T (X side)
-// or the transposed contractions (Y side); one CTA per 64 x 64 output tile.
-// dims: every dimer; lists: the per-monomer dimer lists; R: per monomer at
-// r_off[mon], (o v)^2 doubles row-major.  T = float or double storage.
-cudaError_t launch_coupling_fp32(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists,
+// or the transposed contractions (Y side); one CTA per output tile with
+// q0 >= p0, writing both mirror halves.  tiles: ntile[0] tiles of edge 64,
+// then ntile[1] of edge 48, then ntile[2] of edge 32 (host array of three
+// counts).  dims: every dimer; lists: the per-monomer dimer lists; R: per
+// monomer at r_off[mon], (o v)^2 doubles row-major.  T = float or double.
+cudaError_t launch_coupling_fp32(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists,
                                  const int* mdim, const long long* r_off, const float* VT, double* R,
                                  cudaStream_t s);
-cudaError_t launch_coupling_fp64(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists,
+cudaError_t launch_coupling_fp64(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists,
                                  const int* mdim, const long long* r_off, const double* VT, double* R,
                                  cudaStream_t s);
 

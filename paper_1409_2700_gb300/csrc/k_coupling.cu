@@ -7,32 +7,53 @@
 //   X side: R_X[p][q] += sum_{r=(j,b)} S_T[r][p] S_V[r][q] + S_V[r][p] S_T[r][q]
 //   Y side: R_Y[p][q] += sum_{r=(i,a)} S_T[p][r] S_V[q][r] + S_V[p][r] S_T[q][r]
 // (the Y side reads the stored rows as columns).
-// One CTA per 64 x 64 tile of one monomer's R; it walks the monomer's
-// dimers in ascending order and their rows in chunks of 32 staged in shared
-// memory, each thread accumulating a 4 x 4 block (rows ty + 16 u, columns
-// tx + 16 w) in registers: per row 16 loads feed 32 FMAs.  Every sum has a
-// fixed order, so R is deterministic run to run.
+// R is symmetric, so only tiles with q0 >= p0 run, each writing R[p][q] and
+// its mirror R[q][p] for p <= q (R is exactly symmetric).  A monomer's tiles
+// have edge 64, 48 or 32, whichever covers its o v rows with the least padded
+// work, one launch per edge.  A CTA walks the monomer's dimers in ascending
+// order and their rows in chunks of 32 (16 in FP64) staged in shared memory
+// (rows padded by 4 so the transposed Y side stages without bank conflicts,
+// eight rows by four columns per warp); each thread accumulates a contiguous
+// 4 x 4 block in registers: per row four 4-wide shared loads feed 32 FMAs.
+// Every sum has a fixed order, so R is deterministic run to run.
 #include "internal.h"
 
 namespace mcpt {
 namespace {
 
-constexpr int kCT = 64;          // output tile edge
-constexpr int kCThreads = 256;
 template <typename T>
-__host__ __device__ constexpr int ck() { return sizeof(T) == 8 ? 16 : 32; }   // rows per staged chunk (32 KB of operands)
+__host__ __device__ constexpr int ck() { return sizeof(T) == 8 ? 16 : 32; }   // rows per staged chunk
+template <int CT>
+__host__ __device__ constexpr int cthreads() { return ((CT / 4) * (CT / 4) + 31) / 32 * 32; }
 
 template <typename T>
-__global__ void __launch_bounds__(kCThreads)
+__device__ __forceinline__ void ld4(const T* p, T (&x)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    }
+}
+
+template <typename T, int CT>
+__global__ void __launch_bounds__(cthreads<CT>())
 k_coupling(const CoupTile* __restrict__ tiles, const CoupDim* __restrict__ dims, MonomerLists L,
            const int* __restrict__ mdim, const long long* __restrict__ r_off, const T* __restrict__ VT,
            double* __restrict__ R)
 {
-    constexpr int kCK = ck<T>();
+    constexpr int kCK = ck<T>(), kLD = CT + 4, kNT = cthreads<CT>(), kTW = CT / 4;
     const CoupTile tile = tiles[blockIdx.x];
     const int mon = tile.mon, m = mdim[mon];
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    __shared__ T sTp[kCK][kCT], sVp[kCK][kCT], sTq[kCK][kCT], sVq[kCK][kCT];
+    const bool diag = tile.p0 == tile.q0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool active = tid < kTW * kTW;
+    const int ty = tid / kTW, tx = tid % kTW;
+    // [0] T rows p, [1] V rows p, [2] T rows q, [3] V rows q
+    __shared__ __align__(16) T sm[4][kCK][kLD];
+    const int qs = diag ? 0 : 2;      // a diagonal tile reads its p operands twice
     T acc[4][4];
 #pragma unroll
     for (int u = 0; u < 4; u++)
@@ -45,76 +66,94 @@ k_coupling(const CoupTile* __restrict__ tiles, const CoupDim* __restrict__ dims,
         const T* Tm = V + (long long)cd.mX * cd.mY;
         const bool xside = cd.X == mon;
         const int K = xside ? cd.mY : cd.mX;        // rows summed over
-        const int ld = cd.mX;                       // row length of the stored [(j,b)][(i,a)]
+        const long long ld = cd.mX;                 // row length of the stored [(j,b)][(i,a)]
         for (int k0 = 0; k0 < K; k0 += kCK) {
             __syncthreads();
-            // stage rows k0.. of the four operand columns blocks (p and q tiles)
-            for (int e = tid; e < kCK * kCT; e += kCThreads) {
-                int r, c;
-                if (xside) { r = e / kCT; c = e % kCT; }      // contiguous along the (i,a) columns
-                else       { c = e / kCK; r = e % kCK; }      // contiguous along the (i,a) rows read
-                const int k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
-                T tp = T(0), vp = T(0), tq = T(0), vq = T(0);
-                if (k < K) {
-                    if (xside) {
-                        const long long rowk = (long long)k * ld;
+            if (xside) {                            // rows k of the stored matrices, contiguous along c
+                for (int e = tid; e < kCK * CT; e += kNT) {
+                    const int r = e / CT, c = e % CT, k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
+                    T tp = T(0), vp = T(0), tq = T(0), vq = T(0);
+                    if (k < K) {
+                        const long long rowk = k * ld;
                         if (p < m) { tp = Tm[rowk + p]; vp = V[rowk + p]; }
-                        if (q < m) { tq = Tm[rowk + q]; vq = V[rowk + q]; }
-                    } else {
-                        if (p < m) { tp = Tm[(long long)p * ld + k]; vp = V[(long long)p * ld + k]; }
-                        if (q < m) { tq = Tm[(long long)q * ld + k]; vq = V[(long long)q * ld + k]; }
+                        if (!diag && q < m) { tq = Tm[rowk + q]; vq = V[rowk + q]; }
                     }
+                    sm[0][r][c] = tp; sm[1][r][c] = vp;
+                    if (!diag) { sm[2][r][c] = tq; sm[3][r][c] = vq; }
                 }
-                sTp[r][c] = tp; sVp[r][c] = vp; sTq[r][c] = tq; sVq[r][c] = vq;
+            } else {                                // columns k of the stored rows p, q: 8 rows x 4 columns a warp
+                constexpr int kRG = kCK / 8;
+                for (int g = warp; g < kRG * (CT / 4); g += kNT / 32) {
+                    const int r = (g % kRG) * 8 + (lane & 7), c = (g / kRG) * 4 + (lane >> 3);
+                    const int k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
+                    T tp = T(0), vp = T(0), tq = T(0), vq = T(0);
+                    if (k < K) {
+                        if (p < m) { tp = Tm[p * ld + k]; vp = V[p * ld + k]; }
+                        if (!diag && q < m) { tq = Tm[q * ld + k]; vq = V[q * ld + k]; }
+                    }
+                    sm[0][r][c] = tp; sm[1][r][c] = vp;
+                    if (!diag) { sm[2][r][c] = tq; sm[3][r][c] = vq; }
+                }
             }
             __syncthreads();
-            const int kn = min(kCK, K - k0);
-            for (int r = 0; r < kn; r++) {
-                T at[4], av[4], bt[4], bv[4];
+            if (active) {
+                const int kn = min(kCK, K - k0);
+#pragma unroll 2
+                for (int r = 0; r < kn; r++) {
+                    T at[4], av[4], bt[4], bv[4];
+                    ld4(&sm[0][r][4 * ty], at);
+                    ld4(&sm[1][r][4 * ty], av);
+                    ld4(&sm[qs][r][4 * tx], bt);
+                    ld4(&sm[qs + 1][r][4 * tx], bv);
 #pragma unroll
-                for (int u = 0; u < 4; u++) { at[u] = sTp[r][ty + 16 * u]; av[u] = sVp[r][ty + 16 * u]; }
+                    for (int u = 0; u < 4; u++)
 #pragma unroll
-                for (int w = 0; w < 4; w++) { bt[w] = sTq[r][tx + 16 * w]; bv[w] = sVq[r][tx + 16 * w]; }
-#pragma unroll
-                for (int u = 0; u < 4; u++)
-#pragma unroll
-                    for (int w = 0; w < 4; w++) acc[u][w] = fma(at[u], bv[w], fma(av[u], bt[w], acc[u][w]));
+                        for (int w = 0; w < 4; w++) acc[u][w] = fma(at[u], bv[w], fma(av[u], bt[w], acc[u][w]));
+                }
             }
         }
     }
+    if (!active) return;
     double* Rm = R + r_off[mon];
 #pragma unroll
     for (int u = 0; u < 4; u++)
 #pragma unroll
         for (int w = 0; w < 4; w++) {
-            const int p = tile.p0 + ty + 16 * u, q = tile.q0 + tx + 16 * w;
-            if (p < m && q < m) Rm[(long long)p * m + q] = (double)acc[u][w];
+            const int p = tile.p0 + 4 * ty + u, q = tile.q0 + 4 * tx + w;
+            if (p < m && q < m && p <= q) {
+                Rm[(long long)p * m + q] = (double)acc[u][w];
+                Rm[(long long)q * m + p] = (double)acc[u][w];
+            }
         }
 }
 
 template <typename T>
-cudaError_t launch(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists, const int* mdim,
+cudaError_t launch(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists, const int* mdim,
                    const long long* r_off, const T* VT, double* R, cudaStream_t s)
 {
-    if (ntiles <= 0) return cudaSuccess;
-    k_coupling<T><<<ntiles, kCThreads, 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
+    // tiles: the edge-64 tiles, then the edge-48, then the edge-32 ones
+    if (ntile[0] > 0) k_coupling<T, 64><<<ntile[0], cthreads<64>(), 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
+    tiles += ntile[0];
+    if (ntile[1] > 0) k_coupling<T, 48><<<ntile[1], cthreads<48>(), 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
+    tiles += ntile[1];
+    if (ntile[2] > 0) k_coupling<T, 32><<<ntile[2], cthreads<32>(), 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_coupling_fp32(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists,
+cudaError_t launch_coupling_fp32(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists,
                                  const int* mdim, const long long* r_off, const float* VT, double* R,
                                  cudaStream_t s)
 {
-    return launch<float>(tiles, ntiles, dims, lists, mdim, r_off, VT, R, s);
+    return launch<float>(tiles, ntile, dims, lists, mdim, r_off, VT, R, s);
 }
 
-cudaError_t launch_coupling_fp64(const CoupTile* tiles, int ntiles, const CoupDim* dims, MonomerLists lists,
+cudaError_t launch_coupling_fp64(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists,
                                  const int* mdim, const long long* r_off, const double* VT, double* R,
                                  cudaStream_t s)
 {
-    return launch<double>(tiles, ntiles, dims, lists, mdim, r_off, VT, R, s);
+    return launch<double>(tiles, ntile, dims, lists, mdim, r_off, VT, R, s);
 }
 
 }  // namespace mcpt

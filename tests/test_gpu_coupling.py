@@ -48,7 +48,7 @@ def test_coupling_lattice_2x2x2(lat8, lat8_coupling, prec):
             err = np.abs(R - ref).max() / scale
             worst = max(worst, err)
             assert err <= TOL[prec], (prec, X, err)
-            assert np.allclose(R, R.T, rtol=0, atol=TOL[prec] * scale)
+            assert np.array_equal(R, R.T)
             assert abs(np.trace(R) - mj[X]) <= max(TOL[prec], 1e-12) * abs(mj[X]) * 10
         print(f"{prec}: coupling max rel err {worst:.2e}")
         # again: deterministic
@@ -60,22 +60,24 @@ def test_coupling_lattice_2x2x2(lat8, lat8_coupling, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_coupling_uneven_and_occupation_blocks(prec):
-    """Monomers of different sizes in a chain X0 - X1 - X2 (X1 couples to
-    both); X1 has 20 occupied orbitals, so the tensor-core forms run its
-    dimers as occupation blocks that write into the same stored (ia|jb)."""
+    """Monomers of different sizes in a chain X0 - X1 - X2 - X3 (X1 and X2
+    couple to both sides); X1 has 20 occupied orbitals, so the tensor-core
+    forms run its dimers as occupation blocks that write into the same stored
+    (ia|jb).  The o v sizes 21, 400, 95, 128 take output tiles of edge 32,
+    48 (ragged), 48 and 64; a fifth monomer has no dimers and R = 0."""
     rng = np.random.default_rng(31)
-    sizes = [(10, 3), (40, 20), (24, 5)]
+    sizes = [(10, 3), (40, 20), (24, 5), (36, 4), (12, 2)]
     mons = []
     for n, o in sizes:
         C = np.linalg.qr(rng.standard_normal((n, n)))[0]
         e = np.concatenate([np.sort(rng.uniform(-1.5, -0.5, o)), np.sort(rng.uniform(0.2, 3.0, n - o))])
         mons.append((C, e, o))
-    pairs = [(0, 1), (1, 2)]
+    pairs = [(0, 1), (1, 2), (2, 3)]
     blks = {}
     for X, Y in pairs:
         nX, nY = sizes[X][0], sizes[Y][0]
         blks[(X, Y)] = (rng.standard_normal((nX, nX, nY, nY)) * 1e-3, rng.standard_normal((nX, nY, nY, nX)) * 1e-3)
-    R = {m: np.zeros(((sizes[m][1] * (sizes[m][0] - sizes[m][1])),) * 2) for m in range(3)}
+    R = {m: np.zeros(((sizes[m][1] * (sizes[m][0] - sizes[m][1])),) * 2) for m in range(len(sizes))}
     for X, Y in pairs:
         (CX, eX, oX), (CY, eY, oY) = mons[X], mons[Y]
         V = oracle.transform_J(blks[(X, Y)][0], CX, CY, oX, oY)
@@ -87,8 +89,12 @@ def test_coupling_uneven_and_occupation_blocks(prec):
             A, K = blks[(X, Y)]
             ctx.add_dimer(X, Y, np.concatenate([A.ravel(), K.ravel()]), M.MCPT_AO_BLOCKS)
         ctx.run()
-        for m in range(3):
+        for m in range(len(sizes)):
             G = ctx.coupling(m, *sizes[m])
+            assert np.array_equal(G, G.T)
+            if m == 4:
+                assert not G.any()
+                continue
             err = np.abs(G - R[m]).max() / np.abs(R[m]).max()
             print(f"{prec} monomer {m} ({sizes[m][0]} AO, {sizes[m][1]} occ): rel err {err:.2e}")
             assert err <= TOL[prec]
