@@ -60,9 +60,11 @@ typedef enum {
 typedef enum {
     MCPT_FP64 = 0,    /* FP64 everywhere (CUDA-core DFMA) */
     MCPT_TF32 = 1,    /* AO integrals and C rounded to TF32 (round-to-nearest), tcgen05 MMA, FP32 accumulate */
-    MCPT_BF16X3 = 2,  /* both operands as three BF16 digits of a fixed-point value relative to each
-                         vector's largest exponent (rank kernel, n_Y <= 96): 6 tcgen05 MMAs per step whose
-                         FP32 sums are exact integers; elsewhere a hi/lo BF16 split */
+    MCPT_BF16X3 = 2,  /* both operands as 32-bit fixed-point values relative to the largest power of
+                         two of each integral row chunk (32 values) and each C_Y column, cut into four
+                         BF16 digits; the tcgen05 MMAs add only integer digit products whose FP32 partial
+                         sums stay below 2^24, so every tensor-core accumulation is exact (the Kronecker
+                         kernel, selected only by MCPT_TC_KERNEL=kron, keeps a hi/lo BF16 split) */
     MCPT_FP32C = 3    /* FP32 FMA with error-free TwoProduct/TwoSum compensation (Ogita-Rump-Oishi) */
 } mcpt_precision;
 
@@ -185,7 +187,7 @@ mcpt_status mcpt_energies(mcpt_handle h, double *per_monomer_J, double *per_mono
  *   mcpt_run of every dimer since the integrals last changed), ECUDA. */
 mcpt_status mcpt_coupling(mcpt_handle h, int X, double *R);
 
-/* Per-phase timing and launch counts of every run since the previous call/* Per-phase timing and launch counts of every run since the previous call
+/* Per-phase timing and launch counts of every run since the previous call
  * (timing requires options.timing = 1; CUDA events are recorded on the
  * handle's stream around each phase, and this call waits for the stream).
  * ms[0] = first half (the AO-reading transform kernel), ms[1] = finish

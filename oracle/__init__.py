@@ -76,6 +76,8 @@ def lib():
             L.oracle_dimers.restype = I
             L.oracle_coupling_add.argtypes = [_dp, _dp, _dp, I, I, I, I, _dp, _dp]
             L.oracle_coupling_add.restype = None
+            L.oracle_singles_add.argtypes = [_dp, _dp, _dp, I, I, I, I, _dp, _dp]
+            L.oracle_singles_add.restype = None
             L.oracle_max_threads.argtypes = []
             L.oracle_max_threads.restype = I
             _lib = L
@@ -165,6 +167,37 @@ def coupling_add(V, epsX, epsY, oX, oY, RX, RY):
         assert R.dtype == np.float64 and R.flags.c_contiguous
     nX, nY = epsX.shape[0], epsY.shape[0]
     lib().oracle_coupling_add(_p(V), _p(epsX), _p(epsY), nX, nY, oX, oY, _p(RX), _p(RY))
+
+
+def singles_add(V, tX, tY, sX, sY):
+    """Add one dimer's singles environment term of Eq. (tm1) to sX ([oX][vX])
+    and sY ([oY][vY]), in place.  V: (ia|kc) as [oX][vX][oY][vY]; tX, tY:
+    the monomers' singles amplitudes t^a_i as [o][v]."""
+    V, tX, tY = _f64(V), _f64(tX), _f64(tY)
+    oX, vX, oY, vY = V.shape
+    assert tX.shape == (oX, vX) and tY.shape == (oY, vY)
+    for s in (sX, sY):
+        assert s.dtype == np.float64 and s.flags.c_contiguous
+    assert sX.shape == (oX, vX) and sY.shape == (oY, vY)
+    lib().oracle_singles_add(_p(V), _p(tX), _p(tY), oX, vX, oY, vY, _p(sX), _p(sY))
+
+
+def singles_lattice(w, t, dimers=None, blocks=None):
+    """The singles environment term of every monomer of workload w over the
+    listed dimers (default all), for amplitudes t = {X: [oX][vX]}: {X: s_X}."""
+    ds = range(w.n_dimers) if dimers is None else dimers
+    mons, S = {}, {}
+    for d in ds:
+        X, Y = w.pairs[d]
+        for m in (X, Y):
+            if m not in mons:
+                mons[m] = w.monomer(m)
+                S[m] = np.zeros((w.nocc[m], w.nao[m] - w.nocc[m]))
+        mX, mY = mons[X], mons[Y]
+        A = blocks[d][0] if blocks is not None else w.blocks(d)[0]
+        V = transform_J(A, mX.C, mY.C, mX.nocc, mY.nocc)
+        singles_add(V, t[X], t[Y], S[X], S[Y])
+    return S
 
 
 def coupling_lattice(w, dimers=None, blocks=None):

@@ -181,6 +181,34 @@ void oracle_coupling_add(const double *V, const double *epsX, const double *epsY
     free(T);
 }
 
+/* The environment term of the monomer singles equation, Eq. (tm1): monomer
+ * X receives from each neighbour Y the sum over Y's occupied k and virtual c
+ * of v^{ak}_{ic} t^c_k, with v^{ak}_{ic} = (i a|k c) = V[i][a][k][c] and Y's
+ * singles amplitudes tY[k][c] (oY x vY row-major):
+ *   sX[(i,a)] += sum_{k,c} V[i][a][k][c] tY[k][c]
+ * and Y receives the same from X:
+ *   sY[(k,c)] += sum_{i,a} V[i][a][k][c] tX[i][a]. */
+void oracle_singles_add(const double *V, const double *tX, const double *tY,
+                        int oX, int vX, int oY, int vY, double *sX, double *sY)
+{
+    for (int i = 0; i < oX; i++)
+    for (int a = 0; a < vX; a++) {
+        double s = 0.0;
+        for (int k = 0; k < oY; k++)
+        for (int c = 0; c < vY; c++)
+            s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tY[k * vY + c];
+        sX[i * vX + a] += s;
+    }
+    for (int k = 0; k < oY; k++)
+    for (int c = 0; c < vY; c++) {
+        double s = 0.0;
+        for (int i = 0; i < oX; i++)
+        for (int a = 0; a < vX; a++)
+            s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tX[i * vX + a];
+        sY[k * vY + c] += s;
+    }
+}
+
 /* One dimer term {E_J, E_K} from the two AO blocks.  Returns 0 on success. */
 int oracle_dimer(const double *A, const double *K,
                  const double *CX, const double *epsX,

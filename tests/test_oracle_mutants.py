@@ -34,6 +34,10 @@ MUTANTS = {
                                             "s += V[q * mY + r] * T[p * mY + r] + V[p * mY + r] * T[p * mY + r];"),
     "coupling without the denominator": ("T[e] = V[e] / (epsX[i] + epsY[k] - epsX[oX + a] - epsY[oY + c]);",
                                          "T[e] = V[e];"),
+    "singles reads the amplitudes transposed": ("s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tY[k * vY + c];",
+                                                "s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tY[c * oY + k];"),
+    "singles Y side takes its own amplitudes": ("s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tX[i * vX + a];",
+                                                "s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tY[k * vY + c];"),
 }
 
 CHECKS = r'''
@@ -92,6 +96,19 @@ V2 = rng.standard_normal((2, 3, 1, 3)); e2X = np.array([-1.0, -0.7, 0.4, 0.9, 2.
 R2X = np.zeros((6, 6)); R2Y = np.zeros((3, 3))
 oracle.coupling_add(V2, e2X, e2Y, 2, 1, R2X, R2Y)
 check("coupling symmetric", np.array_equal(R2X, R2X.T) and np.array_equal(R2Y, R2Y.T))
+# singles of Eq. (tm1) against the AO-density route
+for (n1, n2, o1, o2) in [(6, 8, 1, 5), (7, 6, 2, 3)]:
+    A1 = rng.standard_normal((n1, n1, n2, n2))
+    C1 = rng.standard_normal((n1, n1)); C2 = rng.standard_normal((n2, n2))
+    t1 = rng.standard_normal((o1, n1 - o1)); t2 = rng.standard_normal((o2, n2 - o2))
+    V1 = oracle.transform_J(A1, C1, C2, o1, o2)
+    s1 = np.zeros_like(t1); s2 = np.zeros_like(t2)
+    oracle.singles_add(V1, t1, t2, s1, s2)
+    P2 = C2[:, :o2] @ t2 @ C2[:, o2:].T; P1 = C1[:, :o1] @ t1 @ C1[:, o1:].T
+    r1 = C1[:, :o1].T @ np.einsum("mnls,ls->mn", A1, P2) @ C1[:, o1:]
+    r2 = C2[:, :o2].T @ np.einsum("mnls,mn->ls", A1, P1) @ C2[:, o2:]
+    check("singles X", np.abs(s1 - r1).max() <= 1e-12 * np.abs(r1).max())
+    check("singles Y", np.abs(s2 - r2).max() <= 1e-12 * np.abs(r2).max())
 print("FAILS:" + ",".join(fails))
 '''
 

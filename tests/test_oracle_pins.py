@@ -381,3 +381,55 @@ def test_coupling_rank1_closed_form():
     w_ = np.outer(y[:oY], y[oY:]).ravel()
     refY = 2 * D * s * s * np.sum(x[:oX] ** 2) * np.sum(x[oX:] ** 2) * np.outer(w_, w_)
     assert np.max(np.abs(RY - refY)) <= 1e-13 * np.max(np.abs(refY))
+
+
+# ---------------------------------------------------------------- singles environment term (Eq. tm1)
+def _ao_route_singles(A, CX, CY, oX, oY, tX, tY):
+    """sum_{kc} (ia|kc) t_kc through the AO integrals: the amplitudes become
+    an AO matrix P = C_occ t C_virt^T of the neighbour, contracted with the
+    Coulomb block over the neighbour's two AO indices and projected onto
+    (i, a) -- no four-index MO tensor is formed."""
+    PY = CY[:, :oY] @ tY @ CY[:, oY:].T
+    PX = CX[:, :oX] @ tX @ CX[:, oX:].T
+    FX = np.einsum("mnls,ls->mn", A, PY)
+    FY = np.einsum("mnls,mn->ls", A, PX)
+    return CX[:, :oX].T @ FX @ CX[:, oX:], CY[:, :oY].T @ FY @ CY[:, oY:]
+
+
+def test_singles_against_ao_route():
+    """The environment term of Eq. (tm1), v^{ak}_{ic} t^c_k summed over the
+    neighbour's (k, c), agrees with the AO-density route for both monomers,
+    on non-symmetric integrals and unequal sizes."""
+    rng = np.random.default_rng(24)
+    for nX, nY, oX, oY in [(7, 6, 2, 3), (9, 5, 4, 1), (6, 8, 1, 5)]:
+        A, K, CX, eX, CY, eY = rand_dimer(rng, nX, nY, oX, oY)
+        tX = rng.standard_normal((oX, nX - oX))
+        tY = rng.standard_normal((oY, nY - oY))
+        V = oracle.transform_J(A, CX, CY, oX, oY)
+        sX, sY = np.zeros_like(tX), np.zeros_like(tY)
+        oracle.singles_add(V, tX, tY, sX, sY)
+        rX, rY = _ao_route_singles(A, CX, CY, oX, oY, tX, tY)
+        assert np.max(np.abs(sX - rX)) <= 1e-13 * np.max(np.abs(rX))
+        assert np.max(np.abs(sY - rY)) <= 1e-13 * np.max(np.abs(rY))
+        # the pairing t_X . s_X = t_Y . s_Y = t_X^T V t_Y is symmetric
+        assert abs(np.sum(tX * sX) - np.sum(tY * sY)) <= 1e-13 * np.sum(np.abs(tX * sX))
+
+
+def test_singles_accumulates_and_is_linear():
+    """Calls add into s; zero amplitudes give exactly zero; the term is
+    linear in t."""
+    rng = np.random.default_rng(25)
+    oX, vX, oY, vY = 3, 4, 2, 5
+    V = rng.standard_normal((oX, vX, oY, vY))
+    tX, tY = rng.standard_normal((oX, vX)), rng.standard_normal((oY, vY))
+    s1X, s1Y = np.zeros((oX, vX)), np.zeros((oY, vY))
+    oracle.singles_add(V, tX, tY, s1X, s1Y)
+    s2X, s2Y = s1X.copy(), s1Y.copy()
+    oracle.singles_add(V, tX, tY, s2X, s2Y)
+    assert np.array_equal(s2X, 2 * s1X) and np.array_equal(s2Y, 2 * s1Y)
+    zX, zY = np.zeros((oX, vX)), np.zeros((oY, vY))
+    oracle.singles_add(V, np.zeros_like(tX), np.zeros_like(tY), zX, zY)
+    assert not zX.any() and not zY.any()
+    s3X, s3Y = np.zeros((oX, vX)), np.zeros((oY, vY))
+    oracle.singles_add(V, 4.0 * tX, 4.0 * tY, s3X, s3Y)
+    assert np.array_equal(s3X, 4 * s1X) and np.array_equal(s3Y, 4 * s1Y)
