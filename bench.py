@@ -353,6 +353,25 @@ def our_arm(args, ws, rank, local):
                             "alg_gflop_per_step": cflops / 1e9,
                             "max_rel_trace_minus_monomer_EJ": trace_err,
                             "what": "R_X = sum_Y (T V^t + V T^t) of Eq. (tm2) at T = vD, every monomer"}
+        # ---- the singles environment term of Eq. (tm1) from the same stored
+        # (ia|kc), for seeded amplitudes: host-synchronous calls (amplitudes in,
+        # result out) timed by wall clock; s(2t) = 2 s(t) holds bit for bit
+        trng = np.random.default_rng(7)
+        t1 = [trng.standard_normal((w.nocc[X], w.nao[X] - w.nocc[X])) * 0.01 for X in range(w.n_monomers)]
+        s1 = cc.singles(t1)
+        reps = 10
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            cc.singles(t1)
+        sms = (time.perf_counter() - t0) / reps * 1e3
+        s2 = cc.singles([2.0 * x for x in t1])
+        vbytes = sum(2 * 4 * (w.nocc[X] * (w.nao[X] - w.nocc[X])) * (w.nocc[Y] * (w.nao[Y] - w.nocc[Y]))
+                     for X, Y in w.pairs) * (2 if args.precision == "fp64" else 1)
+        line["coupling"]["singles"] = {
+            "ms_per_call": sms, "alg_bytes_per_call": vbytes,
+            "linear_bitwise": bool(all(np.array_equal(b, 2.0 * a) for a, b in zip(s1, s2))),
+            "what": "s_X = sum_Y sum_kc (ia|kc) t_kc(Y) of Eq. (tm1), every monomer; wall clock per "
+                    "mcpt_singles call including the amplitude and result copies"}
         cc.close()
 
         # ---- the plain FP64 GPU form on the same resident inputs

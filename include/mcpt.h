@@ -187,6 +187,22 @@ mcpt_status mcpt_energies(mcpt_handle h, double *per_monomer_J, double *per_mono
  *   mcpt_run of every dimer since the integrals last changed), ECUDA. */
 mcpt_status mcpt_coupling(mcpt_handle h, int X, double *R);
 
+/* Environment term of the monomer singles equation, Eq. (tm1) (the sum over
+ * the neighbours' occupied k and virtual c), from the integrals of the last
+ * mcpt_run of every dimer in a context created with options.coupling = 1:
+ *   s_X[(i,a)] = sum_{Y, k, c} (i a|k c) t^c_k(Y)
+ * over every registered dimer containing X.  t: host array of every
+ * monomer's singles amplitudes t^a_i, monomer by monomer in id order, each
+ * o_X x v_X row-major (index i * v_X + a), sum_X o_X v_X doubles in all; it
+ * is copied before the call returns.  s: host output of the same layout.
+ * Waits for the handle's stream.  Arithmetic: the form's storage type per
+ * dimer (FP32 for the mixed forms, in partial sums of 32 terms added in
+ * FP64), FP64 over dimers in ascending order; deterministic.
+ * Errors: EINVAL (NULL, or a non-finite t with validate = 1), ESTATE
+ *   (options.coupling = 0, or no mcpt_run of every dimer since the
+ *   integrals last changed), ETIMEOUT, ECUDA. */
+mcpt_status mcpt_singles(mcpt_handle h, const double *t, double *s);
+
 /* Per-phase timing and launch counts of every run since the previous call
  * (timing requires options.timing = 1; CUDA events are recorded on the
  * handle's stream around each phase, and this call waits for the stream).

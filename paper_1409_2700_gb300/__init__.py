@@ -29,7 +29,7 @@ MCPT_UPDATE_ASYNC = 1
 # every symbol include/mcpt.h declares
 EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer",
            "mcpt_set_precision",
-           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_collect_stats", "mcpt_num_monomers",
+           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_collect_stats", "mcpt_num_monomers",
            "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
 
 
@@ -74,9 +74,10 @@ def lib():
         L.mcpt_run_range.argtypes = [H, I, I]
         L.mcpt_energies.argtypes = [H, P, P, P, P]
         L.mcpt_coupling.argtypes = [H, I, P]
+        L.mcpt_singles.argtypes = [H, P, P]
         L.mcpt_collect_stats.argtypes = [H, ctypes.POINTER(mcpt_run_stats)]
         for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer", "mcpt_set_precision", "mcpt_run",
-                  "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_collect_stats"):
+                  "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_collect_stats"):
             getattr(L, f).restype = I
         L.mcpt_num_monomers.argtypes = [H]
         L.mcpt_num_monomers.restype = I
@@ -171,6 +172,14 @@ def mcpt_coupling(h, X: int, dim: int) -> np.ndarray:
     return R
 
 
+def mcpt_singles(h, t: np.ndarray) -> np.ndarray:
+    """t: every monomer's [o][v] amplitudes concatenated (FP64, 1-D)."""
+    t = np.ascontiguousarray(t, dtype=np.float64).ravel()
+    s = np.empty_like(t)
+    _check(h, lib().mcpt_singles(h, _ptr(t), _ptr(s)))
+    return s
+
+
 def mcpt_collect_stats(h) -> mcpt_run_stats:
     s = mcpt_run_stats()
     _check(h, lib().mcpt_collect_stats(h, ctypes.byref(s)))
@@ -251,6 +260,19 @@ class Context:
         """R_X of Eq. (tm2)'s dimer coupling, (nocc (nao - nocc))^2, after a run
         of a context created with coupling=True."""
         return mcpt_coupling(self.h, X, nocc * (nao - nocc))
+
+    def singles(self, t):
+        """Eq. (tm1)'s environment term s_X = sum_{Y,k,c} (ia|kc) t^c_k(Y) of
+        every monomer, for amplitudes t = [t_X as (o_X, v_X)] in monomer id
+        order, after a run of a context created with coupling=True; returns
+        the list of s_X of the same shapes."""
+        t = [np.asarray(x, dtype=np.float64) for x in t]
+        flat = mcpt_singles(self.h, np.concatenate([x.ravel() for x in t]) if t else np.empty(0))
+        out, off = [], 0
+        for x in t:
+            out.append(flat[off:off + x.size].reshape(x.shape))
+            off += x.size
+        return out
 
     def stats(self):
         """Timing and launch counts of the runs since the previous call."""

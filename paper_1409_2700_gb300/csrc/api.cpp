@@ -91,6 +91,10 @@ struct mcpt_ctx {
     size_t capCoup = 0;
     double* dR = nullptr;            // coupling matrices R_X, per monomer
     size_t capR = 0;
+    double* dS1 = nullptr;           // singles term: amplitudes t, the result s, per-dimer parts
+    size_t capS1 = 0;
+    long long s_total = 0;           // sum over monomers of o v
+    long long s_parts = 0;           // sum over dimers of o_X v_X + o_Y v_Y
     std::vector<long long> r_off;    // host copy of the R offsets
     bool coupled = false;            // R holds the coupling of the current integrals
     int* dFold = nullptr;            // split dimers: (dimer, first block slot, blocks)
@@ -127,6 +131,8 @@ struct mcpt_ctx {
         bool coupling = false;             // the plan stores (ia|jb), T and forms R
         int ntile[3] = {0, 0, 0};          // coupling output tiles of edge 64, 48, 32
         size_t off_tiles = 0, off_dims = 0, off_mdim = 0, off_roff = 0;   // into dCoup
+        int nstiles = 0;                   // singles tiles
+        size_t off_stiles = 0, off_soff = 0, off_poff = 0;
         cudaGraphExec_t graph = nullptr;   // the plan's launch sequence, captured on first use
         int graph_launches = 0;
     } plan;
@@ -846,6 +852,25 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         P.off_dims = put(cds.data(), cds.size() * sizeof(CoupDim));
         P.off_mdim = put(mdim.data(), mdim.size() * sizeof(int));
         P.off_roff = put(h->r_off.data(), h->r_off.size() * sizeof(long long));
+        // singles term: 256 outputs per tile, monomer blocks of o v
+        std::vector<SingTile> stiles;
+        std::vector<long long> soff(N + 1, 0);
+        for (int m = 0; m < N; m++) {
+            soff[m + 1] = soff[m] + mdim[m];
+            for (int p0 = 0; p0 < mdim[m]; p0 += 256) stiles.push_back(SingTile{m, p0});
+        }
+        std::vector<long long> poff(D);
+        long long pacc = 0;
+        for (int d = 0; d < D; d++) {
+            poff[d] = pacc;
+            pacc += cds[d].mX + cds[d].mY;
+        }
+        h->s_total = soff[N];
+        h->s_parts = pacc;
+        P.nstiles = (int)stiles.size();
+        P.off_stiles = put(stiles.data(), stiles.size() * sizeof(SingTile));
+        P.off_soff = put(soff.data(), soff.size() * sizeof(long long));
+        P.off_poff = put(poff.data(), poff.size() * sizeof(long long));
         if ((st = ensure(h, &h->dCoup, &h->capCoup, tab.size()))) return st;
         if ((st = ensure(h, &h->dR, &h->capR, (size_t)roff * sizeof(double)))) return st;
         CK(h, cudaMemcpyAsync(h->dCoup, tab.data(), tab.size(), cudaMemcpyHostToDevice, h->stream));
@@ -1136,6 +1161,44 @@ mcpt_status mcpt_coupling(mcpt_handle h, int X, double* R)
     return MCPT_OK;
 }
 
+mcpt_status mcpt_singles(mcpt_handle h, const double* t, double* s)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_singles: NULL handle");
+    if (!t || !s) return fail(h, MCPT_EINVAL, "mcpt_singles: t or s is NULL");
+    if (!h->coupling) return fail(h, MCPT_ESTATE, "mcpt_singles: the context was created with coupling = 0");
+    if (!h->coupled)
+        return fail(h, MCPT_ESTATE, "mcpt_singles: no mcpt_run of every dimer since the integrals last changed");
+    const mcpt_ctx::Plan& P = h->plan;
+    const size_t M = (size_t)h->s_total;
+    if (h->validate && !all_finite(t, M)) return fail(h, MCPT_EINVAL, "mcpt_singles: t has a non-finite value");
+    if (M == 0) return MCPT_OK;
+    CK(h, cudaSetDevice(h->device));
+    mcpt_status st;
+    if ((st = ensure(h, &h->dS1, &h->capS1, (2 * M + (size_t)h->s_parts) * sizeof(double)))) return st;
+    CK(h, cudaMemcpyAsync(h->dS1, t, M * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const char* tab = static_cast<const char*>(h->dCoup);
+    const SingTile* tiles = reinterpret_cast<const SingTile*>(tab + P.off_stiles);
+    const CoupDim* cds = reinterpret_cast<const CoupDim*>(tab + P.off_dims);
+    const int* mdim = reinterpret_cast<const int*>(tab + P.off_mdim);
+    const long long* soff = reinterpret_cast<const long long*>(tab + P.off_soff);
+    const long long* poff = reinterpret_cast<const long long*>(tab + P.off_poff);
+    const int N = (int)h->mons.size(), D = (int)h->dims.size();
+    MonomerLists L{h->dLists, h->dLists + N + 1, N};
+    double* part = h->dS1 + 2 * M;
+    if (P.prec == MCPT_FP64)
+        CK(h, launch_singles_fp64(tiles, P.nstiles, cds, D, L, mdim, soff, poff, static_cast<const double*>(h->dVT),
+                                  h->dS1, part, h->dS1 + M, h->stream));
+    else
+        CK(h, launch_singles_fp32(tiles, P.nstiles, cds, D, L, mdim, soff, poff, static_cast<const float*>(h->dVT),
+                                  h->dS1, part, h->dS1 + M, h->stream));
+    CK(h, cudaMemcpyAsync(s, h->dS1 + M, M * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    int status = 0;
+    CK(h, cudaMemcpy(&status, h->dFlag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) return fail(h, MCPT_ETIMEOUT, "mcpt_singles: a device-side wait gave up (status 0x%x)", status);
+    return MCPT_OK;
+}
+
 mcpt_status mcpt_collect_stats(mcpt_handle h, mcpt_run_stats* out)
 {
     if (!h || !out) return fail(h, MCPT_EINVAL, "mcpt_collect_stats: NULL argument");
@@ -1193,6 +1256,7 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dVT);
     cudaFree(h->dCoup);
     cudaFree(h->dR);
+    cudaFree(h->dS1);
     cudaFree(h->dPart);
     cudaFree(h->dE2);
     cudaFree(h->dMon);

@@ -118,6 +118,25 @@ cudaError_t launch_coupling_fp64(const CoupTile* tiles, const int* ntile, const 
                                  const int* mdim, const long long* r_off, const double* VT, double* R,
                                  cudaStream_t s);
 
+// Singles environment term of Eq. (tm1) from the same stored (ia|kc):
+// s_mon[(i,a)] = sum over the monomer's dimers (ascending) of
+// sum_{(k,c)} (ia|kc) t_other[(k,c)].  Two launches: each (dimer, side)
+// writes its contribution to part (dimer d's X part at part_off[d], its Y
+// part right after, m_X + m_Y doubles in all), then one thread per output
+// (tiles of 256 per monomer) adds the monomer's parts in ascending order.
+// t and s: FP64, monomer blocks of o v (at most 64 x 64 at 128 AO) at
+// s_off[mon].
+struct SingTile {
+    int mon;              // monomer
+    int p0;               // first output (i,a) index of the tile
+};
+cudaError_t launch_singles_fp32(const SingTile* tiles, int ntiles, const CoupDim* dims, int ndims, MonomerLists lists,
+                                const int* mdim, const long long* s_off, const long long* part_off, const float* VT,
+                                const double* t, double* part, double* s, cudaStream_t st);
+cudaError_t launch_singles_fp64(const SingTile* tiles, int ntiles, const CoupDim* dims, int ndims, MonomerLists lists,
+                                const int* mdim, const long long* s_off, const long long* part_off, const double* VT,
+                                const double* t, double* part, double* s, cudaStream_t st);
+
 // Split dimers: E2[dimer] = sum, in block order, of E2[first .. first+n) for
 // each (dimer, first, n) triple of `fold` (device, 3 ints each).
 cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s);

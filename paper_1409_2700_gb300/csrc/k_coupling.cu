@@ -140,6 +140,86 @@ cudaError_t launch(const CoupTile* tiles, const int* ntile, const CoupDim* dims,
     return cudaGetLastError();
 }
 
+// Singles environment term of Eq. (tm1): s_X[(i,a)] = sum over X's dimers
+// (ascending) of sum_{(k,c)} (ia|kc) t_Y[(k,c)], in two launches.  First one
+// CTA of 256 threads per (dimer, side) forms that dimer's contribution to one
+// of its monomers, with the neighbour's amplitudes converted to the storage
+// type in shared memory: X side, a thread per output column p walks the
+// stored rows in order (partial sums of 32 rows added in FP64); Y side, a warp
+// per output row, a dot product of the stored row with t_X (lanes strided
+// over the row, then a butterfly).  Then one thread per output adds the
+// contributions of the monomer's dimers in ascending order.  Fixed orders
+// throughout, so s is deterministic run to run.
+constexpr int kSThreads = 256;
+constexpr int kSMaxM = 4096;     // o v <= 64 x 64 for any monomer of at most 128 AO
+
+template <typename T>
+__global__ void __launch_bounds__(kSThreads)
+k_singles_part(const CoupDim* __restrict__ dims, const long long* __restrict__ s_off,
+               const long long* __restrict__ part_off, const T* __restrict__ VT, const double* __restrict__ t,
+               double* __restrict__ part)
+{
+    __shared__ T st[kSMaxM];
+    const int d = blockIdx.x >> 1, side = blockIdx.x & 1;
+    const CoupDim cd = dims[d];
+    const T* V = VT + cd.vt_off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int mo = side == 0 ? cd.mY : cd.mX;                 // length of the neighbour's amplitudes
+    const double* to = t + s_off[side == 0 ? cd.Y : cd.X];
+    for (int e = tid; e < mo; e += kSThreads) st[e] = (T)to[e];
+    __syncthreads();
+    double* out = part + part_off[d] + (side == 0 ? 0 : cd.mX);
+    if (side == 0) {
+        for (int p = tid; p < cd.mX; p += kSThreads) {
+            double acc = 0.0;
+            for (int r0 = 0; r0 < cd.mY; r0 += 32) {
+                const int r1 = min(r0 + 32, cd.mY);
+                T x = T(0);
+#pragma unroll 8
+                for (int r = r0; r < r1; r++) x = fma(V[(long long)r * cd.mX + p], st[r], x);
+                acc += (double)x;
+            }
+            out[p] = acc;
+        }
+    } else {
+        for (int r = warp; r < cd.mY; r += kSThreads / 32) {
+            const T* row = V + (long long)r * cd.mX;
+            T x = T(0);
+            for (int q = lane; q < cd.mX; q += 32) x = fma(row[q], st[q], x);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) out[r] = (double)x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSThreads)
+k_singles_sum(const SingTile* __restrict__ tiles, const CoupDim* __restrict__ dims, MonomerLists L,
+              const int* __restrict__ mdim, const long long* __restrict__ s_off,
+              const long long* __restrict__ part_off, const double* __restrict__ part, double* __restrict__ s)
+{
+    const SingTile tile = tiles[blockIdx.x];
+    const int mon = tile.mon, p = tile.p0 + threadIdx.x;
+    if (p >= mdim[mon]) return;
+    double acc = 0.0;
+    for (int li = L.start[mon]; li < L.start[mon + 1]; li++) {
+        const int d = L.list[li];
+        const CoupDim cd = dims[d];
+        acc += part[part_off[d] + (cd.X == mon ? 0 : cd.mX) + p];
+    }
+    s[s_off[mon] + p] = acc;
+}
+
+template <typename T>
+cudaError_t launch_s(const SingTile* tiles, int ntiles, const CoupDim* dims, int ndims, MonomerLists lists,
+                     const int* mdim, const long long* s_off, const long long* part_off, const T* VT,
+                     const double* t, double* part, double* s, cudaStream_t st)
+{
+    if (ndims > 0) k_singles_part<T><<<2 * ndims, kSThreads, 0, st>>>(dims, s_off, part_off, VT, t, part);
+    if (ntiles > 0) k_singles_sum<<<ntiles, kSThreads, 0, st>>>(tiles, dims, lists, mdim, s_off, part_off, part, s);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_coupling_fp32(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists,
@@ -154,6 +234,20 @@ cudaError_t launch_coupling_fp64(const CoupTile* tiles, const int* ntile, const 
                                  cudaStream_t s)
 {
     return launch<double>(tiles, ntile, dims, lists, mdim, r_off, VT, R, s);
+}
+
+cudaError_t launch_singles_fp32(const SingTile* tiles, int ntiles, const CoupDim* dims, int ndims, MonomerLists lists,
+                                const int* mdim, const long long* s_off, const long long* part_off, const float* VT,
+                                const double* t, double* part, double* s, cudaStream_t st)
+{
+    return launch_s<float>(tiles, ntiles, dims, ndims, lists, mdim, s_off, part_off, VT, t, part, s, st);
+}
+
+cudaError_t launch_singles_fp64(const SingTile* tiles, int ntiles, const CoupDim* dims, int ndims, MonomerLists lists,
+                                const int* mdim, const long long* s_off, const long long* part_off, const double* VT,
+                                const double* t, double* part, double* s, cudaStream_t st)
+{
+    return launch_s<double>(tiles, ntiles, dims, ndims, lists, mdim, s_off, part_off, VT, t, part, s, st);
 }
 
 }  // namespace mcpt
