@@ -38,7 +38,11 @@ def parse():
     p.add_argument("--workload", default="lattice-5x5x5-cheb1")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=192, help="dimers in the oracle's timed sample")
-    p.add_argument("--no-extras", action="store_true", help="skip e2e, CPU baseline and the FP64 comparison")
+    p.add_argument("--no-extras", action="store_true",
+                   help="report none of the extras (coupling, FP64 form, e2e, CPU baseline)")
+    p.add_argument("--extras", default="coupling,fp64,e2e,cpu",
+                   help="comma-separated extras to report after the headline (default all of "
+                        "coupling,fp64,e2e,cpu)")
     p.add_argument("--max-dimers", type=int, default=0,
                    help="keep only the first N dimers of the workload (smaller cases for profiling)")
     p.add_argument("--alias-blocks", action="store_true",
@@ -326,7 +330,8 @@ def our_arm(args, ws, rank, local):
     line["graph"] = {"value": w.n_dimers / (gms * 1e-3), "unit": UNIT, "ms_per_step": gms}
     gctx.close()
 
-    if not args.no_extras and rank == 0:
+    extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
+    if rank == 0 and "coupling" in extras:
         # ---- the dimer -> monomer doubles coupling of Eq. (tm2) at first order on
         # the same inputs: the same runs with coupling on, the difference timed
         cc = make_ctx(args.precision, False, coupling=True)
@@ -374,31 +379,32 @@ def our_arm(args, ws, rank, local):
                     "mcpt_singles call including the amplitude and result copies"}
         cc.close()
 
-        # ---- the plain FP64 GPU form on the same resident inputs
-        if args.precision != "fp64":
-            c64 = make_ctx("fp64", True)
-            c64.run()
-            c64.energies()
-            c64.stats()
-            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            n64 = max(2, args.steps // 4)
-            with torch.cuda.stream(stream):
-                f0.record(stream)
-                for _ in range(n64):
-                    c64.run()
-                f1.record(stream)
-            torch.cuda.synchronize()
-            s64 = c64.stats()
-            _, _, pd64, tot64 = c64.energies()
-            ms64 = f0.elapsed_time(f1) / n64
-            fp64 = {"value": w.n_dimers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                    "transform_tflops": s64.alg_flops / (ms64 * 1e-3) / 1e12,
-                    "first_half_ms": s64.ms[0] / s64.runs}
-            if g is not None:
-                fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
-            line["fp64_form"] = fp64
-            c64.close()
+    # ---- the plain FP64 GPU form on the same resident inputs
+    if rank == 0 and "fp64" in extras and args.precision != "fp64":
+        c64 = make_ctx("fp64", True)
+        c64.run()
+        c64.energies()
+        c64.stats()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = max(2, args.steps // 4)
+        with torch.cuda.stream(stream):
+            f0.record(stream)
+            for _ in range(n64):
+                c64.run()
+            f1.record(stream)
+        torch.cuda.synchronize()
+        s64 = c64.stats()
+        _, _, pd64, tot64 = c64.energies()
+        ms64 = f0.elapsed_time(f1) / n64
+        fp64 = {"value": w.n_dimers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                "transform_tflops": s64.alg_flops / (ms64 * 1e-3) / 1e12,
+                "first_half_ms": s64.ms[0] / s64.runs}
+        if g is not None:
+            fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
+        line["fp64_form"] = fp64
+        c64.close()
 
+    if rank == 0 and "e2e" in extras:
         # ---- end to end through the C ABI from pinned host buffers
         host = torch.empty(buf.numel(), dtype=torch.float64, pin_memory=True)
         host.copy_(buf)
@@ -439,6 +445,7 @@ def our_arm(args, ws, rank, local):
                                    "mcpt_run, mcpt_energies; context, monomers and plan set up once"}
         del host
 
+    if rank == 0 and "cpu" in extras:
         # ---- the oracle on the host cores, bounded sample
         import oracle
         oracle.build()

@@ -11,11 +11,14 @@
 // its mirror R[q][p] for p <= q (R is exactly symmetric).  A monomer's tiles
 // have edge 64, 48 or 32, whichever covers its o v rows with the least padded
 // work, one launch per edge.  A CTA walks the monomer's dimers in ascending
-// order and their rows in chunks of 32 (16 in FP64) staged in shared memory
-// (rows padded by 4 so the transposed Y side stages without bank conflicts,
-// eight rows by four columns per warp); each thread accumulates a contiguous
-// 4 x 4 block in registers: per row four 4-wide shared loads feed 32 FMAs.
-// Every sum has a fixed order, so R is deterministic run to run.
+// order and their rows in chunks of 32 (16 in FP64), staged in shared memory
+// by cp.async into two buffers: the next chunk is in flight while the
+// current one is summed.  (Chunks of 16 or 24 rows, which fit five CTAs of
+// edge 48 per SM, measured slower: the barriers cost more than the wave.)  Rows are padded by 4 so the transposed Y side
+// stages without bank conflicts (eight rows by four columns per warp); each
+// thread accumulates a contiguous 4 x 4 block in registers: per row four
+// 4-wide shared loads feed 32 FMAs.  Every sum has a fixed order, so R is
+// deterministic run to run.
 #include "internal.h"
 
 namespace mcpt {
@@ -25,6 +28,8 @@ template <typename T>
 __host__ __device__ constexpr int ck() { return sizeof(T) == 8 ? 16 : 32; }   // rows per staged chunk
 template <int CT>
 __host__ __device__ constexpr int cthreads() { return ((CT / 4) * (CT / 4) + 31) / 32 * 32; }
+template <typename T, int CT>
+__host__ __device__ constexpr size_t coupling_smem() { return 2 * 4 * ck<T>() * (CT + 4) * sizeof(T); }
 
 template <typename T>
 __device__ __forceinline__ void ld4(const T* p, T (&x)[4])
@@ -38,21 +43,74 @@ __device__ __forceinline__ void ld4(const T* p, T (&x)[4])
     }
 }
 
+// One element copy global -> shared; an invalid source writes zero (no read).
+template <typename T>
+__device__ __forceinline__ void cp_elem(T* dst, const T* src, bool ok, const T* any)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(ok ? src : any), "n"(sizeof(T)), "r"(ok ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+
+// Start the copies of rows k0 .. k0 + kCK of one dimer's operands into
+// buffer B (4 planes: T and V of the p columns, T and V of the q columns),
+// committed as one group per thread.
+template <typename T, int CT>
+__device__ __forceinline__ void stage_chunk(T* B, const CoupDim& cd, bool xside, int k0, const T* VT, int m,
+                                            const CoupTile& tile, bool diag, int tid)
+{
+    constexpr int kCK = ck<T>(), kLD = CT + 4, kNT = cthreads<CT>(), kPL = kCK * kLD;
+    const T* V = VT + cd.vt_off;
+    const T* Tm = V + (long long)cd.mX * cd.mY;
+    const int K = xside ? cd.mY : cd.mX;
+    const long long ld = cd.mX;
+    if (xside) {                                // rows k of the stored matrices, contiguous along c
+        for (int e = tid; e < kCK * CT; e += kNT) {
+            const int r = e / CT, c = e % CT, k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
+            const bool okk = k < K;
+            const long long rowk = (long long)k * ld;
+            T* d = B + r * kLD + c;
+            cp_elem(d, Tm + rowk + p, okk && p < m, VT);
+            cp_elem(d + kPL, V + rowk + p, okk && p < m, VT);
+            if (!diag) {
+                cp_elem(d + 2 * kPL, Tm + rowk + q, okk && q < m, VT);
+                cp_elem(d + 3 * kPL, V + rowk + q, okk && q < m, VT);
+            }
+        }
+    } else {                                    // columns k of the stored rows p, q: 8 rows x 4 columns a warp
+        constexpr int kRG = kCK / 8;
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int g = warp; g < kRG * (CT / 4); g += kNT / 32) {
+            const int r = (g % kRG) * 8 + (lane & 7), c = (g / kRG) * 4 + (lane >> 3);
+            const int k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
+            const bool okk = k < K;
+            T* d = B + r * kLD + c;
+            cp_elem(d, Tm + p * ld + k, okk && p < m, VT);
+            cp_elem(d + kPL, V + p * ld + k, okk && p < m, VT);
+            if (!diag) {
+                cp_elem(d + 2 * kPL, Tm + q * ld + k, okk && q < m, VT);
+                cp_elem(d + 3 * kPL, V + q * ld + k, okk && q < m, VT);
+            }
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <typename T, int CT>
 __global__ void __launch_bounds__(cthreads<CT>())
 k_coupling(const CoupTile* __restrict__ tiles, const CoupDim* __restrict__ dims, MonomerLists L,
            const int* __restrict__ mdim, const long long* __restrict__ r_off, const T* __restrict__ VT,
            double* __restrict__ R)
 {
-    constexpr int kCK = ck<T>(), kLD = CT + 4, kNT = cthreads<CT>(), kTW = CT / 4;
+    constexpr int kCK = ck<T>(), kLD = CT + 4, kTW = CT / 4, kPL = kCK * kLD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* buf = reinterpret_cast<T*>(smem_raw);   // 2 buffers x 4 planes x kCK x kLD
     const CoupTile tile = tiles[blockIdx.x];
     const int mon = tile.mon, m = mdim[mon];
     const bool diag = tile.p0 == tile.q0;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const bool active = tid < kTW * kTW;
     const int ty = tid / kTW, tx = tid % kTW;
-    // [0] T rows p, [1] V rows p, [2] T rows q, [3] V rows q
-    __shared__ __align__(16) T sm[4][kCK][kLD];
     const int qs = diag ? 0 : 2;      // a diagonal tile reads its p operands twice
     T acc[4][4];
 #pragma unroll
@@ -60,59 +118,51 @@ k_coupling(const CoupTile* __restrict__ tiles, const CoupDim* __restrict__ dims,
 #pragma unroll
         for (int w = 0; w < 4; w++) acc[u][w] = T(0);
 
-    for (int li = L.start[mon]; li < L.start[mon + 1]; li++) {
-        const CoupDim cd = dims[L.list[li]];
-        const T* V = VT + cd.vt_off;
-        const T* Tm = V + (long long)cd.mX * cd.mY;
-        const bool xside = cd.X == mon;
-        const int K = xside ? cd.mY : cd.mX;        // rows summed over
-        const long long ld = cd.mX;                 // row length of the stored [(j,b)][(i,a)]
-        for (int k0 = 0; k0 < K; k0 += kCK) {
-            __syncthreads();
-            if (xside) {                            // rows k of the stored matrices, contiguous along c
-                for (int e = tid; e < kCK * CT; e += kNT) {
-                    const int r = e / CT, c = e % CT, k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
-                    T tp = T(0), vp = T(0), tq = T(0), vq = T(0);
-                    if (k < K) {
-                        const long long rowk = k * ld;
-                        if (p < m) { tp = Tm[rowk + p]; vp = V[rowk + p]; }
-                        if (!diag && q < m) { tq = Tm[rowk + q]; vq = V[rowk + q]; }
-                    }
-                    sm[0][r][c] = tp; sm[1][r][c] = vp;
-                    if (!diag) { sm[2][r][c] = tq; sm[3][r][c] = vq; }
-                }
-            } else {                                // columns k of the stored rows p, q: 8 rows x 4 columns a warp
-                constexpr int kRG = kCK / 8;
-                for (int g = warp; g < kRG * (CT / 4); g += kNT / 32) {
-                    const int r = (g % kRG) * 8 + (lane & 7), c = (g / kRG) * 4 + (lane >> 3);
-                    const int k = k0 + r, p = tile.p0 + c, q = tile.q0 + c;
-                    T tp = T(0), vp = T(0), tq = T(0), vq = T(0);
-                    if (k < K) {
-                        if (p < m) { tp = Tm[p * ld + k]; vp = V[p * ld + k]; }
-                        if (!diag && q < m) { tq = Tm[q * ld + k]; vq = V[q * ld + k]; }
-                    }
-                    sm[0][r][c] = tp; sm[1][r][c] = vp;
-                    if (!diag) { sm[2][r][c] = tq; sm[3][r][c] = vq; }
-                }
+    // the chunk sequence: (dimer li, rows k0) in order; `next` is staged one ahead
+    int li = L.start[mon];
+    const int lend = L.start[mon + 1];
+    if (li >= lend) goto write;
+    {
+        CoupDim cd = dims[L.list[li]];
+        int k0 = 0, b = 0;
+        stage_chunk<T, CT>(buf, cd, cd.X == mon, 0, VT, m, tile, diag, tid);
+        for (;;) {
+            const int K = cd.X == mon ? cd.mY : cd.mX;
+            const int kn = min(kCK, K - k0);
+            // the chunk after this one
+            int nli = li, nk0 = k0 + kCK;
+            if (nk0 >= K) { nli = li + 1; nk0 = 0; }
+            const bool more = nli < lend;
+            CoupDim ncd = cd;
+            if (more) {
+                if (nli != li) ncd = dims[L.list[nli]];
+                stage_chunk<T, CT>(buf + (b ^ 1) * 4 * kPL, ncd, ncd.X == mon, nk0, VT, m, tile, diag, tid);
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            } else {
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
             }
             __syncthreads();
             if (active) {
-                const int kn = min(kCK, K - k0);
+                const T* S = buf + b * 4 * kPL;
 #pragma unroll 2
                 for (int r = 0; r < kn; r++) {
                     T at[4], av[4], bt[4], bv[4];
-                    ld4(&sm[0][r][4 * ty], at);
-                    ld4(&sm[1][r][4 * ty], av);
-                    ld4(&sm[qs][r][4 * tx], bt);
-                    ld4(&sm[qs + 1][r][4 * tx], bv);
+                    ld4(S + r * kLD + 4 * ty, at);
+                    ld4(S + kPL + r * kLD + 4 * ty, av);
+                    ld4(S + qs * kPL + r * kLD + 4 * tx, bt);
+                    ld4(S + (qs + 1) * kPL + r * kLD + 4 * tx, bv);
 #pragma unroll
                     for (int u = 0; u < 4; u++)
 #pragma unroll
                         for (int w = 0; w < 4; w++) acc[u][w] = fma(at[u], bv[w], fma(av[u], bt[w], acc[u][w]));
                 }
             }
+            __syncthreads();            // buffer b is refilled two chunks on
+            if (!more) break;
+            li = nli; k0 = nk0; cd = ncd; b ^= 1;
         }
     }
+write:
     if (!active) return;
     double* Rm = R + r_off[mon];
 #pragma unroll
@@ -127,17 +177,28 @@ k_coupling(const CoupTile* __restrict__ tiles, const CoupDim* __restrict__ dims,
         }
 }
 
+template <typename T, int CT>
+cudaError_t launch_edge(const CoupTile* tiles, int n, const CoupDim* dims, MonomerLists lists, const int* mdim,
+                        const long long* r_off, const T* VT, double* R, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    constexpr size_t smem = coupling_smem<T, CT>();
+    cudaError_t e = cudaFuncSetAttribute(k_coupling<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_coupling<T, CT><<<n, cthreads<CT>(), smem, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch(const CoupTile* tiles, const int* ntile, const CoupDim* dims, MonomerLists lists, const int* mdim,
                    const long long* r_off, const T* VT, double* R, cudaStream_t s)
 {
     // tiles: the edge-64 tiles, then the edge-48, then the edge-32 ones
-    if (ntile[0] > 0) k_coupling<T, 64><<<ntile[0], cthreads<64>(), 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
-    tiles += ntile[0];
-    if (ntile[1] > 0) k_coupling<T, 48><<<ntile[1], cthreads<48>(), 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
-    tiles += ntile[1];
-    if (ntile[2] > 0) k_coupling<T, 32><<<ntile[2], cthreads<32>(), 0, s>>>(tiles, dims, lists, mdim, r_off, VT, R);
-    return cudaGetLastError();
+    cudaError_t e = launch_edge<T, 64>(tiles, ntile[0], dims, lists, mdim, r_off, VT, R, s);
+    if (e == cudaSuccess) e = launch_edge<T, 48>(tiles + ntile[0], ntile[1], dims, lists, mdim, r_off, VT, R, s);
+    if (e == cudaSuccess)
+        e = launch_edge<T, 32>(tiles + ntile[0] + ntile[1], ntile[2], dims, lists, mdim, r_off, VT, R, s);
+    return e;
 }
 
 // Singles environment term of Eq. (tm1): s_X[(i,a)] = sum over X's dimers
