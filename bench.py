@@ -405,45 +405,72 @@ def our_arm(args, ws, rank, local):
         c64.close()
 
     if rank == 0 and "e2e" in extras:
-        # ---- end to end through the C ABI from pinned host buffers
+        # ---- end to end through the C ABI from pinned host buffers, in two
+        # input layouts: the blocks (BLOCKS) and their unique elements under
+        # the real-orbital pair symmetry (PACKED, expanded on the device)
         host = torch.empty(buf.numel(), dtype=torch.float64, pin_memory=True)
         host.copy_(buf)
+        shapes = {}
+        poffs, ptot = [], 0
+        for d in range(w.n_dimers):
+            X, Y = w.pairs[d]
+            key = (w.nao[X], w.nao[Y])
+            if key not in shapes:
+                shapes[key] = torch.from_numpy(synth.packed_gather_index(*key)).to(buf.device)
+            poffs.append(ptot)
+            ptot += shapes[key].numel()
+        phost = torch.empty(ptot, dtype=torch.float64, pin_memory=True)
+        for d in range(w.n_dimers):                 # input preparation (untimed): gather the unique elements
+            X, Y = w.pairs[d]
+            idx = shapes[(w.nao[X], w.nao[Y])]
+            phost[poffs[d]:poffs[d] + idx.numel()].copy_(buf[offs[d]:offs[d] + 2 * w.nao[X] ** 2 * w.nao[Y] ** 2][idx])
         torch.cuda.synchronize()
-        hbase = host.data_ptr()
-        blk_bytes = sum(2 * 8 * (w.nao[w.pairs[d][0]] ** 2) * (w.nao[w.pairs[d][1]] ** 2) for d in range(w.n_dimers))
         d2h = 8 * (2 * w.n_monomers + 2 * w.n_dimers + 2)
         del ctx
         torch.cuda.synchronize()
-        # one context for the whole sequence (set up untimed: monomers, dimers,
-        # the plan and its graph); every timed step copies that step's integrals
-        # from pinned host memory into it (mcpt_update_dimer, asynchronous),
-        # runs, and reads the energies back
-        c = M.Context(precision=args.precision, device=local, validate=False)
-        for m in mons:
-            c.add_monomer(m.C, m.eps, m.nocc)
-        for d in range(w.n_dimers):
-            X, Y = w.pairs[d]
-            c.add_dimer(X, Y, hbase + 8 * offs[d], M.MCPT_AO_BLOCKS, on_device=0)
-        c.run()
-        c.energies()
-        t_e2e = []
-        for k in range(args.e2e_steps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
+
+        def e2e(layout, base, doffs):
+            # one context for the whole sequence (set up untimed: monomers,
+            # dimers, the plan and its graph); every timed step copies that
+            # step's integrals from pinned host memory into it
+            # (mcpt_update_dimer, asynchronous), runs, and reads the energies back
+            c = M.Context(precision=args.precision, device=local, validate=False)
+            for m in mons:
+                c.add_monomer(m.C, m.eps, m.nocc)
             for d in range(w.n_dimers):
-                c.update_dimer(d, hbase + 8 * offs[d], M.MCPT_AO_BLOCKS, on_device=0, asynchronous=True)
+                X, Y = w.pairs[d]
+                c.add_dimer(X, Y, base + 8 * doffs[d], layout, on_device=0)
             c.run()
-            out = c.energies()
-            t1 = time.perf_counter()
-            if k > 0:
-                t_e2e.append(t1 - t0)
-        c.close()
-        e2e_s = statistics.median(t_e2e)
-        line["e2e"] = {"value": w.n_dimers / e2e_s, "unit": UNIT, "h2d_bytes_per_step": blk_bytes,
-                       "d2h_bytes_per_step": d2h, "s_per_step": e2e_s, "steps": len(t_e2e),
-                       "per_step": "mcpt_update_dimer of every dimer from pinned host memory (asynchronous), "
-                                   "mcpt_run, mcpt_energies; context, monomers and plan set up once"}
-        del host
+            c.energies()
+            ts, same = [], True
+            for k in range(args.e2e_steps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for d in range(w.n_dimers):
+                    c.update_dimer(d, base + 8 * doffs[d], layout, on_device=0, asynchronous=True)
+                c.run()
+                out = c.energies()
+                t1 = time.perf_counter()
+                same = same and bool(np.array_equal(out[2], pd))
+                if k > 0:
+                    ts.append(t1 - t0)
+            c.close()
+            return statistics.median(ts), len(ts), same
+
+        blk_bytes = sum(2 * 8 * (w.nao[w.pairs[d][0]] ** 2) * (w.nao[w.pairs[d][1]] ** 2) for d in range(w.n_dimers))
+        ps, pn, psame = e2e(M.MCPT_AO_PACKED, phost.data_ptr(), poffs)
+        bs, bn, bsame = e2e(M.MCPT_AO_BLOCKS, host.data_ptr(), offs)
+        line["e2e"] = {"value": w.n_dimers / ps, "unit": UNIT, "h2d_bytes_per_step": 8 * ptot,
+                       "d2h_bytes_per_step": d2h, "s_per_step": ps, "steps": pn,
+                       "terms_equal_resident_run": psame,
+                       "per_step": "mcpt_update_dimer of every dimer's symmetry-packed integrals (MCPT_AO_PACKED: "
+                                   "the unique elements, expanded on the device) from pinned host memory "
+                                   "(asynchronous), mcpt_run, mcpt_energies; context, monomers and plan set up once"}
+        line["e2e_blocks"] = {"value": w.n_dimers / bs, "unit": UNIT, "h2d_bytes_per_step": blk_bytes,
+                              "d2h_bytes_per_step": d2h, "s_per_step": bs, "steps": bn,
+                              "terms_equal_resident_run": bsame,
+                              "per_step": "the same with the BLOCKS layout (both blocks in full)"}
+        del host, phost
 
     if rank == 0 and "cpu" in extras:
         # ---- the oracle on the host cores, bounded sample

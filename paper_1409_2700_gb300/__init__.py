@@ -23,7 +23,7 @@ MCPT_OK, MCPT_EINVAL, MCPT_ENOMEM, MCPT_ECUDA, MCPT_ESTATE, MCPT_ETIMEOUT, MCPT_
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
 MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C = range(4)
 PRECISIONS = {"fp64": MCPT_FP64, "tf32": MCPT_TF32, "bf16x3": MCPT_BF16X3, "fp32c": MCPT_FP32C}
-MCPT_AO_FULL, MCPT_AO_BLOCKS = 0, 1
+MCPT_AO_FULL, MCPT_AO_BLOCKS, MCPT_AO_PACKED = 0, 1, 2
 MCPT_UPDATE_ASYNC = 1
 
 # every symbol include/mcpt.h declares

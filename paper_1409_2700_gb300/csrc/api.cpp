@@ -91,6 +91,11 @@ struct mcpt_ctx {
     size_t capCoup = 0;
     double* dR = nullptr;            // coupling matrices R_X, per monomer
     size_t capR = 0;
+    double* dPack[2] = {nullptr, nullptr};   // staging of host symmetry-packed integrals (two,
+    size_t capPack[2] = {0, 0};              // filled alternately on the copy stream)
+    int pack_next = 0;
+    cudaStream_t copy_stream = nullptr;      // host -> device copies of packed integrals
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     double* dS1 = nullptr;           // singles term: amplitudes t, the result s, per-dimer parts
     size_t capS1 = 0;
     long long s_total = 0;           // sum over monomers of o v
@@ -370,12 +375,82 @@ mcpt_status mcpt_add_monomer(mcpt_handle h, const double* C, const double* eps, 
     return MCPT_OK;
 }
 
+static mcpt_status check_device_ptr(mcpt_handle h, const void* p, const char* who)
+{
+    cudaPointerAttributes pa;
+    cudaError_t e = cudaPointerGetAttributes(&pa, p);
+    if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != h->device) {
+        cudaGetLastError();
+        return fail(h, MCPT_EINVAL, "%s: on_device=1 but ao_eri is not device memory of device %d", who, h->device);
+    }
+    return MCPT_OK;
+}
+
+// Symmetry-packed integrals (X < Y): host data staged on the device, then
+// expanded into `storage` (or new arena memory) in the BLOCKS layout; the
+// record owns that storage.  Host data goes through two staging buffers
+// filled on a copy stream, so that the copy of the next dimer overlaps the
+// expansion of this one on the handle's stream.  Unless `async`, waits so
+// that the caller's buffer is free on return.
+static mcpt_status make_record_packed(mcpt_handle h, int X, int Y, const double* ao, int on_device,
+                                      double* storage, bool async, DimerRec& r, const char* who)
+{
+    if (X > Y) return fail(h, MCPT_EINVAL, "%s: packed integrals must be given with X < Y", who);
+    const int nX = h->mons[X].nao, nY = h->mons[Y].nao;
+    const size_t blk = (size_t)nX * nX * nY * nY;
+    const size_t np = packed_elems(nX, nY);
+    mcpt_status st;
+    const double* src = ao;
+    int sb = -1;                         // staging buffer of host data
+    if (on_device) {
+        if ((st = check_device_ptr(h, ao, who))) return st;
+        if (h->validate) {
+            CK(h, cudaMemsetAsync(h->dFlag, 0, sizeof(int), h->stream));
+            CK(h, launch_check_finite(ao, (long long)np, h->dFlag, h->stream));
+            int flag = 0;
+            CK(h, cudaMemcpyAsync(&flag, h->dFlag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            if (flag) return fail(h, MCPT_EINVAL, "%s: non-finite integral", who);
+        }
+    } else {
+        if (h->validate && !all_finite(ao, np)) return fail(h, MCPT_EINVAL, "%s: non-finite integral", who);
+        if (!h->copy_stream) {
+            CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+            for (int b = 0; b < 2; b++) {
+                CK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming));
+                CK(h, cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming));
+            }
+        }
+        sb = h->pack_next;
+        h->pack_next ^= 1;
+        if ((st = ensure(h, &h->dPack[sb], &h->capPack[sb], np * sizeof(double)))) return st;
+        CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_free[sb], 0));    // its last expansion has read it
+        CK(h, cudaMemcpyAsync(h->dPack[sb], ao, np * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream));
+        CK(h, cudaEventRecord(h->ev_copied[sb], h->copy_stream));
+        CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[sb], 0));
+        src = h->dPack[sb];
+    }
+    void* dst = storage;
+    if (!dst && (st = arena_alloc(h, 2 * blk * sizeof(double), &dst))) return st;
+    CK(h, launch_unpack(src, static_cast<double*>(dst), nX, nY, h->stream));
+    if (sb >= 0) CK(h, cudaEventRecord(h->ev_free[sb], h->stream));
+    if (!async) CK(h, cudaStreamSynchronize(h->stream));
+    const double* b = static_cast<const double*>(dst);
+    r.owned = static_cast<double*>(dst);
+    r.E[0] = b;
+    r.st[0][0] = (long long)nX * nY * nY; r.st[0][1] = (long long)nY * nY; r.st[0][2] = nY;
+    r.E[1] = b + blk;
+    r.st[1][0] = (long long)nY * nY * nX; r.st[1][1] = (long long)nY * nX; r.st[1][2] = nX;
+    return MCPT_OK;
+}
+
 // Point record r (monomers X, Y in the caller's order; r.X < r.Y) at the
 // dimer's integrals: device data in place (borrowed), host data copied into
 // `storage` (2 nX^2 nY^2 doubles of library memory) or into new arena memory.
 static mcpt_status make_record(mcpt_handle h, int X, int Y, const double* ao, mcpt_ao_layout layout, int on_device,
                                double* storage, bool async, DimerRec& r, const char* who)
 {
+    if (layout == MCPT_AO_PACKED) return make_record_packed(h, X, Y, ao, on_device, storage, async, r, who);
     const int nX = h->mons[X].nao, nY = h->mons[Y].nao, n = nX + nY;
     const size_t blk = (size_t)nX * nX * nY * nY;
     if (on_device) {
@@ -486,7 +561,7 @@ mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_a
         return fail(h, MCPT_EINVAL, "mcpt_add_dimer: unknown monomer id (%d, %d) of %d", X, Y, N);
     if (X == Y) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: X == Y == %d", X);
     if (!ao) return fail(h, MCPT_EINVAL, "mcpt_add_dimer: ao_eri is NULL");
-    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS)
+    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS && layout != MCPT_AO_PACKED)
         return fail(h, MCPT_EINVAL, "mcpt_add_dimer: bad layout %d", (int)layout);
     if (on_device && X > Y)
         return fail(h, MCPT_EINVAL, "mcpt_add_dimer: device integrals must be given with X < Y");
@@ -515,18 +590,20 @@ mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double* ao, mcpt_ao_l
     if (id < 0 || id >= (int)h->dims.size())
         return fail(h, MCPT_EINVAL, "mcpt_update_dimer: unknown dimer id %d of %zu", id, h->dims.size());
     if (!ao) return fail(h, MCPT_EINVAL, "mcpt_update_dimer: ao_eri is NULL");
-    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS)
+    if (layout != MCPT_AO_FULL && layout != MCPT_AO_BLOCKS && layout != MCPT_AO_PACKED)
         return fail(h, MCPT_EINVAL, "mcpt_update_dimer: bad layout %d", (int)layout);
     if (flags & ~MCPT_UPDATE_ASYNC) return fail(h, MCPT_EINVAL, "mcpt_update_dimer: unknown flags 0x%x", flags);
     CK(h, cudaSetDevice(h->device));
     const DimerRec& old = h->dims[id];
     DimerRec r = old;
     r.computed = false;
-    // host data reuses the dimer's library storage when it has some
-    mcpt_status st = make_record(h, old.X, old.Y, ao, layout, on_device, on_device ? nullptr : old.owned,
+    // host data (and packed data from anywhere) reuses the dimer's library
+    // storage when it has some
+    const bool packed = layout == MCPT_AO_PACKED;
+    mcpt_status st = make_record(h, old.X, old.Y, ao, layout, on_device, on_device && !packed ? nullptr : old.owned,
                                  (flags & MCPT_UPDATE_ASYNC) != 0, r, "mcpt_update_dimer");
     if (st) return st;
-    if (on_device) r.owned = old.owned;     // keep the storage for a later host update
+    if (on_device && !packed) r.owned = old.owned;     // keep the storage for a later host update
     if (r.E[0] != old.E[0] || r.E[1] != old.E[1] || std::memcmp(r.st, old.st, sizeof r.st))
         h->plan.valid = false;              // the tensor maps name the old addresses
     h->dims[id] = r;
@@ -1257,6 +1334,12 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dCoup);
     cudaFree(h->dR);
     cudaFree(h->dS1);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(h->dPack[b]);
+        if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
+        if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     cudaFree(h->dPart);
     cudaFree(h->dE2);
     cudaFree(h->dMon);

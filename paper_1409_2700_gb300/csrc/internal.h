@@ -146,6 +146,10 @@ cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists,
                           double* mon /* 2*n_mon */, double* total /* 2 */, cudaStream_t s);
 
 // Finiteness check of n doubles; sets *flag to 1 if any is NaN/Inf.
+// Symmetry-packed dimer integrals (MCPT_AO_PACKED): packed_elems(nX, nY)
+// doubles expanded into blocks = [A | K] (BLOCKS layout, 2 nX^2 nY^2).
+size_t packed_elems(int nX, int nY);
+cudaError_t launch_unpack(const double* packed, double* blocks, int nX, int nY, cudaStream_t s);
 cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s);
 // Same for a strided 4-index block.
 cudaError_t launch_check_finite4(const double* x, const int dims[4], const long long st[3],

@@ -213,6 +213,39 @@ def extract_blocks(G, nX: int):
     return np.ascontiguousarray(A), np.ascontiguousarray(K)
 
 
+def packed_elems(nX: int, nY: int) -> int:
+    """Length of the symmetry-packed [A_p | K_p] of an nX + nY dimer."""
+    tX, tY, pq = nX * (nX + 1) // 2, nY * (nY + 1) // 2, nX * nY
+    return tX * tY + pq * (pq + 1) // 2
+
+
+def packed_gather_index(nX: int, nY: int):
+    """Flat indices into [A | K] (BLOCKS layout, 2 nX^2 nY^2) whose elements,
+    in order, form the packed layout: packed = blocks[index]."""
+    ix, iy = np.tril_indices(nX), np.tril_indices(nY)
+    ia = ((ix[0][:, None] * nX + ix[1][:, None]) * nY + iy[0][None, :]) * nY + iy[1][None, :]
+    ip = np.tril_indices(nX * nY)
+    mu, la = np.divmod(ip[0], nY)
+    nu, sg = np.divmod(ip[1], nY)
+    ik = nX * nX * nY * nY + ((mu * nY + la) * nY + sg) * nX + nu
+    return np.concatenate([ia.ravel(), ik]).astype(np.int64)
+
+
+def pack_blocks(A, K):
+    """The unique elements of symmetric A[mu][nu][lam][sig] and
+    K[mu][lam][sig][nu] in the packed order of the library's MCPT_AO_PACKED
+    layout (layout conversion only): A_p[t(mu,nu)][t(lam,sig)] over
+    mu >= nu, lam >= sig, then the lower triangle of M[P][Q] =
+    K[mu][lam][sig][nu], P = mu nY + lam, Q = nu nY + sig; t(a,b) =
+    a(a+1)/2 + b.  Elements above the triangles are not read."""
+    nX, nY = A.shape[0], A.shape[2]
+    ix, iy = np.tril_indices(nX), np.tril_indices(nY)
+    Ap = A[ix[0], ix[1]][:, iy[0], iy[1]]
+    M = np.transpose(K, (0, 1, 3, 2)).reshape(nX * nY, nX * nY)
+    ip = np.tril_indices(nX * nY)
+    return np.concatenate([Ap.ravel(), M[ip]])
+
+
 # ----------------------------------------------------------------- lattices
 @dataclass
 class Workload:
