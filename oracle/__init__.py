@@ -78,6 +78,9 @@ def lib():
             L.oracle_coupling_add.restype = None
             L.oracle_singles_add.argtypes = [_dp, _dp, _dp, I, I, I, I, _dp, _dp]
             L.oracle_singles_add.restype = None
+            L.oracle_td2.argtypes = [_dp, _dp, _dp, _dp, _dp, _dp, I, I, I, I, _dp, _dp, _dp, _dp, I,
+                                     _dp, _dp, _dp]
+            L.oracle_td2.restype = I
             L.oracle_max_threads.argtypes = []
             L.oracle_max_threads.restype = I
             _lib = L
@@ -198,6 +201,25 @@ def singles_lattice(w, t, dimers=None, blocks=None):
         V = transform_J(A, mX.C, mY.C, mX.nocc, mY.nocc)
         singles_add(V, t[X], t[Y], S[X], S[Y])
     return S
+
+
+def td2(A, K, CX, epsX, CY, epsY, oX, oY, n_iter, GX=None, GY=None, UX=None, UY=None):
+    """Eq. (td2) dimer amplitudes after n_iter Jacobi steps from zero and the
+    energies at them: (T [oX][vX][oY][vY], (E_J, E_K), per-step max |dT|).
+    GX, GY: monomer ring matrices, UX, UY: monomer amplitude matrices
+    (2T - T'), each (o v) x (o v) or None (zero)."""
+    A, K, CX, CY = _f64(A), _f64(K), _f64(CX), _f64(CY)
+    epsX, epsY = _f64(epsX), _f64(epsY)
+    nX, nY = CX.shape[0], CY.shape[0]
+    T = np.empty(_shape_mo(nX, nY, oX, oY)[0])
+    E = np.empty(2)
+    delta = np.empty(max(n_iter, 1))
+    opt = [None if M is None else _f64(M) for M in (GX, GY, UX, UY)]
+    ptrs = [None if M is None else _p(M) for M in opt]
+    if lib().oracle_td2(_p(A), _p(K), _p(CX), _p(epsX), _p(CY), _p(epsY), nX, nY, oX, oY,
+                        *ptrs, n_iter, _p(T), _p(E), _p(delta)):
+        raise MemoryError("oracle_td2")
+    return T, (E[0], E[1]), delta[:n_iter]
 
 
 def coupling_lattice(w, dimers=None, blocks=None):

@@ -209,6 +209,129 @@ void oracle_singles_add(const double *V, const double *tX, const double *tY,
     }
 }
 
+/* Dimer doubles amplitudes of Eq. (td2) by Jacobi steps from T = 0, and the
+ * dimer energy of Eq. (ed2) at the final amplitudes.
+ *
+ * i, i1 (a, a1) run over X's occupied (virtual) orbitals, j, j1 (b, b1) over
+ * Y's.  With g[p][q][r][s] = (p q|r s) the full MO transformation of the
+ * Coulomb block (p, q MOs of X; r, s MOs of Y) and physicist integrals
+ * <pq|rs> = (pr|qs), the equation's terms are
+ *   v^{ab}_{ij}       = (ia|jb)                     = v[i][a][j][b]
+ *   v^{ab}_{a1 b1}    = (a a1|b b1)                 (particle ladder)
+ *   v^{i1 j1}_{ij}    = (i1 i|j1 j)                 (hole ladder)
+ *   v^{b i1}_{b1 i}   = (b b1|i1 i) = (i1 i|b b1)   (enters with -)
+ *   v^{a j1}_{a1 j}   = (a a1|j1 j)                 (enters with -)
+ *   (2 v^{i1 a}_{a1 i} - v^{a i1}_{a1 i})           monomer X ring matrix GX[(i,a)][(i1,a1)]
+ *   (2 v^{j1 b}_{b1 j} - v^{b j1}_{b1 j})           monomer Y ring matrix GY[(j,b)][(j1,b1)]
+ *   v^{i1 b}_{a1 j} (2 T^{a a1}_{i i1} - T^{a a1}_{i1 i}) = sum UX[(i,a)][(i1,a1)] v[i1][a1][j][b]
+ *   v^{j1 a}_{b1 i} (2 T^{b b1}_{j j1} - T^{b b1}_{j1 j}) = sum UY[(j,b)][(j1,b1)] v[i][a][j1][b1]
+ * GX, GY, UX, UY are the monomers' own quantities (row-major (o v)^2,
+ * index i*v + a), given by the caller; NULL means zero.  Each step sets
+ *   T <- D (v + S + L(T)),  D = 1/(e_i + e_j - e_a - e_b),
+ * S the two monomer-amplitude terms and L the six amplitude-dependent terms
+ * with their signs as printed; the sign of the energy-tensor term is taken
+ * as for the first-order amplitude (so that one step gives T = v D).
+ * Energies: E_J = 4 sum v T (Eq. ed2), E_K = -2 sum (ib|ja) T.
+ * T: out, [oX][vX][oY][vY]; E: out {E_J, E_K}; delta: out (n_iter values,
+ * or NULL), max |T_new - T_old| of each step.  Returns 0 on success. */
+int oracle_td2(const double *A, const double *K,
+               const double *CX, const double *epsX, const double *CY, const double *epsY,
+               int nX, int nY, int oX, int oY,
+               const double *GX, const double *GY, const double *UX, const double *UY,
+               int n_iter, double *T, double *E, double *delta)
+{
+    const int vX = nX - oX, vY = nY - oY;
+    const size_t mX = (size_t)oX * vX, mY = (size_t)oY * vY, nt = mX * mY;
+    const size_t ng = (size_t)nX * nX * nY * nY;
+    int n[4] = {nX, nX, nY, nY};
+    double *g = malloc(ng * sizeof(double));
+    double *v = malloc(nt * sizeof(double));
+    double *W = malloc(nt * sizeof(double));
+    double *S = malloc(nt * sizeof(double));
+    double *Tn = malloc(nt * sizeof(double));
+    int rc = -1;
+    if (!g || !v || !W || !S || !Tn) goto out;
+    if (transform4(A, n, CX, nX, 0, nX, CX, nX, 0, nX, CY, nY, 0, nY, CY, nY, 0, nY, g)) goto out;
+    if (oracle_transform_K(K, CX, CY, nX, nY, oX, oY, W)) goto out;
+#define G4(p, q, r, s) g[(((size_t)(p) * nX + (q)) * nY + (r)) * nY + (s)]
+#define IDX(i, a, j, b) ((((size_t)(i) * vX + (a)) * oY + (j)) * vY + (b))
+    for (int i = 0; i < oX; i++)
+    for (int a = 0; a < vX; a++)
+    for (int j = 0; j < oY; j++)
+    for (int b = 0; b < vY; b++)
+        v[IDX(i, a, j, b)] = G4(i, oX + a, j, oY + b);
+    for (int i = 0; i < oX; i++)
+    for (int a = 0; a < vX; a++)
+    for (int j = 0; j < oY; j++)
+    for (int b = 0; b < vY; b++) {
+        double s = 0.0;
+        if (UX)
+            for (int i1 = 0; i1 < oX; i1++)
+            for (int a1 = 0; a1 < vX; a1++)
+                s += UX[((size_t)i * vX + a) * mX + (size_t)i1 * vX + a1] * v[IDX(i1, a1, j, b)];
+        if (UY)
+            for (int j1 = 0; j1 < oY; j1++)
+            for (int b1 = 0; b1 < vY; b1++)
+                s += UY[((size_t)j * vY + b) * mY + (size_t)j1 * vY + b1] * v[IDX(i, a, j1, b1)];
+        S[IDX(i, a, j, b)] = s;
+    }
+    memset(T, 0, nt * sizeof(double));
+    for (int it = 0; it < n_iter; it++) {
+        double dmax = 0.0;
+        for (int i = 0; i < oX; i++)
+        for (int a = 0; a < vX; a++)
+        for (int j = 0; j < oY; j++)
+        for (int b = 0; b < vY; b++) {
+            double r = v[IDX(i, a, j, b)] + S[IDX(i, a, j, b)];
+            for (int a1 = 0; a1 < vX; a1++)                 /* particle ladder */
+            for (int b1 = 0; b1 < vY; b1++)
+                r += G4(oX + a, oX + a1, oY + b, oY + b1) * T[IDX(i, a1, j, b1)];
+            for (int i1 = 0; i1 < oX; i1++)                 /* hole ladder */
+            for (int j1 = 0; j1 < oY; j1++)
+                r += G4(i1, i, j1, j) * T[IDX(i1, a, j1, b)];
+            for (int i1 = 0; i1 < oX; i1++)                 /* - v^{b i1}_{b1 i} T^{a b1}_{i1 j} */
+            for (int b1 = 0; b1 < vY; b1++)
+                r -= G4(i1, i, oY + b, oY + b1) * T[IDX(i1, a, j, b1)];
+            for (int a1 = 0; a1 < vX; a1++)                 /* - v^{a j1}_{a1 j} T^{a1 b}_{i j1} */
+            for (int j1 = 0; j1 < oY; j1++)
+                r -= G4(oX + a, oX + a1, j1, j) * T[IDX(i, a1, j1, b)];
+            if (GX)
+                for (int i1 = 0; i1 < oX; i1++)
+                for (int a1 = 0; a1 < vX; a1++)
+                    r += GX[((size_t)i * vX + a) * mX + (size_t)i1 * vX + a1] * T[IDX(i1, a1, j, b)];
+            if (GY)
+                for (int j1 = 0; j1 < oY; j1++)
+                for (int b1 = 0; b1 < vY; b1++)
+                    r += GY[((size_t)j * vY + b) * mY + (size_t)j1 * vY + b1] * T[IDX(i, a, j1, b1)];
+            const double t = r / (epsX[i] + epsY[j] - epsX[oX + a] - epsY[oY + b]);
+            const double dt = fabs(t - T[IDX(i, a, j, b)]);
+            if (dt > dmax) dmax = dt;
+            Tn[IDX(i, a, j, b)] = t;
+        }
+        memcpy(T, Tn, nt * sizeof(double));
+        if (delta) delta[it] = dmax;
+    }
+    {
+        double ej = 0.0, ek = 0.0;
+        for (int i = 0; i < oX; i++)
+        for (int a = 0; a < vX; a++)
+        for (int j = 0; j < oY; j++)
+        for (int b = 0; b < vY; b++) {
+            const double t = T[IDX(i, a, j, b)];
+            ej += 4.0 * v[IDX(i, a, j, b)] * t;
+            ek += -2.0 * W[(((size_t)i * vY + b) * oY + j) * vX + a] * t;
+        }
+        E[0] = ej;
+        E[1] = ek;
+    }
+#undef G4
+#undef IDX
+    rc = 0;
+out:
+    free(g); free(v); free(W); free(S); free(Tn);
+    return rc;
+}
+
 /* One dimer term {E_J, E_K} from the two AO blocks.  Returns 0 on success. */
 int oracle_dimer(const double *A, const double *K,
                  const double *CX, const double *epsX,

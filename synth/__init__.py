@@ -39,6 +39,14 @@ TAG_EPS_VIRT = 3
 TAG_B = 4
 TAG_SIZES = 5
 TAG_R = 6
+TAG_RING = 7
+TAG_UAMP = 8
+# scales of the synthetic monomer doubles matrices of Eq. (td2): the ring
+# matrix 2 v^{i1 a}_{a1 i} - v^{a i1}_{a1 i} (monomer integrals, ~1e-3 at
+# kappa = 0.01) and 2 T^{a a1}_{i i1} - T^{a a1}_{i1 i} (first-order monomer
+# amplitudes, ~v D)
+RING_SCALE = 2e-3
+UAMP_SCALE = 1e-3
 
 _M0, _M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 _W0, _W1 = np.uint64(0x9E3779B9), np.uint64(0xBB67AE85)
@@ -119,6 +127,19 @@ def monomer(X: int, nao: int, nocc: int, seed: int = SEED) -> Monomer:
     eo = np.sort(-1.5 + uniforms(seed, X, 0, TAG_EPS_OCC, nocc))
     ev = np.sort(0.2 + 2.8 * uniforms(seed, X, 0, TAG_EPS_VIRT, nao - nocc))
     return Monomer(np.ascontiguousarray(q), np.concatenate([eo, ev]), nocc)
+
+
+def monomer_doubles(X: int, nao: int, nocc: int, seed: int = SEED):
+    """Synthetic stand-ins for monomer X's quantities in Eq. (td2): the ring
+    matrix G and the amplitude matrix U, each (o v) x (o v) (index i v + a),
+    symmetric like the quantities they stand for: scale (R + R^T) / sqrt(2),
+    R of N(0,1) draws of stream (X, 0, tag)."""
+    m = nocc * (nao - nocc)
+    out = []
+    for tag, scale in ((TAG_RING, RING_SCALE), (TAG_UAMP, UAMP_SCALE)):
+        r = normals(seed, X, 0, tag, m * m).reshape(m, m)
+        out.append(scale * (r + r.T) / math.sqrt(2.0))
+    return out[0], out[1]
 
 
 # ------------------------------------------------------------------ dimers

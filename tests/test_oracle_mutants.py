@@ -38,6 +38,16 @@ MUTANTS = {
                                                 "s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tY[c * oY + k];"),
     "singles Y side takes its own amplitudes": ("s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tX[i * vX + a];",
                                                 "s += V[(((size_t)i * vX + a) * oY + k) * vY + c] * tY[k * vY + c];"),
+    "td2 particle ladder dropped": ("r += G4(oX + a, oX + a1, oY + b, oY + b1) * T[IDX(i, a1, j, b1)];",
+                                    "r += 0.0 * T[IDX(i, a1, j, b1)];"),
+    "td2 hole ladder indices swapped": ("r += G4(i1, i, j1, j) * T[IDX(i1, a, j1, b)];",
+                                        "r += G4(i, i1, j1, j) * T[IDX(i1, a, j1, b)];"),
+    "td2 mixed term sign": ("r -= G4(i1, i, oY + b, oY + b1) * T[IDX(i1, a, j, b1)];",
+                            "r += G4(i1, i, oY + b, oY + b1) * T[IDX(i1, a, j, b1)];"),
+    "td2 ring matrix transposed": ("r += GX[((size_t)i * vX + a) * mX + (size_t)i1 * vX + a1] * T[IDX(i1, a1, j, b)];",
+                                   "r += GX[((size_t)i1 * vX + a1) * mX + (size_t)i * vX + a] * T[IDX(i1, a1, j, b)];"),
+    "td2 energy-tensor sign": ("const double t = r / (epsX[i] + epsY[j] - epsX[oX + a] - epsY[oY + b]);",
+                               "const double t = -r / (epsX[i] + epsY[j] - epsX[oX + a] - epsY[oY + b]);"),
 }
 
 CHECKS = r'''
@@ -109,6 +119,30 @@ for (n1, n2, o1, o2) in [(6, 8, 1, 5), (7, 6, 2, 3)]:
     r2 = C2[:, :o2].T @ np.einsum("mnls,mn->ls", A1, P1) @ C2[:, o2:]
     check("singles X", np.abs(s1 - r1).max() <= 1e-12 * np.abs(r1).max())
     check("singles Y", np.abs(s2 - r2).max() <= 1e-12 * np.abs(r2).max())
+# Eq. (td2): one step is first order; the converged amplitudes satisfy the printed equation
+n1, n2, o1, o2 = 6, 7, 2, 3
+v1, v2 = n1 - o1, n2 - o2
+A3 = rng.standard_normal((n1, n1, n2, n2)) * 0.03; K3 = rng.standard_normal((n1, n2, n2, n1)) * 0.03
+C1 = np.linalg.qr(rng.standard_normal((n1, n1)))[0]; C2 = np.linalg.qr(rng.standard_normal((n2, n2)))[0]
+e1 = np.concatenate([np.sort(rng.uniform(-1.5, -0.5, o1)), np.sort(rng.uniform(0.2, 3.0, v1))])
+e2 = np.concatenate([np.sort(rng.uniform(-1.5, -0.5, o2)), np.sort(rng.uniform(0.2, 3.0, v2))])
+m1, m2 = o1 * v1, o2 * v2
+GX = rng.standard_normal((m1, m1)) * 0.02; GY = rng.standard_normal((m2, m2)) * 0.02
+UX = rng.standard_normal((m1, m1)) * 0.02; UY = rng.standard_normal((m2, m2)) * 0.02
+_, Ea, _ = oracle.td2(A3, K3, C1, e1, C2, e2, o1, o2, 1)
+Eb = oracle.dimer(A3, K3, C1, e1, C2, e2, o1, o2)
+check("td2 one step", abs(Ea[0] - Eb[0]) <= 1e-13 * abs(Eb[0]))
+T3, E3, _ = oracle.td2(A3, K3, C1, e1, C2, e2, o1, o2, 80, GX, GY, UX, UY)
+def mo(sl):
+    return np.einsum("mnls,mp,nq,lr,st->pqrt", A3, C1[:, sl[0]], C1[:, sl[1]], C2[:, sl[2]], C2[:, sl[3]])
+ox, vx, oy, vy = slice(0, o1), slice(o1, n1), slice(0, o2), slice(o2, n2)
+v3 = mo((ox, vx, oy, vy))
+L3 = (np.einsum("aAbB,iAjB->iajb", mo((vx, vx, vy, vy)), T3) + np.einsum("IiJj,IaJb->iajb", mo((ox, ox, oy, oy)), T3)
+      - np.einsum("IibB,IajB->iajb", mo((ox, ox, vy, vy)), T3) - np.einsum("aAJj,iAJb->iajb", mo((vx, vx, oy, oy)), T3)
+      + (GX @ T3.reshape(m1, m2)).reshape(T3.shape) + (T3.reshape(m1, m2) @ GY.T).reshape(T3.shape)
+      + (UX @ v3.reshape(m1, m2) + v3.reshape(m1, m2) @ UY.T).reshape(T3.shape))
+ee = e1[:o1, None, None, None] + e2[None, None, :o2, None] - e1[None, o1:, None, None] - e2[None, None, None, o2:]
+check("td2 residual", np.abs(ee * T3 - v3 - L3).max() <= 1e-11 * np.abs(v3).max())
 print("FAILS:" + ",".join(fails))
 '''
 
