@@ -39,10 +39,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=192, help="dimers in the oracle's timed sample")
     p.add_argument("--no-extras", action="store_true",
-                   help="report none of the extras (coupling, FP64 form, e2e, CPU baseline)")
-    p.add_argument("--extras", default="coupling,fp64,e2e,cpu",
+                   help="report none of the extras (coupling, td2, FP64 form, e2e, CPU baseline)")
+    p.add_argument("--extras", default="coupling,td2,fp64,e2e,cpu",
                    help="comma-separated extras to report after the headline (default all of "
-                        "coupling,fp64,e2e,cpu)")
+                        "coupling,td2,fp64,e2e,cpu)")
     p.add_argument("--max-dimers", type=int, default=0,
                    help="keep only the first N dimers of the workload (smaller cases for profiling)")
     p.add_argument("--alias-blocks", action="store_true",
@@ -378,6 +378,56 @@ def our_arm(args, ws, rank, local):
             "what": "s_X = sum_Y sum_kc (ia|kc) t_kc(Y) of Eq. (tm1), every monomer; wall clock per "
                     "mcpt_singles call including the amplitude and result copies"}
         cc.close()
+
+    # ---- the dimer doubles iteration of Eq. (td2) on the same inputs, with
+    # synthetic monomer matrices: 10 Jacobi steps in this form's arithmetic
+    # and in FP64; two sampled dimers against the oracle
+    if rank == 0 and "td2" in extras:
+        import oracle
+        oracle.build()
+        md = {X: synth.monomer_doubles(X, w.nao[X], w.nocc[X]) for X in range(w.n_monomers)}
+        nit = 10
+        td = {}
+        samp = [0, w.n_dimers - 1]
+        refs = []
+        for d in samp:
+            X, Y = w.pairs[d]
+            n4 = 2 * w.nao[X] ** 2 * w.nao[Y] ** 2
+            blk = buf[offs[d]:offs[d] + n4].cpu().numpy()
+            A = blk[:n4 // 2].reshape(w.nao[X], w.nao[X], w.nao[Y], w.nao[Y])
+            K = blk[n4 // 2:].reshape(w.nao[X], w.nao[Y], w.nao[Y], w.nao[X])
+            refs.append(oracle.td2(A, K, mons[X].C, mons[X].eps, mons[Y].C, mons[Y].eps, mons[X].nocc,
+                                   mons[Y].nocc, nit, md[X][0], md[Y][0], md[X][1], md[Y][1])[1])
+        flops = 0.0
+        for X, Y in w.pairs:
+            nX, nY, oX, oY = w.nao[X], w.nao[Y], w.nocc[X], w.nocc[Y]
+            vX, vY = nX - oX, nY - oY
+            mX, mY = oX * vX, oY * vY
+            flops += 2 * (2 * nX ** 2 * nY ** 3 + 2 * nX ** 3 * nY ** 2)          # MO transformation of A
+            flops += 2 * (nX * nY * nY * vX * nX + vX * nX * nY * oY * nY + oY * vX * nX * vY * nY
+                          + vY * oY * vX * oX * nX)                               # (ib|ja) from K
+            flops += 2 * mX * mY * (mX + mY)                                      # monomer-amplitude source
+            flops += nit * 2 * (vX * vY * oX * oY * vX * vY + oX * oY * vX * vY * oX * oY
+                                + mX * mY * (oX * vY + vX * oY) + mX * mY * (mX + mY))  # ladders, mixed, ring
+        for prec in ([args.precision, "fp64"] if args.precision != "fp64" else ["fp64"]):
+            tctx = make_ctx(prec, False)
+            for X in range(w.n_monomers):
+                tctx.set_monomer_doubles(X, *md[X])
+            tctx.td2(1)                          # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            got, dl = tctx.td2(nit)
+            dt = time.perf_counter() - t0
+            tctx.close()
+            err = max(abs(got[d, 0] - r[0]) / abs(r[0]) for d, r in zip(samp, refs))
+            td[prec] = {"s_per_call": dt, "dimers_per_s": w.n_dimers / dt, "tflops": flops / dt / 1e12,
+                        "final_step_max_dT": float(dl[-1]), "sample_max_rel_err_EJ": float(err)}
+        line["td2"] = {"iterations": nit, "alg_gflop": flops / 1e9, "forms": td,
+                       "what": "Eq. (td2) dimer doubles amplitudes by Jacobi steps from zero for every dimer "
+                               "(full MO transformation of the Coulomb block, ladders, mixed Coulomb terms, "
+                               "synthetic monomer ring and amplitude matrices), energies at the final "
+                               "amplitudes; wall clock per mcpt_td2 call; the error is against the FP64 oracle "
+                               "on the first and last dimer"}
 
     # ---- the plain FP64 GPU form on the same resident inputs
     if rank == 0 and "fp64" in extras and args.precision != "fp64":

@@ -221,6 +221,35 @@ mcpt_status mcpt_coupling(mcpt_handle h, int X, double *R);
  *   integrals last changed), ETIMEOUT, ECUDA. */
 mcpt_status mcpt_singles(mcpt_handle h, const double *t, double *s);
 
+/* Monomer X's own quantities in the dimer doubles equation, Eq. (td2),
+ * each (o_X v_X) x (o_X v_X) row-major with index i * v_X + a (host
+ * pointers, copied; NULL = zero, the default):
+ *   G[(i,a)][(i1,a1)] = 2 v^{i1 a}_{a1 i} - v^{a i1}_{a1 i}   (ring matrix)
+ *   U[(i,a)][(i1,a1)] = 2 T^{a a1}_{i i1} - T^{a a1}_{i1 i}   (monomer doubles)
+ * Errors: EINVAL (unknown X, non-finite with validate = 1). */
+mcpt_status mcpt_set_monomer_doubles(mcpt_handle h, int X, const double *G, const double *U);
+
+/* The dimer doubles amplitudes of Eq. (td2) for every registered dimer by
+ * n_iter Jacobi steps from zero,
+ *   T <- D (v + S + L(T)),  D = 1 / (e_i + e_j - e_a - e_b),
+ * with v = (ia|jb), S = sum U_X v + v U_Y^T (the monomer-amplitude terms)
+ * and L(T) the particle ladder (a a1|b b1), the hole ladder (i1 i|j1 j),
+ * -(i1 i|b b1) and -(a a1|j1 j) contractions and the two ring-matrix
+ * terms, all with their printed signs; the energy-tensor term's sign is
+ * read as for the first-order amplitude, so one step gives T = v D and the
+ * first-order terms of mcpt_run.  The integrals come from the dimers'
+ * registered AO blocks (the full MO transformation of the Coulomb block,
+ * the (ib|ja) part of the exchange block), formed on the device.
+ * per_dimer: 2 D doubles {E_J, E_K} at the final amplitudes (E_J = 4 sum v T,
+ *   Eq. (ed2); E_K = -2 sum (ib|ja) T), or NULL.
+ * delta: n_iter doubles, the largest |T_new - T_old| over all dimers at each
+ *   step, or NULL.
+ * Arithmetic: FP64 in the FP64 form, FP32 otherwise (energy sums FP64).
+ * Dimers run in batches under max(options.wave_bytes, 4 GiB) of scratch.
+ * Synchronous.  Errors: EINVAL (n_iter outside [1, 10000]), ESTATE (no
+ * dimers), ENOMEM, ECUDA. */
+mcpt_status mcpt_td2(mcpt_handle h, int n_iter, double *per_dimer, double *delta);
+
 /* Per-phase timing and launch counts of every run since the previous call
  * (timing requires options.timing = 1; CUDA events are recorded on the
  * handle's stream around each phase, and this call waits for the stream).

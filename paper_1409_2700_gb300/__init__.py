@@ -29,7 +29,8 @@ MCPT_UPDATE_ASYNC = 1
 # every symbol include/mcpt.h declares
 EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer",
            "mcpt_set_precision",
-           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_collect_stats", "mcpt_num_monomers",
+           "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_set_monomer_doubles", "mcpt_td2",
+           "mcpt_collect_stats", "mcpt_num_monomers",
            "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
 
 
@@ -75,9 +76,12 @@ def lib():
         L.mcpt_energies.argtypes = [H, P, P, P, P]
         L.mcpt_coupling.argtypes = [H, I, P]
         L.mcpt_singles.argtypes = [H, P, P]
+        L.mcpt_set_monomer_doubles.argtypes = [H, I, P, P]
+        L.mcpt_td2.argtypes = [H, I, P, P]
         L.mcpt_collect_stats.argtypes = [H, ctypes.POINTER(mcpt_run_stats)]
         for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer", "mcpt_set_precision", "mcpt_run",
-                  "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_collect_stats"):
+                  "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_set_monomer_doubles",
+                  "mcpt_td2", "mcpt_collect_stats"):
             getattr(L, f).restype = I
         L.mcpt_num_monomers.argtypes = [H]
         L.mcpt_num_monomers.restype = I
@@ -180,6 +184,20 @@ def mcpt_singles(h, t: np.ndarray) -> np.ndarray:
     return s
 
 
+def mcpt_set_monomer_doubles(h, X: int, G, U) -> None:
+    G = None if G is None else np.ascontiguousarray(G, dtype=np.float64)
+    U = None if U is None else np.ascontiguousarray(U, dtype=np.float64)
+    _check(h, lib().mcpt_set_monomer_doubles(h, X, None if G is None else _ptr(G), None if U is None else _ptr(U)))
+
+
+def mcpt_td2(h, n_iter: int):
+    """(per_dimer [D, 2] {E_J, E_K}, delta [n_iter])."""
+    D = lib().mcpt_num_dimers(h)
+    pd, dl = np.empty((D, 2)), np.empty(n_iter)
+    _check(h, lib().mcpt_td2(h, n_iter, _ptr(pd), _ptr(dl)))
+    return pd, dl
+
+
 def mcpt_collect_stats(h) -> mcpt_run_stats:
     s = mcpt_run_stats()
     _check(h, lib().mcpt_collect_stats(h, ctypes.byref(s)))
@@ -273,6 +291,15 @@ class Context:
             out.append(flat[off:off + x.size].reshape(x.shape))
             off += x.size
         return out
+
+    def set_monomer_doubles(self, X, G=None, U=None):
+        """Monomer X's ring matrix G and amplitude matrix U of Eq. (td2)."""
+        mcpt_set_monomer_doubles(self.h, X, G, U)
+
+    def td2(self, n_iter):
+        """Eq. (td2) by n_iter Jacobi steps for every dimer: (per-dimer
+        {E_J, E_K} at the final amplitudes, per-step max |dT|)."""
+        return mcpt_td2(self.h, n_iter)
 
     def stats(self):
         """Timing and launch counts of the runs since the previous call."""

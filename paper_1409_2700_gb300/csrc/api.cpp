@@ -66,6 +66,15 @@ struct mcpt_ctx {
     size_t mem_used = 0;
 
     std::vector<MonomerRec> mons;
+    std::vector<std::vector<double>> monG, monU;   // Eq. (td2) monomer matrices (empty: zero)
+    void* dTd2 = nullptr;            // Eq. (td2): batch arena, tables, monomer matrices, outputs
+    size_t capTd2 = 0;
+    void* dTd2Tab = nullptr;
+    size_t capTd2Tab = 0;
+    void* dTd2Mon = nullptr;
+    size_t capTd2Mon = 0;
+    void* dTd2Out = nullptr;
+    size_t capTd2Out = 0;
     std::vector<double> hC, hE;
     double* dC = nullptr;
     float* dCf = nullptr;            // FP32 copy of the coefficient pool (mixed forms)
@@ -1276,6 +1285,255 @@ mcpt_status mcpt_singles(mcpt_handle h, const double* t, double* s)
     return MCPT_OK;
 }
 
+mcpt_status mcpt_set_monomer_doubles(mcpt_handle h, int X, const double* G, const double* U)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_set_monomer_doubles: NULL handle");
+    if (X < 0 || X >= (int)h->mons.size())
+        return fail(h, MCPT_EINVAL, "mcpt_set_monomer_doubles: unknown monomer %d of %zu", X, h->mons.size());
+    const size_t m = (size_t)h->mons[X].nocc * (h->mons[X].nao - h->mons[X].nocc);
+    if (h->validate && ((G && !all_finite(G, m * m)) || (U && !all_finite(U, m * m))))
+        return fail(h, MCPT_EINVAL, "mcpt_set_monomer_doubles: non-finite value");
+    h->monG.resize(h->mons.size());
+    h->monU.resize(h->mons.size());
+    h->monG[X] = G ? std::vector<double>(G, G + m * m) : std::vector<double>();
+    h->monU[X] = U ? std::vector<double>(U, U + m * m) : std::vector<double>();
+    return MCPT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+struct Td2Tables {
+    std::vector<Td2Dim> dims;
+    std::vector<long long> goff;
+    std::vector<QStep<double, T>> q1[2];        // first steps (FP64 AO input) of K and A
+    std::vector<QStep<T, T>> q[2][3];          // steps 2-4 of K and A
+    std::vector<PGemm<T>> pg[8];               // source X, source Y, terms L1..L6
+    int maxM[2][4] = {{0}}, maxN[2][4] = {{0}}, maxR[8] = {0}, maxC[8] = {0};
+    int maxE = 0;
+};
+
+inline PAxis ax(int n1, long long s0, long long s1) { return PAxis{n1 > 0 ? n1 : 1, s0, s1}; }
+
+template <typename T>
+mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
+{
+    const int N = (int)h->mons.size(), D = (int)h->dims.size();
+    mcpt_status st = upload_static(h);
+    if (st) return st;
+    // monomer matrices in the arithmetic type, G then U per monomer that has them
+    h->monG.resize(N);
+    h->monU.resize(N);
+    std::vector<long long> gOff(N, -1), uOff(N, -1);
+    std::vector<T> pool;
+    for (int m = 0; m < N; m++) {
+        if (!h->monG[m].empty()) { gOff[m] = (long long)pool.size(); pool.insert(pool.end(), h->monG[m].begin(), h->monG[m].end()); }
+        if (!h->monU[m].empty()) { uOff[m] = (long long)pool.size(); pool.insert(pool.end(), h->monU[m].begin(), h->monU[m].end()); }
+    }
+    const T* dMon = nullptr;
+    if (!pool.empty()) {
+        if ((st = ensure(h, &h->dTd2Mon, &h->capTd2Mon, pool.size() * sizeof(T)))) return st;
+        CK(h, cudaMemcpyAsync(h->dTd2Mon, pool.data(), pool.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+        dMon = static_cast<const T*>(h->dTd2Mon);
+    }
+    // outputs: 2 D energies, then n_iter 8-byte slots of max |dT| bits
+    const size_t outBytes = (2 * (size_t)D + (size_t)n_iter) * sizeof(double);
+    if ((st = ensure(h, &h->dTd2Out, &h->capTd2Out, outBytes))) return st;
+    double* dE = static_cast<double*>(h->dTd2Out);
+    unsigned long long* dDelta = reinterpret_cast<unsigned long long*>(dE + 2 * (size_t)D);
+    CK(h, cudaMemsetAsync(dDelta, 0, (size_t)n_iter * sizeof(unsigned long long), h->stream));
+    const size_t budget = std::max(h->wave_bytes, (size_t)4 << 30);
+    auto round64 = [](long long x) { return (x + 63) / 64 * 64; };
+    int b0 = 0;
+    while (b0 < D) {
+        // ---- the batch: consecutive dimers under the budget
+        long long tot[8] = {0};            // sections: g, s0, s1, V, W, R0, R, Tc
+        int b1 = b0;
+        while (b1 < D && b1 - b0 < 65535) {
+            const MonomerRec& mX = h->mons[h->dims[b1].X];
+            const MonomerRec& mY = h->mons[h->dims[b1].Y];
+            const long long big = round64((long long)mX.nao * mX.nao * mY.nao * mY.nao);
+            const long long sm = round64((long long)mX.nocc * (mX.nao - mX.nocc) * mY.nocc * (mY.nao - mY.nocc));
+            const long long need = (3 * big + 5 * sm) * (long long)sizeof(T);
+            long long cur = 0;
+            for (int k = 0; k < 8; k++) cur += tot[k];
+            if (b1 > b0 && (size_t)(cur * (long long)sizeof(T) + need) > budget) break;
+            for (int k = 0; k < 3; k++) tot[k] += big;
+            for (int k = 3; k < 8; k++) tot[k] += sm;
+            b1++;
+        }
+        const int nb = b1 - b0;
+        long long sec[8], acc = 0;
+        for (int k = 0; k < 8; k++) { sec[k] = acc; acc += tot[k]; }
+        if ((st = ensure(h, &h->dTd2, &h->capTd2, (size_t)acc * sizeof(T)))) return st;
+        T* arena = static_cast<T*>(h->dTd2);
+        // ---- tables
+        Td2Tables<T> tb;
+        long long run[8];
+        for (int k = 0; k < 8; k++) run[k] = sec[k];
+        for (int d = b0; d < b1; d++) {
+            const DimerRec& r = h->dims[d];
+            const MonomerRec& mX = h->mons[r.X];
+            const MonomerRec& mY = h->mons[r.Y];
+            const int nX = mX.nao, nY = mY.nao, oX = mX.nocc, oY = mY.nocc, vX = nX - oX, vY = nY - oY;
+            const long long mXl = (long long)oX * vX, mYl = (long long)oY * vY;
+            const long long big = round64((long long)nX * nX * nY * nY), sm = round64(mXl * mYl);
+            const long long g = run[0], s0 = run[1], s1 = run[2];
+            Td2Dim td{nX, nY, oX, oY, mX.offE, mY.offE, run[3], run[4], run[5], run[6], run[7]};
+            for (int k = 0; k < 3; k++) run[k] += big;
+            for (int k = 3; k < 8; k++) run[k] += sm;
+            tb.dims.push_back(td);
+            tb.goff.push_back(g);
+            const double* CX = h->dC + mX.offC;
+            const double* CY = h->dC + mY.offC;
+            // K[mu][lam][sig][nu]: nu -> a, sig -> j, lam -> b, mu -> i  => W[i][b][j][a]
+            tb.q1[0].push_back(QStep<double, T>{r.E[1], r.st[1][0], r.st[1][1], r.st[1][2], nY, nY, CX, nX, oX,
+                                                nX * nY * nY, vX, nX, arena + s0});
+            tb.q[0][0].push_back(QStep<T, T>{arena + s0, nY, 0, 0, 1, 1, CY, nY, 0, vX * nX * nY, oY, nY, arena + s1});
+            tb.q[0][1].push_back(QStep<T, T>{arena + s1, nY, 0, 0, 1, 1, CY, nY, oY, oY * vX * nX, vY, nY, arena + s0});
+            tb.q[0][2].push_back(QStep<T, T>{arena + s0, nX, 0, 0, 1, 1, CX, nX, 0, vY * oY * vX, oX, nX, arena + td.W});
+            // A[mu][nu][lam][sig]: sig, lam, nu, mu -> all MOs  => g[p][q][r][s]
+            tb.q1[1].push_back(QStep<double, T>{r.E[0], r.st[0][0], r.st[0][1], r.st[0][2], nX, nY, CY, nY, 0,
+                                                nX * nX * nY, nY, nY, arena + s0});
+            tb.q[1][0].push_back(QStep<T, T>{arena + s0, nY, 0, 0, 1, 1, CY, nY, 0, nY * nX * nX, nY, nY, arena + s1});
+            tb.q[1][1].push_back(QStep<T, T>{arena + s1, nX, 0, 0, 1, 1, CX, nX, 0, nY * nY * nX, nX, nX, arena + s0});
+            tb.q[1][2].push_back(QStep<T, T>{arena + s0, nX, 0, 0, 1, 1, CX, nX, 0, nX * nY * nY, nX, nX, arena + g});
+            const int Mk[4] = {nX * nY * nY, vX * nX * nY, oY * vX * nX, vY * oY * vX};
+            const int Nk[4] = {vX, oY, vY, oX};
+            const int Ma[4] = {nX * nX * nY, nY * nX * nX, nY * nY * nX, nX * nY * nY};
+            const int Na[4] = {nY, nY, nX, nX};
+            for (int k = 0; k < 4; k++) {
+                tb.maxM[0][k] = std::max(tb.maxM[0][k], Mk[k]);
+                tb.maxN[0][k] = std::max(tb.maxN[0][k], Nk[k]);
+                tb.maxM[1][k] = std::max(tb.maxM[1][k], Ma[k]);
+                tb.maxN[1][k] = std::max(tb.maxN[1][k], Na[k]);
+            }
+            tb.maxE = std::max(tb.maxE, (int)(mXl * mYl));
+            // strides: amplitudes [i][a][j][b], g [p][q][r][s]
+            const long long si = vX * mYl, sa = mYl, sj = vY, sb = 1;
+            const long long sp = (long long)nX * nY * nY, sq = (long long)nY * nY, sr = nY, ss = 1;
+            T* Gb = arena + g;
+            T* Tc = arena + td.Tc;
+            T* R = arena + td.R;
+            T* R0 = arena + td.R0;
+            T* V = arena + td.V;
+            const int iX = (int)mXl, iY = (int)mYl;
+            PGemm<T> none{};
+            none.wr = none.wk = none.zk = none.zc = none.orow = none.ocol = ax(1, 0, 0);
+            // sources: U_X V and V U_Y^T into R0
+            PGemm<T> sx = none, sy = none;
+            if (uOff[r.X] >= 0)
+                sx = PGemm<T>{dMon + uOff[r.X], ax(iX, 0, iX), ax(iX, 0, 1), V, ax(iX, 0, iY), ax(iY, 0, 1),
+                              R0, ax(iX, 0, iY), ax(iY, 0, 1), iX, iY, iX, T(1)};
+            if (uOff[r.Y] >= 0)
+                sy = PGemm<T>{dMon + uOff[r.Y], ax(iY, 0, iY), ax(iY, 0, 1), V, ax(iY, 0, 1), ax(iX, 0, iY),
+                              R0, ax(iY, 0, 1), ax(iX, 0, iY), iY, iX, iY, T(1)};
+            // L1 particle ladder: R[(a,b)][(i,j)] += g[oX+a][oX+a1][oY+b][oY+b1] T[(a1,b1)][(i,j)]
+            PGemm<T> l1{Gb + oX * sp + oX * sq + oY * sr + oY * ss, ax(vY, sp, sr), ax(vY, sq, ss),
+                        Tc, ax(vY, sa, sb), ax(oY, si, sj), R, ax(vY, sa, sb), ax(oY, si, sj),
+                        vX * vY, oX * oY, vX * vY, T(1)};
+            // L2 hole ladder: R[(i,j)][(a,b)] += g[i1][i][j1][j] T[(i1,j1)][(a,b)]
+            PGemm<T> l2{Gb, ax(oY, sq, ss), ax(oY, sp, sr), Tc, ax(oY, si, sj), ax(vY, sa, sb),
+                        R, ax(oY, si, sj), ax(vY, sa, sb), oX * oY, vX * vY, oX * oY, T(1)};
+            // L3: R[(i,b)][(a,j)] -= g[i1][i][oY+b][oY+b1] T[(i1,b1)][(a,j)]
+            PGemm<T> l3{Gb + oY * sr + oY * ss, ax(vY, sq, sr), ax(vY, sp, ss), Tc, ax(vY, si, sb), ax(oY, sa, sj),
+                        R, ax(vY, si, sb), ax(oY, sa, sj), oX * vY, vX * oY, oX * vY, T(-1)};
+            // L4: R[(a,j)][(i,b)] -= g[oX+a][oX+a1][j1][j] T[(a1,j1)][(i,b)]
+            PGemm<T> l4{Gb + oX * sp + oX * sq, ax(oY, sp, ss), ax(oY, sq, sr), Tc, ax(oY, sa, sj), ax(vY, si, sb),
+                        R, ax(oY, sa, sj), ax(vY, si, sb), vX * oY, oX * vY, vX * oY, T(-1)};
+            // L5, L6: monomer ring matrices
+            PGemm<T> l5 = none, l6 = none;
+            if (gOff[r.X] >= 0)
+                l5 = PGemm<T>{dMon + gOff[r.X], ax(iX, 0, iX), ax(iX, 0, 1), Tc, ax(iX, 0, iY), ax(iY, 0, 1),
+                              R, ax(iX, 0, iY), ax(iY, 0, 1), iX, iY, iX, T(1)};
+            if (gOff[r.Y] >= 0)
+                l6 = PGemm<T>{dMon + gOff[r.Y], ax(iY, 0, iY), ax(iY, 0, 1), Tc, ax(iY, 0, 1), ax(iX, 0, iY),
+                              R, ax(iY, 0, 1), ax(iX, 0, iY), iY, iX, iY, T(1)};
+            const PGemm<T> all[8] = {sx, sy, l1, l2, l3, l4, l5, l6};
+            for (int k = 0; k < 8; k++) {
+                tb.pg[k].push_back(all[k]);
+                tb.maxR[k] = std::max(tb.maxR[k], all[k].R);
+                tb.maxC[k] = std::max(tb.maxC[k], all[k].C);
+            }
+        }
+        // ---- upload the tables (one buffer, 16-byte aligned pieces)
+        std::vector<unsigned char> tab;
+        auto put = [&](const void* src, size_t bytes) {
+            tab.resize((tab.size() + 15) & ~(size_t)15);
+            const size_t off = tab.size();
+            tab.resize(off + bytes);
+            std::memcpy(tab.data() + off, src, bytes);
+            return off;
+        };
+        const size_t oDims = put(tb.dims.data(), nb * sizeof(Td2Dim));
+        const size_t oG = put(tb.goff.data(), nb * sizeof(long long));
+        size_t oQ1[2], oQ[2][3], oP[8];
+        for (int f = 0; f < 2; f++) {
+            oQ1[f] = put(tb.q1[f].data(), nb * sizeof(QStep<double, T>));
+            for (int k = 0; k < 3; k++) oQ[f][k] = put(tb.q[f][k].data(), nb * sizeof(QStep<T, T>));
+        }
+        for (int k = 0; k < 8; k++) oP[k] = put(tb.pg[k].data(), nb * sizeof(PGemm<T>));
+        if ((st = ensure(h, &h->dTd2Tab, &h->capTd2Tab, tab.size()))) return st;
+        CK(h, cudaMemcpyAsync(h->dTd2Tab, tab.data(), tab.size(), cudaMemcpyHostToDevice, h->stream));
+        const unsigned char* tbase = static_cast<const unsigned char*>(h->dTd2Tab);
+        auto at = [&](size_t off) { return static_cast<const void*>(tbase + off); };
+        const Td2Dim* dDims = static_cast<const Td2Dim*>(at(oDims));
+        // ---- transformations: K (W), then A (g)
+        for (int f = 0; f < 2; f++) {
+            CK(h, launch_qstep(static_cast<const QStep<double, T>*>(at(oQ1[f])), nb, tb.maxM[f][0], tb.maxN[f][0],
+                               h->stream));
+            for (int k = 0; k < 3; k++)
+                CK(h, launch_qstep(static_cast<const QStep<T, T>*>(at(oQ[f][k])), nb, tb.maxM[f][k + 1],
+                                   tb.maxN[f][k + 1], h->stream));
+        }
+        CK(h, launch_td2_init<T>(dDims, static_cast<const long long*>(at(oG)), nb, tb.maxE, arena, h->stream));
+        for (int k = 0; k < 2; k++)
+            CK(h, launch_pgemm(static_cast<const PGemm<T>*>(at(oP[k])), nb, tb.maxR[k], tb.maxC[k], h->stream));
+        // ---- Jacobi steps
+        for (int it = 0; it < n_iter; it++) {
+            CK(h, cudaMemcpyAsync(arena + sec[6], arena + sec[5], (size_t)tot[5] * sizeof(T),
+                                  cudaMemcpyDeviceToDevice, h->stream));
+            for (int k = 2; k < 8; k++)
+                CK(h, launch_pgemm(static_cast<const PGemm<T>*>(at(oP[k])), nb, tb.maxR[k], tb.maxC[k], h->stream));
+            CK(h, launch_td2_update<T>(dDims, nb, tb.maxE, h->dE, arena, dDelta + it, h->stream));
+        }
+        CK(h, launch_td2_energy<T>(dDims, nb, arena, dE + 2 * (size_t)b0, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));        // the tables are reused by the next batch
+        b0 = b1;
+    }
+    std::vector<unsigned long long> bits(n_iter);
+    if (per_dimer) CK(h, cudaMemcpy(per_dimer, dE, 2 * (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(bits.data(), dDelta, (size_t)n_iter * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    if (delta)
+        for (int it = 0; it < n_iter; it++) {
+            if (sizeof(T) == 4) {
+                const unsigned int u = (unsigned int)(bits[it] & 0xffffffffu);
+                float f;
+                std::memcpy(&f, &u, sizeof f);
+                delta[it] = f;
+            } else {
+                std::memcpy(&delta[it], &bits[it], sizeof(double));
+            }
+        }
+    return MCPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcpt_status mcpt_td2(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_td2: NULL handle");
+    if (n_iter < 1 || n_iter > 10000) return fail(h, MCPT_EINVAL, "mcpt_td2: n_iter=%d outside [1, 10000]", n_iter);
+    if (h->dims.empty()) return fail(h, MCPT_ESTATE, "mcpt_td2: no dimers registered");
+    CK(h, cudaSetDevice(h->device));
+    return h->prec == MCPT_FP64 ? td2_run<double>(h, n_iter, per_dimer, delta)
+                                : td2_run<float>(h, n_iter, per_dimer, delta);
+}
+
 mcpt_status mcpt_collect_stats(mcpt_handle h, mcpt_run_stats* out)
 {
     if (!h || !out) return fail(h, MCPT_EINVAL, "mcpt_collect_stats: NULL argument");
@@ -1334,6 +1592,10 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dCoup);
     cudaFree(h->dR);
     cudaFree(h->dS1);
+    cudaFree(h->dTd2);
+    cudaFree(h->dTd2Tab);
+    cudaFree(h->dTd2Mon);
+    cudaFree(h->dTd2Out);
     for (int b = 0; b < 2; b++) {
         cudaFree(h->dPack[b]);
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);

@@ -137,6 +137,66 @@ cudaError_t launch_singles_fp64(const SingTile* tiles, int ntiles, const CoupDim
                                 const int* mdim, const long long* s_off, const long long* part_off, const double* VT,
                                 const double* t, double* part, double* s, cudaStream_t st);
 
+// ---- dimer doubles iteration of Eq. (td2) ----
+// One quarter step of a four-index transformation, per dimer of a batch:
+//   Out[n][m] = sum_k C[k][c0 + n] In(m, k),  n < N, m < M, k < K,
+// In(m, k) = in[(m / (d1 d2)) st0 + ((m / d2) % d1) st1 + (m % d2) st2 + k]
+// (the contracted index is the innermost, stride 1); Out is [N][M]
+// contiguous, so the new index comes first and four steps return the
+// original index order.  ldc: row length of C.
+template <typename TI, typename TO>
+struct QStep {
+    const TI* in;
+    long long st0, st1, st2;
+    int d1, d2;
+    const double* C;
+    int ldc, c0;
+    int M, N, K;
+    TO* out;
+};
+// A pair-indexed contraction, per dimer of a batch:
+//   Out(r, c) += alpha sum_k W(r, k) Z(k, c),  r < R, c < C, k < K,
+// each operand addressed by separable two-index axes: an index x of an axis
+// {n1, s0, s1} sits at (x / n1) s0 + (x % n1) s1.
+struct PAxis {
+    int n1;
+    long long s0, s1;
+};
+template <typename T>
+struct PGemm {
+    const T* W;
+    PAxis wr, wk;
+    const T* Z;
+    PAxis zk, zc;
+    T* out;
+    PAxis orow, ocol;
+    int R, C, K;
+    T alpha;
+};
+// Per-dimer state of the iteration (element offsets into the batch arena of
+// type T; [i][a][j][b] order for V, R0, R and the amplitudes Tc; [i][b][j][a] for W).
+struct Td2Dim {
+    int nX, nY, oX, oY;
+    int eX, eY;                       // offsets of the monomers' orbital energies
+    long long V, W, R0, R, Tc;
+};
+template <typename TI, typename TO>
+cudaError_t launch_qstep(const QStep<TI, TO>* steps, int nd, int max_m, int max_n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pgemm(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s);
+// V, R0 <- (ia|jb) gathered from the full MO block g (per dimer at g_off[d]:
+// [p][q][r][s] over all MOs); Tc <- 0.
+template <typename T>
+cudaError_t launch_td2_init(const Td2Dim* dims, const long long* g_off, int nd, int max_m, T* arena, cudaStream_t s);
+// Tc <- R / (e_i + e_j - e_a - e_b); delta_bits <- max |Tc_new - Tc_old|
+// (the bits of a non-negative T, compared as unsigned integers).
+template <typename T>
+cudaError_t launch_td2_update(const Td2Dim* dims, int nd, int max_m, const double* eps, T* arena,
+                              void* delta_bits, cudaStream_t s);
+// E[2d] = 4 sum V Tc, E[2d+1] = -2 sum W Tc, FP64, fixed order (one CTA per dimer).
+template <typename T>
+cudaError_t launch_td2_energy(const Td2Dim* dims, int nd, const T* arena, double* E, cudaStream_t s);
+
 // Split dimers: E2[dimer] = sum, in block order, of E2[first .. first+n) for
 // each (dimer, first, n) triple of `fold` (device, 3 ints each).
 cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s);
