@@ -1307,12 +1307,12 @@ namespace {
 template <typename T>
 struct Td2Tables {
     std::vector<Td2Dim> dims;
-    std::vector<long long> goff;
+    std::vector<long long> goff, wdoff;
     std::vector<QStep<double, T>> q1[2];        // first steps (FP64 AO input) of K and A
     std::vector<QStep<T, T>> q[2][3];          // steps 2-4 of K and A
     std::vector<PGemm<T>> pg[8];               // source X, source Y, terms L1..L6
     int maxM[2][4] = {{0}}, maxN[2][4] = {{0}}, maxR[8] = {0}, maxC[8] = {0};
-    int maxE = 0;
+    int maxE = 0, maxVV = 0;
 };
 
 inline PAxis ax(int n1, long long s0, long long s1) { return PAxis{n1 > 0 ? n1 : 1, s0, s1}; }
@@ -1349,30 +1349,33 @@ mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
     int b0 = 0;
     while (b0 < D) {
         // ---- the batch: consecutive dimers under the budget
-        long long tot[8] = {0};            // sections: g, s0, s1, V, W, R0, R, Tc
+        long long tot[9] = {0};            // sections: g, s0, s1, V, W, R0, R, Tc, packed ladder
         int b1 = b0;
         while (b1 < D && b1 - b0 < 65535) {
             const MonomerRec& mX = h->mons[h->dims[b1].X];
             const MonomerRec& mY = h->mons[h->dims[b1].Y];
             const long long big = round64((long long)mX.nao * mX.nao * mY.nao * mY.nao);
             const long long sm = round64((long long)mX.nocc * (mX.nao - mX.nocc) * mY.nocc * (mY.nao - mY.nocc));
-            const long long need = (3 * big + 5 * sm) * (long long)sizeof(T);
+            const long long vv = (long long)(mX.nao - mX.nocc) * (mY.nao - mY.nocc);
+            const long long lad = round64(vv * ((vv + 3) / 4 * 4));
+            const long long need = (3 * big + 5 * sm + lad) * (long long)sizeof(T);
             long long cur = 0;
-            for (int k = 0; k < 8; k++) cur += tot[k];
+            for (int k = 0; k < 9; k++) cur += tot[k];
             if (b1 > b0 && (size_t)(cur * (long long)sizeof(T) + need) > budget) break;
             for (int k = 0; k < 3; k++) tot[k] += big;
             for (int k = 3; k < 8; k++) tot[k] += sm;
+            tot[8] += lad;
             b1++;
         }
         const int nb = b1 - b0;
-        long long sec[8], acc = 0;
-        for (int k = 0; k < 8; k++) { sec[k] = acc; acc += tot[k]; }
+        long long sec[9], acc = 0;
+        for (int k = 0; k < 9; k++) { sec[k] = acc; acc += tot[k]; }
         if ((st = ensure(h, &h->dTd2, &h->capTd2, (size_t)acc * sizeof(T)))) return st;
         T* arena = static_cast<T*>(h->dTd2);
         // ---- tables
         Td2Tables<T> tb;
-        long long run[8];
-        for (int k = 0; k < 8; k++) run[k] = sec[k];
+        long long run[9];
+        for (int k = 0; k < 9; k++) run[k] = sec[k];
         for (int d = b0; d < b1; d++) {
             const DimerRec& r = h->dims[d];
             const MonomerRec& mX = h->mons[r.X];
@@ -1380,12 +1383,16 @@ mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
             const int nX = mX.nao, nY = mY.nao, oX = mX.nocc, oY = mY.nocc, vX = nX - oX, vY = nY - oY;
             const long long mXl = (long long)oX * vX, mYl = (long long)oY * vY;
             const long long big = round64((long long)nX * nX * nY * nY), sm = round64(mXl * mYl);
-            const long long g = run[0], s0 = run[1], s1 = run[2];
+            const int vv = vX * vY, ldw = (vv + 3) / 4 * 4;
+            const long long g = run[0], s0 = run[1], s1 = run[2], wd = run[8];
             Td2Dim td{nX, nY, oX, oY, mX.offE, mY.offE, run[3], run[4], run[5], run[6], run[7]};
             for (int k = 0; k < 3; k++) run[k] += big;
             for (int k = 3; k < 8; k++) run[k] += sm;
+            run[8] += round64((long long)vv * ldw);
             tb.dims.push_back(td);
             tb.goff.push_back(g);
+            tb.wdoff.push_back(wd);
+            tb.maxVV = std::max(tb.maxVV, vv);
             const double* CX = h->dC + mX.offC;
             const double* CY = h->dC + mY.offC;
             // K[mu][lam][sig][nu]: nu -> a, sig -> j, lam -> b, mu -> i  => W[i][b][j][a]
@@ -1430,10 +1437,11 @@ mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
             if (uOff[r.Y] >= 0)
                 sy = PGemm<T>{dMon + uOff[r.Y], ax(iY, 0, iY), ax(iY, 0, 1), V, ax(iY, 0, 1), ax(iX, 0, iY),
                               R0, ax(iY, 0, 1), ax(iX, 0, iY), iY, iX, iY, T(1)};
-            // L1 particle ladder: R[(a,b)][(i,j)] += g[oX+a][oX+a1][oY+b][oY+b1] T[(a1,b1)][(i,j)]
-            PGemm<T> l1{Gb + oX * sp + oX * sq + oY * sr + oY * ss, ax(vY, sp, sr), ax(vY, sq, ss),
+            // L1 particle ladder: R[(a,b)][(i,j)] += Wd[(a,b)][(a1,b1)] T[(a1,b1)][(i,j)], Wd the
+            // packed g[oX+a][oX+a1][oY+b][oY+b1] (dense rows of ldw)
+            PGemm<T> l1{arena + wd, ax(vv, 0, ldw), ax(1, 0, 1),
                         Tc, ax(vY, sa, sb), ax(oY, si, sj), R, ax(vY, sa, sb), ax(oY, si, sj),
-                        vX * vY, oX * oY, vX * vY, T(1)};
+                        vv, oX * oY, vv, T(1)};
             // L2 hole ladder: R[(i,j)][(a,b)] += g[i1][i][j1][j] T[(i1,j1)][(a,b)]
             PGemm<T> l2{Gb, ax(oY, sq, ss), ax(oY, sp, sr), Tc, ax(oY, si, sj), ax(vY, sa, sb),
                         R, ax(oY, si, sj), ax(vY, sa, sb), oX * oY, vX * vY, oX * oY, T(1)};
@@ -1469,6 +1477,7 @@ mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
         };
         const size_t oDims = put(tb.dims.data(), nb * sizeof(Td2Dim));
         const size_t oG = put(tb.goff.data(), nb * sizeof(long long));
+        const size_t oWd = put(tb.wdoff.data(), nb * sizeof(long long));
         size_t oQ1[2], oQ[2][3], oP[8];
         for (int f = 0; f < 2; f++) {
             oQ1[f] = put(tb.q1[f].data(), nb * sizeof(QStep<double, T>));
@@ -1489,13 +1498,16 @@ mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
                                    tb.maxN[f][k + 1], h->stream));
         }
         CK(h, launch_td2_init<T>(dDims, static_cast<const long long*>(at(oG)), nb, tb.maxE, arena, h->stream));
+        CK(h, launch_pack_ladder<T>(dDims, static_cast<const long long*>(at(oG)), static_cast<const long long*>(at(oWd)),
+                                    nb, tb.maxVV, arena, h->stream));
         for (int k = 0; k < 2; k++)
             CK(h, launch_pgemm(static_cast<const PGemm<T>*>(at(oP[k])), nb, tb.maxR[k], tb.maxC[k], h->stream));
         // ---- Jacobi steps
         for (int it = 0; it < n_iter; it++) {
             CK(h, cudaMemcpyAsync(arena + sec[6], arena + sec[5], (size_t)tot[5] * sizeof(T),
                                   cudaMemcpyDeviceToDevice, h->stream));
-            for (int k = 2; k < 8; k++)
+            CK(h, launch_pgemm_dw(static_cast<const PGemm<T>*>(at(oP[2])), nb, tb.maxR[2], tb.maxC[2], h->stream));
+            for (int k = 3; k < 8; k++)
                 CK(h, launch_pgemm(static_cast<const PGemm<T>*>(at(oP[k])), nb, tb.maxR[k], tb.maxC[k], h->stream));
             CK(h, launch_td2_update<T>(dDims, nb, tb.maxE, h->dE, arena, dDelta + it, h->stream));
         }

@@ -184,6 +184,15 @@ template <typename TI, typename TO>
 cudaError_t launch_qstep(const QStep<TI, TO>* steps, int nd, int max_m, int max_n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pgemm(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s);
+// The same contraction with W a dense row-major matrix: row r at W + r * ld,
+// ld = wr.s1 a multiple of 4 and the padding zero (wk unused).
+template <typename T>
+cudaError_t launch_pgemm_dw(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s);
+// Wd[(a,b)][(a1,b1)] = g[oX+a][oX+a1][oY+b][oY+b1] per dimer at wd_off[d],
+// rows of ld = round4(vX vY) with zero padding.
+template <typename T>
+cudaError_t launch_pack_ladder(const Td2Dim* dims, const long long* g_off, const long long* wd_off, int nd,
+                               int max_rows, T* arena, cudaStream_t s);
 // V, R0 <- (ia|jb) gathered from the full MO block g (per dimer at g_off[d]:
 // [p][q][r][s] over all MOs); Tc <- 0.
 template <typename T>

@@ -16,6 +16,18 @@
 namespace mcpt {
 namespace {
 
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&x)[4])
+{
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    } else {
+        const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+        x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    }
+}
+
 // ---------------------------------------------------------------- quarter steps
 constexpr int kQM = 64, kQN = 32, kQK = 32, kQThreads = 256;
 
@@ -27,8 +39,15 @@ k_qstep(const QStep<TI, TO>* __restrict__ steps)
     const int m0 = blockIdx.x * kQM, n0 = blockIdx.y * kQN;
     if (m0 >= q.M || n0 >= q.N) return;
     __shared__ TO sIn[kQK][kQM + 1];           // [k][m]
-    __shared__ TO sC[kQK][kQN];                // [k][n]
+    __shared__ __align__(16) TO sC[kQK][kQN];  // [k][n]
+    __shared__ long long rowOff[kQM];          // In(m0 + mm, 0)
     const int tid = threadIdx.x, tm = tid & 31, tn = tid >> 5;   // outputs m = tm + 32 u, n = 4 tn + w
+    if (tid < kQM) {
+        const int m = m0 + tid;
+        rowOff[tid] = m < q.M ? (long long)(m / (q.d1 * q.d2)) * q.st0 + (long long)((m / q.d2) % q.d1) * q.st1 +
+                                    (long long)(m % q.d2) * q.st2
+                              : 0;
+    }
     TO acc[2][4];
 #pragma unroll
     for (int u = 0; u < 2; u++)
@@ -36,15 +55,10 @@ k_qstep(const QStep<TI, TO>* __restrict__ steps)
         for (int w = 0; w < 4; w++) acc[u][w] = TO(0);
     for (int k0 = 0; k0 < q.K; k0 += kQK) {
         const int kn = min(kQK, q.K - k0);
+        __syncthreads();                       // row offsets ready; previous chunk consumed
         for (int e = tid; e < kQM * kQK; e += kQThreads) {
-            const int mm = e / kQK, kk = e % kQK, m = m0 + mm, k = k0 + kk;
-            TO x = TO(0);
-            if (m < q.M && k < q.K) {
-                const long long o = (long long)(m / (q.d1 * q.d2)) * q.st0 + (long long)((m / q.d2) % q.d1) * q.st1 +
-                                    (long long)(m % q.d2) * q.st2 + k;
-                x = (TO)q.in[o];
-            }
-            sIn[kk][mm] = x;
+            const int mm = e / kQK, kk = e % kQK, k = k0 + kk;
+            sIn[kk][mm] = (m0 + mm < q.M && k < q.K) ? (TO)q.in[rowOff[mm] + k] : TO(0);
         }
         for (int e = tid; e < kQK * kQN; e += kQThreads) {
             const int kk = e / kQN, nn = e % kQN, k = k0 + kk, n = n0 + nn;
@@ -53,14 +67,14 @@ k_qstep(const QStep<TI, TO>* __restrict__ steps)
         __syncthreads();
         for (int k = 0; k < kn; k++) {
             const TO a0 = sIn[k][tm], a1 = sIn[k][tm + 32];
+            TO c[4];
+            ld4(&sC[k][4 * tn], c);
 #pragma unroll
             for (int w = 0; w < 4; w++) {
-                const TO c = sC[k][4 * tn + w];
-                acc[0][w] = fma(a0, c, acc[0][w]);
-                acc[1][w] = fma(a1, c, acc[1][w]);
+                acc[0][w] = fma(a0, c[w], acc[0][w]);
+                acc[1][w] = fma(a1, c[w], acc[1][w]);
             }
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int u = 0; u < 2; u++)
@@ -72,60 +86,190 @@ k_qstep(const QStep<TI, TO>* __restrict__ steps)
 }
 
 // ---------------------------------------------------------------- pair contractions
-constexpr int kPT = 32, kPThreads = 256;
+constexpr int kPR = 64, kPC = 32, kPK = 32, kPThreads = 256;
 
 __device__ __forceinline__ long long ax_off(const PAxis& a, int x)
 {
     return (long long)(x / a.n1) * a.s0 + (long long)(x % a.n1) * a.s1;
 }
 
+// 64 x 32 output tile; thread (tr, tc) holds rows 4 tr .. 4 tr + 3 and
+// columns 2 tc, 2 tc + 1: per k six shared loads (the four row values are
+// broadcast within half-warps) feed 8 FMAs.  The staged operands are kept
+// [row][k] with an odd stride, so that the gathers (consecutive threads
+// along k, usually the operand's contiguous index) store without bank
+// conflicts.  Operand offsets are tabulated per tile (rows, columns) and
+// per chunk (k), so the gathers do no division.
 template <typename T>
 __global__ void __launch_bounds__(kPThreads)
 k_pgemm(const PGemm<T>* __restrict__ tabs)
 {
     const PGemm<T> g = tabs[blockIdx.z];
-    const int r0 = blockIdx.x * kPT, c0 = blockIdx.y * kPT;
+    const int r0 = blockIdx.x * kPR, c0 = blockIdx.y * kPC;
     if (r0 >= g.R || c0 >= g.C) return;
-    __shared__ T sW[kPT][kPT + 1];             // [k][r]
-    __shared__ T sZ[kPT][kPT + 1];             // [k][c]
-    __shared__ long long oWr[kPT], oZc[kPT], oOr[kPT], oOc[kPT], oWk[kPT], oZk[kPT];
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;  // outputs r = ty + 8 u, c = tx
-    if (tid < kPT) {
+    __shared__ T sW[kPR][kPK + 1];             // [r][k]
+    __shared__ T sZ[kPC][kPK + 1];             // [c][k]
+    __shared__ long long oWr[kPR], oOr[kPR], oZc[kPC], oOc[kPC], oWk[kPK], oZk[kPK];
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    if (tid < kPR) {
         oWr[tid] = r0 + tid < g.R ? ax_off(g.wr, r0 + tid) : 0;
         oOr[tid] = r0 + tid < g.R ? ax_off(g.orow, r0 + tid) : 0;
-    } else if (tid < 2 * kPT) {
-        const int c = c0 + tid - kPT;
-        oZc[tid - kPT] = c < g.C ? ax_off(g.zc, c) : 0;
-        oOc[tid - kPT] = c < g.C ? ax_off(g.ocol, c) : 0;
+    } else if (tid < kPR + kPC) {
+        const int c = c0 + tid - kPR;
+        oZc[tid - kPR] = c < g.C ? ax_off(g.zc, c) : 0;
+        oOc[tid - kPR] = c < g.C ? ax_off(g.ocol, c) : 0;
     }
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int k0 = 0; k0 < g.K; k0 += kPT) {
-        const int kn = min(kPT, g.K - k0);
+    T acc[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; u++) acc[u][0] = acc[u][1] = T(0);
+    for (int k0 = 0; k0 < g.K; k0 += kPK) {
+        const int kn = min(kPK, g.K - k0);
         __syncthreads();                       // offsets ready; previous chunk consumed
-        if (tid < kPT) oWk[tid] = k0 + tid < g.K ? ax_off(g.wk, k0 + tid) : 0;
-        else if (tid < 2 * kPT) oZk[tid - kPT] = k0 + tid - kPT < g.K ? ax_off(g.zk, k0 + tid - kPT) : 0;
+        if (tid < kPK) oWk[tid] = k0 + tid < g.K ? ax_off(g.wk, k0 + tid) : 0;
+        else if (tid < 2 * kPK) oZk[tid - kPK] = k0 + tid - kPK < g.K ? ax_off(g.zk, k0 + tid - kPK) : 0;
         __syncthreads();
-        for (int e = tid; e < kPT * kPT; e += kPThreads) {
-            const int a = e / kPT, kk = e % kPT;                   // a: row (W) or column (Z) in the tile
-            const bool okk = kk < kn;
-            sW[kk][a] = (okk && r0 + a < g.R) ? g.W[oWr[a] + oWk[kk]] : T(0);
-            sZ[kk][a] = (okk && c0 + a < g.C) ? g.Z[oZk[kk] + oZc[a]] : T(0);
+        for (int e = tid; e < kPR * kPK; e += kPThreads) {
+            const int a = e / kPK, kk = e % kPK;                  // W row a of the tile
+            sW[a][kk] = (kk < kn && r0 + a < g.R) ? g.W[oWr[a] + oWk[kk]] : T(0);
+        }
+        for (int e = tid; e < kPC * kPK; e += kPThreads) {
+            const int a = e / kPK, kk = e % kPK;                  // Z column a of the tile
+            sZ[a][kk] = (kk < kn && c0 + a < g.C) ? g.Z[oZk[kk] + oZc[a]] : T(0);
         }
         __syncthreads();
         for (int k = 0; k < kn; k++) {
-            const T z = sZ[k][tx];
+            T w[4];
 #pragma unroll
-            for (int u = 0; u < 4; u++) acc[u] = fma(sW[k][ty + 8 * u], z, acc[u]);
+            for (int u = 0; u < 4; u++) w[u] = sW[4 * tr + u][k];
+            const T z0 = sZ[2 * tc][k], z1 = sZ[2 * tc + 1][k];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                acc[u][0] = fma(w[u], z0, acc[u][0]);
+                acc[u][1] = fma(w[u], z1, acc[u][1]);
+            }
         }
     }
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
-        const int r = ty + 8 * u, c = tx;
-        if (r0 + r < g.R && c0 + c < g.C) {
-            T* o = g.out + oOr[r] + oOc[c];
-            *o = fma(g.alpha, acc[u], *o);
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int r = 4 * tr + u, c = 2 * tc + v;
+            if (r0 + r < g.R && c0 + c < g.C) {
+                T* o = g.out + oOr[r] + oOc[c];
+                *o = fma(g.alpha, acc[u][v], *o);
+            }
+        }
+}
+
+// The particle ladder with its integrals packed once per dimer into a dense
+// row-major matrix Wd[(a,b)][(a1,b1)] (row length ld, a multiple of 4, the
+// padding zero), which is constant over the steps: 64 x 32 output tiles as
+// above, the W rows streamed by 16-byte cp.async into two buffers (the next
+// chunk in flight while the current one is summed), the amplitudes gathered
+// through their offset tables.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_pack_ladder(const Td2Dim* __restrict__ dims, const long long* __restrict__ g_off,
+              const long long* __restrict__ wd_off, T* __restrict__ arena)
+{
+    const Td2Dim d = dims[blockIdx.y];
+    const int vX = d.nX - d.oX, vY = d.nY - d.oY, n = vX * vY, ld = (n + 3) / 4 * 4;
+    const int row = blockIdx.x;                // (a, b)
+    if (row >= n) return;
+    const int a = row / vY, b = row % vY;
+    const T* g = arena + g_off[blockIdx.y];
+    T* w = arena + wd_off[blockIdx.y] + (long long)row * ld;
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+        T x = T(0);
+        if (k < n) {
+            const int a1 = k / vY, b1 = k % vY;
+            x = g[(((long long)(d.oX + a) * d.nX + d.oX + a1) * d.nY + d.oY + b) * d.nY + d.oY + b1];
+        }
+        w[k] = x;
+    }
+}
+
+constexpr int kLS = kPK + 4;                   // staged W row stride (16-byte aligned rows)
+
+template <typename T>
+__device__ __forceinline__ void stage_w(T (*sW)[kLS], const T* __restrict__ W, int ld, int R, int r0, int k0,
+                                        int tid)
+{
+    constexpr int kV = 16 / sizeof(T);         // elements per 16-byte copy
+    constexpr int kG = kPK / kV;               // copies per row and chunk
+    for (int e = tid; e < kPR * kG; e += kPThreads) {
+        const int r = e / kG, c = (e % kG) * kV, k = k0 + c;
+        const bool ok = r0 + r < R && k < ld;
+        const T* src = ok ? W + (long long)(r0 + r) * ld + k : W;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(&sW[r][c])),
+                     "l"(src), "r"(ok ? 16 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPThreads)
+k_pgemm_dw(const PGemm<T>* __restrict__ tabs)
+{
+    const PGemm<T> g = tabs[blockIdx.z];
+    const int r0 = blockIdx.x * kPR, c0 = blockIdx.y * kPC;
+    if (r0 >= g.R || c0 >= g.C) return;
+    const int ld = (int)g.wr.s1;               // dense W: row r at r * ld
+    __shared__ __align__(16) T sW[2][kPR][kLS];
+    __shared__ T sZ[kPC][kPK + 1];
+    __shared__ long long oOr[kPR], oZc[kPC], oOc[kPC], oZk[kPK];
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    if (tid < kPR) {
+        oOr[tid] = r0 + tid < g.R ? ax_off(g.orow, r0 + tid) : 0;
+    } else if (tid < kPR + kPC) {
+        const int c = c0 + tid - kPR;
+        oZc[tid - kPR] = c < g.C ? ax_off(g.zc, c) : 0;
+        oOc[tid - kPR] = c < g.C ? ax_off(g.ocol, c) : 0;
+    }
+    T acc[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; u++) acc[u][0] = acc[u][1] = T(0);
+    stage_w(sW[0], g.W, ld, g.R, r0, 0, tid);
+    int b = 0;
+    for (int k0 = 0; k0 < g.K; k0 += kPK, b ^= 1) {
+        const int kn = min(kPK, g.K - k0);
+        __syncthreads();                       // offsets ready; buffers of the previous chunk consumed
+        if (k0 + kPK < g.K) {
+            stage_w(sW[b ^ 1], g.W, ld, g.R, r0, k0 + kPK, tid);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        if (tid < kPK) oZk[tid] = k0 + tid < g.K ? ax_off(g.zk, k0 + tid) : 0;
+        __syncthreads();
+        for (int e = tid; e < kPC * kPK; e += kPThreads) {
+            const int a = e / kPK, kk = e % kPK;
+            sZ[a][kk] = (kk < kn && c0 + a < g.C) ? g.Z[oZk[kk] + oZc[a]] : T(0);
+        }
+        __syncthreads();
+        for (int k = 0; k < kn; k++) {
+            T w[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) w[u] = sW[b][4 * tr + u][k];
+            const T z0 = sZ[2 * tc][k], z1 = sZ[2 * tc + 1][k];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                acc[u][0] = fma(w[u], z0, acc[u][0]);
+                acc[u][1] = fma(w[u], z1, acc[u][1]);
+            }
         }
     }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            const int r = 4 * tr + u, c = 2 * tc + v;
+            if (r0 + r < g.R && c0 + c < g.C) {
+                T* o = g.out + oOr[r] + oOc[c];
+                *o = fma(g.alpha, acc[u][v], *o);
+            }
+        }
 }
 
 // ---------------------------------------------------------------- elementwise parts
@@ -145,13 +289,20 @@ k_td2_init(const Td2Dim* __restrict__ dims, const long long* __restrict__ g_off,
     arena[d.Tc + e] = T(0);
 }
 
+// Raise the running maximum at p (bits of a non-negative value) to x; the
+// plain read first skips the atomic when x cannot raise it (most CTAs once
+// a large value is in), so the updates do not serialise on one address.
 __device__ __forceinline__ void max_bits(void* p, float x)
 {
-    atomicMax(static_cast<unsigned int*>(p), __float_as_uint(x));
+    unsigned int* q = static_cast<unsigned int*>(p);
+    const unsigned int u = __float_as_uint(x);
+    if (u > *(volatile unsigned int*)q) atomicMax(q, u);
 }
 __device__ __forceinline__ void max_bits(void* p, double x)
 {
-    atomicMax(static_cast<unsigned long long*>(p), (unsigned long long)__double_as_longlong(x));
+    unsigned long long* q = static_cast<unsigned long long*>(p);
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    if (u > *(volatile unsigned long long*)q) atomicMax(q, u);
 }
 
 template <typename T>
@@ -173,7 +324,14 @@ k_td2_update(const Td2Dim* __restrict__ dims, const double* __restrict__ eps, T*
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) dt = fmax(dt, __shfl_xor_sync(0xffffffffu, dt, o));
-    if ((threadIdx.x & 31) == 0 && dt > T(0)) max_bits(delta_bits, dt);
+    __shared__ T wmax[8];                      // one atomic per CTA, not per warp
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = dt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T m = wmax[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmax(m, wmax[w]);
+        if (m > T(0)) max_bits(delta_bits, m);
+    }
 }
 
 template <typename T>
@@ -222,8 +380,26 @@ template <typename T>
 cudaError_t launch_pgemm(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s)
 {
     if (nd <= 0 || max_r <= 0 || max_c <= 0) return cudaSuccess;     // no dimer has this term
-    const dim3 grid((max_r + kPT - 1) / kPT, (max_c + kPT - 1) / kPT, nd);
+    const dim3 grid((max_r + kPR - 1) / kPR, (max_c + kPC - 1) / kPC, nd);
     k_pgemm<T><<<grid, kPThreads, 0, s>>>(tabs);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pgemm_dw(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s)
+{
+    if (nd <= 0 || max_r <= 0 || max_c <= 0) return cudaSuccess;
+    const dim3 grid((max_r + kPR - 1) / kPR, (max_c + kPC - 1) / kPC, nd);
+    k_pgemm_dw<T><<<grid, kPThreads, 0, s>>>(tabs);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pack_ladder(const Td2Dim* dims, const long long* g_off, const long long* wd_off, int nd,
+                               int max_rows, T* arena, cudaStream_t s)
+{
+    if (nd <= 0 || max_rows <= 0) return cudaSuccess;
+    k_pack_ladder<T><<<dim3(max_rows, nd), 256, 0, s>>>(dims, g_off, wd_off, arena);
     return cudaGetLastError();
 }
 
@@ -257,6 +433,12 @@ template cudaError_t launch_qstep<float, float>(const QStep<float, float>*, int,
 template cudaError_t launch_qstep<double, double>(const QStep<double, double>*, int, int, int, cudaStream_t);
 template cudaError_t launch_pgemm<float>(const PGemm<float>*, int, int, int, cudaStream_t);
 template cudaError_t launch_pgemm<double>(const PGemm<double>*, int, int, int, cudaStream_t);
+template cudaError_t launch_pgemm_dw<float>(const PGemm<float>*, int, int, int, cudaStream_t);
+template cudaError_t launch_pgemm_dw<double>(const PGemm<double>*, int, int, int, cudaStream_t);
+template cudaError_t launch_pack_ladder<float>(const Td2Dim*, const long long*, const long long*, int, int, float*,
+                                               cudaStream_t);
+template cudaError_t launch_pack_ladder<double>(const Td2Dim*, const long long*, const long long*, int, int, double*,
+                                                cudaStream_t);
 template cudaError_t launch_td2_init<float>(const Td2Dim*, const long long*, int, int, float*, cudaStream_t);
 template cudaError_t launch_td2_init<double>(const Td2Dim*, const long long*, int, int, double*, cudaStream_t);
 template cudaError_t launch_td2_update<float>(const Td2Dim*, int, int, const double*, float*, void*, cudaStream_t);
