@@ -39,10 +39,10 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=192, help="dimers in the oracle's timed sample")
     p.add_argument("--no-extras", action="store_true",
-                   help="report none of the extras (coupling, td2, FP64 form, e2e, CPU baseline)")
-    p.add_argument("--extras", default="coupling,td2,fp64,e2e,cpu",
+                   help="report none of the extras (coupling, td2, df, FP64 form, e2e, CPU baseline)")
+    p.add_argument("--extras", default="coupling,td2,df,fp64,e2e,cpu",
                    help="comma-separated extras to report after the headline (default all of "
-                        "coupling,td2,fp64,e2e,cpu)")
+                        "coupling,td2,df,fp64,e2e,cpu)")
     p.add_argument("--max-dimers", type=int, default=0,
                    help="keep only the first N dimers of the workload (smaller cases for profiling)")
     p.add_argument("--alias-blocks", action="store_true",
@@ -428,6 +428,50 @@ def our_arm(args, ws, rank, local):
                                "synthetic monomer ring and amplitude matrices), energies at the final "
                                "amplitudes; wall clock per mcpt_td2 call; the error is against the FP64 oracle "
                                "on the first and last dimer"}
+
+    # ---- the density-fitted route on the same lattice: every dimer's
+    # three-index factors resident on the device (generated, untimed), the
+    # terms from them; checked against the stored four-index oracle values
+    if rank == 0 and "df" in extras:
+        import synth.device as sdev
+        Bs = []
+        for d in range(w.n_dimers):
+            X, Y = w.pairs[d]
+            Bs.append(sdev.factors(X, Y, w.nao[X], w.nao[Y], seed=w.seed))
+        torch.cuda.synchronize()
+        df = {}
+        dbytes = sum(B.numel() * 8 for B in Bs)
+        for prec in ([args.precision, "fp64"] if args.precision != "fp64" else ["fp64"]):
+            dctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False)
+            for m in mons:
+                dctx.add_monomer(m.C, m.eps, m.nocc)
+            for d in range(w.n_dimers):
+                X, Y = w.pairs[d]
+                dctx.add_dimer_df(X, Y, Bs[d].data_ptr(), Bs[d].shape[0], synth.scale_for_distance(w.R[d]),
+                                  on_device=1)
+            for _ in range(args.warmup):
+                dctx.run_df()
+            reps = 5
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                dctx.run_df()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            _, _, dpd, dtot = dctx.df_energies()
+            dctx.close()
+            ent = {"value": w.n_dimers / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                   "achieved_gbs": dbytes / (ms * 1e-3) / 1e9, "bytes_per_step": dbytes}
+            if g is not None:
+                ent["max_rel_err_vs_four_index_oracle"] = float(np.max(np.abs(dpd - g[0]) / np.abs(g[0][:, :1])))
+                ent["lattice_J_err_eh"] = float(dtot[0] - g[1][0])
+            df[prec] = ent
+        del Bs
+        line["df"] = {"forms": df, "what": "density-fitted route (three-index factors B^Q, naux 192, 6.3 MB per "
+                                           "dimer, device-resident): half-transformations, pair contractions over "
+                                           "Q with the FP64 energy epilogue, per-monomer reduction; mcpt_run_df "
+                                           "timed with CUDA events (it waits for its work)"}
 
     # ---- the plain FP64 GPU form on the same resident inputs
     if rank == 0 and "fp64" in extras and args.precision != "fp64":

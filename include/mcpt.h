@@ -250,6 +250,38 @@ mcpt_status mcpt_set_monomer_doubles(mcpt_handle h, int X, const double *G, cons
  * dimers), ENOMEM, ECUDA. */
 mcpt_status mcpt_td2(mcpt_handle h, int n_iter, double *per_dimer, double *delta);
 
+/* Density-fitted route (not the paper's four-index transformation): dimer
+ * terms from three-index factors, with
+ *   (ia|jb) = s sum_Q (C_X^T B^Q_XX C_X)_{ia} (C_Y^T B^Q_YY C_Y)_{jb}
+ *   (ib|ja) = s sum_Q (C_X^T B^Q_XY C_Y)_{ib} (C_Y^T B^Q_YX C_X)_{ja}
+ * and the same D, E_J, E_K and per-monomer accumulation as mcpt_run.  Exact
+ * whenever the integrals are (mu nu|lam sig) = s sum_Q B^Q_{mu nu} B^Q_{lam sig}
+ * on the dimer blocks.
+ * mcpt_add_dimer_df registers dimer X-Y (X < Y) in a list of its own (ids
+ * 0, 1, ... in call order): B is naux x n x n FP64 row-major over the dimer's
+ * n = nX + nY AO functions, X's first; on_device = 0: host, copied before the
+ * call returns; 1: device memory of the handle's device, BORROWED until the
+ * last mcpt_run_df that uses it has completed.  s scales the dimer's
+ * integrals (1 for plain factors).
+ * Errors: EINVAL (unknown ids, X >= Y, duplicate, NULL, naux < 1, non-finite
+ *   s, non-finite factors with validate = 1), ENOMEM, ECUDA. */
+mcpt_status mcpt_add_dimer_df(mcpt_handle h, int X, int Y, const double *B, int naux, double s,
+                              int on_device, int *id_out);
+/* Compute every density-fitted dimer's terms and their per-monomer sums on
+ * the handle's stream; FP64 in the FP64 form, FP32 otherwise (the
+ * denominators and energy sums FP64).  Waits for the work.
+ * Errors: ESTATE (no such dimers), EUNSUPPORTED (a dimer whose factor slice
+ *   B^Q, C_X, C_Y and occupied rows, n^2 + n_X^2 + n_Y^2 + (o_X + o_Y) n
+ *   values, exceed 200 KB of shared memory: above about 56 + 56 AO in FP64,
+ *   80 + 80 in FP32), ENOMEM, ECUDA. */
+mcpt_status mcpt_run_df(mcpt_handle h);
+/* Results of the last mcpt_run_df, as mcpt_energies (per-monomer halves of
+ * the density-fitted dimers, per-dimer {E_J, E_K} in their id order, the
+ * Neumaier totals); each pointer may be NULL.  Errors: ESTATE (no run since
+ * the last dimer was added), ECUDA. */
+mcpt_status mcpt_df_energies(mcpt_handle h, double *per_monomer_J, double *per_monomer_K,
+                             double *per_dimer, double *total);
+
 /* Per-phase timing and launch counts of every run since the previous call
  * (timing requires options.timing = 1; CUDA events are recorded on the
  * handle's stream around each phase, and this call waits for the stream).

@@ -30,6 +30,7 @@ MCPT_UPDATE_ASYNC = 1
 EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer",
            "mcpt_set_precision",
            "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_set_monomer_doubles", "mcpt_td2",
+           "mcpt_add_dimer_df", "mcpt_run_df", "mcpt_df_energies",
            "mcpt_collect_stats", "mcpt_num_monomers",
            "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
 
@@ -78,10 +79,13 @@ def lib():
         L.mcpt_singles.argtypes = [H, P, P]
         L.mcpt_set_monomer_doubles.argtypes = [H, I, P, P]
         L.mcpt_td2.argtypes = [H, I, P, P]
+        L.mcpt_add_dimer_df.argtypes = [H, I, I, P, I, ctypes.c_double, I, ctypes.POINTER(I)]
+        L.mcpt_run_df.argtypes = [H]
+        L.mcpt_df_energies.argtypes = [H, P, P, P, P]
         L.mcpt_collect_stats.argtypes = [H, ctypes.POINTER(mcpt_run_stats)]
         for f in ("mcpt_create", "mcpt_add_monomer", "mcpt_add_dimer", "mcpt_update_dimer", "mcpt_set_precision", "mcpt_run",
                   "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_set_monomer_doubles",
-                  "mcpt_td2", "mcpt_collect_stats"):
+                  "mcpt_td2", "mcpt_add_dimer_df", "mcpt_run_df", "mcpt_df_energies", "mcpt_collect_stats"):
             getattr(L, f).restype = I
         L.mcpt_num_monomers.argtypes = [H]
         L.mcpt_num_monomers.restype = I
@@ -198,6 +202,27 @@ def mcpt_td2(h, n_iter: int):
     return pd, dl
 
 
+def mcpt_add_dimer_df(h, X: int, Y: int, B, naux: int, s: float, on_device: int) -> int:
+    if isinstance(B, np.ndarray):
+        B = np.ascontiguousarray(B, dtype=np.float64)
+    out = ctypes.c_int()
+    _check(h, lib().mcpt_add_dimer_df(h, X, Y, _ptr(B), naux, s, on_device, ctypes.byref(out)))
+    return out.value
+
+
+def mcpt_run_df(h) -> None:
+    _check(h, lib().mcpt_run_df(h))
+
+
+def mcpt_df_energies(h, n_df: int):
+    """(per_monomer_J [N], per_monomer_K [N], per_dimer [n_df, 2], total [2])."""
+    N = lib().mcpt_num_monomers(h)
+    mj, mk = np.empty(N), np.empty(N)
+    pd, tot = np.empty((n_df, 2)), np.empty(2)
+    _check(h, lib().mcpt_df_energies(h, _ptr(mj), _ptr(mk), _ptr(pd), _ptr(tot)))
+    return mj, mk, pd, tot
+
+
 def mcpt_collect_stats(h) -> mcpt_run_stats:
     s = mcpt_run_stats()
     _check(h, lib().mcpt_collect_stats(h, ctypes.byref(s)))
@@ -291,6 +316,21 @@ class Context:
             out.append(flat[off:off + x.size].reshape(x.shape))
             off += x.size
         return out
+
+    def add_dimer_df(self, X, Y, B, naux, s=1.0, on_device=None):
+        """Register dimer X-Y (X < Y) of the density-fitted route by its
+        factors B[naux][n][n]; returns its id in that route's list."""
+        if on_device is None:
+            on_device = 0 if isinstance(B, np.ndarray) else 1
+        i = mcpt_add_dimer_df(self.h, X, Y, B, naux, s, on_device)
+        self.n_df = i + 1
+        return i
+
+    def run_df(self):
+        mcpt_run_df(self.h)
+
+    def df_energies(self):
+        return mcpt_df_energies(self.h, getattr(self, "n_df", 0))
 
     def set_monomer_doubles(self, X, G=None, U=None):
         """Monomer X's ring matrix G and amplitude matrix U of Eq. (td2)."""

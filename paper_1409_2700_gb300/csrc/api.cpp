@@ -31,6 +31,13 @@ struct MonomerRec {
     int offC, offE;
 };
 
+struct DfRec {                // a dimer of the density-fitted route
+    int X, Y;
+    const double* B;          // naux x (nX+nY)^2 FP64 on the device (library copy or borrowed)
+    int naux;
+    double s;
+};
+
 struct DimerRec {
     int X, Y;
     const double* E[2];
@@ -67,6 +74,15 @@ struct mcpt_ctx {
 
     std::vector<MonomerRec> mons;
     std::vector<std::vector<double>> monG, monU;   // Eq. (td2) monomer matrices (empty: zero)
+    std::vector<DfRec> dfs;          // density-fitted route: dimers, scratch, results
+    std::set<std::pair<int, int>> df_pairs;
+    void* dDf = nullptr;
+    size_t capDf = 0;
+    double* dDfOut = nullptr;        // E2 (2 per dimer), monomer halves (2 N), totals (2)
+    size_t capDfOut = 0;
+    int* dDfLists = nullptr;
+    size_t capDfLists = 0;
+    bool df_ran = false;
     void* dTd2 = nullptr;            // Eq. (td2): batch arena, tables, monomer matrices, outputs
     size_t capTd2 = 0;
     void* dTd2Tab = nullptr;
@@ -1285,6 +1301,126 @@ mcpt_status mcpt_singles(mcpt_handle h, const double* t, double* s)
     return MCPT_OK;
 }
 
+mcpt_status mcpt_add_dimer_df(mcpt_handle h, int X, int Y, const double* B, int naux, double s, int on_device,
+                              int* id_out)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_add_dimer_df: NULL handle");
+    const int N = (int)h->mons.size();
+    if (X < 0 || X >= N || Y < 0 || Y >= N)
+        return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: unknown monomer id (%d, %d) of %d", X, Y, N);
+    if (X >= Y) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: factors must be given with X < Y (%d, %d)", X, Y);
+    if (!B) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: B is NULL");
+    if (naux < 1) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: naux=%d < 1", naux);
+    if (!std::isfinite(s)) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: s is not finite");
+    const std::pair<int, int> key(X, Y);
+    if (h->df_pairs.count(key)) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: duplicate dimer (%d, %d)", X, Y);
+    const int n = h->mons[X].nao + h->mons[Y].nao;
+    const size_t elems = (size_t)naux * n * n;
+    CK(h, cudaSetDevice(h->device));
+    DfRec r{X, Y, B, naux, s};
+    mcpt_status st;
+    if (on_device) {
+        if ((st = check_device_ptr(h, B, "mcpt_add_dimer_df"))) return st;
+        if (h->validate) {
+            CK(h, cudaMemsetAsync(h->dFlag, 0, sizeof(int), h->stream));
+            CK(h, launch_check_finite(B, (long long)elems, h->dFlag, h->stream));
+            int flag = 0;
+            CK(h, cudaMemcpyAsync(&flag, h->dFlag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            if (flag) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: non-finite factor");
+        }
+    } else {
+        if (h->validate && !all_finite(B, elems)) return fail(h, MCPT_EINVAL, "mcpt_add_dimer_df: non-finite factor");
+        void* dst = nullptr;
+        if ((st = arena_alloc(h, elems * sizeof(double), &dst))) return st;
+        CK(h, cudaMemcpyAsync(dst, B, elems * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        r.B = static_cast<const double*>(dst);
+    }
+    h->dfs.push_back(r);
+    h->df_pairs.insert(key);
+    h->df_ran = false;
+    if (id_out) *id_out = (int)h->dfs.size() - 1;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_run_df(mcpt_handle h)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_run_df: NULL handle");
+    const int N = (int)h->mons.size(), D = (int)h->dfs.size();
+    if (D == 0) return fail(h, MCPT_ESTATE, "mcpt_run_df: no density-fitted dimers registered");
+    CK(h, cudaSetDevice(h->device));
+    mcpt_status st = upload_static(h);
+    if (st) return st;
+    const bool fp64 = h->prec == MCPT_FP64;
+    const size_t es = fp64 ? sizeof(double) : sizeof(float);
+    std::vector<DfDim> dims(D);
+    long long hoff = 0;
+    int poff = 0, max_naux = 0, max_pairs = 0, max_on = 0, max_v = 0;
+    for (int d = 0; d < D; d++) {
+        const DfRec& r = h->dfs[d];
+        const MonomerRec& mX = h->mons[r.X];
+        const MonomerRec& mY = h->mons[r.Y];
+        const int nX = mX.nao, nY = mY.nao, oX = mX.nocc, oY = mY.nocc, vX = nX - oX, vY = nY - oY;
+        // shared memory of the half-transformation: B^Q, C_X, C_Y and the occupied rows
+        const int on = (nX + nY) * (nX + nY) + nX * nX + nY * nY + (oX + oY) * (nX + nY);
+        if ((size_t)on * es > (size_t)200 * 1024)
+            return fail(h, MCPT_EUNSUPPORTED, "mcpt_run_df: dimer %d (%d + %d AO) needs %zu bytes of shared memory",
+                        d, nX, nY, (size_t)on * es);
+        dims[d] = DfDim{r.B, r.naux, nX, nY, oX, oY, mX.offC, mY.offC, mX.offE, mY.offE, r.s, hoff, poff, d};
+        hoff += (long long)r.naux * ((long long)oX * vX + (long long)oY * vY + (long long)oX * vY + (long long)oY * vX);
+        hoff = (hoff + 63) / 64 * 64;
+        poff += oX * oY;
+        max_naux = std::max(max_naux, r.naux);
+        max_pairs = std::max(max_pairs, oX * oY);
+        max_on = std::max(max_on, on);
+        max_v = std::max(max_v, std::max(vX, vY));
+    }
+    // monomer lists of the density-fitted dimers (CSR, ascending dimer id)
+    std::vector<int> cnt(N + 1, 0), lists(N + 1 + 2 * (size_t)D);
+    for (const auto& r : h->dfs) { cnt[r.X + 1]++; cnt[r.Y + 1]++; }
+    for (int m = 0; m < N; m++) cnt[m + 1] += cnt[m];
+    std::copy(cnt.begin(), cnt.end(), lists.begin());
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (int d = 0; d < D; d++) {
+        lists[N + 1 + fill[h->dfs[d].X]++] = d;
+        lists[N + 1 + fill[h->dfs[d].Y]++] = d;
+    }
+    // scratch: table, half-transformed blocks, pair partials
+    const size_t tab = ((size_t)D * sizeof(DfDim) + 255) & ~(size_t)255;
+    const size_t halfb = ((size_t)hoff * es + 255) & ~(size_t)255;
+    const size_t partb = 2 * (size_t)poff * sizeof(double);
+    if ((st = ensure(h, &h->dDf, &h->capDf, tab + halfb + partb))) return st;
+    if ((st = ensure(h, &h->dDfOut, &h->capDfOut, (2 * (size_t)D + 2 * (size_t)N + 2) * sizeof(double)))) return st;
+    if ((st = ensure(h, &h->dDfLists, &h->capDfLists, lists.size() * sizeof(int)))) return st;
+    char* base = static_cast<char*>(h->dDf);
+    CK(h, cudaMemcpyAsync(base, dims.data(), (size_t)D * sizeof(DfDim), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->dDfLists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    double* E2 = h->dDfOut;
+    CK(h, launch_df(fp64, reinterpret_cast<const DfDim*>(base), D, max_naux, max_pairs, max_on, max_v, h->dC, h->dE,
+                    base + tab, reinterpret_cast<double*>(base + tab + halfb), E2, h->stream));
+    MonomerLists L{h->dDfLists, h->dDfLists + N + 1, N};
+    CK(h, launch_reduce(E2, D, L, E2 + 2 * (size_t)D, E2 + 2 * (size_t)D + 2 * (size_t)N, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));   // the host tables go out of scope
+    h->df_ran = true;
+    return MCPT_OK;
+}
+
+mcpt_status mcpt_df_energies(mcpt_handle h, double* mon_J, double* mon_K, double* per_dimer, double* total)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_df_energies: NULL handle");
+    if (!h->df_ran) return fail(h, MCPT_ESTATE, "mcpt_df_energies: no mcpt_run_df since the last dimer was added");
+    const int N = (int)h->mons.size(), D = (int)h->dfs.size();
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const double* E2 = h->dDfOut;
+    if (mon_J) CK(h, cudaMemcpy(mon_J, E2 + 2 * (size_t)D, N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (mon_K) CK(h, cudaMemcpy(mon_K, E2 + 2 * (size_t)D + N, N * sizeof(double), cudaMemcpyDeviceToHost));
+    if (per_dimer) CK(h, cudaMemcpy(per_dimer, E2, 2 * (size_t)D * sizeof(double), cudaMemcpyDeviceToHost));
+    if (total) CK(h, cudaMemcpy(total, E2 + 2 * (size_t)D + 2 * (size_t)N, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    return MCPT_OK;
+}
+
 mcpt_status mcpt_set_monomer_doubles(mcpt_handle h, int X, const double* G, const double* U)
 {
     if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_set_monomer_doubles: NULL handle");
@@ -1608,6 +1744,9 @@ void mcpt_destroy(mcpt_handle h)
     cudaFree(h->dTd2Tab);
     cudaFree(h->dTd2Mon);
     cudaFree(h->dTd2Out);
+    cudaFree(h->dDf);
+    cudaFree(h->dDfOut);
+    cudaFree(h->dDfLists);
     for (int b = 0; b < 2; b++) {
         cudaFree(h->dPack[b]);
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);

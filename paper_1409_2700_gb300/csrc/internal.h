@@ -206,6 +206,27 @@ cudaError_t launch_td2_update(const Td2Dim* dims, int nd, int max_m, const doubl
 template <typename T>
 cudaError_t launch_td2_energy(const Td2Dim* dims, int nd, const T* arena, double* E, cudaStream_t s);
 
+// ---- density-fitted route ----
+// One dimer given by its three-index factors B[naux][n][n] (n = nX + nY, X's
+// functions first, FP64 device memory): (ia|jb) = s sum_Q (C_X^T B^Q_XX C_X)_{ia}
+// (C_Y^T B^Q_YY C_Y)_{jb}, (ib|ja) = s sum_Q (C_X^T B^Q_XY C_Y)_{ib} (C_Y^T B^Q_YX C_X)_{ja}.
+struct DfDim {
+    const double* B;
+    int naux, nX, nY, oX, oY;
+    int cX, cY, eX, eY;       // offsets of C and eps in the monomer pools
+    double s;
+    long long h_off;          // half-transformed blocks: naux x (oX vX + oY vY + oX vY + oY vX) elements
+    int p_off;                // first pair partial (pairs of doubles)
+    int id;                   // row of E2
+};
+// Terms of nd dimers into E2 (2 doubles each): FP64 arithmetic if fp64,
+// else FP32 (energy epilogue FP64).  max_on = max over dimers of the
+// half-transformation's shared elements n^2 + nX^2 + nY^2 + (oX + oY) n;
+// max_v = max(vX, vY); half: scratch of the half-transformed blocks;
+// part: 2 doubles per occupied pair.
+cudaError_t launch_df(bool fp64, const DfDim* dims, int nd, int max_naux, int max_pairs, int max_on, int max_v,
+                      const double* C, const double* eps, void* half, double* part, double* E2, cudaStream_t s);
+
 // Split dimers: E2[dimer] = sum, in block order, of E2[first .. first+n) for
 // each (dimer, first, n) triple of `fold` (device, 3 ints each).
 cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s);
