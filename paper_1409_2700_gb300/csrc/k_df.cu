@@ -12,9 +12,19 @@
 // tiles over Q, staged in chunks, and applies the FP64 epilogue; the pairs'
 // partial energies are added per dimer in fixed order (k_df_sum).
 #include "internal.h"
+#include "convert.h"
 
 namespace mcpt {
 namespace {
+
+// FP64 -> T; to FP32 on the integer pipes (a cvt.f32.f64 would issue on the
+// small FP64 unit for every element read).
+template <typename T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return f32_from_f64(x); }
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -32,9 +42,9 @@ k_df_half(const DfDim* __restrict__ dims, const double* __restrict__ C, T* __res
     T* sCY = sCX + nX * nX;
     T* uX = sCY + nY * nY;
     T* uY = uX + oX * n;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) sB[e] = (T)B[e];
-    for (int e = threadIdx.x; e < nX * nX; e += blockDim.x) sCX[e] = (T)C[d.cX + e];
-    for (int e = threadIdx.x; e < nY * nY; e += blockDim.x) sCY[e] = (T)C[d.cY + e];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) sB[e] = from_f64<T>(B[e]);
+    for (int e = threadIdx.x; e < nX * nX; e += blockDim.x) sCX[e] = from_f64<T>(C[d.cX + e]);
+    for (int e = threadIdx.x; e < nY * nY; e += blockDim.x) sCY[e] = from_f64<T>(C[d.cY + e]);
     __syncthreads();
     for (int e = threadIdx.x; e < (oX + oY) * n; e += blockDim.x) {
         const int r = e / n, c = e % n;

@@ -12,9 +12,24 @@
 // the energy tensor (k_td2_update).  Each output tile is written by one CTA
 // and every sum has a fixed order, so the results are deterministic.
 #include "internal.h"
+#include "convert.h"
 
 namespace mcpt {
 namespace {
+
+// FP64 -> T; to FP32 on the integer pipes (a cvt.f32.f64 would issue on the
+// small FP64 unit for every element read).
+template <typename T>
+__device__ __forceinline__ T from_f64(double x);
+template <>
+__device__ __forceinline__ float from_f64<float>(double x) { return f32_from_f64(x); }
+template <>
+__device__ __forceinline__ double from_f64<double>(double x) { return x; }
+// An element of a quarter step's input (FP64 AO block or the previous step's T) as TO.
+template <typename TO>
+__device__ __forceinline__ TO to_out(double x) { return from_f64<TO>(x); }
+template <typename TO>
+__device__ __forceinline__ TO to_out(float x) { return (TO)x; }
 
 template <typename T>
 __device__ __forceinline__ void ld4(const T* p, T (&x)[4])
@@ -58,11 +73,11 @@ k_qstep(const QStep<TI, TO>* __restrict__ steps)
         __syncthreads();                       // row offsets ready; previous chunk consumed
         for (int e = tid; e < kQM * kQK; e += kQThreads) {
             const int mm = e / kQK, kk = e % kQK, k = k0 + kk;
-            sIn[kk][mm] = (m0 + mm < q.M && k < q.K) ? (TO)q.in[rowOff[mm] + k] : TO(0);
+            sIn[kk][mm] = (m0 + mm < q.M && k < q.K) ? to_out<TO>(q.in[rowOff[mm] + k]) : TO(0);
         }
         for (int e = tid; e < kQK * kQN; e += kQThreads) {
             const int kk = e / kQN, nn = e % kQN, k = k0 + kk, n = n0 + nn;
-            sC[kk][nn] = (k < q.K && n < q.N) ? (TO)q.C[(long long)k * q.ldc + q.c0 + n] : TO(0);
+            sC[kk][nn] = (k < q.K && n < q.N) ? from_f64<TO>(q.C[(long long)k * q.ldc + q.c0 + n]) : TO(0);
         }
         __syncthreads();
         for (int k = 0; k < kn; k++) {
@@ -318,7 +333,7 @@ k_td2_update(const Td2Dim* __restrict__ dims, const double* __restrict__ eps, T*
         const int ia = e / mY, jb = e % mY;
         const int i = ia / vX, a = ia % vX, j = jb / vY, b = jb % vY;
         const double den = eps[d.eX + i] + eps[d.eY + j] - eps[d.eX + d.oX + a] - eps[d.eY + d.oY + b];
-        const T t = arena[d.R + e] / (T)den;
+        const T t = arena[d.R + e] / from_f64<T>(den);
         dt = fabs(t - arena[d.Tc + e]);
         arena[d.Tc + e] = t;
     }
