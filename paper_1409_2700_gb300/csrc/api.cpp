@@ -1573,8 +1573,8 @@ mcpt_status td2_run(mcpt_handle h, int n_iter, double* per_dimer, double* delta)
             if (uOff[r.Y] >= 0)
                 sy = PGemm<T>{dMon + uOff[r.Y], ax(iY, 0, iY), ax(iY, 0, 1), V, ax(iY, 0, 1), ax(iX, 0, iY),
                               R0, ax(iY, 0, 1), ax(iX, 0, iY), iY, iX, iY, T(1)};
-            // L1 particle ladder: R[(a,b)][(i,j)] += Wd[(a,b)][(a1,b1)] T[(a1,b1)][(i,j)], Wd the
-            // packed g[oX+a][oX+a1][oY+b][oY+b1] (dense rows of ldw)
+            // L1 particle ladder: R[(a,b)][(i,j)] += Wt[(a1,b1)][(a,b)] T[(a1,b1)][(i,j)], Wt the
+            // packed g[oX+a][oX+a1][oY+b][oY+b1] (k-major, dense rows of ldw)
             PGemm<T> l1{arena + wd, ax(vv, 0, ldw), ax(1, 0, 1),
                         Tc, ax(vY, sa, sb), ax(oY, si, sj), R, ax(vY, sa, sb), ax(oY, si, sj),
                         vv, oX * oY, vv, T(1)};

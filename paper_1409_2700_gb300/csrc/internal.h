@@ -184,11 +184,11 @@ template <typename TI, typename TO>
 cudaError_t launch_qstep(const QStep<TI, TO>* steps, int nd, int max_m, int max_n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pgemm(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s);
-// The same contraction with W a dense row-major matrix: row r at W + r * ld,
-// ld = wr.s1 a multiple of 4 and the padding zero (wk unused).
+// The same contraction with W given k-major as a dense matrix Wt[k][r] at
+// W + k * ld + r, ld = wr.s1 a multiple of 4 and the padding zero (wk unused).
 template <typename T>
 cudaError_t launch_pgemm_dw(const PGemm<T>* tabs, int nd, int max_r, int max_c, cudaStream_t s);
-// Wd[(a,b)][(a1,b1)] = g[oX+a][oX+a1][oY+b][oY+b1] per dimer at wd_off[d],
+// Wt[(a1,b1)][(a,b)] = g[oX+a][oX+a1][oY+b][oY+b1] per dimer at wd_off[d],
 // rows of ld = round4(vX vY) with zero padding.
 template <typename T>
 cudaError_t launch_pack_ladder(const Td2Dim* dims, const long long* g_off, const long long* wd_off, int nd,

@@ -176,12 +176,13 @@ k_pgemm(const PGemm<T>* __restrict__ tabs)
         }
 }
 
-// The particle ladder with its integrals packed once per dimer into a dense
-// row-major matrix Wd[(a,b)][(a1,b1)] (row length ld, a multiple of 4, the
-// padding zero), which is constant over the steps: 64 x 32 output tiles as
-// above, the W rows streamed by 16-byte cp.async into two buffers (the next
-// chunk in flight while the current one is summed), the amplitudes gathered
-// through their offset tables.
+// The particle ladder with its integrals packed once per dimer, k-major, into
+// a dense matrix Wt[(a1,b1)][(a,b)] = (a a1|b b1) (row length ld, a multiple
+// of 4, the padding zero), constant over the steps: 64 x 32 output tiles, the
+// W chunk (32 k-rows x 64 output rows) streamed by 16-byte cp.async straight
+// into a [k][r] layout (two buffers: the next chunk in flight while the
+// current one is summed), the amplitudes gathered into [k][c] through their
+// offset tables; per k one 4-wide and one 2-wide shared load feed 8 FMAs.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_pack_ladder(const Td2Dim* __restrict__ dims, const long long* __restrict__ g_off,
@@ -191,36 +192,51 @@ k_pack_ladder(const Td2Dim* __restrict__ dims, const long long* __restrict__ g_o
     const int vX = d.nX - d.oX, vY = d.nY - d.oY, n = vX * vY, ld = (n + 3) / 4 * 4;
     const int row = blockIdx.x;                // (a, b)
     if (row >= n) return;
-    const int a = row / vY, b = row % vY;
+    const int a1 = row / vY, b1 = row % vY;    // row of Wt: (a1, b1); column (a, b)
     const T* g = arena + g_off[blockIdx.y];
     T* w = arena + wd_off[blockIdx.y] + (long long)row * ld;
-    for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+    for (int c = threadIdx.x; c < ld; c += blockDim.x) {
         T x = T(0);
-        if (k < n) {
-            const int a1 = k / vY, b1 = k % vY;
+        if (c < n) {
+            const int a = c / vY, b = c % vY;
             x = g[(((long long)(d.oX + a) * d.nX + d.oX + a1) * d.nY + d.oY + b) * d.nY + d.oY + b1];
         }
-        w[k] = x;
+        w[c] = x;
     }
 }
 
-constexpr int kLS = kPK + 4;                   // staged W row stride (16-byte aligned rows)
+constexpr int kLS = kPR + 4;                   // staged W row stride [k][r] (16-byte aligned rows)
+constexpr int kZS = kPC + 2;                   // staged Z row stride [k][c] (8-byte aligned pairs)
 
+// Rows k0 .. k0 + kPK of Wt, columns r0 .. r0 + kPR, into sW[k][r]; rows
+// beyond K and columns beyond ld are zero-filled without reading.
 template <typename T>
-__device__ __forceinline__ void stage_w(T (*sW)[kLS], const T* __restrict__ W, int ld, int R, int r0, int k0,
+__device__ __forceinline__ void stage_w(T (*sW)[kLS], const T* __restrict__ W, int ld, int K, int r0, int k0,
                                         int tid)
 {
     constexpr int kV = 16 / sizeof(T);         // elements per 16-byte copy
-    constexpr int kG = kPK / kV;               // copies per row and chunk
-    for (int e = tid; e < kPR * kG; e += kPThreads) {
-        const int r = e / kG, c = (e % kG) * kV, k = k0 + c;
-        const bool ok = r0 + r < R && k < ld;
-        const T* src = ok ? W + (long long)(r0 + r) * ld + k : W;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(&sW[r][c])),
+    constexpr int kG = kPR / kV;               // copies per k-row
+    for (int e = tid; e < kPK * kG; e += kPThreads) {
+        const int kk = e / kG, c = (e % kG) * kV, k = k0 + kk, r = r0 + c;
+        const bool ok = k < K && r < ld;
+        const T* src = ok ? W + (long long)k * ld + r : W;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((unsigned)__cvta_generic_to_shared(&sW[kk][c])),
                      "l"(src), "r"(ok ? 16 : 0)
                      : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void ld2(const T* p, T& x0, T& x1)
+{
+    if constexpr (sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        x0 = v.x; x1 = v.y;
+    } else {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        x0 = v.x; x1 = v.y;
+    }
 }
 
 template <typename T>
@@ -230,9 +246,9 @@ k_pgemm_dw(const PGemm<T>* __restrict__ tabs)
     const PGemm<T> g = tabs[blockIdx.z];
     const int r0 = blockIdx.x * kPR, c0 = blockIdx.y * kPC;
     if (r0 >= g.R || c0 >= g.C) return;
-    const int ld = (int)g.wr.s1;               // dense W: row r at r * ld
-    __shared__ __align__(16) T sW[2][kPR][kLS];
-    __shared__ T sZ[kPC][kPK + 1];
+    const int ld = (int)g.wr.s1;               // dense Wt: row k at k * ld
+    __shared__ __align__(16) T sW[2][kPK][kLS];
+    __shared__ __align__(16) T sZ[kPK][kZS];
     __shared__ long long oOr[kPR], oZc[kPC], oOc[kPC], oZk[kPK];
     const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
     if (tid < kPR) {
@@ -245,13 +261,13 @@ k_pgemm_dw(const PGemm<T>* __restrict__ tabs)
     T acc[4][2];
 #pragma unroll
     for (int u = 0; u < 4; u++) acc[u][0] = acc[u][1] = T(0);
-    stage_w(sW[0], g.W, ld, g.R, r0, 0, tid);
+    stage_w(sW[0], g.W, ld, g.K, r0, 0, tid);
     int b = 0;
     for (int k0 = 0; k0 < g.K; k0 += kPK, b ^= 1) {
         const int kn = min(kPK, g.K - k0);
         __syncthreads();                       // offsets ready; buffers of the previous chunk consumed
         if (k0 + kPK < g.K) {
-            stage_w(sW[b ^ 1], g.W, ld, g.R, r0, k0 + kPK, tid);
+            stage_w(sW[b ^ 1], g.W, ld, g.K, r0, k0 + kPK, tid);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
@@ -259,15 +275,14 @@ k_pgemm_dw(const PGemm<T>* __restrict__ tabs)
         if (tid < kPK) oZk[tid] = k0 + tid < g.K ? ax_off(g.zk, k0 + tid) : 0;
         __syncthreads();
         for (int e = tid; e < kPC * kPK; e += kPThreads) {
-            const int a = e / kPK, kk = e % kPK;
-            sZ[a][kk] = (kk < kn && c0 + a < g.C) ? g.Z[oZk[kk] + oZc[a]] : T(0);
+            const int kk = e / kPC, c = e % kPC;
+            sZ[kk][c] = (kk < kn && c0 + c < g.C) ? g.Z[oZk[kk] + oZc[c]] : T(0);
         }
         __syncthreads();
         for (int k = 0; k < kn; k++) {
-            T w[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) w[u] = sW[b][4 * tr + u][k];
-            const T z0 = sZ[2 * tc][k], z1 = sZ[2 * tc + 1][k];
+            T w[4], z0, z1;
+            ld4(&sW[b][k][4 * tr], w);
+            ld2(&sZ[k][2 * tc], z0, z1);
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 acc[u][0] = fma(w[u], z0, acc[u][0]);
