@@ -9,9 +9,8 @@
 // first, u_X = C_X,occ^T B^Q[X rows] and u_Y = C_Y,occ^T B^Q[Y rows] (over
 // all n columns), then the four o x v half-transformed blocks.
 // k_df_pair: one CTA per (dimer, occupied pair i, j) sums the two vX x vY
-// tiles over Q, staged in chunks, each thread a 2 x 2 block of (a, b), and
-// applies the FP64 epilogue; the pairs' partial energies are added per dimer
-// in fixed order (k_df_sum).
+// tiles over Q, staged in chunks, and applies the FP64 epilogue; the pairs'
+// partial energies are added per dimer in fixed order (k_df_sum).
 #include "internal.h"
 #include "convert.h"
 
@@ -140,15 +139,11 @@ k_df_pair(const DfDim* __restrict__ dims, const double* __restrict__ eps, const 
     T* sxy = syy + kDQ * vY;                   // [kDQ][vY]: xy[Q][i][.]
     T* syx = sxy + kDQ * vY;                   // [kDQ][vX]: yx[Q][j][.]
     double* red = reinterpret_cast<double*>(syx + kDQ * vX + (kDQ * vX) % 2);
-    const int hX = (vX + 1) / 2, hY = (vY + 1) / 2, nblk = hX * hY;   // 2 x 2 blocks of (a, b)
+    const int nab = vX * vY;
     double ej = 0.0, ek = 0.0;
-    // the thread owns the 2 x 2 block (2 ba, 2 bb) of each group of 256 blocks
-    for (int g0 = 0; g0 < nblk; g0 += 256) {
-        const int blk = g0 + threadIdx.x;
-        const bool act = blk < nblk;
-        const int a0 = act ? 2 * (blk / hY) : 0, b0 = act ? 2 * (blk % hY) : 0;
-        const int a1 = min(a0 + 1, vX - 1), b1 = min(b0 + 1, vY - 1);    // clamped reads at odd edges
-        T v[2][2] = {{T(0), T(0)}, {T(0), T(0)}}, w[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    // the thread owns the (a, b) elements e0 + tid + 256 u of each block of 1024
+    for (int e0 = 0; e0 < nab; e0 += 256 * 4) {
+        T v[4] = {T(0), T(0), T(0), T(0)}, w[4] = {T(0), T(0), T(0), T(0)};
         for (int q0 = 0; q0 < d.naux; q0 += kDQ) {
             const int qn = min(kDQ, d.naux - q0);
             __syncthreads();
@@ -163,33 +158,31 @@ k_df_pair(const DfDim* __restrict__ dims, const double* __restrict__ eps, const 
                 sxy[qq * vY + b] = xy[(long long)(q0 + qq) * xb + i * vY + b];
             }
             __syncthreads();
-            if (act) {
-                for (int qq = 0; qq < qn; qq++) {
-                    const T x0 = sxx[qq * vX + a0], x1 = sxx[qq * vX + a1];
-                    const T z0 = syx[qq * vX + a0], z1 = syx[qq * vX + a1];
-                    const T y0 = syy[qq * vY + b0], y1 = syy[qq * vY + b1];
-                    const T c0 = sxy[qq * vY + b0], c1 = sxy[qq * vY + b1];
-                    v[0][0] = fma(x0, y0, v[0][0]); v[0][1] = fma(x0, y1, v[0][1]);
-                    v[1][0] = fma(x1, y0, v[1][0]); v[1][1] = fma(x1, y1, v[1][1]);
-                    w[0][0] = fma(c0, z0, w[0][0]); w[0][1] = fma(c1, z0, w[0][1]);
-                    w[1][0] = fma(c0, z1, w[1][0]); w[1][1] = fma(c1, z1, w[1][1]);
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int e = e0 + threadIdx.x + 256 * u;
+                if (e < nab) {
+                    const int a = e / vY, b = e % vY;
+                    T vv = v[u], ww = w[u];
+                    for (int qq = 0; qq < qn; qq++) {
+                        vv = fma(sxx[qq * vX + a], syy[qq * vY + b], vv);
+                        ww = fma(sxy[qq * vY + b], syx[qq * vX + a], ww);
+                    }
+                    v[u] = vv;
+                    w[u] = ww;
                 }
             }
         }
-        if (act) {
 #pragma unroll
-            for (int u = 0; u < 2; u++)
-#pragma unroll
-                for (int t = 0; t < 2; t++) {
-                    const int a = a0 + u, b = b0 + t;
-                    if (a < vX && b < vY) {
-                        const double D =
-                            1.0 / (eps[d.eX + i] + eps[d.eY + j] - eps[d.eX + oX + a] - eps[d.eY + oY + b]);
-                        const double vs = d.s * (double)v[u][t], ws = d.s * (double)w[u][t];
-                        ej += 4.0 * vs * vs * D;
-                        ek += -2.0 * vs * ws * D;
-                    }
-                }
+        for (int u = 0; u < 4; u++) {
+            const int e = e0 + threadIdx.x + 256 * u;
+            if (e < nab) {
+                const int a = e / vY, b = e % vY;
+                const double D = 1.0 / (eps[d.eX + i] + eps[d.eY + j] - eps[d.eX + oX + a] - eps[d.eY + oY + b]);
+                const double vs = d.s * (double)v[u], ws = d.s * (double)w[u];
+                ej += 4.0 * vs * vs * D;
+                ek += -2.0 * vs * ws * D;
+            }
         }
     }
     red[threadIdx.x] = ej;
