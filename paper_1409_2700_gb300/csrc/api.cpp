@@ -278,7 +278,7 @@ size_t hbytes_for(mcpt_precision p, int nX, int nY, int oX, int oY)
     return 2 * (size_t)nX * nY * oX * oY * elem;
 }
 
-mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY, int oX, int oY)
+mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY)
 {
     switch (h->prec) {
     case MCPT_FP64:
@@ -801,7 +801,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         const DimerRec& r = h->dims[d];
         const MonomerRec& mX = h->mons[r.X];
         const MonomerRec& mY = h->mons[r.Y];
-        mcpt_status st = check_supported(h, d, mX.nao, mY.nao, mX.nocc, mY.nocc);
+        mcpt_status st = check_supported(h, d, mX.nao, mY.nao);
         if (st) return st;
         DimerDesc base{};
         base.E[0] = r.E[0];
