@@ -8,7 +8,6 @@ directly; Box-Muller's log/cos/sin may differ by an ulp).
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 import subprocess
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import load_context, rand_dimer
+from helpers import load_context
 
 pytestmark = pytest.mark.gpu
 

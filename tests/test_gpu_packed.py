@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 import synth
-from helpers import host_workload, load_context
+from helpers import host_workload
 
 pytestmark = pytest.mark.gpu
 

@@ -4,7 +4,6 @@ not by the oracle itself (CPU only).
 Each test names the mistake class it guards against: a transposed operand, a
 wrong index, a dropped term, a wrong sign or factor.
 """
-import math
 
 import numpy as np
 import pytest
