@@ -51,3 +51,14 @@ def test_gather_index_matches_packer():
         A, K = synth.eri_blocks(B + np.transpose(B, (0, 2, 1)), nX, 0.3)
         flat = np.concatenate([A.ravel(), K.ravel()])
         assert np.array_equal(flat[synth.packed_gather_index(nX, nY)], synth.pack_blocks(A, K))
+
+
+def test_monomer_doubles_are_seeded_symmetric_and_scaled():
+    G, U = synth.monomer_doubles(7, 32, 5)
+    G2, U2 = synth.monomer_doubles(7, 32, 5)
+    assert G.shape == U.shape == (135, 135)
+    assert np.array_equal(G, G2) and np.array_equal(U, U2)                  # seeded
+    assert np.array_equal(G, G.T) and np.array_equal(U, U.T)                # symmetric
+    assert not np.array_equal(G, synth.monomer_doubles(8, 32, 5)[0])        # per monomer
+    assert 0.5 * synth.RING_SCALE < G.std() < 2 * synth.RING_SCALE
+    assert 0.5 * synth.UAMP_SCALE < U.std() < 2 * synth.UAMP_SCALE
