@@ -1,8 +1,12 @@
 // k_tc.cu -- first half of the dimer transformation on the 5th-generation
 // tensor cores (tcgen05, sm_103a), TF32 or BF16x3 operands, FP32 accumulate.
 //
-// The two occupied quarter transformations of Eq. (dp2e) are fused into one
-// GEMM per dimer form (see internal.h for the axis naming):
+// Two kernels.  The "rank" kernel (further down; the one every supported
+// size runs) contracts p2 on the tensor cores and applies p0 as a rank-1
+// update in the epilogue.  The Kronecker kernel described here, selected
+// only by MCPT_TC_KERNEL=kron, fuses both occupied quarter transformations
+// of Eq. (dp2e) into one GEMM per dimer form (see internal.h for the axis
+// naming):
 //   H[(p1,p3)][(i,j)] = sum_{(p0,p2)} E[p0][p1][p2][p3] * W[(p0,p2)][(i,j)],
 //   W[(p0,p2)][(i,j)] = C_X[p0][i] C_Y[p2][j]            (Kronecker product)
 // M = rows (p1,p3) in tiles of 128, N = nocc_X*nocc_Y padded to 16, K = (p0,p2).
@@ -632,8 +636,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // independent from element to element.
 // BF16x3 goes further and makes every tensor-core sum exact.  Each operand
 // vector is held in 32-bit fixed point relative to its largest power of two:
-// an integral row (p1,p3) of one p0 over all p2, x ~ 2^(e-31) N_x, and a C_Y
-// column j, c ~ 2^(f-31) N_c, |N| <= 2^32, cut into four balanced base-256
+// an integral row (p1,p3) of one p0 over one chunk of 32 p2 values (each
+// (p0, chunk) is a unit of its own), x ~ 2^(e-31) N_x, and a C_Y column j,
+// c ~ 2^(f-31) N_c, |N| <= 2^32, cut into four balanced base-256
 // digits N = d0 2^24 + d1 2^16 + d2 2^8 + d3 (|d0| <= 256, the others <= 128,
 // each exact in BF16).  The digits come from the FP32 value by round-to-
 // nearest-even FMAs (FP32 pipe), so every integral keeps its 24 FP32 bits
@@ -643,10 +648,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
 // (four MMAs per K step: A_u times the stacked digit planes B_0..B_(3-u) of
 // C_Y, N = 64, 48, 32, 16, landing in the four 16-column TMEM slots of levels
 // u..3) are sums of at most
-// 4 n2 integer products, each below 2^16: for n2 <= 128 every partial sum is
-// an integer below 2^24, so the tensor core adds them without rounding.  The
-// epilogue forms T = 2^(e+f-14) (L0 + 2^-8 L1 + 2^-16 L2 + 2^-24 L3) in FP32
-// with round-to-nearest; the dropped digit products lie below 2^-31 of the
+// 4 x 32 integer products per unit, each at most 2^16, so every partial sum
+// is an integer below 2^24 and the tensor core adds them without rounding.
+// The epilogue forms each unit's T = 2^(e+f-14) (L0 + 2^-8 L1 + 2^-16 L2 +
+// 2^-24 L3) in FP32 with round-to-nearest and adds it into H through the
+// rank-1 update (the chunks of a row are summed there, in FP32 with
+// round-to-nearest); the dropped digit products lie below 2^-31 of the
 // vectors' largest terms.
 // BIG = false: the rank-1 accumulators live in registers (o_X, o_Y <= 8),
 // T slots use all 512 TMEM columns.  BIG = true (o_X, o_Y <= 16): the
