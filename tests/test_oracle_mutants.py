@@ -48,6 +48,12 @@ MUTANTS = {
                                    "r += GX[((size_t)i1 * vX + a1) * mX + (size_t)i * vX + a] * T[IDX(i1, a1, j, b)];"),
     "td2 energy-tensor sign": ("const double t = r / (epsX[i] + epsY[j] - epsX[oX + a] - epsY[oY + b]);",
                                "const double t = -r / (epsX[i] + epsY[j] - epsX[oX + a] - epsY[oY + b]);"),
+    "factor route exchange factors swapped": (
+        "W[(((size_t)i * vY + b) * oY + j) * vX + a] += s * xy[i * vY + b] * yx[j * vX + a];",
+        "W[(((size_t)i * vY + b) * oY + j) * vX + a] += s * xy[i * vY + b] * xx[i * vX + a];"),
+    "factor route scale dropped": (
+        "V[(((size_t)i * vX + a) * oY + j) * vY + b] += s * xx[i * vX + a] * yy[j * vY + b];",
+        "V[(((size_t)i * vX + a) * oY + j) * vY + b] += xx[i * vX + a] * yy[j * vY + b];"),
 }
 
 CHECKS = r'''
@@ -143,6 +149,16 @@ L3 = (np.einsum("aAbB,iAjB->iajb", mo((vx, vx, vy, vy)), T3) + np.einsum("IiJj,I
       + (UX @ v3.reshape(m1, m2) + v3.reshape(m1, m2) @ UY.T).reshape(T3.shape))
 ee = e1[:o1, None, None, None] + e2[None, None, :o2, None] - e1[None, o1:, None, None] - e2[None, None, None, o2:]
 check("td2 residual", np.abs(ee * T3 - v3 - L3).max() <= 1e-11 * np.abs(v3).max())
+# density-fitted factor route against the four-index transformation of the blocks it defines
+n5, n6, o5, o6 = 6, 5, 2, 2
+B5 = rng.standard_normal((4, n5 + n6, n5 + n6))
+B5 = B5 + np.transpose(B5, (0, 2, 1))
+A5, K5 = synth.eri_blocks(B5, n5, 0.7)
+C5 = np.linalg.qr(rng.standard_normal((n5, n5)))[0]; C6 = np.linalg.qr(rng.standard_normal((n6, n6)))[0]
+V5, W5 = oracle.factor_route(B5, 0.7, C5, C6, o5, o6)
+V5r = oracle.transform_J(A5, C5, C6, o5, o6); W5r = oracle.transform_K(K5, C5, C6, o5, o6)
+check("factor route J", np.abs(V5 - V5r).max() <= 1e-12 * np.abs(V5r).max())
+check("factor route K", np.abs(W5 - W5r).max() <= 1e-12 * np.abs(W5r).max())
 print("FAILS:" + ",".join(fails))
 '''
 
