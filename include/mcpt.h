@@ -76,7 +76,12 @@ typedef enum {
                          BF16 digits; the tcgen05 MMAs add only integer digit products whose FP32 partial
                          sums stay below 2^24, so every tensor-core accumulation is exact (the Kronecker
                          kernel, selected only by MCPT_TC_KERNEL=kron, keeps a hi/lo BF16 split) */
-    MCPT_FP32C = 3    /* FP32 FMA with error-free TwoProduct/TwoSum compensation (Ogita-Rump-Oishi) */
+    MCPT_FP32C = 3,   /* FP32 FMA with error-free TwoProduct/TwoSum compensation (Ogita-Rump-Oishi) */
+    MCPT_BF16X2 = 4   /* as MCPT_BF16X3 for C_Y (32-bit fixed point, four digits), but each integral
+                         row chunk in 16-bit fixed point (two BF16 digits, rounded half up in magnitude,
+                         read from the high word of each double): exact tensor-core sums with half the
+                         digit work and half the MMAs; integrals carry 2^-17 of their chunk's largest
+                         power of two as rounding error */
 } mcpt_precision;
 
 typedef enum {
@@ -332,7 +337,8 @@ const char *mcpt_last_error(mcpt_handle h);
  * one stream are ordered.  Nothing in the array needs to start at zero --
  * every call overwrites all of the scratch it reads.
  * Errors (message via mcpt_last_error(NULL)): EINVAL for NULL pointers, sizes
- * outside the limits above; ECUDA if set-up or a launch fails. */
+ * outside the limits above; ECUDA if set-up or a launch fails.  A successful
+ * call clears that message. */
 mcpt_status mcpt_dimer_fp64_noalloc(const double *A, const double *K,
                                     const double *C_X, const double *eps_X, int nX, int nocc_X,
                                     const double *C_Y, const double *eps_Y, int nY, int nocc_Y,

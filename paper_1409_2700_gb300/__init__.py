@@ -21,8 +21,9 @@ LIB_PATH = os.path.join(_HERE, "libmcpt.so")
 
 MCPT_OK, MCPT_EINVAL, MCPT_ENOMEM, MCPT_ECUDA, MCPT_ESTATE, MCPT_ETIMEOUT, MCPT_EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
-MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C = range(4)
-PRECISIONS = {"fp64": MCPT_FP64, "tf32": MCPT_TF32, "bf16x3": MCPT_BF16X3, "fp32c": MCPT_FP32C}
+MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C, MCPT_BF16X2 = range(5)
+PRECISIONS = {"fp64": MCPT_FP64, "tf32": MCPT_TF32, "bf16x3": MCPT_BF16X3, "fp32c": MCPT_FP32C,
+              "bf16x2": MCPT_BF16X2}
 MCPT_AO_FULL, MCPT_AO_BLOCKS, MCPT_AO_PACKED = 0, 1, 2
 MCPT_UPDATE_ASYNC = 1
 

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <memory>
 #include <set>
 #include <sstream>
 #include <string>
@@ -104,12 +105,8 @@ struct mcpt_ctx {
     char* arena_ptr = nullptr;
     size_t arena_left = 0;
 
-    DimerDesc* dDesc = nullptr;
-    size_t capDesc = 0;
-    void* dH = nullptr;
+    void* dH = nullptr;              // first-half result of one wave (shared by every plan)
     size_t capH = 0;
-    void* dWork = nullptr;
-    size_t capWork = 0;
     void* dVT = nullptr;             // coupling: every dimer's (ia|jb) and T = vD
     size_t capVT = 0;
     void* dCoup = nullptr;           // coupling tables: tiles, per-dimer info, monomer sizes, R offsets
@@ -127,12 +124,6 @@ struct mcpt_ctx {
     long long s_parts = 0;           // sum over dimers of o_X v_X + o_Y v_Y
     std::vector<long long> r_off;    // host copy of the R offsets
     bool coupled = false;            // R holds the coupling of the current integrals
-    int* dFold = nullptr;            // split dimers: (dimer, first block slot, blocks)
-    size_t capFold = 0;
-    void* dFin = nullptr;            // second-half tasks of waves above 32 AO (+ first-task indices)
-    size_t capFin = 0;
-    double* dPart = nullptr;         // their FP64 partial sums
-    size_t capPart = 0;
     double* dE2 = nullptr;
     size_t capE2 = 0;
     double* dMon = nullptr;
@@ -143,7 +134,6 @@ struct mcpt_ctx {
     double* dTot = nullptr;
     int* dFlag = nullptr;            // [0] validation flag, [1] device wait status
 
-    std::vector<DimerDesc> hDesc;
     struct Wave {
         int b, nd, max_rows, max_occ, max_ao;
         TcLaunch tc;
@@ -151,10 +141,31 @@ struct mcpt_ctx {
         int ntasks;                  // 0: one CTA per dimer (<= 32 AO)
         size_t part_off;             // first partial (pairs of doubles) in dPart
     };
+    // A plan is the host work of a run that does not change between runs of
+    // the same dimer range and precision (descriptors, waves, tensor maps and
+    // work items, second-half tasks, the captured graph), with the device
+    // buffers only it uses.  The context keeps several, so that runs that
+    // alternate between ranges (waves of a streamed lattice) replan nothing.
+    // A plan also names buffers every plan shares (dH, dE2, dMon, dLists, the
+    // coefficient pools, the coupling arrays); when one of those is
+    // reallocated `epoch` advances and plans built before it are rebuilt.
     struct Plan {
         bool valid = false;
+        unsigned long long epoch = 0;      // the context's buffer epoch the plan was built against
+        unsigned long long last_use = 0;
         mcpt_precision prec = MCPT_FP64;
         int first = 0, count = 0;
+        std::vector<DimerDesc> hDesc;
+        DimerDesc* dDesc = nullptr;
+        size_t capDesc = 0;
+        void* dWork = nullptr;             // tensor maps and work items of the tensor-core waves
+        size_t capWork = 0;
+        int* dFold = nullptr;              // split dimers: (dimer, first block slot, blocks)
+        size_t capFold = 0;
+        void* dFin = nullptr;              // second-half tasks of waves above 32 AO (+ first-task indices)
+        size_t capFin = 0;
+        double* dPart = nullptr;           // their FP64 partial sums
+        size_t capPart = 0;
         std::vector<Wave> waves;
         double alg_bytes = 0, alg_flops = 0, alg_flops_half = 0;
         int nfold = 0;                     // split dimers whose block results are folded
@@ -165,7 +176,10 @@ struct mcpt_ctx {
         size_t off_stiles = 0, off_soff = 0, off_poff = 0;
         cudaGraphExec_t graph = nullptr;   // the plan's launch sequence, captured on first use
         int graph_launches = 0;
-    } plan;
+    };
+    std::vector<std::unique_ptr<Plan>> plans;
+    Plan* coup = nullptr;                  // the plan whose run formed the current coupling
+    unsigned long long epoch = 1, use_clock = 0;
     RunEvents rev;
     mcpt_run_stats stats{};
     bool ran = false;
@@ -233,6 +247,37 @@ mcpt_status ensure(mcpt_ctx* h, T** p, size_t* cap, size_t bytes)
     return MCPT_OK;
 }
 
+// A grow-only buffer that plans name: reallocating it advances the epoch, so
+// the plans (and graphs) built against the old address are rebuilt.
+template <typename T>
+mcpt_status ensure_shared(mcpt_ctx* h, T** p, size_t* cap, size_t bytes)
+{
+    if (*cap >= bytes && *p) return MCPT_OK;
+    h->epoch++;
+    return ensure(h, p, cap, bytes);
+}
+
+void free_plan(mcpt_ctx* h, mcpt_ctx::Plan* P)
+{
+    if (P->graph) cudaGraphExecDestroy(P->graph);
+    dev_free(h, P->dDesc, P->capDesc);
+    dev_free(h, P->dWork, P->capWork);
+    dev_free(h, P->dFold, P->capFold);
+    dev_free(h, P->dFin, P->capFin);
+    dev_free(h, P->dPart, P->capPart);
+    *P = mcpt_ctx::Plan{};
+}
+
+// Forget every plan (the dimer or monomer set changed, or integral addresses
+// did): their descriptors, slots and tensor maps no longer hold.
+void drop_plans(mcpt_ctx* h)
+{
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& P : h->plans) free_plan(h, P.get());
+    h->plans.clear();
+    h->coup = nullptr;
+}
+
 // Bump allocation from 256-byte aligned arena chunks (integral blocks owned
 // by the library live here until mcpt_destroy).
 mcpt_status arena_alloc(mcpt_ctx* h, size_t bytes, void** out)
@@ -266,7 +311,9 @@ bool all_finite(const double* x, size_t n)
     return true;
 }
 
-bool is_tensor_form(mcpt_precision p) { return p == MCPT_TF32 || p == MCPT_BF16X3; }
+bool is_tensor_form(mcpt_precision p) { return p == MCPT_TF32 || p == MCPT_BF16X3 || p == MCPT_BF16X2; }
+
+TcKind tc_kind_of(mcpt_precision p) { return p == MCPT_TF32 ? TC_TF32 : p == MCPT_BF16X2 ? TC_BF16X2 : TC_BF16X3; }
 
 // Occupied pairs padded to 16 (N of the Kronecker tensor-core GEMM).
 int npad_for(int oX, int oY) { return (oX * oY + 15) / 16 * 16; }
@@ -289,6 +336,7 @@ mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY)
         return MCPT_OK;
     case MCPT_TF32:
     case MCPT_BF16X3:
+    case MCPT_BF16X2:
         if ((nX & 1) || (nY & 1) || nX > kMaxAOTensor || nY > kMaxAOTensor)
             return fail(h, MCPT_EUNSUPPORTED,
                         "dimer %d: tensor-core forms need even AO counts <= %d (got %d, %d)", d,
@@ -328,7 +376,7 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     mcpt_options o;
     mcpt_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < MCPT_FP64 || o.precision > MCPT_FP32C)
+    if (o.precision < MCPT_FP64 || o.precision > MCPT_BF16X2)
         return fail(nullptr, MCPT_EINVAL, "mcpt_create: bad precision %d", (int)o.precision);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -394,7 +442,7 @@ mcpt_status mcpt_add_monomer(mcpt_handle h, const double* C, const double* eps, 
     h->hE.insert(h->hE.end(), eps, eps + nao);
     h->mons.push_back(m);
     h->mon_dirty = true;
-    h->plan.valid = false;
+    drop_plans(h);
     h->lists_dirty = true;
     if (id_out) *id_out = (int)h->mons.size() - 1;
     return MCPT_OK;
@@ -602,7 +650,7 @@ mcpt_status mcpt_add_dimer(mcpt_handle h, int X, int Y, const double* ao, mcpt_a
     h->dims.push_back(r);
     h->pairs.insert(key);
     h->coupled = false;
-    h->plan.valid = false;
+    drop_plans(h);
     h->lists_dirty = true;
     if (id_out) *id_out = (int)h->dims.size() - 1;
     return MCPT_OK;
@@ -630,7 +678,7 @@ mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double* ao, mcpt_ao_l
     if (st) return st;
     if (on_device && !packed) r.owned = old.owned;     // keep the storage for a later host update
     if (r.E[0] != old.E[0] || r.E[1] != old.E[1] || std::memcmp(r.st, old.st, sizeof r.st))
-        h->plan.valid = false;              // the tensor maps name the old addresses
+        drop_plans(h);                      // the tensor maps name the old addresses
     h->dims[id] = r;
     h->coupled = false;
     return MCPT_OK;
@@ -639,20 +687,19 @@ mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double* ao, mcpt_ao_l
 mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p)
 {
     if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_set_precision: NULL handle");
-    if (p < MCPT_FP64 || p > MCPT_FP32C) return fail(h, MCPT_EINVAL, "mcpt_set_precision: bad precision %d", (int)p);
-    if (h->prec != p) h->plan.valid = false;
-    h->prec = p;
+    if (p < MCPT_FP64 || p > MCPT_BF16X2) return fail(h, MCPT_EINVAL, "mcpt_set_precision: bad precision %d", (int)p);
+    h->prec = p;                            // plans are kept per precision
     return MCPT_OK;
 }
 
 static mcpt_status upload_static(mcpt_handle h)
 {
     if (h->mon_dirty) {
-        mcpt_status st = ensure(h, &h->dC, &h->capC, h->hC.size() * sizeof(double));
+        mcpt_status st = ensure_shared(h, &h->dC, &h->capC, h->hC.size() * sizeof(double));
         if (st) return st;
-        st = ensure(h, &h->dE, &h->capE, h->hE.size() * sizeof(double));
+        st = ensure_shared(h, &h->dE, &h->capE, h->hE.size() * sizeof(double));
         if (st) return st;
-        st = ensure(h, &h->dCf, &h->capCf, h->hC.size() * sizeof(float));
+        st = ensure_shared(h, &h->dCf, &h->capCf, h->hC.size() * sizeof(float));
         if (st) return st;
         std::vector<float> cf(h->hC.begin(), h->hC.end());
         CK(h, cudaMemcpyAsync(h->dC, h->hC.data(), h->hC.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -673,7 +720,7 @@ static mcpt_status upload_static(mcpt_handle h)
             lists[N + 1 + fill[h->dims[d].X]++] = d;
             lists[N + 1 + fill[h->dims[d].Y]++] = d;
         }
-        mcpt_status st = ensure(h, &h->dLists, &h->capLists, lists.size() * sizeof(int));
+        mcpt_status st = ensure_shared(h, &h->dLists, &h->capLists, lists.size() * sizeof(int));
         if (st) return st;
         CK(h, cudaMemcpyAsync(h->dLists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
@@ -713,7 +760,7 @@ static std::string tune_key(mcpt_ctx* h, mcpt_precision prec, const DimerDesc* d
     for (auto& c : dev)
         if (c == ' ') c = '_';
     char buf[160];
-    snprintf(buf, sizeof buf, "%s:%s:%d:%016llx", prec == MCPT_TF32 ? "tf32" : "bf16x3", dev.c_str(), nd, f);
+    snprintf(buf, sizeof buf, "%s:%s:%d:%016llx", prec == MCPT_TF32 ? "tf32" : prec == MCPT_BF16X2 ? "bf16x2" : "bf16x3", dev.c_str(), nd, f);
     return buf;
 }
 
@@ -734,11 +781,11 @@ static void tune_load(mcpt_ctx* h)
 
 // Time every candidate launch of wave `wv` on the handle's stream (one
 // warm-up launch, then three timed ones) and return the fastest.
-static mcpt_status tune_wave(mcpt_handle h, TcKind kind, const mcpt_ctx::Wave& wv, void* work, size_t work_bytes,
-                             TcTune* best, float* best_ms)
+static mcpt_status tune_wave(mcpt_handle h, const mcpt_ctx::Plan& P, TcKind kind, const mcpt_ctx::Wave& wv,
+                             void* work, size_t work_bytes, TcTune* best, float* best_ms)
 {
     TcTune cand[16];
-    const int n = tc_candidates(kind, h->hDesc.data() + wv.b, wv.nd, cand, 16);
+    const int n = tc_candidates(kind, P.hDesc.data() + wv.b, wv.nd, cand, 16);
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
@@ -747,7 +794,7 @@ static mcpt_status tune_wave(mcpt_handle h, TcKind kind, const mcpt_ctx::Wave& w
     for (int c = 0; c < n; c++) {
         TcLaunch L{};
         char err[256] = {0};
-        if (tc_prepare(kind, h->hDesc.data() + wv.b, h->dDesc + wv.b, wv.nd, h->dCf, static_cast<float*>(h->dH),
+        if (tc_prepare(kind, P.hDesc.data() + wv.b, P.dDesc + wv.b, wv.nd, h->dCf, static_cast<float*>(h->dH),
                        work, work_bytes, h->dFlag + 1, h->stream, &cand[c], &L, err, sizeof err) != cudaSuccess)
             continue;
         cudaError_t e = tc_launch(L, h->stream);
@@ -773,12 +820,11 @@ static mcpt_status tune_wave(mcpt_handle h, TcKind kind, const mcpt_ctx::Wave& w
     return MCPT_OK;
 }
 
-static mcpt_status build_plan(mcpt_handle h, int first, int count)
+static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int count)
 {
     const int D = (int)h->dims.size();
     const int N = (int)h->mons.size();
     const mcpt_precision prec = h->prec;
-    auto& P = h->plan;
     P.valid = false;
     P.waves.clear();
     if (P.graph) {
@@ -786,7 +832,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         P.graph = nullptr;
     }
 
-    h->hDesc.clear();
+    P.hDesc.clear();
     // the coupling needs every dimer's amplitudes at once: full runs only
     const bool coupled_plan = h->coupling && first == 0 && count == D;
     long long vt_total = 0;
@@ -838,7 +884,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
                 dd.slot = bx * by > 1 ? D + nblk_extra++ : d;
                 const size_t hb = hbytes_for(prec, dd.nX, dd.nY, dd.oX, dd.oY);
                 const size_t elem = prec == MCPT_FP64 ? 8 : 4;
-                const int kk = (int)h->hDesc.size();
+                const int kk = (int)P.hDesc.size();
                 if (kk > wbeg && (wave_h + hb > h->wave_bytes || kk - wbeg >= 65535)) {
                     waves.emplace_back(wbeg, kk);
                     max_wave_h = std::max(max_wave_h, wave_h);
@@ -847,7 +893,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
                 }
                 dd.h_off = (long long)(wave_h / elem);
                 wave_h += hb;
-                h->hDesc.push_back(dd);
+                P.hDesc.push_back(dd);
             }
         const double nx = mX.nao, ny = mY.nao, ox = mX.nocc, oy = mY.nocc, vx = nx - ox, vy = ny - oy;
         alg_bytes += 2.0 * nx * nx * ny * ny * 8.0;
@@ -855,15 +901,15 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
                                   ox * vx * oy * vy * nx);
         alg_flops_half += 2.0 * 2.0 * (nx * nx * ny * ny * oy + ox * nx * nx * ny * oy);
     }
-    const int ndesc = (int)h->hDesc.size();
+    const int ndesc = (int)P.hDesc.size();
     waves.emplace_back(wbeg, ndesc);
     max_wave_h = std::max(max_wave_h, wave_h);
 
     mcpt_status st = upload_static(h);
     if (st) return st;
-    if ((st = ensure(h, &h->dDesc, &h->capDesc, ndesc * sizeof(DimerDesc)))) return st;
-    if ((st = ensure(h, &h->dH, &h->capH, max_wave_h))) return st;
-    if (!fold.empty() && (st = ensure(h, &h->dFold, &h->capFold, fold.size() * sizeof(int)))) return st;
+    if ((st = ensure(h, &P.dDesc, &P.capDesc, ndesc * sizeof(DimerDesc)))) return st;
+    if ((st = ensure_shared(h, &h->dH, &h->capH, max_wave_h))) return st;
+    if (!fold.empty() && (st = ensure(h, &P.dFold, &P.capFold, fold.size() * sizeof(int)))) return st;
     // per-dimer results, then the results of split dimers' blocks (kept across
     // plans: a larger array copies the dimers' results over)
     const size_t e2_bytes = (size_t)2 * (D + nblk_extra) * sizeof(double);
@@ -880,23 +926,24 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         }
         h->dE2 = static_cast<double*>(q);
         h->capE2 = e2_bytes;
+        h->epoch++;
     }
-    if ((st = ensure(h, &h->dMon, &h->capMon, (size_t)2 * N * sizeof(double) + 2 * sizeof(double)))) return st;
+    if ((st = ensure_shared(h, &h->dMon, &h->capMon, (size_t)2 * N * sizeof(double) + 2 * sizeof(double)))) return st;
     h->dTot = h->dMon + 2 * N;
     std::vector<size_t> work_off;
     if (is_tensor_form(prec)) {
         size_t total = 0;
         for (auto& w : waves) {
             work_off.push_back(total);
-            total += (tc_work_bytes(prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3, h->hDesc.data() + w.first, w.second - w.first) + 255) & ~(size_t)255;
+            total += (tc_work_bytes(tc_kind_of(prec), P.hDesc.data() + w.first, w.second - w.first) + 255) & ~(size_t)255;
         }
-        if ((st = ensure(h, &h->dWork, &h->capWork, total))) return st;
+        if ((st = ensure(h, &P.dWork, &P.capWork, total))) return st;
     }
     P.coupling = coupled_plan;
     P.ntile[0] = P.ntile[1] = P.ntile[2] = 0;
     if (coupled_plan) {
         const size_t elem = prec == MCPT_FP64 ? sizeof(double) : sizeof(float);
-        if ((st = ensure(h, &h->dVT, &h->capVT, (size_t)vt_total * elem))) return st;
+        if ((st = ensure_shared(h, &h->dVT, &h->capVT, (size_t)vt_total * elem))) return st;
         // tables: output tiles, per-dimer info, monomer sizes o v, R offsets
         std::vector<CoupDim> cds(D);
         std::vector<int> mdim(N);
@@ -973,14 +1020,14 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         P.off_stiles = put(stiles.data(), stiles.size() * sizeof(SingTile));
         P.off_soff = put(soff.data(), soff.size() * sizeof(long long));
         P.off_poff = put(poff.data(), poff.size() * sizeof(long long));
-        if ((st = ensure(h, &h->dCoup, &h->capCoup, tab.size()))) return st;
-        if ((st = ensure(h, &h->dR, &h->capR, (size_t)roff * sizeof(double)))) return st;
+        if ((st = ensure_shared(h, &h->dCoup, &h->capCoup, tab.size()))) return st;
+        if ((st = ensure_shared(h, &h->dR, &h->capR, (size_t)roff * sizeof(double)))) return st;
         CK(h, cudaMemcpyAsync(h->dCoup, tab.data(), tab.size(), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));   // tab is pageable and goes out of scope
     }
-    CK(h, cudaMemcpyAsync(h->dDesc, h->hDesc.data(), ndesc * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(P.dDesc, P.hDesc.data(), ndesc * sizeof(DimerDesc), cudaMemcpyHostToDevice, h->stream));
     if (!fold.empty())
-        CK(h, cudaMemcpyAsync(h->dFold, fold.data(), fold.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(P.dFold, fold.data(), fold.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
     P.nfold = (int)fold.size() / 3;
 
     // second-half tasks of the waves with monomers above 32 AO: [tasks][first-task index per dimer]
@@ -991,10 +1038,10 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
     for (size_t w = 0; w < waves.size(); w++) {
         const int b = waves[w].first, nd = waves[w].second - b;
         int max_ao = 0;
-        for (int k = b; k < b + nd; k++) max_ao = std::max(max_ao, std::max(h->hDesc[k].nX, h->hDesc[k].nY));
+        for (int k = b; k < b + nd; k++) max_ao = std::max(max_ao, std::max(P.hDesc[k].nX, P.hDesc[k].nY));
         if (max_ao <= 32) continue;
         std::vector<FinTask> t;
-        finish_tasks(h->hDesc.data() + b, nd, 1 << 22, &t);
+        finish_tasks(P.hDesc.data() + b, nd, 1 << 22, &t);
         std::vector<int> first(nd);
         for (size_t q = 0; q < t.size(); q++)
             if (t[q].pr0 == 0) first[t[q].dimer] = (int)q;
@@ -1009,9 +1056,9 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         parts += t.size();
     }
     if (!fin_host.empty()) {
-        if ((st = ensure(h, &h->dFin, &h->capFin, fin_host.size()))) return st;
-        if ((st = ensure(h, &h->dPart, &h->capPart, parts * 2 * sizeof(double)))) return st;
-        CK(h, cudaMemcpyAsync(h->dFin, fin_host.data(), fin_host.size(), cudaMemcpyHostToDevice, h->stream));
+        if ((st = ensure(h, &P.dFin, &P.capFin, fin_host.size()))) return st;
+        if ((st = ensure(h, &P.dPart, &P.capPart, parts * 2 * sizeof(double)))) return st;
+        CK(h, cudaMemcpyAsync(P.dFin, fin_host.data(), fin_host.size(), cudaMemcpyHostToDevice, h->stream));
         CK(h, cudaStreamSynchronize(h->stream));   // fin_host is pageable and goes out of scope
     }
 
@@ -1023,27 +1070,27 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
         wv.ntasks = ntasks[w];
         wv.part_off = part_off[w];
         for (int k = wv.b; k < wv.b + wv.nd; k++) {
-            const DimerDesc& dd = h->hDesc[k];
+            const DimerDesc& dd = P.hDesc[k];
             wv.max_rows = std::max(wv.max_rows, dd.nX * dd.nY);
             wv.max_occ = std::max(wv.max_occ, std::max(dd.oX, dd.oY));
             wv.max_ao = std::max(wv.max_ao, std::max(dd.nX, dd.nY));
         }
         if (is_tensor_form(prec)) {
             char tcerr[256] = {0};
-            const size_t end = (w + 1 < work_off.size()) ? work_off[w + 1] : h->capWork;
-            const TcKind kind = prec == MCPT_TF32 ? TC_TF32 : TC_BF16X3;
-            void* work = static_cast<char*>(h->dWork) + work_off[w];
+            const size_t end = (w + 1 < work_off.size()) ? work_off[w + 1] : P.capWork;
+            const TcKind kind = tc_kind_of(prec);
+            void* work = static_cast<char*>(P.dWork) + work_off[w];
             TcTune tune{};
             bool tuned = false;
             if (!h->tune_cache.empty()) {
                 tune_load(h);
-                const std::string key = tune_key(h, prec, h->hDesc.data() + wv.b, wv.nd);
+                const std::string key = tune_key(h, prec, P.hDesc.data() + wv.b, wv.nd);
                 auto it = h->tuned.find(key);
                 if (it != h->tuned.end()) {
                     tune = it->second;
                 } else {
                     float ms = 0;
-                    mcpt_status st2 = tune_wave(h, kind, wv, work, end - work_off[w], &tune, &ms);
+                    mcpt_status st2 = tune_wave(h, P, kind, wv, work, end - work_off[w], &tune, &ms);
                     if (st2) return st2;
                     h->tuned[key] = tune;
                     std::ofstream out(h->tune_cache, std::ios::app);
@@ -1052,7 +1099,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
                 }
                 tuned = tune.variant1 != 0;
             }
-            cudaError_t e = tc_prepare(kind, h->hDesc.data() + wv.b, h->dDesc + wv.b, wv.nd, h->dCf,
+            cudaError_t e = tc_prepare(kind, P.hDesc.data() + wv.b, P.dDesc + wv.b, wv.nd, h->dCf,
                                        static_cast<float*>(h->dH), work, end - work_off[w], h->dFlag + 1,
                                        h->stream, tuned ? &tune : nullptr, &wv.tc, tcerr, sizeof tcerr);
             if (e != cudaSuccess)
@@ -1068,6 +1115,7 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
     P.alg_flops = alg_flops;
     P.alg_flops_half = alg_flops_half;
     P.valid = true;
+    P.epoch = h->epoch;
     return MCPT_OK;
 }
 
@@ -1075,19 +1123,19 @@ static mcpt_status build_plan(mcpt_handle h, int first, int count)
 // (no host synchronisation, no allocation): status reset, then per wave the
 // first half and the second half, then the per-monomer reduction.  With `ev`
 // (timing), CUDA events are recorded around the phases.
-static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev, int* launches_out)
+static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std::vector<cudaEvent_t>* ev,
+                               int* launches_out)
 {
-    const auto& P = h->plan;
     const int D = (int)h->dims.size();
     const int N = (int)h->mons.size();
-    const mcpt_precision prec = h->prec;
+    const mcpt_precision prec = P.prec;
     const size_t W = P.waves.size();
     CK(h, cudaMemsetAsync(h->dFlag + 1, 0, sizeof(int), h->stream));
     if (ev) CK(h, cudaEventRecord((*ev)[0], h->stream));
     int launches = 0;
     for (size_t w = 0; w < W; w++) {
         const auto& wv = P.waves[w];
-        const DimerDesc* wd = h->dDesc + wv.b;
+        const DimerDesc* wd = P.dDesc + wv.b;
         switch (prec) {
         case MCPT_FP64:
             CK(h, launch_half_fp64(wd, wv.nd, wv.max_rows, wv.max_occ, h->dC, static_cast<double*>(h->dH), h->stream));
@@ -1097,14 +1145,15 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
             break;
         case MCPT_TF32:
         case MCPT_BF16X3:
+        case MCPT_BF16X2:
             CK(h, tc_launch(wv.tc, h->stream));
             break;
         }
         launches++;
         if (ev) CK(h, cudaEventRecord((*ev)[1 + 2 * w], h->stream));
         const FinTask* tasks =
-            wv.ntasks ? reinterpret_cast<const FinTask*>(static_cast<const char*>(h->dFin) + wv.fin_off) : nullptr;
-        double* part = wv.ntasks ? h->dPart + 2 * wv.part_off : nullptr;
+            wv.ntasks ? reinterpret_cast<const FinTask*>(static_cast<const char*>(P.dFin) + wv.fin_off) : nullptr;
+        double* part = wv.ntasks ? P.dPart + 2 * wv.part_off : nullptr;
         if (prec == MCPT_FP64)
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
                                      tasks, wv.ntasks, part, P.coupling ? static_cast<double*>(h->dVT) : nullptr,
@@ -1117,7 +1166,7 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
         if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
     }
     if (P.nfold) {
-        CK(h, launch_fold(h->dFold, P.nfold, h->dE2, h->stream));
+        CK(h, launch_fold(P.dFold, P.nfold, h->dE2, h->stream));
         launches++;
     }
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
@@ -1142,14 +1191,59 @@ static mcpt_status enqueue_run(mcpt_handle h, const std::vector<cudaEvent_t>* ev
     return MCPT_OK;
 }
 
+// Plans kept per context; beyond this the least recently used is rebuilt.
+constexpr size_t kMaxPlans = 64;
+
+// The plan of (first, count, precision): a cached one that is still valid,
+// else one (re)built, reusing the stale entry of the same key or the least
+// recently used slot.
+static mcpt_status get_plan(mcpt_handle h, int first, int count, mcpt_ctx::Plan** out)
+{
+    mcpt_ctx::Plan* hit = nullptr;
+    for (auto& p : h->plans)
+        if (p->first == first && p->count == count && p->prec == h->prec && (p->valid || !hit)) {
+            hit = p.get();
+            if (p->valid) break;
+        }
+    if (!hit || !hit->valid || hit->epoch != h->epoch) {
+        if (!hit) {
+            if (h->plans.size() < kMaxPlans) {
+                h->plans.emplace_back(new mcpt_ctx::Plan());
+                hit = h->plans.back().get();
+            } else {
+                hit = h->plans[0].get();
+                for (auto& p : h->plans)
+                    if (p->last_use < hit->last_use) hit = p.get();
+                CK(h, cudaStreamSynchronize(h->stream));   // its buffers may still be in use
+                if (h->coup == hit) h->coup = nullptr;
+            }
+        }
+        if (hit->graph) {
+            CK(h, cudaStreamSynchronize(h->stream));
+            cudaGraphExecDestroy(hit->graph);
+            hit->graph = nullptr;
+        }
+        hit->prec = h->prec;
+        hit->first = first;
+        hit->count = count;
+        mcpt_status st = build_plan(h, *hit, first, count);
+        if (st) {
+            hit->valid = false;
+            return st;
+        }
+    }
+    hit->last_use = ++h->use_clock;
+    *out = hit;
+    return MCPT_OK;
+}
+
 static mcpt_status run_impl(mcpt_handle h, int first, int count)
 {
     CK(h, cudaSetDevice(h->device));
-    auto& P = h->plan;
-    if (!P.valid || P.first != first || P.count != count || P.prec != h->prec) {
-        mcpt_status st = build_plan(h, first, count);
-        if (st) return st;
-    }
+    mcpt_ctx::Plan* Pp = nullptr;
+    mcpt_status pst = get_plan(h, first, count, &Pp);
+    if (pst) return pst;
+    auto& P = *Pp;
     RunEvents& re = h->rev;
     const size_t W = P.waves.size();
     int launches = 0;
@@ -1167,14 +1261,14 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
                 ev.push_back(e);
             }
         }
-        mcpt_status st = enqueue_run(h, &ev, &launches);
+        mcpt_status st = enqueue_run(h, P, &ev, &launches);
         re.pending.push_back(std::move(ev));
         if (st) return st;
     } else if (h->graphs && cap == cudaStreamCaptureStatusNone) {
         // replay the plan's launches as one CUDA graph (captured on first use)
         if (!P.graph) {
             CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
-            mcpt_status st = enqueue_run(h, nullptr, &launches);
+            mcpt_status st = enqueue_run(h, P, nullptr, &launches);
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(h->stream, &g);
             if (st) {
@@ -1190,7 +1284,7 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
         CK(h, cudaGraphLaunch(P.graph, h->stream));
         launches = P.graph_launches;
     } else {
-        mcpt_status st = enqueue_run(h, nullptr, &launches);
+        mcpt_status st = enqueue_run(h, P, nullptr, &launches);
         if (st) return st;
     }
 
@@ -1203,6 +1297,7 @@ static mcpt_status run_impl(mcpt_handle h, int first, int count)
     h->stats.alg_flops_half = P.alg_flops_half;
     h->ran = true;
     h->coupled = P.coupling;
+    if (P.coupling) h->coup = &P;
     return MCPT_OK;
 }
 
@@ -1270,7 +1365,8 @@ mcpt_status mcpt_singles(mcpt_handle h, const double* t, double* s)
     if (!h->coupling) return fail(h, MCPT_ESTATE, "mcpt_singles: the context was created with coupling = 0");
     if (!h->coupled)
         return fail(h, MCPT_ESTATE, "mcpt_singles: no mcpt_run of every dimer since the integrals last changed");
-    const mcpt_ctx::Plan& P = h->plan;
+    if (!h->coup) return fail(h, MCPT_ESTATE, "mcpt_singles: no coupling plan");
+    const mcpt_ctx::Plan& P = *h->coup;
     const size_t M = (size_t)h->s_total;
     if (h->validate && !all_finite(t, M)) return fail(h, MCPT_EINVAL, "mcpt_singles: t has a non-finite value");
     if (M == 0) return MCPT_OK;
@@ -1726,16 +1822,12 @@ void mcpt_destroy(mcpt_handle h)
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    if (h->plan.graph) cudaGraphExecDestroy(h->plan.graph);
+    for (auto& P : h->plans) free_plan(h, P.get());
     for (void* p : h->owned) cudaFree(p);
     cudaFree(h->dC);
     cudaFree(h->dCf);
     cudaFree(h->dE);
-    cudaFree(h->dDesc);
     cudaFree(h->dH);
-    cudaFree(h->dWork);
-    cudaFree(h->dFin);
-    cudaFree(h->dFold);
     cudaFree(h->dVT);
     cudaFree(h->dCoup);
     cudaFree(h->dR);
@@ -1753,7 +1845,6 @@ void mcpt_destroy(mcpt_handle h)
         if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
-    cudaFree(h->dPart);
     cudaFree(h->dE2);
     cudaFree(h->dMon);
     cudaFree(h->dLists);

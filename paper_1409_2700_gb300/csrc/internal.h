@@ -250,7 +250,7 @@ cudaError_t launch_check_finite4(const double* x, const int dims[4], const long 
 void set_thread_error(const char* msg);
 
 // ---- tensor-core first half (tcgen05) ----
-enum TcKind { TC_TF32 = 0, TC_BF16X3 = 1 };
+enum TcKind { TC_TF32 = 0, TC_BF16X3 = 1, TC_BF16X2 = 2 };
 
 // Everything one launch of the tensor-core kernel needs; filled by
 // tc_prepare (host work: tensor maps, work items, their upload), replayed by

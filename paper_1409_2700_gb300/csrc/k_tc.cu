@@ -82,7 +82,7 @@ struct TcParams {
     unsigned int f_stage_bytes;    // bytes per staging slot
     unsigned int w_stage_bytes;    // bytes per W slot
     unsigned int tmem_cols;
-    int kind;                      // TC_TF32 / TC_BF16X3
+    int kind;                      // TC_TF32 / TC_BF16X3 / TC_BF16X2
     int kcs_max;                   // largest p2 chunk count of the launch (rank variant)
 };
 
@@ -688,7 +688,7 @@ struct __align__(8) RankShared {
 
 // TMEM columns of one p0 unit and units in the ring.
 template <int KIND, bool BIG>
-__host__ __device__ constexpr int unit_cols() { return KIND == TC_BF16X3 ? 4 * kNT : kNT; }
+__host__ __device__ constexpr int unit_cols() { return KIND != TC_TF32 ? 4 * kNT : kNT; }
 template <int KIND, bool BIG>
 __host__ __device__ constexpr int n_units() { return (BIG ? 256 : 512) / unit_cols<KIND, BIG>(); }
 // Shared bytes of the A ring (two slots; BF16x3 uses two tiles per slot) and
@@ -700,11 +700,11 @@ __host__ __device__ constexpr size_t a_ring_bytes(int kind) { return 2 * (size_t
 // chunk kc in bytes 64 (kc % 2) .. +63 of the row.
 __host__ __device__ constexpr size_t w_stride_bytes(int kind, int kcs_max)
 {
-    return kind == TC_BF16X3 ? (size_t)((kcs_max + 1) / 2) * 64 * 128 : (size_t)kcs_max * 2 * kNT * 128;
+    return kind != TC_TF32 ? (size_t)((kcs_max + 1) / 2) * 64 * 128 : (size_t)kcs_max * 2 * kNT * 128;
 }
 __host__ __device__ constexpr size_t fx_scale_bytes(int kind)
 {
-    return kind == TC_BF16X3 ? kFxUnits * (128 + kNT) * 4 + 2 * 16 * kNT * 4 : 0;
+    return kind != TC_TF32 ? kFxUnits * (128 + kNT) * 4 + 2 * 16 * kNT * 4 : 0;
 }
 
 // ---- BF16x3 fixed-point digits
@@ -932,6 +932,62 @@ __device__ __forceinline__ int convert_row_fx1(const double* __restrict__ F, uns
     return emax;
 }
 
+// BF16x2: row r of one staged box as the two digit planes of a 16-bit fixed
+// point, tile [d0 | d1] (bytes 0-63 / 64-127), chunks c0 and c0 + 2 of 8 p2.
+// Only the high word of each double is read: its 20 mantissa bits hold every
+// bit above the rounding position.  The row chunk's largest exponent field
+// emax (bitwise maximum of |hi|, combined with the partner lane l ^ 16) fixes
+// y = |x| 2^(15 - e), e = emax - 1023, built on the integer pipes (the
+// exponent moved by 142 - emax modulo 2^9; elements below 2^-141 of the
+// row's largest, and invalid rows, become 0).  N = floor(y + 1/2): half up in
+// magnitude, so a truncated value that sits exactly on a half rounds away
+// from zero as the full double would (the dropped low word only adds
+// magnitude).  Balanced digits N = 256 d0 + d1, d0 = rne(N / 256) in
+// [0, 256], d1 in [-128, 128], exact in BF16; the sign of x goes on both.
+__device__ __forceinline__ int convert_row_fx2(const double* __restrict__ F, unsigned char* __restrict__ A,
+                                               const ConvRow& cr, int n3, int c0)
+{
+    const unsigned* __restrict__ hw = reinterpret_cast<const unsigned*>(F + cr.src) + 1;
+    unsigned h[2][8];
+    unsigned m = 0;
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            h[q][e] = hw[2 * ((c0 + 2 * q) * 8 + e) * n3];
+            m = max(m, h[q][e] & 0x7FFFFFFFu);
+        }
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    const int emax = cr.valid ? (int)(m >> 20) : 0;
+    const unsigned add = (unsigned)((142 - emax) & 511) << 23;
+    const unsigned thr = cr.valid ? (unsigned)max(1, emax - 141) << 20 : 0xFFFFFFFFu;
+    const float2 half = make_float2(0.5f, 0.5f);
+    const float2 magic = make_float2(12582912.0f, 12582912.0f);      // 1.5 * 2^23
+    const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int c = c0 + 2 * q;
+        unsigned w0[4], w1[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const unsigned ha = h[q][e], hb = h[q][e + 1];
+            float2 y;
+            y.x = (ha & 0x7FFFFFFFu) < thr ? 0.f : __uint_as_float(ha * 8u + add);
+            y.y = (hb & 0x7FFFFFFFu) < thr ? 0.f : __uint_as_float(hb * 8u + add);
+            const float2 u = __fadd2_rn(y, half);                                   // exact
+            const float2 d0 = __fadd2_rn(__ffma2_rn(u, make_float2(0x1p-8f, 0x1p-8f), magic), nmagic);
+            const float2 r = __ffma2_rn(d0, make_float2(-256.0f, -256.0f), u);        // exact
+            const float2 d1 = __fadd2_rn(__fadd2_rd(r, magic), nmagic);              // floor(r)
+            const unsigned sg = __byte_perm(ha, hb, 0x7030) & 0x80008000u;           // sign bits of both
+            w0[e / 2] = pack_bf16(d0.x, d0.y) ^ sg;
+            w1[e / 2] = pack_bf16(d1.x, d1.y) ^ sg;
+        }
+        *reinterpret_cast<uint4*>(A + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4*>(A + cr.dst + (((4 + c) ^ cr.r7) << 4)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    }
+    return emax;
+}
+
 // T[row][j] of one p0 for this lane's row: TF32 reads the p0's unit; BF16x3
 // adds the units of the p2 chunks in chunk order (FP32, round to nearest).
 // Frees each unit's slot after reading it.  False on timeout/abort.
@@ -940,11 +996,11 @@ __device__ __forceinline__ bool load_p0_T(float (&T)[16], RankShared* sh, unsign
                                           const float* exps, const float* scu, int r, int lane, volatile int* abort,
                                           int* status)
 {
-    const int nunits = KIND == TC_BF16X3 ? kcs : 1;
+    const int nunits = KIND != TC_TF32 ? kcs : 1;
     for (int u = 0; u < nunits; u++, gS++) {
         const int s = gS % NS;
         if (!mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, status, 18)) return false;
-        if (KIND == TC_BF16X3 && !mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, status, 23)) return false;
+        if (KIND != TC_TF32 && !mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, status, 23)) return false;
         tc_fence_after();
         unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT, u > 0);
         tc_fence_before();
@@ -957,7 +1013,7 @@ __device__ __forceinline__ bool load_p0_T(float (&T)[16], RankShared* sh, unsign
 template <int KIND, bool BIG>
 __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams P)
 {
-    constexpr bool FX = KIND == TC_BF16X3;          // fixed-point digit planes
+    constexpr bool FX = KIND != TC_TF32;            // fixed-point digit planes (BF16x3, BF16x2)
     constexpr int UC = unit_cols<KIND, BIG>();      // TMEM columns per p0 unit
     constexpr int NS = n_units<KIND, BIG>();        // p0 units in the ring
     constexpr int CXW = BIG ? kOBig : kOB;          // staged C_X occupied columns per row
@@ -1087,11 +1143,11 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                 if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
                                 tc_fence_after();
                                 const unsigned dt = tmem + (unsigned)(s * UC);
-                                // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3]; the B tile
-                                // stacks C_Y's digits B0..B3 as rows 0-63.  A_u x [B0..B(3-u)] lands
-                                // A_u B_v in the slot of level u + v; A0's MMA opens all four slots.
+                                // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3] (BF16x3
+                                // only); the B tile stacks C_Y's digits B0..B3 as rows 0-63.
+                                // A_u x [B0..B(3-u)] lands A_u B_v in the slot of level u + v;
+                                // A0's MMA opens all four slots.
                                 const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
-                                const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
                                 const unsigned long long bk =
                                     sw128_desc(Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128) +
                                     (unsigned long long)((kc & 1) * 4);
@@ -1100,8 +1156,11 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                     const unsigned acc = k > 0 ? 1u : 0u;
                                     tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[0], acc);
                                     tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[1], 1u);
-                                    tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
-                                    tc_mma<KIND>(dt + 3 * kNT, a2 + 4 + 2 * k, bk + 2 * k, idesc_fx[3], 1u);
+                                    if constexpr (KIND == TC_BF16X3) {
+                                        const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
+                                        tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
+                                        tc_mma<KIND>(dt + 3 * kNT, a2 + 4 + 2 * k, bk + 2 * k, idesc_fx[3], 1u);
+                                    }
                                 }
                                 tc_commit(&sh->empty_a[as]);
                                 any = true;
@@ -1234,9 +1293,12 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                             if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
                                 break;
                             unsigned char* At = Ar + (size_t)as * ASLOT;
-                            const int emax = convert_row_fx1(
-                                reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes), At, At + kABytes, cr,
-                                g.n3, c0);
+                            const double* Fs = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
+                            int emax;
+                            if constexpr (KIND == TC_BF16X3)
+                                emax = convert_row_fx1(Fs, At, At + kABytes, cr, g.n3, c0);
+                            else
+                                emax = convert_row_fx2(Fs, At, cr, g.n3, c0);
                             fence_async_smem();
                             __syncwarp();
                             if (lane == 0) {
@@ -1417,6 +1479,7 @@ int choose_variant(TcKind kind, const DimerDesc* h, int nd)
         nymax = std::max(nymax, h[k].nY);
     }
     const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
+    if (kind == TC_BF16X2) return omax <= kOB ? 1 : 2;   // rank kernels only (the tensor-core size limits fit them)
     const char* env = getenv("MCPT_TC_KERNEL");
     if (env && !strcmp(env, "kron")) return 0;
     if (env && !strcmp(env, "rankbig") && fits_rank) return 2;
@@ -1620,8 +1683,16 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.kind = L.kind;
     P.kcs_max = L.kcs_max;
     void (*fn)(const TcParams);
-    if (L.variant == 1) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32, false> : k_half_tc_rank<TC_BF16X3, false>;
-    else if (L.variant == 2) fn = L.kind == TC_TF32 ? k_half_tc_rank<TC_TF32, true> : k_half_tc_rank<TC_BF16X3, true>;
+    if (L.variant == 1)
+        fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, false>
+             : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, false>
+                                   : k_half_tc_rank<TC_BF16X3, false>;
+    else if (L.variant == 2)
+        fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, true>
+             : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, true>
+                                   : k_half_tc_rank<TC_BF16X3, true>;
+    else if (L.kind == TC_BF16X2)
+        return cudaErrorNotSupported;   // the Kronecker kernel has no 16-bit fixed-point form
     else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
