@@ -224,5 +224,6 @@ extern "C" mcpt_status mcpt_dimer_fp64_noalloc(const double* A, const double* K,
     e = cudaGetLastError();
     if (e != cudaSuccess)
         return noalloc_fail(MCPT_ECUDA, "mcpt_dimer_fp64_noalloc: launch failed (CUDA error %lld)", (long long)e);
+    set_thread_error("");   // a successful call leaves no stale message for mcpt_last_error(NULL)
     return MCPT_OK;
 }

@@ -1,12 +1,13 @@
-"""The allocation-free entry point (mcpt_dimer_fp64_noalloc) against the
-handle-based path.  It is for callers that may not allocate device memory;
-its scratch is a fixed array inside the library, shared by every call, so
-this test makes several calls in a row with different dimers and checks each
-result -- a call that read leftovers of the previous one would show.  This
-file is collected last on purpose."""
+"""The allocation-free entry point (mcpt_dimer_fp64_noalloc) against the CPU
+oracle and the handle-based path.  It is for callers that may not allocate
+device memory; its scratch is a fixed array inside the library, shared by
+every call, so this test makes several calls in a row with different dimers
+and checks each result -- a call that read leftovers of the previous one
+would show.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from helpers import rand_dimer
 
@@ -36,7 +37,7 @@ def _noalloc(torch, A, K, CX, eX, CY, eY, oX, oY):
     return E2.cpu().numpy()
 
 
-def test_noalloc_matches_handle_path_on_consecutive_calls():
+def test_noalloc_matches_oracle_on_consecutive_calls():
     torch = pytest.importorskip("torch")
     w = synth.workload("lattice-2x2x2")
     cases = []
@@ -46,14 +47,19 @@ def test_noalloc_matches_handle_path_on_consecutive_calls():
         A, K = w.blocks(d)
         cases.append((A, K, mX.C, mX.eps, mY.C, mY.eps, mX.nocc, mY.nocc))
     rng = np.random.default_rng(21)
-    cases.append((*rand_dimer(rng, 7, 12, 3, 2), 3, 2))   # smaller, odd, non-symmetric
+    cases.append((*rand_dimer(rng, 7, 12, 3, 2), 3, 2))     # small, odd, non-symmetric
+    cases.append((*rand_dimer(rng, 96, 20, 7, 3), 7, 3))    # 96 AO: the second half's shared-memory limit
+    refs = [oracle.dimer(*c) for c in cases]
     # two rounds over all cases: every call follows one with other sizes
     for _ in range(2):
-        for A, K, CX, eX, CY, eY, oX, oY in cases:
-            ref = _existing(A, K, CX, eX, CY, eY, oX, oY)
-            got = _noalloc(torch, A, K, CX, eX, CY, eY, oX, oY)
+        for c, ref in zip(cases, refs):
+            got = _noalloc(torch, *c)
             assert abs(got[0] - ref[0]) <= TOL * abs(ref[0]), (got, ref)
             assert abs(got[1] - ref[1]) <= TOL * abs(ref[0]), (got, ref)
+    # and the handle-based FP64 path agrees on the same inputs
+    for c, ref in zip(cases[:3], refs):
+        got = _existing(*c)
+        assert abs(got[0] - ref[0]) <= TOL * abs(ref[0]), (got, ref)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -67,3 +73,9 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(M.McptError) as ei:
         M.mcpt_dimer_fp64_noalloc(buf, buf, buf, buf, 128, 5, buf, buf, 32, 5, buf)
     assert ei.value.status == M.MCPT_EINVAL
+    # a following valid call clears the message
+    rng = np.random.default_rng(22)
+    A, K, CX, eX, CY, eY = rand_dimer(rng, 6, 5, 2, 2)
+    got = _noalloc(torch, A, K, CX, eX, CY, eY, 2, 2)
+    assert np.all(np.isfinite(got))
+    assert M.mcpt_last_error(None) == ""
