@@ -34,10 +34,12 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "fp32c", "fp64"])
-    p.add_argument("--workload", default="lattice-5x5x5-cheb1")
+    p.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "bf16x2", "fp32c", "fp64"])
+    p.add_argument("--workload", default="lattice-10x10x10-cheb2")
+    p.add_argument("--wave-gb", type=float, default=WAVE_BUDGET / (1 << 30),
+                   help="streamed workloads: GiB of integral blocks per wave (one wave = one step)")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--cpu-sample", type=int, default=192, help="dimers in the oracle's timed sample")
+    p.add_argument("--cpu-sample", type=int, default=1024, help="dimers in the oracle's timed sample (at most)")
     p.add_argument("--no-extras", action="store_true",
                    help="report none of the extras (coupling, td2, df, FP64 form, e2e, CPU baseline)")
     p.add_argument("--extras", default="coupling,td2,df,fp64,e2e,cpu",
@@ -135,6 +137,19 @@ def measured_peaks():
         with open(path) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+_FP64_RATE = {}
+
+
+def fp64_rate(device):
+    """The FP64 FMA rate the FP64 form is bound by, measured once per run by
+    the library's microbenchmark (mcpt_fp64_fma_rate)."""
+    if device not in _FP64_RATE:
+        import paper_1409_2700_gb300 as M
+        t, ms = M.mcpt_fp64_fma_rate(device)
+        _FP64_RATE[device] = {"tflops": t, "kind": f"measured: library DFMA microbenchmark, this run ({ms:.0f} ms)"}
+    return _FP64_RATE[device]
 
 
 # DRAM traffic of the first-half kernel per dimer, from the full ncu captures
@@ -267,11 +282,12 @@ def our_arm(args, ws, rank, local):
     per_launch_bytes = st.alg_bytes / st.waves
     peaks, peak_kind = measured_peaks()
     if args.precision == "fp64":
-        # FP64 pipe bound: nominal 1.25 TFLOP/s FP64 on GB300 (no measured figure)
+        # FP64 pipe bound: the measured FP64 FMA rate
+        rate = fp64_rate(local)
         achieved = st.alg_flops_half / st.waves / (transform_ms / st.waves * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None, "kernel": "k_half_fp64",
-                "peak_kind": "nominal FP64 rate"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": rate["tflops"], "unit": "TFLOP/s",
+                "frac": achieved / rate["tflops"], "traffic": None, "kernel": "k_half_fp64",
+                "peak_kind": rate["kind"]}
     else:
         achieved = per_launch_bytes / (transform_ms / st.waves * 1e-3) / 1e9
         tpd = TRAFFIC_PER_DIMER.get((args.precision, w.nao[0], w.nocc[0]))
@@ -493,6 +509,10 @@ def our_arm(args, ws, rank, local):
         fp64 = {"value": w.n_dimers / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                 "transform_tflops": s64.alg_flops / (ms64 * 1e-3) / 1e12,
                 "first_half_ms": s64.ms[0] / s64.runs}
+        rate = fp64_rate(local)
+        a64 = s64.alg_flops_half / (s64.ms[0] / s64.runs * 1e-3) / 1e12
+        fp64["roofline"] = {"bound": "alu", "achieved": a64, "peak": rate["tflops"], "unit": "TFLOP/s",
+                            "frac": a64 / rate["tflops"], "kernel": "k_half_fp64", "peak_kind": rate["kind"]}
         if g is not None:
             fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
         line["fp64_form"] = fp64
@@ -596,11 +616,35 @@ def our_arm(args, ws, rank, local):
 
 
 # ------------------------------------------------------------------ streamed workloads
-# Workloads whose integral blocks exceed device memory: every pass regenerates
-# each wave's blocks on the device (untimed) and runs the wave; the step time
-# is the device time of the waves' runs (CUDA events around each run).
+# Workloads whose integral blocks exceed device memory (706 GB for the
+# 10x10x10 lattice) run in waves through one context: every dimer is
+# registered once with an address inside one wave buffer, and a producer
+# writes each wave's blocks there (device generation, untimed) before the
+# wave runs.  A step is one wave: one pass of the whole path over one batch
+# of the workload's dimers (about WAVE_BUDGET bytes of integrals).  Steps
+# walk the waves in order and wrap around; when the steps end before the
+# lattice does, the remaining waves run untimed so that the lattice energy
+# can be checked against the stored oracle values.
 STREAMED = {"lattice-10x10x10-cheb2", "uneven-4096", "lattice-7x7x7-cheb1-ao128"}
-WAVE_BUDGET = 96 << 30
+WAVE_BUDGET = 36 << 30
+
+
+def _alg_bytes(w, d0, n):
+    return float(sum(2 * 8 * w.nao[w.pairs[d][0]] ** 2 * w.nao[w.pairs[d][1]] ** 2 for d in range(d0, d0 + n)))
+
+
+def _alg_flops(w, d0, n):
+    """(all, first half) algorithmic transform flops of dimers d0 .. d0+n-1:
+    the occupied-first factorised count, both forms."""
+    tot = half = 0.0
+    for d in range(d0, d0 + n):
+        X, Y = w.pairs[d]
+        nx, ny, ox, oy = w.nao[X], w.nao[Y], w.nocc[X], w.nocc[Y]
+        vx, vy = nx - ox, ny - oy
+        h = 4.0 * (nx * nx * ny * ny * oy + ox * nx * nx * ny * oy)
+        half += h
+        tot += h + 4.0 * (ox * nx * oy * ny * vy + ox * vx * oy * vy * nx)
+    return tot, half
 
 
 def streamed_arm(args, ws, rank, local):
@@ -616,71 +660,270 @@ def streamed_arm(args, ws, rank, local):
     w = synth.workload(args.workload)
     if args.max_dimers:
         w.pairs, w.R = w.pairs[:args.max_dimers], w.R[:args.max_dimers]
+    extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
     stream = torch.cuda.Stream()
-    ctx = M.Context(precision=args.precision, device=local, stream=stream.cuda_stream, validate=False,
-                    timing=True, graphs=False)
-    for X in range(w.n_monomers):
-        m = w.monomer(X)
-        ctx.add_monomer(m.C, m.eps, m.nocc)
-    alg_bytes = float(sum(2 * 8 * w.nao[X] ** 2 * w.nao[Y] ** 2 for X, Y in w.pairs))
+    mons = [w.monomer(X) for X in range(w.n_monomers)]
+
+    def make_ctx(prec, timing, graphs=True):
+        c = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing,
+                      graphs=graphs)
+        for m in mons:
+            c.add_monomer(m.C, m.eps, m.nocc)
+        return c
+
+    ctx = make_ctx(args.precision, True)
+    ctxs = [ctx]
+    c64 = None
+    if rank == 0 and "fp64" in extras and args.precision != "fp64":
+        c64 = make_ctx("fp64", True)
+        ctxs.append(c64)
     with torch.cuda.stream(stream):
-        st = Streamed(ctx, w.pairs, w.nao, WAVE_BUDGET)
+        st = Streamed(ctxs, w.pairs, w.nao, int(args.wave_gb * (1 << 30)))
+        nw = len(st)
+        st.buf.zero_()
         synth.device.fill_views(w, st.views(0))
-        for _ in range(max(args.warmup, 3)):      # warm-up runs of the first wave
-            st.run(0)
+        # plans of every wave built before timing (runs on whatever the buffer holds)
+        for k in range(nw):
+            st.run(k)
+        for _ in range(max(args.warmup, 3)):
+            ctx.run(*st.waves[0])
         stream.synchronize()
-        ctx.stats()
-        ev = []
-        t_gen = 0.0
+        for c in ctxs:
+            c.stats()
+        ev, ev64, done, done64 = [], [], set(), set()
+        t_gen, timed_dimers, timed_bytes, timed_flops, timed_half, filled = 0.0, 0, 0.0, 0.0, 0.0, 0
+        wave_flops = [_alg_flops(w, *st.waves[k]) for k in range(nw)]
         with Clocks(local) as clk:
-            for _ in range(args.steps):
-                for k in range(len(st)):
+            for step in range(args.steps):
+                k = step % nw
+                if filled != k:                            # the buffer holds wave `filled`
                     t0 = time.perf_counter()
-                    if not (args.steps == 1 and k == 0):
-                        synth.device.fill_views(w, st.views(k))
+                    synth.device.fill_views(w, st.views(k))
                     stream.synchronize()
                     t_gen += time.perf_counter() - t0
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    st.run(k)
-                    e1.record(stream)
-                    ev.append((e0, e1))
-                stream.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    ms = max_over_ranks(ws, ms)
-    stt = ctx.stats()
+                    filled = k
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.run(*st.waves[k])
+                e1.record(stream)
+                ev.append((e0, e1))
+                timed_dimers += st.waves[k][1]
+                timed_bytes += _alg_bytes(w, *st.waves[k])
+                timed_flops += wave_flops[k][0]
+                timed_half += wave_flops[k][1]
+                done.add(k)
+                if c64 is not None and k not in done64:
+                    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    f0.record(stream)
+                    c64.run(*st.waves[k])
+                    f1.record(stream)
+                    ev64.append((f0, f1, st.waves[k][1]))
+                    done64.add(k)
+            stream.synchronize()
+        clocks = clk.summary()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        stt = ctx.stats()
+        s64 = c64.stats() if c64 is not None else None
+        # the waves the steps did not reach, untimed, so that the lattice is complete
+        for k in range(nw):
+            if k in done and (c64 is None or k in done64):
+                continue
+            if filled != k:
+                synth.device.fill_views(w, st.views(k))
+                filled = k
+            if k not in done:
+                ctx.run(*st.waves[k])
+            if c64 is not None and k not in done64:
+                c64.run(*st.waves[k])
+        stream.synchronize()
+
     mj, mk, pd, tot = ctx.energies()
-    ms_step = ms / args.steps
+    nsteps = len(ev)
+    ms = max_over_ranks(ws, ms)
+    ms_step = ms / nsteps
     peaks, peak_kind = measured_peaks()
-    first_half_ms = stt.ms[0] / args.steps
+    first_half_ms = stt.ms[0]
     if args.precision == "fp64":
-        roof = {"bound": "alu", "achieved": None, "peak": 1.25, "unit": "TFLOP/s", "frac": None, "traffic": None,
-                "kernel": "k_half_fp64", "peak_kind": "nominal FP64 rate"}
+        rate = fp64_rate(local)
+        achieved = timed_half / (first_half_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": rate["tflops"], "unit": "TFLOP/s",
+                "frac": achieved / rate["tflops"], "traffic": None, "kernel": "k_half_fp64",
+                "peak_kind": rate["kind"]}
     else:
-        achieved = alg_bytes / (first_half_ms * 1e-3) / 1e9
+        achieved = timed_bytes / (first_half_ms * 1e-3) / 1e9
+        tpd = TRAFFIC_PER_DIMER.get((args.precision, w.nao[0], w.nocc[0]))
+        uniform = len(set(w.nao)) == 1 and len(set(w.nocc)) == 1
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3") else "k_half_fp32c",
-                "peak_kind": peak_kind, "note": "all first-half launches of a pass (one or more per wave)"}
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": tpd * timed_dimers / nsteps if (tpd and uniform) else None,
+                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3", "bf16x2") else "k_half_fp32c",
+                "peak_kind": peak_kind,
+                "per": "one wave's first-half launch (traffic scaled from the ncu capture per dimer)"}
     line = {
-        "metric": METRIC, "value": ws * w.n_dimers / (ms_step * 1e-3), "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "metric": METRIC, "value": ws * timed_dimers / (ms * 1e-3), "unit": UNIT, "n_gpus": ws,
+        "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "n_dimers": w.n_dimers, "n_monomers": w.n_monomers,
                    "nao": sorted(set(w.nao)), "nocc": sorted(set(w.nocc)), "precision": args.precision,
-                   "inputs_gb": round(alg_bytes / 1e9, 1), "waves": len(st),
-                   "timed": "device time of the waves' runs; on-device generation of each wave untimed",
-                   "l2": "inputs larger than L2"},
-        "phase_ms_per_step": {"first_half": first_half_ms, "finish": stt.ms[1] / args.steps,
-                              "reduce": stt.ms[2] / args.steps},
-        "generation_s_per_step": t_gen / args.steps,
+                   "inputs_gb": round(_alg_bytes(w, 0, w.n_dimers) / 1e9, 1), "waves": nw,
+                   "dimers_per_step": round(timed_dimers / nsteps, 1),
+                   "step": "one wave: every dimer of the wave through the whole path (first half, second half "
+                           "with FP64 denominators and energies, per-monomer reduction); waves in lattice order",
+                   "timed": "CUDA events around each wave's run; on-device generation of each wave untimed",
+                   "l2": "inputs (tens of GB per wave) larger than L2"},
+        "phase_ms_per_step": {"first_half": stt.ms[0] / nsteps, "finish": stt.ms[1] / nsteps,
+                              "reduce": stt.ms[2] / nsteps},
+        "transform_tflops": timed_flops / (ms * 1e-3) / 1e12,
+        "generation_s_per_step": t_gen / nsteps,
         "roofline": roof,
         "gpu_launches": stt.launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "lattice_E": {"J": tot[0], "K": tot[1]},
     }
-    del st
-    ctx.close()
+
+    # ---- accuracy against the stored oracle values (tests/golden), every dimer
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        import make_lattice_oracle as golden
+        g = None if args.max_dimers else golden.load(args.workload)
+    except Exception:
+        g = None
+    if g is not None:
+        Eo, to = g
+        line["error_eh"] = {"lattice_J": float(tot[0] - to[0]), "lattice_K": float(tot[1] - to[1]),
+                            "max_dimer_J": float(np.max(np.abs(pd[:, 0] - Eo[:, 0]))),
+                            "max_dimer_K": float(np.max(np.abs(pd[:, 1] - Eo[:, 1]))),
+                            "max_dimer_rel_J": float(np.max(np.abs(pd[:, 0] - Eo[:, 0]) / np.abs(Eo[:, 0]))),
+                            "reference": f"FP64 oracle (factor route), stored values of all {w.n_dimers} dimers"}
+
+    # ---- the plain FP64 GPU form on the same waves (each wave once)
+    if c64 is not None:
+        _, _, pd64, tot64 = c64.energies()
+        ms64 = sum(a.elapsed_time(b) for a, b, _ in ev64)
+        n64 = sum(n for _, _, n in ev64)
+        rate = fp64_rate(local)
+        half64 = sum(wave_flops[k][1] for k in done64)
+        fp64 = {"value": n64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / len(ev64), "waves": len(ev64),
+                "first_half_ms_per_step": s64.ms[0] / len(ev64),
+                "roofline": {"bound": "alu", "achieved": half64 / (s64.ms[0] * 1e-3) / 1e12, "peak": rate["tflops"],
+                             "unit": "TFLOP/s", "kernel": "k_half_fp64", "peak_kind": rate["kind"]}}
+        fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / rate["tflops"]
+        if g is not None:
+            fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
+            fp64["max_dimer_rel_J"] = float(np.max(np.abs(pd64[:, 0] - g[0][:, 0]) / np.abs(g[0][:, 0])))
+        line["fp64_form"] = fp64
+
+    # ---- the oracle on the host cores: evenly spaced dimers of the wave in the
+    # buffer, four-index blocks copied from the device, about 10 s of CPU work
+    if rank == 0 and "cpu" in extras:
+        import oracle
+        oracle.build()
+        first, count = st.waves[filled]
+        ds = [first + k for k in range(0, count, max(1, count // max(1, args.cpu_sample)))][:args.cpu_sample]
+        Eo_s, done_s, tc = [], [], 0.0
+        for c0 in range(0, len(ds), 64):
+            items = []
+            for d in ds[c0:c0 + 64]:
+                X, Y = w.pairs[d]
+                nX, nY = w.nao[X], w.nao[Y]
+                blk = st.buf[st.offs[d]:st.offs[d] + 2 * nX * nX * nY * nY].cpu().numpy()
+                items.append((blk[:nX * nX * nY * nY].reshape(nX, nX, nY, nY),
+                              blk[nX * nX * nY * nY:].reshape(nX, nY, nY, nX),
+                              mons[X].C, mons[X].eps, mons[Y].C, mons[Y].eps, mons[X].nocc, mons[Y].nocc))
+            t0 = time.perf_counter()
+            Eo_s.append(oracle.dimers_parallel(items))
+            tc += time.perf_counter() - t0
+            done_s += ds[c0:c0 + len(items)]
+            if tc > 12.0:
+                break
+        Eo_s = np.concatenate(Eo_s)
+        line["cpu_baseline"] = {"value": len(done_s) / tc, "unit": UNIT, "cores": oracle.max_threads(),
+                                "kind": "oracle",
+                                "sample": f"{len(done_s)} evenly spaced dimers of one wave of {args.workload} "
+                                          f"(four-index FP64 oracle from the device blocks, {tc:.1f} s wall)"}
+        line["sample_error_eh"] = {"max_dimer_J": float(np.max(np.abs(pd[done_s, 0] - Eo_s[:, 0]))),
+                                   "max_dimer_K": float(np.max(np.abs(pd[done_s, 1] - Eo_s[:, 1]))),
+                                   "dimers": len(done_s), "reference": "four-index FP64 oracle"}
+
+    # ---- end to end through the C ABI from pinned host buffers: a context
+    # holding the dimers of the first waves, each step one wave: every dimer's
+    # symmetry-packed integrals copied from pinned host memory
+    # (mcpt_update_dimer, asynchronous, expanded on the device), mcpt_run of
+    # the wave, mcpt_energies read back
+    if rank == 0 and "e2e" in extras:
+        ne = max(1, min(args.e2e_steps, nw, 2))
+        idx = {}
+        hosts, poffs = [], []
+        for k in range(ne):
+            if filled != k:
+                synth.device.fill_views(w, st.views(k))
+                filled = k
+            first, count = st.waves[k]
+            offs_k, tot_k = [], 0
+            for d in range(first, first + count):
+                key = (w.nao[w.pairs[d][0]], w.nao[w.pairs[d][1]])
+                if key not in idx:
+                    idx[key] = torch.from_numpy(synth.packed_gather_index(*key)).to(st.buf.device)
+                offs_k.append(tot_k)
+                tot_k += idx[key].numel()
+            hk = torch.empty(tot_k, dtype=torch.float64, pin_memory=True)
+            for j, d in enumerate(range(first, first + count)):      # input preparation (untimed)
+                key = (w.nao[w.pairs[d][0]], w.nao[w.pairs[d][1]])
+                hk[offs_k[j]:offs_k[j] + idx[key].numel()].copy_(st.buf[st.offs[d]:st.offs[d] + st.elems[d]][idx[key]])
+            stream.synchronize()
+            hosts.append(hk)
+            poffs.append(offs_k)
+        del idx
+        wl = list(st.waves)
+        for c in ctxs:
+            c.close()
+        del st
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        ce = M.Context(precision=args.precision, device=local, validate=False)
+        for m in mons:
+            ce.add_monomer(m.C, m.eps, m.nocc)
+        ranges, base_id = [], 0
+        wave_of = []
+        for k in range(ne):
+            first, count = wl[k]
+            for j, d in enumerate(range(first, first + count)):
+                X, Y = w.pairs[d]
+                ce.add_dimer(X, Y, hosts[k].data_ptr() + 8 * poffs[k][j], M.MCPT_AO_PACKED, on_device=0)
+            ranges.append((base_id, count, first))
+            base_id += count
+        for lo, n, _ in ranges:
+            ce.run(lo, n)
+        ce.energies()
+        ts, same, h2d = [], True, 0
+        for rep in range(2):
+            for k, (lo, n, first) in enumerate(ranges):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for j in range(n):
+                    ce.update_dimer(lo + j, hosts[k].data_ptr() + 8 * poffs[k][j], M.MCPT_AO_PACKED, on_device=0,
+                                    asynchronous=True)
+                ce.run(lo, n)
+                out = ce.energies()
+                t1 = time.perf_counter()
+                same = same and bool(np.array_equal(out[2][lo:lo + n], pd[first:first + n]))
+                if rep > 0 or ne == 1:
+                    ts.append((t1 - t0, n, hosts[k].numel() * 8))
+        ce.close()
+        e2e_s = sum(t for t, _, _ in ts)
+        line["e2e"] = {"value": sum(n for _, n, _ in ts) / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": sum(b for _, _, b in ts) / len(ts),
+                       "d2h_bytes_per_step": 8 * (2 * w.n_monomers + 2 * base_id + 2),
+                       "s_per_step": e2e_s / len(ts), "steps": len(ts),
+                       "terms_equal_streamed_run": same,
+                       "per_step": "one wave: mcpt_update_dimer of each of its dimers from pinned host memory "
+                                   "(MCPT_AO_PACKED: the unique elements, asynchronous, expanded on the device), "
+                                   "mcpt_run of the wave, mcpt_energies"}
+        del hosts
+    else:
+        for c in ctxs:
+            c.close()
+        del st
     if rank == 0:
         print(json.dumps(line))
 

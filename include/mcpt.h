@@ -108,6 +108,14 @@ typedef struct {
                                  coupling R_X of Eq. (tm2) at first order (see mcpt_coupling); the
                                  dimers' (ia|jb) and T = vD stay on the device (2 o_X v_X o_Y v_Y
                                  elements each) */
+    unsigned long long wait_limit_ns; /* limit of each device-side wait of the tensor-core kernels
+                                 (0 = 4 s); when one runs out the kernel gives up, drains its own
+                                 copies and MMAs, frees its tensor memory and returns, and the next
+                                 mcpt_energies reports MCPT_ETIMEOUT */
+    int withhold_load;        /* test aid, 0 = off: N > 0 makes the first CTA of each tensor-core
+                                 launch stop issuing integral loads after N - 1 of them, so that its
+                                 consumers wait for a load that never comes and give up at
+                                 wait_limit_ns (failure detection without a device fault) */
 } mcpt_options;
 
 /* Defaults: device 0, own stream, MCPT_FP64, validate 1, 1 GiB waves, no cache, no timing,
@@ -343,6 +351,15 @@ mcpt_status mcpt_dimer_fp64_noalloc(const double *A, const double *K,
                                     const double *C_X, const double *eps_X, int nX, int nocc_X,
                                     const double *C_Y, const double *eps_Y, int nY, int nocc_Y,
                                     double *E2, void *stream);
+
+/* Measured FP64 FMA rate of `device` (a microbenchmark: independent FMA
+ * chains on every SM, timed with CUDA events after a warm-up launch).  Not a
+ * step of the path and without counterpart in the paper: the FP64 form is
+ * bound by this pipe, and its roofline needs the rate.  *tflops receives
+ * TFLOP/s (2 flops per FMA), *ms_per_launch (may be NULL) the time of one
+ * timed launch (~0.5 s of work on a GB300).  Errors (mcpt_last_error(NULL)):
+ * EINVAL for tflops NULL, ECUDA. */
+mcpt_status mcpt_fp64_fma_rate(int device, double *tflops, double *ms_per_launch);
 
 /* Release the handle and every library-owned device buffer.  Borrowed
  * pointers are not touched.  NULL is a no-op. */

@@ -33,7 +33,8 @@ EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_
            "mcpt_run", "mcpt_run_range", "mcpt_energies", "mcpt_coupling", "mcpt_singles", "mcpt_set_monomer_doubles", "mcpt_td2",
            "mcpt_add_dimer_df", "mcpt_run_df", "mcpt_df_energies",
            "mcpt_collect_stats", "mcpt_num_monomers",
-           "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc")
+           "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc",
+           "mcpt_fp64_fma_rate")
 
 
 class McptError(RuntimeError):
@@ -46,7 +47,7 @@ class mcpt_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("validate", ctypes.c_int), ("wave_bytes", ctypes.c_size_t), ("tune_cache", ctypes.c_char_p),
                 ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int),
-                ("coupling", ctypes.c_int)]
+                ("coupling", ctypes.c_int), ("wait_limit_ns", ctypes.c_ulonglong), ("withhold_load", ctypes.c_int)]
 
 
 class mcpt_run_stats(ctypes.Structure):
@@ -98,6 +99,8 @@ def lib():
         L.mcpt_destroy.restype = None
         L.mcpt_dimer_fp64_noalloc.argtypes = [P, P, P, P, I, I, P, P, I, I, P, P]
         L.mcpt_dimer_fp64_noalloc.restype = I
+        L.mcpt_fp64_fma_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.mcpt_fp64_fma_rate.restype = I
         _lib = L
     return _lib
 
@@ -248,13 +251,21 @@ def mcpt_dimer_fp64_noalloc(A, K, C_X, eps_X, nX, nocc_X, C_Y, eps_Y, nY, nocc_Y
     _check(None, st)
 
 
+def mcpt_fp64_fma_rate(device: int = 0):
+    """(TFLOP/s, ms per launch) of the device's FP64 FMA pipe, measured by the
+    library's microbenchmark (the FP64 form's roofline denominator)."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(None, lib().mcpt_fp64_fma_rate(device, ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
+
+
 # ----------------------------------------------------------- convenience
 class Context:
     """Owns one mcpt handle.  ``stream`` is a cudaStream_t as an int (e.g.
     ``torch.cuda.current_stream().cuda_stream``) or None for a library stream."""
 
     def __init__(self, precision="fp64", device=0, stream=None, validate=True, wave_bytes=0, timing=False,
-                 mem_cap_bytes=0, graphs=True, tune_cache=None, coupling=False):
+                 mem_cap_bytes=0, graphs=True, tune_cache=None, coupling=False, wait_limit_ns=0, withhold_load=0):
         o = mcpt_default_options()
         if tune_cache is not None:
             o.tune_cache = os.fsencode(tune_cache)
@@ -267,6 +278,8 @@ class Context:
         o.mem_cap_bytes = mem_cap_bytes
         o.graphs = int(bool(graphs))
         o.coupling = int(bool(coupling))
+        o.wait_limit_ns = int(wait_limit_ns)
+        o.withhold_load = int(withhold_load)
         self.validate = bool(validate)
         self.stream = stream
         self.h = mcpt_create(o)

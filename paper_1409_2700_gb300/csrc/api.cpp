@@ -70,6 +70,8 @@ struct mcpt_ctx {
     int timing = 0;
     int graphs = 1;
     int coupling = 0;
+    unsigned long long wait_ns = 0;  // limit of each device-side wait (0 = the kernels' default)
+    int withhold = 0;                // test aid: see mcpt_options.withhold_load
     size_t mem_cap = 0;
     size_t mem_used = 0;
 
@@ -378,6 +380,7 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     if (opt) o = *opt;
     if (o.precision < MCPT_FP64 || o.precision > MCPT_BF16X2)
         return fail(nullptr, MCPT_EINVAL, "mcpt_create: bad precision %d", (int)o.precision);
+    if (o.withhold_load < 0) return fail(nullptr, MCPT_EINVAL, "mcpt_create: withhold_load %d < 0", o.withhold_load);
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || ndev == 0) {
@@ -405,6 +408,8 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     h->timing = o.timing;
     h->graphs = o.graphs;
     h->coupling = o.coupling;
+    h->wait_ns = o.wait_limit_ns;
+    h->withhold = o.withhold_load;
     h->mem_cap = o.mem_cap_bytes;
     if (o.stream) {
         h->stream = static_cast<cudaStream_t>(o.stream);
@@ -1104,6 +1109,8 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
                                        h->stream, tuned ? &tune : nullptr, &wv.tc, tcerr, sizeof tcerr);
             if (e != cudaSuccess)
                 return fail(h, MCPT_ECUDA, "tensor-core plan: %s (%s)", cudaGetErrorString(e), tcerr);
+            wv.tc.wait_ns = h->wait_ns;
+            wv.tc.withhold = h->withhold;
         }
         P.waves.push_back(wv);
     }

@@ -266,15 +266,19 @@ struct TcLaunch {
     int sf;                     // FP64 staging stages
     unsigned f_stage_bytes, w_stage_bytes, tmem_cols;
     int kind;
-    int variant;                // 0: Kronecker (p0,p2) GEMM, 1: p2 GEMM + FP32 rank-1 epilogue
+    int variant;                // 0: Kronecker (p0,p2) GEMM; 1, 3: p2 GEMM + FP32 rank-1 epilogue in registers
+                                // (occupations <= 8, <= 5); 2: the same with TMEM accumulators (<= 16)
     int kcs_max;                // p2 chunks of 32 (largest n_Y of the launch)
     int grid;
     size_t smem;
+    unsigned long long wait_ns; // limit of each device-side wait (0 = 4 s)
+    int withhold;               // test aid: CTA 0 issues only withhold - 1 integral loads (0 = off)
 };
 
 // Launch choices of one tensor-core launch (0 in a field = the default):
 // kernel variant + 1 (1 Kronecker, 2 rank with register accumulators, 3 rank
-// with TMEM accumulators), FP64 staging depth, CTAs.
+// with TMEM accumulators, 4 rank with register accumulators for occupations
+// <= 5), FP64 staging depth, CTAs.
 struct TcTune {
     int variant1;
     int sf;

@@ -84,6 +84,8 @@ struct TcParams {
     unsigned int tmem_cols;
     int kind;                      // TC_TF32 / TC_BF16X3 / TC_BF16X2
     int kcs_max;                   // largest p2 chunk count of the launch (rank variant)
+    unsigned long long wait_ns;    // limit of each wait (kWaitNs if 0)
+    int withhold;                  // test aid: CTA 0 issues only withhold - 1 integral loads (0 = off)
 };
 
 // ------------------------------------------------------------------ PTX
@@ -124,14 +126,14 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity
 
 // Wait for the phase of parity `parity` to complete; false on timeout/abort.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity, volatile int* abort, int* status,
-                                          int where)
+                                          int where, unsigned long long limit = kWaitNs)
 {
     if (mbar_test(b, parity)) return true;
     const unsigned long long t0 = now_ns();
     while (true) {
         if (mbar_test(b, parity)) return true;
         if (*abort) return false;
-        if (now_ns() - t0 > kWaitNs) {
+        if (now_ns() - t0 > limit) {
             *abort = 1;
             atomicCAS(status, 0, kErrTimeoutBase + where);
             return false;
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                     for (int mt = 0; mt < item.mts; mt++, gF++) {
                         const int s = gF % P.sf;
                         const unsigned ph = (gF / P.sf) & 1;
-                        if (!mbar_wait(&sh->empty_f[s], ph ^ 1, &sh->abort, P.status, 1)) break;
+                        if (!mbar_wait(&sh->empty_f[s], ph ^ 1, &sh->abort, P.status, 1, P.wait_ns)) break;
                         mbar_arrive_tx(&sh->full_f[s], box);
                         tma_load_4d(Fr + (size_t)s * P.f_stage_bytes, map, &sh->full_f[s], 0, kc * kKC,
                                     (item.mt0 + mt) * g.p1t, p0);
@@ -409,16 +411,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
                 const unsigned idesc = make_idesc(KIND, g.N);
                 const int b = li & 1;
-                if (!mbar_wait(&sh->tmem_empty[b], ((li >> 1) & 1) ^ 1, &sh->abort, P.status, 2)) break;
+                if (!mbar_wait(&sh->tmem_empty[b], ((li >> 1) & 1) ^ 1, &sh->abort, P.status, 2, P.wait_ns)) break;
                 tc_fence_after();
                 bool ok = true;
                 for (int kb = 0; kb < g.kblocks && ok; kb++, gW++) {
                     const int ws = gW & 1;
-                    if (!(ok = mbar_wait(&sh->full_w[ws], (gW >> 1) & 1, &sh->abort, P.status, 3))) break;
+                    if (!(ok = mbar_wait(&sh->full_w[ws], (gW >> 1) & 1, &sh->abort, P.status, 3, P.wait_ns))) break;
                     const unsigned long long bdesc = sw128_desc(Wr + (size_t)ws * P.w_stage_bytes);
                     for (int mt = 0; mt < item.mts; mt++, gA++) {
                         const int as = gA & 1;
-                        if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, &sh->abort, P.status, 4))) break;
+                        if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, &sh->abort, P.status, 4, P.wait_ns))) break;
                         tc_fence_after();
                         const unsigned long long adesc = sw128_desc(Ar + (size_t)as * kABytes);
                         const unsigned dt = tmem + (unsigned)(b * kAccCols + mt * g.N);
@@ -468,7 +470,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                 const int p0 = kb / g.kcs, kc = kb % g.kcs;
                 // ---- W tile of this K-block: row n = (i, j), K = p2 in the chunk
                 const int ws = gW & 1;
-                if (!(ok = mbar_wait(&sh->empty_w[ws], ((gW >> 1) & 1) ^ 1, &sh->abort, P.status, 5))) break;
+                if (!(ok = mbar_wait(&sh->empty_w[ws], ((gW >> 1) & 1) ^ 1, &sh->abort, P.status, 5, P.wait_ns))) break;
                 unsigned char* W = Wr + (size_t)ws * P.w_stage_bytes;
                 if (KIND == TC_TF32) {
                     for (int task = ct; task < g.N * 8; task += 128) {
@@ -519,9 +521,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
                 // ---- A tiles of this K-block, one per M-tile of the item
                 for (int mt = 0; mt < item.mts; mt++, gF++, gA++) {
                     const int s = gF % P.sf;
-                    if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, &sh->abort, P.status, 6))) break;
+                    if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, &sh->abort, P.status, 6, P.wait_ns))) break;
                     const int as = gA & 1;
-                    if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, &sh->abort, P.status, 7))) break;
+                    if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, &sh->abort, P.status, 7, P.wait_ns))) break;
                     const double* F = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
                     unsigned char* A = Ar + (size_t)as * kABytes;
                     if (KIND == TC_TF32) {
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
             const int b = li & 1;
-            if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, &sh->abort, P.status, 8)) break;
+            if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, &sh->abort, P.status, 8, P.wait_ns)) break;
             tc_fence_after();
             const int npairs = g.o0 * g.o2;
             float* Hf = P.H + d.h_off + (long long)item.form * npairs * g.rows;
@@ -664,6 +666,7 @@ constexpr int kNT = 16;           // TMEM slot width = MMA N
 constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns (16 slots when BIG)
 constexpr int kFxUnits = 8;       // BF16x3: 4-slot p0 units in 512 columns (4 when BIG)
 constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
+constexpr int kOB5 = 5;           // the same sized for o_X, o_Y <= 5 (fewer rank-1 FMAs)
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
 constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
 constexpr int kEpiWarp0 = 2 + kConvWarps;
@@ -862,29 +865,56 @@ __device__ __forceinline__ void convert_row(const double* __restrict__ F, unsign
     }
 }
 
-// T[(p1,p3) = this lane's row][j] of one unit, written to T (add = false) or
-// added to it.  TF32: the slot itself.  BF16x3: the four digit levels
-// combined in FP32 (round to nearest), ((L3/256 + L2)/256 + L1)/256 + L0, one
-// level at a time (16 registers in flight), times the row and column scales.
-template <int KIND>
-__device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[16], const float* srow, const float* scol, bool add)
+// Columns 0..NJ-1 of 32 lanes x 32-bit TMEM starting at taddr, without the
+// wait (NJ = 8 or 16; tcgen05.wait::ld before use).
+template <int NJ>
+__device__ __forceinline__ void tmem_ld_cols(unsigned taddr, unsigned (&r)[NJ])
 {
-    if constexpr (KIND == TC_TF32) {
-        tmem_ld16(taddr, T);
+    if constexpr (NJ == 16) {
+        tmem_ld16_nowait(taddr, r);
     } else {
-        float v[16], w[16];
-        tmem_ld16(taddr + 3 * kNT, v);
+        static_assert(NJ == 8, "8 or 16 columns");
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+    }
+}
+
+// Digit levels the epilogue combines: BF16x3 four, BF16x2 three (its fourth,
+// A0 B3 + A1 B2, lies 2^-24 below the first and is not formed).
+template <int KIND>
+__host__ __device__ constexpr int n_levels() { return KIND == TC_BF16X3 ? 4 : KIND == TC_BF16X2 ? 3 : 1; }
+
+// T[(p1,p3) = this lane's row][j < NJ] of one unit, written to T (add =
+// false) or added to it.  TF32: the slot itself.  Fixed-point forms: the
+// digit levels, loaded together, combined in FP32 (round to nearest) as
+// ((L3/256 + L2)/256 + L1)/256 + L0, times the unit's row scale and, with
+// COLS, the item's column scales (without, the caller applies those once
+// per output).
+template <int KIND, int NJ, bool COLS>
+__device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[NJ], const float* srow, const float* scol, bool add)
+{
+    constexpr int NL = n_levels<KIND>();
+    unsigned raw[NL][NJ];
 #pragma unroll
-        for (int l = 2; l >= 0; l--) {
-            tmem_ld16(taddr + (unsigned)(l * kNT), w);
+    for (int l = 0; l < NL; l++) tmem_ld_cols<NJ>(taddr + (unsigned)(l * kNT), raw[l]);
+    tmem_wait_ld();
+    if constexpr (KIND == TC_TF32) {
 #pragma unroll
-            for (int j = 0; j < 16; j++) v[j] = fmaf(v[j], 0x1p-8f, w[j]);
-        }
+        for (int j = 0; j < NJ; j++) T[j] = add ? T[j] + __uint_as_float(raw[0][j]) : __uint_as_float(raw[0][j]);
+    } else {
+        float v[NJ];
+#pragma unroll
+        for (int j = 0; j < NJ; j++) v[j] = __uint_as_float(raw[NL - 1][j]);
+#pragma unroll
+        for (int l = NL - 2; l >= 0; l--)
+#pragma unroll
+            for (int j = 0; j < NJ; j++) v[j] = fmaf(v[j], 0x1p-8f, __uint_as_float(raw[l][j]));
         const float sr = *srow;
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const float x = v[j] * (sr * scol[j]);
-            T[j] = add ? T[j] + x : x;
+        for (int j = 0; j < NJ; j++) {
+            const float f = COLS ? sr * scol[j] : sr;
+            T[j] = add ? fmaf(v[j], f, T[j]) : v[j] * f;
         }
     }
 }
@@ -937,13 +967,15 @@ __device__ __forceinline__ int convert_row_fx1(const double* __restrict__ F, uns
 // Only the high word of each double is read: its 20 mantissa bits hold every
 // bit above the rounding position.  The row chunk's largest exponent field
 // emax (bitwise maximum of |hi|, combined with the partner lane l ^ 16) fixes
-// y = |x| 2^(15 - e), e = emax - 1023, built on the integer pipes (the
-// exponent moved by 142 - emax modulo 2^9; elements below 2^-141 of the
-// row's largest, and invalid rows, become 0).  N = floor(y + 1/2): half up in
-// magnitude, so a truncated value that sits exactly on a half rounds away
-// from zero as the full double would (the dropped low word only adds
-// magnitude).  Balanced digits N = 256 d0 + d1, d0 = rne(N / 256) in
-// [0, 256], d1 in [-128, 128], exact in BF16; the sign of x goes on both.
+// y = x 2^(15 - e), e = emax - 1023, built on the integer pipes: the
+// exponent field lowered by emax - 142 while still 11 bits wide (elements
+// below 2^-142 of the row's largest, zeros and invalid rows go negative and
+// are clamped to 0), then moved into FP32 position.  The lowest FP32
+// mantissa bit of y is set: it stands in for the dropped low word, so a
+// truncated value never sits exactly on a rounding tie and round-to-nearest
+// gives the correctly rounded digits of the full double, for either sign.
+// Balanced digits 2^8 d0 + d1 = rn(y): d0 = rn(y / 2^8) in [-256, 256],
+// d1 = rn(y - 2^8 d0) in [-128, 128], both exact in BF16.
 __device__ __forceinline__ int convert_row_fx2(const double* __restrict__ F, unsigned char* __restrict__ A,
                                                const ConvRow& cr, int n3, int c0)
 {
@@ -959,9 +991,9 @@ __device__ __forceinline__ int convert_row_fx2(const double* __restrict__ F, uns
         }
     m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
     const int emax = cr.valid ? (int)(m >> 20) : 0;
-    const unsigned add = (unsigned)((142 - emax) & 511) << 23;
-    const unsigned thr = cr.valid ? (unsigned)max(1, emax - 141) << 20 : 0xFFFFFFFFu;
-    const float2 half = make_float2(0.5f, 0.5f);
+    // |hi| - K keeps the FP32 exponent field e_d - emax + 142 in bits 20-30 (negative
+    // below zero); an invalid row subtracts more than any |hi| so that all of it clamps to 0
+    const int K = cr.valid ? (emax - 142) * (1 << 20) : 0x7FFFFFFF;
     const float2 magic = make_float2(12582912.0f, 12582912.0f);      // 1.5 * 2^23
     const float2 nmagic = make_float2(-12582912.0f, -12582912.0f);
 #pragma unroll
@@ -970,17 +1002,18 @@ __device__ __forceinline__ int convert_row_fx2(const double* __restrict__ F, uns
         unsigned w0[4], w1[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            const unsigned ha = h[q][e], hb = h[q][e + 1];
             float2 y;
-            y.x = (ha & 0x7FFFFFFFu) < thr ? 0.f : __uint_as_float(ha * 8u + add);
-            y.y = (hb & 0x7FFFFFFFu) < thr ? 0.f : __uint_as_float(hb * 8u + add);
-            const float2 u = __fadd2_rn(y, half);                                   // exact
-            const float2 d0 = __fadd2_rn(__ffma2_rn(u, make_float2(0x1p-8f, 0x1p-8f), magic), nmagic);
-            const float2 r = __ffma2_rn(d0, make_float2(-256.0f, -256.0f), u);        // exact
-            const float2 d1 = __fadd2_rn(__fadd2_rd(r, magic), nmagic);              // floor(r)
-            const unsigned sg = __byte_perm(ha, hb, 0x7030) & 0x80008000u;           // sign bits of both
-            w0[e / 2] = pack_bf16(d0.x, d0.y) ^ sg;
-            w1[e / 2] = pack_bf16(d1.x, d1.y) ^ sg;
+            {
+                const unsigned ha = h[q][e], hb = h[q][e + 1];
+                const int ta = max((int)(ha & 0x7FFFFFFFu) - K, 0), tb = max((int)(hb & 0x7FFFFFFFu) - K, 0);
+                y.x = __uint_as_float(((unsigned)ta << 3) | 1u | (ha & 0x80000000u));
+                y.y = __uint_as_float(((unsigned)tb << 3) | 1u | (hb & 0x80000000u));
+            }
+            const float2 d0 = __fadd2_rn(__ffma2_rn(y, make_float2(0x1p-8f, 0x1p-8f), magic), nmagic);
+            const float2 r = __ffma2_rn(d0, make_float2(-256.0f, -256.0f), y);        // exact
+            const float2 d1 = __fadd2_rn(__fadd2_rn(r, magic), nmagic);
+            w0[e / 2] = pack_bf16(d0.x, d0.y);
+            w1[e / 2] = pack_bf16(d1.x, d1.y);
         }
         *reinterpret_cast<uint4*>(A + cr.dst + ((c ^ cr.r7) << 4)) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
         *reinterpret_cast<uint4*>(A + cr.dst + (((4 + c) ^ cr.r7) << 4)) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
@@ -988,21 +1021,27 @@ __device__ __forceinline__ int convert_row_fx2(const double* __restrict__ F, uns
     return emax;
 }
 
-// T[row][j] of one p0 for this lane's row: TF32 reads the p0's unit; BF16x3
-// adds the units of the p2 chunks in chunk order (FP32, round to nearest).
-// Frees each unit's slot after reading it.  False on timeout/abort.
-template <int KIND, int NS, int UC>
-__device__ __forceinline__ bool load_p0_T(float (&T)[16], RankShared* sh, unsigned& gS, int kcs, unsigned lanebase,
-                                          const float* exps, const float* scu, int r, int lane, volatile int* abort,
-                                          int* status)
+// T[row][j < NJ] of one p0 for this lane's row: TF32 reads the p0's unit;
+// the fixed-point forms add the units of the p2 chunks in chunk order (FP32,
+// round to nearest).  With sc (non-null) the first unit's column scales are
+// copied there (COLS = false: the caller applies them).  Frees each unit's
+// slot after reading it.  False on timeout/abort.
+template <int KIND, int NS, int UC, int NJ, bool COLS>
+__device__ __forceinline__ bool load_p0_T(float (&T)[NJ], RankShared* sh, unsigned& gS, int kcs, unsigned lanebase,
+                                          const float* exps, const float* scu, int r, int lane, float* sc,
+                                          volatile int* abort, int* status, unsigned long long lim)
 {
     const int nunits = KIND != TC_TF32 ? kcs : 1;
     for (int u = 0; u < nunits; u++, gS++) {
         const int s = gS % NS;
-        if (!mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, status, 18)) return false;
-        if (KIND != TC_TF32 && !mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, status, 23)) return false;
+        if (!mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, status, 18, lim)) return false;
+        if (KIND != TC_TF32 && !mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, status, 23, lim)) return false;
         tc_fence_after();
-        unit_T<KIND>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT, u > 0);
+        if (KIND != TC_TF32 && sc && u == 0) {
+#pragma unroll
+            for (int j = 0; j < NJ; j++) sc[j] = scu[s * kNT + j];
+        }
+        unit_T<KIND, NJ, COLS>(lanebase + (unsigned)(s * UC), T, exps + s * 128 + r, scu + s * kNT, u > 0);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
@@ -1010,7 +1049,7 @@ __device__ __forceinline__ bool load_p0_T(float (&T)[16], RankShared* sh, unsign
     return true;
 }
 
-template <int KIND, bool BIG>
+template <int KIND, bool BIG, int OB = kOB>
 __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams P)
 {
     constexpr bool FX = KIND != TC_TF32;            // fixed-point digit planes (BF16x3, BF16x2)
@@ -1078,7 +1117,12 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         for (int kc = 0; kc < g.kcs; kc++, gF++) {
                             const int s = gF % P.sf;
                             const unsigned ph = (gF / P.sf) & 1;
-                            if (!(ok = mbar_wait(&sh->empty_f[s], ph ^ 1, abort, P.status, 11))) break;
+                            // test aid: stop issuing; the consumers' waits then run out
+                            if (P.withhold && blockIdx.x == 0 && gF + 1 >= (unsigned)P.withhold) {
+                                ok = false;
+                                break;
+                            }
+                            if (!(ok = mbar_wait(&sh->empty_f[s], ph ^ 1, abort, P.status, 11, P.wait_ns))) break;
                             mbar_arrive_tx(&sh->full_f[s], box);
                             tma_load_4d(Fr + (size_t)s * P.f_stage_bytes, map, &sh->full_f[s], 0, kc * kKC,
                                         (item.mt0 + mt) * g.p1t, p0);
@@ -1104,19 +1148,19 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 const TcItem item = P.items[it];
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
                 const int wp = li & 1;
-                if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, abort, P.status, 12))) break;
+                if (!(ok = mbar_wait(&sh->full_w[wp], (li >> 1) & 1, abort, P.status, 12, P.wait_ns))) break;
                 for (int mt = 0; mt < item.mts && ok; mt++)
                     for (int p0 = 0; p0 < g.n0 && ok; p0++) {
                         if constexpr (!FX) {
                             // one unit per p0: the tensor core accumulates over the p2 chunks
                             const int s = gS % NS;
-                            if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13)))
+                            if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13, P.wait_ns)))
                                 break;
                             tc_fence_after();
                             const unsigned dt = tmem + (unsigned)(s * UC);
                             for (int kc = 0; kc < g.kcs && ok; kc++, gA++) {
                                 const int as = gA & 1;
-                                if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
+                                if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14, P.wait_ns))) break;
                                 tc_fence_after();
                                 const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
                                 unsigned char* wk = Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
@@ -1137,10 +1181,10 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                             // one unit per (p0, p2 chunk): each chunk has its own fixed point
                             for (int kc = 0; kc < g.kcs && ok; kc++, gA++, gS++) {
                                 const int s = gS % NS;
-                                if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13)))
+                                if (!(ok = mbar_wait(&sh->slot_empty[s], ((gS / NS) & 1) ^ 1, abort, P.status, 13, P.wait_ns)))
                                     break;
                                 const int as = gA & 1;
-                                if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14))) break;
+                                if (!(ok = mbar_wait(&sh->full_a[as], (gA >> 1) & 1, abort, P.status, 14, P.wait_ns))) break;
                                 tc_fence_after();
                                 const unsigned dt = tmem + (unsigned)(s * UC);
                                 // digit planes: A tile 1 = [d0 | d1], tile 2 = [d2 | d3] (BF16x3
@@ -1154,8 +1198,10 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
 #pragma unroll
                                 for (int k = 0; k < 2; k++) {
                                     const unsigned acc = k > 0 ? 1u : 0u;
-                                    tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[0], acc);
-                                    tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[1], 1u);
+                                    // BF16x2 forms levels 0-2 only: A0 x [B0..B2], A1 x [B0, B1]
+                                    constexpr int lv = KIND == TC_BF16X2 ? 1 : 0;
+                                    tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[lv], acc);
+                                    tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[lv + 1], 1u);
                                     if constexpr (KIND == TC_BF16X3) {
                                         const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
                                         tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
@@ -1192,7 +1238,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             const int wp = li & 1;
             const ConvRow cr = conv_row(r, g.p1t * g.n3, g.n3);
             // ---- B operand of this item: row j < 16, K = p2: C_Y[p2][j] (zero past o2 / n2)
-            if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, abort, P.status, 15))) break;
+            if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, abort, P.status, 15, P.wait_ns))) break;
             float sc_mine = 0.f;                 // BF16x3: column scale of column ct (< 16)
             int* cx_part = colx + wp * 16 * kNT;
             if constexpr (FX) {
@@ -1209,7 +1255,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 cx_part[part * kNT + j] = fm;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->colx_full[wp]);
-                if (!(ok = mbar_wait(&sh->colx_full[wp], (li >> 1) & 1, abort, P.status, 24))) break;
+                if (!(ok = mbar_wait(&sh->colx_full[wp], (li >> 1) & 1, abort, P.status, 24, P.wait_ns))) break;
                 if (ct < kNT) {
                     int m = 0;
                     for (int q = 0; q < 16; q++) m = max(m, cx_part[q * kNT + ct]);
@@ -1270,9 +1316,9 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                     if constexpr (!FX) {
                         for (int kc = 0; kc < g.kcs; kc++, gF++, gA++) {
                             const int s = gF % P.sf;
-                            if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16))) break;
+                            if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16, P.wait_ns))) break;
                             const int as = gA & 1;
-                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
+                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17, P.wait_ns)))
                                 break;
                             convert_row<KIND>(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes),
                                               Ar + (size_t)as * ASLOT, cr, g.n3, c0);
@@ -1288,9 +1334,9 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         // then the unit's row and column scales for the epilogue
                         for (int kc = 0; kc < g.kcs && ok; kc++, gF++, gA++, gU++) {
                             const int s = gF % P.sf;
-                            if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16))) break;
+                            if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16, P.wait_ns))) break;
                             const int as = gA & 1;
-                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17)))
+                            if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17, P.wait_ns)))
                                 break;
                             unsigned char* At = Ar + (size_t)as * ASLOT;
                             const double* Fs = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
@@ -1306,7 +1352,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                 mbar_arrive(&sh->empty_f[s]);
                             }
                             const int su = gU % NS;
-                            if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22)))
+                            if (!(ok = mbar_wait(&sh->slot_empty[su], ((gU / NS) & 1) ^ 1, abort, P.status, 22, P.wait_ns)))
                                 break;
                             if (c0 == 0) exps[su * 128 + r] = row_scale(emax);
                             if (ct < kNT) scu[su * kNT + ct] = sc_mine;
@@ -1330,36 +1376,40 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             const int par = li & 1;
             float* cx = cxs + par * CXF;
             // stage C_X's occupied columns, row p0 = e, for this item
-            if (!(ok = mbar_wait(&sh->cx_empty[par], ((li >> 1) & 1) ^ 1, abort, P.status, 19))) break;
+            if (!(ok = mbar_wait(&sh->cx_empty[par], ((li >> 1) & 1) ^ 1, abort, P.status, 19, P.wait_ns))) break;
             if (e < g.n0) {
                 const float* CX = P.Cf + d.cX + e * d.nX;
 #pragma unroll
                 for (int i = 0; i < CXW; i++) cx[e * CXW + i] = i < g.o0 ? __ldg(CX + i) : 0.f;
             }
             mbar_arrive(&sh->cx_full[par]);
-            if (!(ok = mbar_wait(&sh->cx_full[par], (li >> 1) & 1, abort, P.status, 20))) break;
+            if (!(ok = mbar_wait(&sh->cx_full[par], (li >> 1) & 1, abort, P.status, 20, P.wait_ns))) break;
             float* Hf = P.H + d.h_off + (long long)item.form * g.o0 * g.o2 * g.rows;
             const unsigned lanebase = tmem + ((unsigned)(q * 32) << 16);
             for (int mt = 0; mt < item.mts && ok; mt++) {
                 const int p1_lo = (item.mt0 + mt) * g.p1t;
                 if constexpr (!BIG) {
-                    float acc[kOB][kOB];
+                    float acc[OB][OB];
 #pragma unroll
-                    for (int i = 0; i < kOB; i++)
+                    for (int i = 0; i < OB; i++)
 #pragma unroll
-                        for (int j = 0; j < kOB; j++) acc[i][j] = 0.f;
+                        for (int j = 0; j < OB; j++) acc[i][j] = 0.f;
+                    float sc[8];   // the item's column scales (fixed-point forms), applied once per output
+#pragma unroll
+                    for (int j = 0; j < 8; j++) sc[j] = 1.f;
                     for (int p0 = 0; p0 < g.n0; p0++) {
-                        float T[16];
-                        if (!(ok = load_p0_T<KIND, NS, UC>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane, abort,
-                                                            P.status)))
+                        float T[8];
+                        if (!(ok = load_p0_T<KIND, NS, UC, 8, false>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
+                                                                      p0 == 0 ? sc : nullptr, abort, P.status,
+                                                                      P.wait_ns)))
                             break;
                         const float4 ca = *reinterpret_cast<const float4*>(cx + p0 * kOB);
                         const float4 cb = *reinterpret_cast<const float4*>(cx + p0 * kOB + 4);
                         const float cv[kOB] = {ca.x, ca.y, ca.z, ca.w, cb.x, cb.y, cb.z, cb.w};
 #pragma unroll
-                        for (int i = 0; i < kOB; i++)
+                        for (int i = 0; i < OB; i++)
 #pragma unroll
-                            for (int j = 0; j < kOB; j++) acc[i][j] = fmaf(cv[i], T[j], acc[i][j]);
+                            for (int j = 0; j < OB; j++) acc[i][j] = fmaf(cv[i], T[j], acc[i][j]);
                     }
                     if (!ok) break;
                     const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
@@ -1369,11 +1419,11 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         const size_t step = (size_t)g.rows;
                         float* q = out;
 #pragma unroll
-                        for (int i = 0; i < kOB; i++) {
+                        for (int i = 0; i < OB; i++) {
                             if (i < g.o0) {
 #pragma unroll
-                                for (int j = 0; j < kOB; j++)
-                                    if (j < g.o2) { *q = acc[i][j]; q += step; }
+                                for (int j = 0; j < OB; j++)
+                                    if (j < g.o2) { *q = acc[i][j] * sc[j]; q += step; }
                             }
                         }
                     }
@@ -1382,8 +1432,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                     const int nchunk = (g.o0 + 3) >> 2;
                     for (int p0 = 0; p0 < g.n0; p0++) {
                         float T[16];
-                        if (!(ok = load_p0_T<KIND, NS, UC>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane, abort,
-                                                            P.status)))
+                        if (!(ok = load_p0_T<KIND, NS, UC, 16, true>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
+                                                                      nullptr, abort, P.status, P.wait_ns)))
                             break;
                         const float* cp = cx + p0 * kOBig;
 #pragma unroll 1
@@ -1455,8 +1505,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode()
     return fn;
 }
 
-// Variant 1 (rank) runs one M-tile per item; variant 0 groups as many M-tiles
-// as one TMEM accumulator set holds.
+// The rank variants (1-3) run one M-tile per item; variant 0 groups as many
+// M-tiles as one TMEM accumulator set holds.
 int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
 {
     const int n1 = f ? d.nY : d.nX, n3 = f ? d.nX : d.nY;
@@ -1467,10 +1517,10 @@ int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
     return (tiles + mmax - 1) / mmax;
 }
 
-// 1: rank kernel, register accumulators (occupations <= 8); 2: rank kernel,
-// TMEM accumulators (<= 16); 0: Kronecker kernel (anything else the
-// tensor-core forms accept).  MCPT_TC_KERNEL=kron|rank|rankbig forces a
-// kernel where the sizes allow it.
+// 3: rank kernel, register accumulators sized for occupations <= 5; 1: the
+// same for <= 8; 2: rank kernel, TMEM accumulators (<= 16); 0: Kronecker
+// kernel (anything else TF32/BF16x3 accept).  MCPT_TC_KERNEL=kron|rank8|rankbig
+// forces a kernel where the sizes allow it.
 int choose_variant(TcKind kind, const DimerDesc* h, int nd)
 {
     int omax = 0, nymax = 0;
@@ -1479,12 +1529,13 @@ int choose_variant(TcKind kind, const DimerDesc* h, int nd)
         nymax = std::max(nymax, h[k].nY);
     }
     const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
-    if (kind == TC_BF16X2) return omax <= kOB ? 1 : 2;   // rank kernels only (the tensor-core size limits fit them)
     const char* env = getenv("MCPT_TC_KERNEL");
-    if (env && !strcmp(env, "kron")) return 0;
+    // BF16x2 runs the rank kernels only (the tensor-core size limits always fit them)
+    if (env && !strcmp(env, "kron") && kind != TC_BF16X2) return 0;
     if (env && !strcmp(env, "rankbig") && fits_rank) return 2;
-    if (!fits_rank) return 0;
-    return omax <= kOB ? 1 : 2;
+    if (env && !strcmp(env, "rank8") && omax <= kOB) return 1;
+    if (!fits_rank) return kind == TC_BF16X2 ? 2 : 0;
+    return omax <= kOB5 ? 3 : omax <= kOB ? 1 : 2;
 }
 
 }  // namespace
@@ -1536,6 +1587,7 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
     }
     std::vector<int> vars;
     if (nymax <= kKCMax * kKC && omax <= kOBig) {
+        if (omax <= kOB5) vars.push_back(3);
         if (omax <= kOB) vars.push_back(1);
         vars.push_back(2);
     } else {
@@ -1682,11 +1734,17 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.tmem_cols = L.tmem_cols;
     P.kind = L.kind;
     P.kcs_max = L.kcs_max;
+    P.wait_ns = L.wait_ns ? L.wait_ns : kWaitNs;
+    P.withhold = L.withhold;
     void (*fn)(const TcParams);
     if (L.variant == 1)
         fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, false>
              : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, false>
                                    : k_half_tc_rank<TC_BF16X3, false>;
+    else if (L.variant == 3)
+        fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, false, kOB5>
+             : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, false, kOB5>
+                                   : k_half_tc_rank<TC_BF16X3, false, kOB5>;
     else if (L.variant == 2)
         fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, true>
              : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, true>

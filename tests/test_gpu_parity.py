@@ -345,8 +345,8 @@ def test_uneven_sizes_batch(prec):
         assert abs(pd[k, 1] - E[k, 1]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
 
 
-@pytest.mark.parametrize("prec,variant", [(p, v) for p in ("tf32", "bf16x3") for v in ("rank", "rankbig", "kron")]
-                         + [("bf16x2", "rank"), ("bf16x2", "rankbig")])
+@pytest.mark.parametrize("prec,variant", [(p, v) for p in ("tf32", "bf16x3") for v in ("rank", "rank8", "rankbig", "kron")]
+                         + [("bf16x2", v) for v in ("rank", "rank8", "rankbig")])
 def test_tensor_core_kernel_variants(lat8, prec, variant, monkeypatch):
     """Both tcgen05 kernels (forced through MCPT_TC_KERNEL) against the oracle.
     The rank-1 variant keeps each tensor-core sum to n2/8 steps; its mean
@@ -433,7 +433,7 @@ def test_autotuner_cache(lat8, prec, tmp_path):
         lines = cache.read_text().splitlines()
         assert len(lines) == 1, lines
     key, variant1, sf, grid, ms = lines[0].split()
-    assert key.startswith(prec + ":") and int(variant1) in (1, 2, 3) and int(sf) >= 2 and int(grid) >= 1
+    assert key.startswith(prec + ":") and int(variant1) in (1, 2, 3, 4) and int(sf) >= 2 and int(grid) >= 1
     print(f"{prec}: tuned {lines[0]}")
     for mj, mk, pd, tot in res:
         assert np.all(np.abs(pd[:, 0] - E[:, 0]) <= PER_DIMER[prec] * np.abs(E[:, 0]))
