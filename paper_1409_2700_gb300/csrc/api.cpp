@@ -933,7 +933,9 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
         h->capE2 = e2_bytes;
         h->epoch++;
     }
-    if ((st = ensure_shared(h, &h->dMon, &h->capMon, (size_t)2 * N * sizeof(double) + 2 * sizeof(double)))) return st;
+    // monomer halves, totals, then the reduction's scratch
+    if ((st = ensure_shared(h, &h->dMon, &h->capMon, ((size_t)2 * N + 2 + 4 * kReduceBlocks) * sizeof(double))))
+        return st;
     h->dTot = h->dMon + 2 * N;
     std::vector<size_t> work_off;
     if (is_tensor_form(prec)) {
@@ -1177,7 +1179,7 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
         launches++;
     }
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
-    CK(h, launch_reduce(h->dE2, D, L, h->dMon, h->dTot, h->stream));
+    CK(h, launch_reduce(h->dE2, D, L, h->dMon, h->dTot, h->dTot + 2, h->stream));
     if (P.coupling) {
         const char* tab = static_cast<const char*>(h->dCoup);
         const CoupTile* tiles = reinterpret_cast<const CoupTile*>(tab + P.off_tiles);
@@ -1192,7 +1194,7 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
                                        h->stream));
         launches += (P.ntile[0] > 0) + (P.ntile[1] > 0) + (P.ntile[2] > 0);
     }
-    launches++;
+    launches += 2;   // the reduction: partial sums, then their merge
     if (ev) CK(h, cudaEventRecord((*ev)[2 * W + 1], h->stream));
     *launches_out = launches;
     return MCPT_OK;
@@ -1494,7 +1496,9 @@ mcpt_status mcpt_run_df(mcpt_handle h)
     const size_t halfb = ((size_t)hoff * es + 255) & ~(size_t)255;
     const size_t partb = 2 * (size_t)poff * sizeof(double);
     if ((st = ensure(h, &h->dDf, &h->capDf, tab + halfb + partb))) return st;
-    if ((st = ensure(h, &h->dDfOut, &h->capDfOut, (2 * (size_t)D + 2 * (size_t)N + 2) * sizeof(double)))) return st;
+    if ((st = ensure(h, &h->dDfOut, &h->capDfOut,
+                     (2 * (size_t)D + 2 * (size_t)N + 2 + 4 * kReduceBlocks) * sizeof(double))))
+        return st;
     if ((st = ensure(h, &h->dDfLists, &h->capDfLists, lists.size() * sizeof(int)))) return st;
     char* base = static_cast<char*>(h->dDf);
     CK(h, cudaMemcpyAsync(base, dims.data(), (size_t)D * sizeof(DfDim), cudaMemcpyHostToDevice, h->stream));
@@ -1503,7 +1507,8 @@ mcpt_status mcpt_run_df(mcpt_handle h)
     CK(h, launch_df(fp64, reinterpret_cast<const DfDim*>(base), D, max_naux, max_pairs, max_on, max_v, h->dC, h->dE,
                     base + tab, reinterpret_cast<double*>(base + tab + halfb), E2, h->stream));
     MonomerLists L{h->dDfLists, h->dDfLists + N + 1, N};
-    CK(h, launch_reduce(E2, D, L, E2 + 2 * (size_t)D, E2 + 2 * (size_t)D + 2 * (size_t)N, h->stream));
+    CK(h, launch_reduce(E2, D, L, E2 + 2 * (size_t)D, E2 + 2 * (size_t)D + 2 * (size_t)N,
+                        E2 + 2 * (size_t)D + 2 * (size_t)N + 2, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));   // the host tables go out of scope
     h->df_ran = true;
     return MCPT_OK;

@@ -231,9 +231,12 @@ cudaError_t launch_df(bool fp64, const DfDim* dims, int nd, int max_naux, int ma
 // each (dimer, first, n) triple of `fold` (device, 3 ints each).
 cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s);
 
-// Per-monomer halves and the compensated lattice total.
+// Per-monomer halves and the compensated lattice total (two launches: the
+// per-monomer sums with the total's block partials, then their merge).
+// scratch: 4 * kReduceBlocks doubles.
+constexpr int kReduceBlocks = 128;
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists,
-                          double* mon /* 2*n_mon */, double* total /* 2 */, cudaStream_t s);
+                          double* mon /* 2*n_mon */, double* total /* 2 */, double* scratch, cudaStream_t s);
 
 // Finiteness check of n doubles; sets *flag to 1 if any is NaN/Inf.
 // Symmetry-packed dimer integrals (MCPT_AO_PACKED): packed_elems(nX, nY)

@@ -509,20 +509,37 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double v)
 }
 
 constexpr int kRedThreads = 256;
+constexpr int kMonThreads = 32;   // per-monomer sums: small blocks, so that many SMs' FP64 pipes share them
 
 // Blocks [0, nbm): one thread per monomer sums half of each of its dimers'
-// terms in ascending dimer order.  Last block: lattice totals from a fixed
-// partition of the dimer list into kRedThreads contiguous chunks (Neumaier
-// within a chunk), merged by a fixed pairwise tree.  Long dependent FP64
-// chains are slow on GB300, so no thread walks more than a chunk.
-__global__ void __launch_bounds__(kRedThreads)
-k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restrict__ mon,
-         double* __restrict__ total)
+// terms in ascending dimer order.  Blocks [nbm, nbm + nbt): lattice-total
+// partials, block b over a fixed contiguous range of the dimer list, its
+// threads over fixed sub-chunks (Neumaier), merged by a fixed pairwise tree
+// (Knuth's TwoSum keeps each merge's rounding); k_total_merge then adds the
+// block partials by the same tree.  Long dependent FP64 chains are slow on
+// GB300 and one SM's FP64 pipe is small, so the work is spread over many
+// blocks; the partition depends only on the dimer count, so every run
+// gives the same bits.
+__device__ __forceinline__ void twosum_merge(double* part, int t, int w)
 {
-    const int nbm = (L.n_mon + kRedThreads - 1) / kRedThreads;
+#pragma unroll
+    for (int f = 0; f < 4; f += 2) {
+        const double a = part[f * kRedThreads + t], b = part[f * kRedThreads + t + w];
+        const double s = a + b;
+        const double bp = s - a;
+        const double err = (a - (s - bp)) + (b - bp);
+        part[f * kRedThreads + t] = s;
+        part[(f + 1) * kRedThreads + t] = part[(f + 1) * kRedThreads + t] + part[(f + 1) * kRedThreads + t + w] + err;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restrict__ mon, int nbm, int nbt,
+         double* __restrict__ partials)
+{
     if ((int)blockIdx.x < nbm) {
-        const int m = blockIdx.x * kRedThreads + threadIdx.x;
-        if (m >= L.n_mon) return;
+        const int m = blockIdx.x * kMonThreads + threadIdx.x;
+        if (threadIdx.x >= kMonThreads || m >= L.n_mon) return;
         double sj = 0, cj = 0, sk = 0, ck = 0;
         for (int k = L.start[m]; k < L.start[m + 1]; k++) {
             const int dslot = L.list[k];
@@ -533,36 +550,41 @@ k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restri
         mon[L.n_mon + m] = sk + ck;
         return;
     }
-    __shared__ double part[4][kRedThreads];
-    const int t = threadIdx.x;
-    const int chunk = (nd + kRedThreads - 1) / kRedThreads;
-    const int lo = t * chunk, hi = min(nd, lo + chunk);
+    __shared__ double part[4 * kRedThreads];
+    const int b = blockIdx.x - nbm, t = threadIdx.x;
+    const int per = (nd + nbt - 1) / nbt;
+    const int b0 = b * per, b1 = min(nd, b0 + per);
+    const int chunk = (per + kRedThreads - 1) / kRedThreads;
+    const int lo = b0 + t * chunk, hi = min(b1, lo + chunk);
     double sj = 0, cj = 0, sk = 0, ck = 0;
     for (int k = lo; k < hi; k++) {
         neumaier_add(sj, cj, E2[2 * k]);
         neumaier_add(sk, ck, E2[2 * k + 1]);
     }
-    part[0][t] = sj; part[1][t] = cj; part[2][t] = sk; part[3][t] = ck;
+    part[t] = sj; part[kRedThreads + t] = cj; part[2 * kRedThreads + t] = sk; part[3 * kRedThreads + t] = ck;
     __syncthreads();
-    // pairwise tree over the chunk partials, fixed pairing: (sum, compensation)
-    // pairs are merged with Knuth's TwoSum so the rounding of each merge is kept
     for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-        if (t < w) {
+        if (t < w) twosum_merge(part, t, w);
+        __syncthreads();
+    }
+    if (t < 4) partials[4 * b + t] = part[t * kRedThreads];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+k_total_merge(const double* __restrict__ partials, int nbt, double* __restrict__ total)
+{
+    __shared__ double part[4 * kRedThreads];
+    const int t = threadIdx.x;
 #pragma unroll
-            for (int f = 0; f < 4; f += 2) {
-                const double a = part[f][t], b = part[f][t + w];
-                const double s = a + b;
-                const double bp = s - a;
-                const double err = (a - (s - bp)) + (b - bp);
-                part[f][t] = s;
-                part[f + 1][t] = part[f + 1][t] + part[f + 1][t + w] + err;
-            }
-        }
+    for (int f = 0; f < 4; f++) part[f * kRedThreads + t] = t < nbt ? partials[4 * t + f] : 0.0;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (t < w) twosum_merge(part, t, w);
         __syncthreads();
     }
     if (t == 0) {
-        total[0] = part[0][0] + part[1][0];
-        total[1] = part[2][0] + part[3][0];
+        total[0] = part[0] + part[kRedThreads];
+        total[1] = part[2 * kRedThreads] + part[3 * kRedThreads];
     }
 }
 
@@ -631,10 +653,15 @@ cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s)
 }
 
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists, double* mon, double* total,
-                          cudaStream_t s)
+                          double* scratch, cudaStream_t s)
 {
-    const int nbm = (lists.n_mon + kRedThreads - 1) / kRedThreads;
-    k_reduce<<<nbm + 1, kRedThreads, 0, s>>>(E2, nd, lists, mon, total);
+    const int nbm = (lists.n_mon + kMonThreads - 1) / kMonThreads;
+    // about 512 dimers per total block, at most kReduceBlocks blocks
+    const int nbt = std::max(1, std::min(kReduceBlocks, (nd + 511) / 512));
+    k_reduce<<<nbm + nbt, kRedThreads, 0, s>>>(E2, nd, lists, mon, nbm, nbt, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_total_merge<<<1, kRedThreads, 0, s>>>(scratch, nbt, total);
     return cudaGetLastError();
 }
 

@@ -185,33 +185,98 @@ __device__ __forceinline__ void tc_mma(unsigned dtmem, unsigned long long adesc,
             : "memory");
 }
 
-// 32 lanes x 16 consecutive 32-bit columns per warp
+// TMEM loads whose destination registers are produced only once the data
+// has landed: the loads and tcgen05.wait::ld sit in one asm statement, so the
+// compiler can neither read nor spill a destination while its load is pending.
+// tmem_ld_l<L>x<J>: L loads of J columns, 16 columns apart, from taddr.
+__device__ __forceinline__ void tmem_ld_l1x8(unsigned taddr, unsigned (&r)[8])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr + 0u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l1x16(unsigned taddr, unsigned (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr + 0u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l3x8(unsigned taddr, unsigned (&r)[24])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%24];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%25];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%26];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l3x16(unsigned taddr, unsigned (&r)[48])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%48];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%49];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%50];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l4x8(unsigned taddr, unsigned (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%33];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%34];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%35];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l4x16(unsigned taddr, unsigned (&r)[64])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_acc64(unsigned taddr, unsigned (&r)[64])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+        : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns per warp, as floats
 __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v)
 {
     unsigned r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tmem_ld_l1x16(taddr, r);
 #pragma unroll
     for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
-// Batched TMEM access for the accumulators that live in TMEM: loads without
-// the wait (issue several, then one tcgen05.wait::ld) and stores.
-__device__ __forceinline__ void tmem_ld16_nowait(unsigned taddr, unsigned (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// TMEM stores of the accumulators that live in TMEM (tcgen05.wait::st before
+// the columns are read again).
 __device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&r)[16])
 {
     asm volatile(
@@ -668,9 +733,15 @@ constexpr int kFxUnits = 8;       // BF16x3: 4-slot p0 units in 512 columns (4 w
 constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
 constexpr int kOB5 = 5;           // the same sized for o_X, o_Y <= 5 (fewer rank-1 FMAs)
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
-constexpr int kConvWarps = 8;     // two converter warps per SM sub-partition
-constexpr int kEpiWarp0 = 2 + kConvWarps;
-constexpr int kRankThreads = (kEpiWarp0 + 4) * 32;
+constexpr int kConvWarps = 8;     // converter warps per group: one unit (128 rows) per group
+// Groups of converter warps take alternate units.  The variant with
+// occupations <= 5 runs two (four converter warps per SM sub-partition: the
+// converters are latency bound) within the register budget that 22 warps
+// leave; the others keep one group and the larger per-thread budget.
+template <bool BIG, int OB>
+__host__ __device__ constexpr int conv_groups() { return (!BIG && OB == 5) ? 2 : 1; }
+template <bool BIG, int OB>
+__host__ __device__ constexpr int rank_threads() { return (2 + kConvWarps * conv_groups<BIG, OB>() + 4) * 32; }
 constexpr int kOBig = 16;         // TMEM accumulators: o_X, o_Y <= 16
 // C_X occupied rows of one item (n0 <= 128), per parity: the register
 // accumulator kernel stages kOB columns, the TMEM one kOBig.
@@ -865,21 +936,6 @@ __device__ __forceinline__ void convert_row(const double* __restrict__ F, unsign
     }
 }
 
-// Columns 0..NJ-1 of 32 lanes x 32-bit TMEM starting at taddr, without the
-// wait (NJ = 8 or 16; tcgen05.wait::ld before use).
-template <int NJ>
-__device__ __forceinline__ void tmem_ld_cols(unsigned taddr, unsigned (&r)[NJ])
-{
-    if constexpr (NJ == 16) {
-        tmem_ld16_nowait(taddr, r);
-    } else {
-        static_assert(NJ == 8, "8 or 16 columns");
-        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                     : "r"(taddr));
-    }
-}
-
 // Digit levels the epilogue combines: BF16x3 four, BF16x2 three (its fourth,
 // A0 B3 + A1 B2, lies 2^-24 below the first and is not formed).
 template <int KIND>
@@ -896,9 +952,13 @@ __device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[NJ], const flo
 {
     constexpr int NL = n_levels<KIND>();
     unsigned raw[NL][NJ];
-#pragma unroll
-    for (int l = 0; l < NL; l++) tmem_ld_cols<NJ>(taddr + (unsigned)(l * kNT), raw[l]);
-    tmem_wait_ld();
+    unsigned(&flat)[NL * NJ] = *reinterpret_cast<unsigned(*)[NL * NJ]>(&raw[0][0]);
+    if constexpr (NL == 1 && NJ == 8) tmem_ld_l1x8(taddr, flat);
+    else if constexpr (NL == 1 && NJ == 16) tmem_ld_l1x16(taddr, flat);
+    else if constexpr (NL == 3 && NJ == 8) tmem_ld_l3x8(taddr, flat);
+    else if constexpr (NL == 3 && NJ == 16) tmem_ld_l3x16(taddr, flat);
+    else if constexpr (NL == 4 && NJ == 8) tmem_ld_l4x8(taddr, flat);
+    else tmem_ld_l4x16(taddr, flat);
     if constexpr (KIND == TC_TF32) {
 #pragma unroll
         for (int j = 0; j < NJ; j++) T[j] = add ? T[j] + __uint_as_float(raw[0][j]) : __uint_as_float(raw[0][j]);
@@ -1050,8 +1110,11 @@ __device__ __forceinline__ bool load_p0_T(float (&T)[NJ], RankShared* sh, unsign
 }
 
 template <int KIND, bool BIG, int OB = kOB>
-__global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams P)
+__global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(const TcParams P)
 {
+    constexpr int NG = conv_groups<BIG, OB>();      // converter groups
+    constexpr int CT = kConvWarps * NG;             // converter warps
+    constexpr int EW0 = 2 + CT;                     // first epilogue warp
     constexpr bool FX = KIND != TC_TF32;            // fixed-point digit planes (BF16x3, BF16x2)
     constexpr int UC = unit_cols<KIND, BIG>();      // TMEM columns per p0 unit
     constexpr int NS = n_units<KIND, BIG>();        // p0 units in the ring
@@ -1077,7 +1140,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
         for (int s = 0; s < P.sf; s++) { mbar_init(&sh->full_f[s], 1); mbar_init(&sh->empty_f[s], kConvWarps); }
         for (int s = 0; s < 2; s++) {
             mbar_init(&sh->full_a[s], kConvWarps); mbar_init(&sh->empty_a[s], 1);
-            mbar_init(&sh->full_w[s], kConvWarps); mbar_init(&sh->empty_w[s], 1);
+            mbar_init(&sh->full_w[s], CT); mbar_init(&sh->empty_w[s], 1);
             mbar_init(&sh->cx_full[s], 128); mbar_init(&sh->cx_empty[s], 128);
         }
         for (int s = 0; s < kSlots; s++) { mbar_init(&sh->slot_full[s], 1); mbar_init(&sh->slot_empty[s], 4); }
@@ -1222,10 +1285,12 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 while (!mbar_test(&sh->drain, 0) && now_ns() - t0 < kWaitNs) {}
             }
         }
-    } else if (warp < kEpiWarp0) {
+    } else if (warp < EW0) {
         // ------------------------------------------------ converters
-        const int ct = threadIdx.x - 64;        // 0 .. 32*kConvWarps-1
-        // tile row and first chunk; BF16x3 keeps both threads of a row in one warp
+        const int cta = threadIdx.x - 64;                // 0 .. 32*CT-1
+        const int grp = cta / (32 * kConvWarps);         // this warp's group: units with gA % NG == grp
+        const int ct = cta % (32 * kConvWarps);          // position within the group
+        // tile row and first chunk; the fixed-point forms keep both threads of a row in one warp
         const int r = FX ? (((ct >> 5) << 4) | (lane & 15)) : (ct & 127);
         const int c0 = FX ? (lane >> 4) : (ct >> 7);
         unsigned gF = 0, gA = 0, gU = 0, li = 0;
@@ -1244,17 +1309,20 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
             if constexpr (FX) {
                 // largest exponent field of each occupied C_Y column: 16 parts x 16
                 // columns, each part a strided eighth of the rows, then combined
-                const int j = ct & 15, part = ct >> 4;
-                int fm = 0;
+                // (the first group forms the parts, every converter reads them)
+                if (grp == 0) {
+                    const int j = ct & 15, part = ct >> 4;
+                    int fm = 0;
 #pragma unroll
-                for (int t = 0; t < 8; t++) {
-                    const int p2 = part + 16 * t;
-                    if (j < g.o2 && p2 < g.n2)
-                        fm = max(fm, (int)((__float_as_uint(__ldg(CY + p2 * d.nY + j)) >> 23) & 0xFFu));
+                    for (int t = 0; t < 8; t++) {
+                        const int p2 = part + 16 * t;
+                        if (j < g.o2 && p2 < g.n2)
+                            fm = max(fm, (int)((__float_as_uint(__ldg(CY + p2 * d.nY + j)) >> 23) & 0xFFu));
+                    }
+                    cx_part[part * kNT + j] = fm;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->colx_full[wp]);
                 }
-                cx_part[part * kNT + j] = fm;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sh->colx_full[wp]);
                 if (!(ok = mbar_wait(&sh->colx_full[wp], (li >> 1) & 1, abort, P.status, 24, P.wait_ns))) break;
                 if (ct < kNT) {
                     int m = 0;
@@ -1267,7 +1335,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                                        : Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                 unsigned char* W1 = W0 + kNT * 128;
                 if (KIND == TC_TF32) {
-                    for (int task = ct; task < kNT * 8; task += 32 * kConvWarps) {
+                    for (int task = cta; task < kNT * 8; task += 32 * CT) {
                         const int j = task >> 3, c = task & 7;
                         unsigned h4[4], l4[4];
 #pragma unroll
@@ -1282,7 +1350,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                     }
                 } else {
                     // C_Y column j in fixed point relative to its largest exponent, four digits
-                    for (int task = ct; task < kNT * 4; task += 32 * kConvWarps) {
+                    for (int task = cta; task < kNT * 4; task += 32 * CT) {
                         const int j = task >> 2, c = task & 3;
                         int fmax = 0;
                         for (int q = 0; q < 16; q++) fmax = max(fmax, cx_part[q * kNT + j]);
@@ -1315,6 +1383,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                 for (int p0 = 0; p0 < g.n0 && ok; p0++) {
                     if constexpr (!FX) {
                         for (int kc = 0; kc < g.kcs; kc++, gF++, gA++) {
+                            if ((int)(gA % NG) != grp) continue;   // the other group's unit
                             const int s = gF % P.sf;
                             if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16, P.wait_ns))) break;
                             const int as = gA & 1;
@@ -1333,6 +1402,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         // one unit per p2 chunk: fused load, row maximum and digit planes,
                         // then the unit's row and column scales for the epilogue
                         for (int kc = 0; kc < g.kcs && ok; kc++, gF++, gA++, gU++) {
+                            if ((int)(gA % NG) != grp) continue;   // the other group's unit
                             const int s = gF % P.sf;
                             if (!(ok = mbar_wait(&sh->full_f[s], (gF / P.sf) & 1, abort, P.status, 16, P.wait_ns))) break;
                             const int as = gA & 1;
@@ -1366,7 +1436,7 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
         // ------------------------------------------------ epilogue
         const int q = warp & 3;
         const int r = q * 32 + lane;                    // accumulator row = TMEM lane
-        const int e = (warp - kEpiWarp0) * 32 + lane;   // 0..127: C_X row this thread stages
+        const int e = (warp - EW0) * 32 + lane;   // 0..127: C_X row this thread stages
         unsigned gS = 0, li = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
@@ -1440,9 +1510,8 @@ __global__ void __launch_bounds__(kRankThreads, 1) k_half_tc_rank(const TcParams
                         for (int ic = 0; ic < nchunk; ic++) {
                             unsigned a[4][16];
                             if (p0 > 0) {
-#pragma unroll
-                                for (int u = 0; u < 4; u++) tmem_ld16_nowait(accbase + (unsigned)((ic * 4 + u) * 16), a[u]);
-                                tmem_wait_ld();
+                                tmem_ld_acc64(accbase + (unsigned)(ic * 64),
+                                              *reinterpret_cast<unsigned(*)[64]>(&a[0][0]));
                             } else {
 #pragma unroll
                                 for (int u = 0; u < 4; u++)
@@ -1754,7 +1823,11 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    fn<<<L.grid, L.variant >= 1 ? kRankThreads : kThreadsTc, L.smem, s>>>(P);
+    const int threads = L.variant == 3   ? rank_threads<false, kOB5>()
+                        : L.variant == 2 ? rank_threads<true, kOB>()
+                        : L.variant == 1 ? rank_threads<false, kOB>()
+                                         : kThreadsTc;
+    fn<<<L.grid, threads, L.smem, s>>>(P);
     return cudaGetLastError();
 }
 
