@@ -1,12 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the first-order MCPT(2) dimer term on one GB300.
 
-Workload (default): lattice-5x5x5-cheb1 -- 125 monomers of 32 AO / 5 occupied
-on a 3.0 A cubic lattice, all 1036 dimers with Chebyshev distance <= 1, the
-dimer's AO integral blocks (2 x 32^4 FP64 = 16.8 MB each, 17.4 GB in all,
-far above the 129 MB L2) resident in HBM.  A step is one mcpt_run over every
-dimer: the first half (the AO-reading transform), the second half with FP64
-denominators and energies, and the per-monomer accumulation.
+Workload (default): lattice-10x10x10-cheb2 -- 1000 monomers of 32 AO / 5
+occupied on a 3.0 A cubic lattice, all 42,092 dimers with Chebyshev distance
+<= 2, 706 GB of FP64 integral blocks (2 x 32^4 per dimer), more than the
+device holds.  They run in waves through one context: each wave's blocks are
+generated on the device (untimed), then one step = one wave (~2,300 dimers,
+36 GB, far above the 129 MB L2) through the whole path -- the first half (the
+AO-reading transform), the second half with FP64 denominators and energies,
+and the per-monomer accumulation -- in the BF16x2 form unless --precision
+says otherwise.  The line carries the full-lattice error against the stored
+oracle values, the FP64 form on the same waves, the CPU oracle on a sample
+and an end-to-end leg through the C ABI from pinned host buffers.
+--workload lattice-5x5x5-cheb1 (resident, 1036 dimers) and the other
+workloads run the same path.
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
 """
@@ -34,11 +41,14 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="tf32", choices=["tf32", "bf16x3", "bf16x2", "fp32c", "fp64"])
+    p.add_argument("--precision", default="bf16x2", choices=["tf32", "bf16x3", "bf16x2", "fp32c", "fp64"])
     p.add_argument("--workload", default="lattice-10x10x10-cheb2")
     p.add_argument("--wave-gb", type=float, default=WAVE_BUDGET / (1 << 30),
                    help="streamed workloads: GiB of integral blocks per wave (one wave = one step)")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--tune", type=int, default=1, help="streamed workloads: autotune each wave's launch choices (1/0)")
+    p.add_argument("--max-waves", type=int, default=64,
+                   help="streamed workloads with more waves run only the waves the steps cover")
     p.add_argument("--cpu-sample", type=int, default=1024, help="dimers in the oracle's timed sample (at most)")
     p.add_argument("--no-extras", action="store_true",
                    help="report none of the extras (coupling, td2, df, FP64 form, e2e, CPU baseline)")
@@ -633,6 +643,13 @@ def _alg_bytes(w, d0, n):
     return float(sum(2 * 8 * w.nao[w.pairs[d][0]] ** 2 * w.nao[w.pairs[d][1]] ** 2 for d in range(d0, d0 + n)))
 
 
+def _tune_lines(path):
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return [ln.strip() for ln in f if ln.strip()]
+
+
 def _alg_flops(w, d0, n):
     """(all, first half) algorithmic transform flops of dimers d0 .. d0+n-1:
     the occupied-first factorised count, both forms."""
@@ -656,29 +673,48 @@ def streamed_arm(args, ws, rank, local):
     import synth.device
     from paper_1409_2700_gb300.stream import Streamed
 
+    from paper_1409_2700_gb300.stream import block_elems, plan_waves
     torch.cuda.set_device(local)
     w = synth.workload(args.workload)
     if args.max_dimers:
         w.pairs, w.R = w.pairs[:args.max_dimers], w.R[:args.max_dimers]
+    n_all = w.n_dimers
+    # a lattice whose generation alone would take many minutes per pass (the
+    # 128-AO one: 4.3 GB and ~0.2 s of FP64 GEMMs per dimer) runs the dimers
+    # of the waves the steps cover, not the whole list
+    budget = int(args.wave_gb * (1 << 30))
+    full_waves = plan_waves([block_elems(w.nao[X], w.nao[Y]) for X, Y in w.pairs], budget // 8)[0]
+    subset = len(full_waves) > args.max_waves
+    if subset:
+        keep = sum(c for _, c in full_waves[:max(1, args.steps)])
+        w.pairs, w.R = w.pairs[:keep], w.R[:keep]
     extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
+    if any(n > 96 for n in w.nao):
+        extras.discard("fp64")                      # the FP64 form handles monomers of up to 96 AO
     stream = torch.cuda.Stream()
     mons = [w.monomer(X) for X in range(w.n_monomers)]
 
+    tune = os.path.join(tempfile.gettempdir(), f"mcpt_tune_{os.getpid()}.txt") if args.tune else None
+
     def make_ctx(prec, timing, graphs=True):
         c = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing,
-                      graphs=graphs)
+                      graphs=graphs, tune_cache=tune if prec != "fp64" else None)
         for m in mons:
             c.add_monomer(m.C, m.eps, m.nocc)
         return c
 
-    ctx = make_ctx(args.precision, True)
-    ctxs = [ctx]
+    # the timed value: each wave's run replayed as its plan's CUDA graph; a
+    # second context with per-phase CUDA events (same launch choices) runs the
+    # same waves for the phase times and the roofline
+    ctx = make_ctx(args.precision, False)
+    ctx_t = make_ctx(args.precision, True)
+    ctxs = [ctx, ctx_t]
     c64 = None
     if rank == 0 and "fp64" in extras and args.precision != "fp64":
         c64 = make_ctx("fp64", True)
         ctxs.append(c64)
     with torch.cuda.stream(stream):
-        st = Streamed(ctxs, w.pairs, w.nao, int(args.wave_gb * (1 << 30)))
+        st = Streamed(ctxs, w.pairs, w.nao, budget)
         nw = len(st)
         st.buf.zero_()
         synth.device.fill_views(w, st.views(0))
@@ -687,8 +723,9 @@ def streamed_arm(args, ws, rank, local):
             st.run(k)
         for _ in range(max(args.warmup, 3)):
             ctx.run(*st.waves[0])
+            ctx_t.run(*st.waves[0])
         stream.synchronize()
-        for c in ctxs:
+        for c in ctxs[1:]:
             c.stats()
         ev, ev64, done, done64 = [], [], set(), set()
         t_gen, timed_dimers, timed_bytes, timed_flops, timed_half, filled = 0.0, 0, 0.0, 0.0, 0.0, 0
@@ -707,6 +744,7 @@ def streamed_arm(args, ws, rank, local):
                 ctx.run(*st.waves[k])
                 e1.record(stream)
                 ev.append((e0, e1))
+                ctx_t.run(*st.waves[k])
                 timed_dimers += st.waves[k][1]
                 timed_bytes += _alg_bytes(w, *st.waves[k])
                 timed_flops += wave_flops[k][0]
@@ -722,7 +760,7 @@ def streamed_arm(args, ws, rank, local):
             stream.synchronize()
         clocks = clk.summary()
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        stt = ctx.stats()
+        stt = ctx_t.stats()
         s64 = c64.stats() if c64 is not None else None
         # the waves the steps did not reach, untimed, so that the lattice is complete
         for k in range(nw):
@@ -733,6 +771,7 @@ def streamed_arm(args, ws, rank, local):
                 filled = k
             if k not in done:
                 ctx.run(*st.waves[k])
+                ctx_t.run(*st.waves[k])
             if c64 is not None and k not in done64:
                 c64.run(*st.waves[k])
         stream.synchronize()
@@ -767,16 +806,21 @@ def streamed_arm(args, ws, rank, local):
                    "nao": sorted(set(w.nao)), "nocc": sorted(set(w.nocc)), "precision": args.precision,
                    "inputs_gb": round(_alg_bytes(w, 0, w.n_dimers) / 1e9, 1), "waves": nw,
                    "dimers_per_step": round(timed_dimers / nsteps, 1),
+                   "dimers_run": w.n_dimers if not subset else
+                   f"the first {w.n_dimers} of {n_all} (the waves the steps cover; {len(full_waves)} waves in all)",
                    "step": "one wave: every dimer of the wave through the whole path (first half, second half "
                            "with FP64 denominators and energies, per-monomer reduction); waves in lattice order",
                    "timed": "CUDA events around each wave's run; on-device generation of each wave untimed",
                    "l2": "inputs (tens of GB per wave) larger than L2"},
         "phase_ms_per_step": {"first_half": stt.ms[0] / nsteps, "finish": stt.ms[1] / nsteps,
-                              "reduce": stt.ms[2] / nsteps},
+                              "reduce": stt.ms[2] / nsteps, "run": stt.ms[3] / nsteps,
+                              "note": "eagerly launched twin context with per-phase CUDA events"},
+        "graphs": "each wave's run replayed as its plan's captured CUDA graph",
+        "autotuner": _tune_lines(tune),
         "transform_tflops": timed_flops / (ms * 1e-3) / 1e12,
         "generation_s_per_step": t_gen / nsteps,
         "roofline": roof,
-        "gpu_launches": stt.launches,
+        "gpu_launches": stt.launches,   # the twin's count: a graph replays the same launches
         "clocks": clocks,
         "lattice_E": {"J": tot[0], "K": tot[1]},
     }
@@ -790,11 +834,16 @@ def streamed_arm(args, ws, rank, local):
         g = None
     if g is not None:
         Eo, to = g
-        line["error_eh"] = {"lattice_J": float(tot[0] - to[0]), "lattice_K": float(tot[1] - to[1]),
-                            "max_dimer_J": float(np.max(np.abs(pd[:, 0] - Eo[:, 0]))),
-                            "max_dimer_K": float(np.max(np.abs(pd[:, 1] - Eo[:, 1]))),
-                            "max_dimer_rel_J": float(np.max(np.abs(pd[:, 0] - Eo[:, 0]) / np.abs(Eo[:, 0]))),
-                            "reference": f"FP64 oracle (factor route), stored values of all {w.n_dimers} dimers"}
+        nd = min(len(Eo), w.n_dimers)
+        err = {"max_dimer_J": float(np.max(np.abs(pd[:nd, 0] - Eo[:nd, 0]))),
+               "max_dimer_K": float(np.max(np.abs(pd[:nd, 1] - Eo[:nd, 1]))),
+               "max_dimer_rel_J": float(np.max(np.abs(pd[:nd, 0] - Eo[:nd, 0]) / np.abs(Eo[:nd, 0]))),
+               "sum_J_of_those_dimers": float(pd[:nd, 0].sum() - Eo[:nd, 0].sum())}
+        if not subset and nd == w.n_dimers and to[0] is not None:
+            err["lattice_J"] = float(tot[0] - to[0])
+            err["lattice_K"] = float(tot[1] - to[1])
+        err["reference"] = f"FP64 oracle (factor route), stored values of {nd} of the {w.n_dimers} dimers run"
+        line["error_eh"] = err
 
     # ---- the plain FP64 GPU form on the same waves (each wave once)
     if c64 is not None:
@@ -809,8 +858,10 @@ def streamed_arm(args, ws, rank, local):
                              "unit": "TFLOP/s", "kernel": "k_half_fp64", "peak_kind": rate["kind"]}}
         fp64["roofline"]["frac"] = fp64["roofline"]["achieved"] / rate["tflops"]
         if g is not None:
-            fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
-            fp64["max_dimer_rel_J"] = float(np.max(np.abs(pd64[:, 0] - g[0][:, 0]) / np.abs(g[0][:, 0])))
+            nd = min(len(g[0]), w.n_dimers)
+            if not subset and nd == w.n_dimers and g[1][0] is not None:
+                fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
+            fp64["max_dimer_rel_J"] = float(np.max(np.abs(pd64[:nd, 0] - g[0][:nd, 0]) / np.abs(g[0][:nd, 0])))
         line["fp64_form"] = fp64
 
     # ---- the oracle on the host cores: evenly spaced dimers of the wave in the

@@ -35,15 +35,35 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
-// Newton steps of the denominator: full FP64 accuracy for the FP64 form.
-template <typename T> constexpr int kSteps = sizeof(T) == 8 ? 2 : 1;
-
-__device__ __forceinline__ double to_f64(double x) { return x; }
 // FP64 to the storage type (FP32 through the integer pipes)
 template <typename T> __device__ __forceinline__ T narrow(double x);
 template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
 template <> __device__ __forceinline__ float narrow<float>(double x) { return f32_from_f64(x); }
-__device__ __forceinline__ double to_f64(float x) { return f64_from_f32(x); }   // integer pipes
+
+// The energy terms of one (i, a, j, b) with v = (ia|jb), vk = (ib|ja) and the
+// FP64 denominator x = e_i + e_j - e_a - e_b: D = 1/x in FP64, then
+// E_J += v^2 D and E_K += v vk D as FP64 sums; *vd (may be null) gets v D.
+// FP64 form: v D by two Newton steps from an FP32 seed, the last folded into
+// the product (full FP64 accuracy).  Mixed forms: D = r + r (1 - x r) from
+// the FP32 seed r (relative error ~2^-46), v^2 and v vk as FP32 products (one
+// rounding of 2^-24, far below the error these forms carry into v): five
+// FP64 operations per term, the fewest that keep D and the sums in FP64.
+template <typename T>
+__device__ __forceinline__ void energy_terms(T v, T vk, double x, double& ej, double& ek, double* vd)
+{
+    if constexpr (sizeof(T) == 8) {
+        const double t = div_newton<2>(v, x);
+        ej = fma(t, v, ej);
+        ek = fma(t, vk, ek);
+        if (vd) *vd = t;
+    } else {
+        const double r = rcp_seed_f64(x);
+        const double D = fma(r, fma(-x, r, 1.0), r);
+        ej = fma(f64_from_f32(v * v), D, ej);
+        ek = fma(f64_from_f32(v * vk), D, ek);
+        if (vd) *vd = f64_from_f32(v) * D;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // Monomers of at most 32 AO: one warp per occupied pair (i, j).
@@ -208,10 +228,8 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 }
                 if (live) {
                     const T vab = SX[lane * 33 + b];
-                    const double va = to_f64(vab);
-                    const double t = div_newton<kSteps<T>>(va, eija - eYv[b]);   // v D
-                    ej = fma(t, va, ej);
-                    ek = fma(t, to_f64(v0 + v1), ek);
+                    double t;
+                    energy_terms<T>(vab, v0 + v1, eija - eYv[b], ej, ek, store ? &t : nullptr);
                     if (store) {
                         const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
                         Vst[e] = vab;
@@ -410,10 +428,8 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
                     const int m = m0 + a, n = n0 + b;
                     if (m < vX && n < vY) {
                         const T vab = Vp[m * vY + n];
-                        const double va = to_f64(vab);
-                        const double t = div_newton<kSteps<T>>(va, eij - (eXv[m] + eYv[n]));   // v D
-                        ej = fma(t, va, ej);
-                        ek = fma(t, to_f64(acc[a][b]), ek);
+                        double t;
+                        energy_terms<T>(vab, acc[a][b], eij - (eXv[m] + eYv[n]), ej, ek, store ? &t : nullptr);
                         if (store) {
                             const long long e =
                                 ((long long)(d.jY0 + j) * vY + n) * mXc + (long long)(d.iX0 + i) * vX + m;
