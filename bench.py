@@ -162,13 +162,12 @@ def fp64_rate(device):
     return _FP64_RATE[device]
 
 
-# DRAM traffic of the first-half kernel per dimer, from the full ncu captures
-# in profiles/k_half_tc_rank_{tf32,bf16x3}_lattice-2x2x2.md
+# DRAM traffic of the first-half kernel per dimer, from the full ncu capture
+# of the current kernel in profiles/k_half_tc_rank_bf16x2_lattice-2x2x2.md
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 28 dimers
-# of 32 AO / 5 occupied, scaled per dimer).  Only valid for those kernels,
-# forms and monomer sizes.
-TRAFFIC_PER_DIMER = {("tf32", 32, 5): (469.900032e6 + 4.843776e6) / 28,
-                     ("bf16x3", 32, 5): (469.928448e6 + 6.055936e6) / 28}
+# of 32 AO / 5 occupied, scaled per dimer).  Only valid for that kernel, form
+# and monomer size; the other forms' kernels changed since their captures.
+TRAFFIC_PER_DIMER = {("bf16x2", 32, 5): (469.901824e6 + 6.035712e6) / 28}
 
 
 def host_sample(w, dimers):
@@ -570,8 +569,7 @@ def our_arm(args, ws, rank, local):
             for k in range(args.e2e_steps + 1):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                for d in range(w.n_dimers):
-                    c.update_dimer(d, base + 8 * doffs[d], layout, on_device=0, asynchronous=True)
+                c.update_dimers(0, w.n_dimers, base, doffs, layout, asynchronous=True)
                 c.run()
                 out = c.energies()
                 t1 = time.perf_counter()
@@ -587,9 +585,10 @@ def our_arm(args, ws, rank, local):
         line["e2e"] = {"value": w.n_dimers / ps, "unit": UNIT, "h2d_bytes_per_step": 8 * ptot,
                        "d2h_bytes_per_step": d2h, "s_per_step": ps, "steps": pn,
                        "terms_equal_resident_run": psame,
-                       "per_step": "mcpt_update_dimer of every dimer's symmetry-packed integrals (MCPT_AO_PACKED: "
-                                   "the unique elements, expanded on the device) from pinned host memory "
-                                   "(asynchronous), mcpt_run, mcpt_energies; context, monomers and plan set up once"}
+                       "per_step": "mcpt_update_dimers of every dimer's symmetry-packed integrals (MCPT_AO_PACKED: "
+                                   "the unique elements, back to back, copied in 256 MB chunks and expanded on the "
+                                   "device) from pinned host memory (asynchronous), mcpt_run, mcpt_energies; context, "
+                                   "monomers and plan set up once"}
         line["e2e_blocks"] = {"value": w.n_dimers / bs, "unit": UNIT, "h2d_bytes_per_step": blk_bytes,
                               "d2h_bytes_per_step": d2h, "s_per_step": bs, "steps": bn,
                               "terms_equal_resident_run": bsame,
@@ -951,9 +950,7 @@ def streamed_arm(args, ws, rank, local):
             for k, (lo, n, first) in enumerate(ranges):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                for j in range(n):
-                    ce.update_dimer(lo + j, hosts[k].data_ptr() + 8 * poffs[k][j], M.MCPT_AO_PACKED, on_device=0,
-                                    asynchronous=True)
+                ce.update_dimers(lo, n, hosts[k].data_ptr(), poffs[k], M.MCPT_AO_PACKED, asynchronous=True)
                 ce.run(lo, n)
                 out = ce.energies()
                 t1 = time.perf_counter()
@@ -967,9 +964,9 @@ def streamed_arm(args, ws, rank, local):
                        "d2h_bytes_per_step": 8 * (2 * w.n_monomers + 2 * base_id + 2),
                        "s_per_step": e2e_s / len(ts), "steps": len(ts),
                        "terms_equal_streamed_run": same,
-                       "per_step": "one wave: mcpt_update_dimer of each of its dimers from pinned host memory "
-                                   "(MCPT_AO_PACKED: the unique elements, asynchronous, expanded on the device), "
-                                   "mcpt_run of the wave, mcpt_energies"}
+                       "per_step": "one wave: mcpt_update_dimers of its dimers from pinned host memory "
+                                   "(MCPT_AO_PACKED: the unique elements, back to back, copied in 256 MB chunks and "
+                                   "expanded on the device, asynchronous), mcpt_run of the wave, mcpt_energies"}
         del hosts
     else:
         for c in ctxs:
