@@ -178,6 +178,22 @@ enum { MCPT_UPDATE_ASYNC = 1 };
 mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double *ao_eri, mcpt_ao_layout layout,
                               int on_device, int flags);
 
+/* mcpt_update_dimer for dimers first .. first+count-1 in one call, host
+ * memory only: dimer first+k's integrals at ao_eri + offsets[k] (elements),
+ * in `layout` (MCPT_AO_BLOCKS or MCPT_AO_PACKED) for its stored order, with
+ * the same flags and ownership rules.  For MCPT_AO_PACKED the dimers whose
+ * data lie back to back in the buffer are copied together, in chunks of up
+ * to 256 MB and 64 dimers through two device staging buffers, and each chunk
+ * is expanded by one launch: with pinned memory and MCPT_UPDATE_ASYNC the
+ * copies run at the link's bandwidth instead of being paced by one call per
+ * dimer.  A dimer whose integrals were borrowed device memory gets storage
+ * of its own (its run plan is rebuilt).  Not a step of the paper's method: the
+ * ingest of a sequence of lattices.
+ * Errors: EINVAL (range, NULL, layout, flags, non-finite with validate=1),
+ *   ENOMEM, ECUDA. */
+mcpt_status mcpt_update_dimers(mcpt_handle h, int first, int count, const double *ao_eri, const size_t *offsets,
+                               mcpt_ao_layout layout, int flags);
+
 /* Switch the transformation arithmetic for later runs (no re-upload). */
 mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p);
 

@@ -34,7 +34,7 @@ EXPORTS = ("mcpt_default_options", "mcpt_create", "mcpt_add_monomer", "mcpt_add_
            "mcpt_add_dimer_df", "mcpt_run_df", "mcpt_df_energies",
            "mcpt_collect_stats", "mcpt_num_monomers",
            "mcpt_num_dimers", "mcpt_last_error", "mcpt_destroy", "mcpt_dimer_fp64_noalloc",
-           "mcpt_fp64_fma_rate")
+           "mcpt_fp64_fma_rate", "mcpt_update_dimers")
 
 
 class McptError(RuntimeError):
@@ -101,6 +101,8 @@ def lib():
         L.mcpt_dimer_fp64_noalloc.restype = I
         L.mcpt_fp64_fma_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.mcpt_fp64_fma_rate.restype = I
+        L.mcpt_update_dimers.argtypes = [H, I, I, P, P, I, I]
+        L.mcpt_update_dimers.restype = I
         _lib = L
     return _lib
 
@@ -147,6 +149,17 @@ def mcpt_update_dimer(h, dimer: int, ao_eri, layout: int, on_device: int, flags:
     if isinstance(ao_eri, np.ndarray):
         ao_eri = np.ascontiguousarray(ao_eri, dtype=np.float64)
     _check(h, lib().mcpt_update_dimer(h, dimer, _ptr(ao_eri), layout, on_device, flags))
+
+
+def mcpt_update_dimers(h, first: int, count: int, ao_eri, offsets, layout: int, flags: int = 0) -> None:
+    """Host integrals of dimers first .. first+count-1: dimer first+k's at
+    element offsets[k] of ao_eri (a numpy array or a host address)."""
+    if isinstance(ao_eri, np.ndarray):
+        ao_eri = np.ascontiguousarray(ao_eri, dtype=np.float64)
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    if off.size != count:
+        raise ValueError("offsets must hold count entries")
+    _check(h, lib().mcpt_update_dimers(h, first, count, _ptr(ao_eri), off.ctypes.data, layout, flags))
 
 
 def mcpt_add_dimer(h, X: int, Y: int, ao_eri, layout: int, on_device: int) -> int:
@@ -300,6 +313,12 @@ class Context:
         if on_device is None:
             on_device = 0 if isinstance(ao_eri, np.ndarray) else 1
         mcpt_update_dimer(self.h, dimer, ao_eri, layout, on_device, MCPT_UPDATE_ASYNC if asynchronous else 0)
+
+    def update_dimers(self, first, count, ao_eri, offsets, layout=MCPT_AO_PACKED, asynchronous=False):
+        """New host integrals for dimers first .. first+count-1 in one call
+        (dimer first+k's at element offsets[k] of ao_eri): back-to-back
+        packed data goes over in large chunks."""
+        mcpt_update_dimers(self.h, first, count, ao_eri, offsets, layout, MCPT_UPDATE_ASYNC if asynchronous else 0)
 
     def set_precision(self, p):
         mcpt_set_precision(self.h, PRECISIONS[p] if isinstance(p, str) else int(p))

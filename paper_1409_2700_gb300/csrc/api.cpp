@@ -689,6 +689,101 @@ mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double* ao, mcpt_ao_l
     return MCPT_OK;
 }
 
+// Many dimers' new integrals in one call (host memory).  Packed data of
+// dimers that lie back to back in the caller's buffer is copied in chunks of
+// up to kUpdateChunk bytes (at most kUnpackBatch dimers) through the two
+// staging buffers on the copy stream, and each chunk is expanded into the
+// dimers' storage by one launch on the handle's stream; BLOCKS data goes
+// dimer by dimer straight into the storage (one copy each is already
+// link-bound).
+constexpr size_t kUpdateChunk = (size_t)256 << 20;
+
+mcpt_status mcpt_update_dimers(mcpt_handle h, int first, int count, const double* ao, const size_t* offsets,
+                               mcpt_ao_layout layout, int flags)
+{
+    if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_update_dimers: NULL handle");
+    const int D = (int)h->dims.size();
+    if (first < 0 || count < 0 || first + count > D)
+        return fail(h, MCPT_EINVAL, "mcpt_update_dimers: [%d, %d) outside [0, %d)", first, first + count, D);
+    if (count == 0) return MCPT_OK;
+    if (!ao || !offsets) return fail(h, MCPT_EINVAL, "mcpt_update_dimers: ao_eri or offsets is NULL");
+    if (layout != MCPT_AO_BLOCKS && layout != MCPT_AO_PACKED)
+        return fail(h, MCPT_EINVAL, "mcpt_update_dimers: layout must be MCPT_AO_BLOCKS or MCPT_AO_PACKED");
+    if (flags & ~MCPT_UPDATE_ASYNC) return fail(h, MCPT_EINVAL, "mcpt_update_dimers: unknown flags 0x%x", flags);
+    if (layout == MCPT_AO_BLOCKS) {
+        for (int k = 0; k < count; k++) {
+            mcpt_status st = mcpt_update_dimer(h, first + k, ao + offsets[k], layout, 0, flags);
+            if (st) return st;
+        }
+        return MCPT_OK;
+    }
+    CK(h, cudaSetDevice(h->device));
+    mcpt_status st;
+    std::vector<size_t> np(count);
+    bool moved = false;
+    for (int k = 0; k < count; k++) {
+        DimerRec& r = h->dims[first + k];
+        const int nX = h->mons[r.X].nao, nY = h->mons[r.Y].nao;
+        np[k] = packed_elems(nX, nY);
+        if (h->validate && !all_finite(ao + offsets[k], np[k]))
+            return fail(h, MCPT_EINVAL, "mcpt_update_dimers: non-finite integral (dimer %d)", first + k);
+        const size_t blk = (size_t)nX * nX * nY * nY;
+        if (!r.owned) {                       // only ever borrowed device data: storage of its own
+            void* dst = nullptr;
+            if ((st = arena_alloc(h, 2 * blk * sizeof(double), &dst))) return st;
+            r.owned = static_cast<double*>(dst);
+        }
+        if (r.E[0] != r.owned) {              // the record points at borrowed data: back to the storage
+            r.E[0] = r.owned;
+            r.st[0][0] = (long long)nX * nY * nY; r.st[0][1] = (long long)nY * nY; r.st[0][2] = nY;
+            r.E[1] = r.owned + blk;
+            r.st[1][0] = (long long)nY * nY * nX; r.st[1][1] = (long long)nY * nX; r.st[1][2] = nX;
+            moved = true;
+        }
+    }
+    if (moved) drop_plans(h);                 // the tensor maps name the old addresses
+    if (!h->copy_stream) {
+        CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; b++) {
+            CK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming));
+            CK(h, cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming));
+        }
+    }
+    const size_t chunk_elems = kUpdateChunk / sizeof(double);
+    for (int k = 0; k < count;) {
+        size_t elems = np[k];
+        int k2 = k + 1;
+        while (k2 < count && k2 - k < kUnpackBatch && offsets[k2] == offsets[k2 - 1] + np[k2 - 1] &&
+               elems + np[k2] <= chunk_elems) {
+            elems += np[k2];
+            k2++;
+        }
+        const int sb = h->pack_next;
+        h->pack_next ^= 1;
+        if ((st = ensure(h, &h->dPack[sb], &h->capPack[sb], elems * sizeof(double)))) return st;
+        CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_free[sb], 0));    // its last expansion has read it
+        CK(h, cudaMemcpyAsync(h->dPack[sb], ao + offsets[k], elems * sizeof(double), cudaMemcpyHostToDevice,
+                              h->copy_stream));
+        CK(h, cudaEventRecord(h->ev_copied[sb], h->copy_stream));
+        CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[sb], 0));
+        UnpackBatch B;
+        B.staging = h->dPack[sb];
+        B.n = k2 - k;
+        for (int j = 0; j < B.n; j++) {
+            const DimerRec& r = h->dims[first + k + j];
+            B.e[j] = UnpackEntry{(long long)(offsets[k + j] - offsets[k]), r.owned, h->mons[r.X].nao,
+                                 h->mons[r.Y].nao};
+        }
+        CK(h, launch_unpack_batch(B, h->stream));
+        CK(h, cudaEventRecord(h->ev_free[sb], h->stream));
+        k = k2;
+    }
+    for (int k = 0; k < count; k++) h->dims[first + k].computed = false;
+    h->coupled = false;
+    if (!(flags & MCPT_UPDATE_ASYNC)) CK(h, cudaStreamSynchronize(h->stream));
+    return MCPT_OK;
+}
+
 mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p)
 {
     if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_set_precision: NULL handle");

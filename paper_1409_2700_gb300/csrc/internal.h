@@ -243,6 +243,20 @@ cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists,
 // doubles expanded into blocks = [A | K] (BLOCKS layout, 2 nX^2 nY^2).
 size_t packed_elems(int nX, int nY);
 cudaError_t launch_unpack(const double* packed, double* blocks, int nX, int nY, cudaStream_t s);
+// Several dimers' packed integrals staged back to back, expanded by one
+// launch: dimer k's packed data at staging + e[k].src, its blocks to e[k].dst.
+struct UnpackEntry {
+    long long src;
+    double* dst;
+    int nX, nY;
+};
+constexpr int kUnpackBatch = 64;
+struct UnpackBatch {
+    const double* staging;
+    int n;
+    UnpackEntry e[kUnpackBatch];
+};
+cudaError_t launch_unpack_batch(const UnpackBatch& B, cudaStream_t s);
 cudaError_t launch_check_finite(const double* x, long long n, int* flag, cudaStream_t s);
 // Same for a strided 4-index block.
 cudaError_t launch_check_finite4(const double* x, const int dims[4], const long long st[3],

@@ -1302,6 +1302,10 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
             const float* CY = P.Cf + d.cY;
             const int wp = li & 1;
             const ConvRow cr = conv_row(r, g.p1t * g.n3, g.n3);
+            // a warp whose rows all lie past the tile's valid rows (n3 > 64 leaves
+            // up to 56 of the 128 rows empty) converts nothing: those rows' MMA
+            // results are never stored, whatever the tile holds there
+            const bool live = __any_sync(0xffffffffu, cr.valid);
             // ---- B operand of this item: row j < 16, K = p2: C_Y[p2][j] (zero past o2 / n2)
             if (!(ok = mbar_wait(&sh->empty_w[wp], ((li >> 1) & 1) ^ 1, abort, P.status, 15, P.wait_ns))) break;
             float sc_mine = 0.f;                 // BF16x3: column scale of column ct (< 16)
@@ -1389,8 +1393,9 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
                             const int as = gA & 1;
                             if (!(ok = mbar_wait(&sh->empty_a[as], ((gA >> 1) & 1) ^ 1, abort, P.status, 17, P.wait_ns)))
                                 break;
-                            convert_row<KIND>(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes),
-                                              Ar + (size_t)as * ASLOT, cr, g.n3, c0);
+                            if (live)
+                                convert_row<KIND>(reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes),
+                                                  Ar + (size_t)as * ASLOT, cr, g.n3, c0);
                             fence_async_smem();
                             __syncwarp();
                             if (lane == 0) {
@@ -1410,11 +1415,13 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
                                 break;
                             unsigned char* At = Ar + (size_t)as * ASLOT;
                             const double* Fs = reinterpret_cast<const double*>(Fr + (size_t)s * P.f_stage_bytes);
-                            int emax;
-                            if constexpr (KIND == TC_BF16X3)
-                                emax = convert_row_fx1(Fs, At, At + kABytes, cr, g.n3, c0);
-                            else
-                                emax = convert_row_fx2(Fs, At, cr, g.n3, c0);
+                            int emax = 0;                   // row scale 0 for rows not converted
+                            if (live) {
+                                if constexpr (KIND == TC_BF16X3)
+                                    emax = convert_row_fx1(Fs, At, At + kABytes, cr, g.n3, c0);
+                                else
+                                    emax = convert_row_fx2(Fs, At, cr, g.n3, c0);
+                            }
                             fence_async_smem();
                             __syncwarp();
                             if (lane == 0) {

@@ -105,3 +105,53 @@ def test_packed_unequal_sizes_and_update():
                         ctx.add_dimer(2, 1, synth.pack_blocks(*blks[(1, 2)]), M.MCPT_AO_PACKED)
                     assert ei.value.status == M.MCPT_EINVAL
         assert np.array_equal(out[True], out[False]), prec
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x2"])
+def test_update_dimers_batched_equals_one_by_one(lat8, prec):
+    """mcpt_update_dimers (one call for many dimers: back-to-back packed data
+    copied in chunks, one expansion launch per chunk) gives the terms of the
+    same integrals registered one by one, bit for bit: first the lattice's
+    own integrals after a doubling (terms x 4), then back, from one pinned
+    buffer asynchronously; BLOCKS data too; a dimer whose data were borrowed
+    device memory gets storage of its own; and a sub-range."""
+    w, mons, blocks, E = lat8
+    ref = _run(w, mons, blocks, prec, packed=False)
+    packed = [synth.pack_blocks(*blocks[d]) for d in range(w.n_dimers)]
+    offs = np.cumsum([0] + [p.size for p in packed[:-1]]).astype(np.uint64)
+    flat = np.concatenate(packed)
+    pinned = torch.from_numpy(flat).pin_memory()
+    with M.Context(precision=prec) as ctx:
+        for X in range(w.n_monomers):
+            m = mons[X]
+            ctx.add_monomer(m.C, m.eps, m.nocc)
+        dev0 = torch.from_numpy(np.concatenate([blocks[0][0].ravel(), blocks[0][1].ravel()])).cuda()
+        X0, Y0 = w.pairs[0]
+        ctx.add_dimer(X0, Y0, dev0.data_ptr(), M.MCPT_AO_BLOCKS, on_device=1)   # borrowed
+        for d in range(1, w.n_dimers):
+            X, Y = w.pairs[d]
+            ctx.add_dimer(X, Y, packed[d], M.MCPT_AO_PACKED)
+        ctx.run()
+        assert np.array_equal(ctx.energies()[2], ref[2])
+        ctx.update_dimers(0, w.n_dimers, 2.0 * flat, offs, M.MCPT_AO_PACKED)
+        with pytest.raises(M.McptError):
+            ctx.energies()                                   # not computed since the update
+        ctx.run()
+        assert np.array_equal(ctx.energies()[2], 4.0 * ref[2])
+        ctx.update_dimers(0, w.n_dimers, pinned.data_ptr(), offs, M.MCPT_AO_PACKED, asynchronous=True)
+        ctx.run()
+        got = ctx.energies()
+        assert np.array_equal(got[2], ref[2]) and np.array_equal(got[3], ref[3])
+        bl = [np.concatenate([blocks[d][0].ravel(), blocks[d][1].ravel()]) for d in range(w.n_dimers)]
+        boffs = np.cumsum([0] + [b.size for b in bl[:-1]]).astype(np.uint64)
+        ctx.update_dimers(0, w.n_dimers, 0.5 * np.concatenate(bl), boffs, M.MCPT_AO_BLOCKS)
+        ctx.run()
+        assert np.array_equal(ctx.energies()[2], 0.25 * ref[2])
+        ctx.update_dimers(5, 10, flat, offs[5:15], M.MCPT_AO_PACKED)   # a sub-range: the rest stays halved
+        ctx.run()
+        got = ctx.energies()[2]
+        assert np.array_equal(got[5:15], ref[2][5:15])
+        assert np.array_equal(got[:5], 0.25 * ref[2][:5]) and np.array_equal(got[15:], 0.25 * ref[2][15:])
+        with pytest.raises(M.McptError) as ei:
+            ctx.update_dimers(20, 10, flat, offs[:10], M.MCPT_AO_PACKED)
+        assert ei.value.status == M.MCPT_EINVAL
