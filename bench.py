@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--wave-gb", type=float, default=WAVE_BUDGET / (1 << 30),
                    help="streamed workloads: GiB of integral blocks per wave (one wave = one step)")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--fp64-epilogue", action="store_true",
+                   help="mixed forms: energy epilogue on the FP64 pipe instead of FP32 pairs (for comparison)")
     p.add_argument("--tune", type=int, default=1, help="streamed workloads: autotune each wave's launch choices (1/0)")
     p.add_argument("--max-waves", type=int, default=64,
                    help="streamed workloads with more waves run only the waves the steps cover")
@@ -253,7 +255,7 @@ def our_arm(args, ws, rank, local):
 
     def make_ctx(prec, timing, coupling=False):
         ctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing,
-                        coupling=coupling)
+                        coupling=coupling, fp64_epilogue=args.fp64_epilogue)
         for m in mons:
             ctx.add_monomer(m.C, m.eps, m.nocc)
         base = buf.data_ptr()
@@ -312,6 +314,7 @@ def our_arm(args, ws, rank, local):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "n_dimers": w.n_dimers, "n_monomers": w.n_monomers,
+                   "energy_epilogue": "fp64-pipe" if args.fp64_epilogue else "fp32-pairs",
                    "nao": w.nao[0], "nocc": w.nocc[0], "precision": args.precision,
                    "inputs_gb": round(buf.numel() * 8 / 1e9, 2), "l2": "inputs (17.4 GB) larger than L2"},
         "transform_tflops": st.alg_flops / (ms_step * 1e-3) / 1e12,
@@ -467,7 +470,7 @@ def our_arm(args, ws, rank, local):
         df = {}
         dbytes = sum(B.numel() * 8 for B in Bs)
         for prec in ([args.precision, "fp64"] if args.precision != "fp64" else ["fp64"]):
-            dctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False)
+            dctx = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, fp64_epilogue=args.fp64_epilogue)
             for m in mons:
                 dctx.add_monomer(m.C, m.eps, m.nocc)
             for d in range(w.n_dimers):
@@ -557,7 +560,7 @@ def our_arm(args, ws, rank, local):
             # dimers, the plan and its graph); every timed step copies that
             # step's integrals from pinned host memory into it
             # (mcpt_update_dimer, asynchronous), runs, and reads the energies back
-            c = M.Context(precision=args.precision, device=local, validate=False)
+            c = M.Context(precision=args.precision, device=local, validate=False, fp64_epilogue=args.fp64_epilogue)
             for m in mons:
                 c.add_monomer(m.C, m.eps, m.nocc)
             for d in range(w.n_dimers):
@@ -697,7 +700,7 @@ def streamed_arm(args, ws, rank, local):
 
     def make_ctx(prec, timing, graphs=True):
         c = M.Context(precision=prec, device=local, stream=stream.cuda_stream, validate=False, timing=timing,
-                      graphs=graphs, tune_cache=tune if prec != "fp64" else None)
+                      graphs=graphs, tune_cache=tune if prec != "fp64" else None, fp64_epilogue=args.fp64_epilogue)
         for m in mons:
             c.add_monomer(m.C, m.eps, m.nocc)
         return c
@@ -802,6 +805,7 @@ def streamed_arm(args, ws, rank, local):
         "steps": nsteps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": args.workload, "n_dimers": w.n_dimers, "n_monomers": w.n_monomers,
+                   "energy_epilogue": "fp64-pipe" if args.fp64_epilogue else "fp32-pairs",
                    "nao": sorted(set(w.nao)), "nocc": sorted(set(w.nocc)), "precision": args.precision,
                    "inputs_gb": round(_alg_bytes(w, 0, w.n_dimers) / 1e9, 1), "waves": nw,
                    "dimers_per_step": round(timed_dimers / nsteps, 1),
@@ -930,7 +934,7 @@ def streamed_arm(args, ws, rank, local):
         del st
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        ce = M.Context(precision=args.precision, device=local, validate=False)
+        ce = M.Context(precision=args.precision, device=local, validate=False, fp64_epilogue=args.fp64_epilogue)
         for m in mons:
             ce.add_monomer(m.C, m.eps, m.nocc)
         ranges, base_id = [], 0

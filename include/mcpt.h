@@ -67,7 +67,8 @@ typedef enum {
 } mcpt_status;
 
 /* Arithmetic of the four-index transformation.  Denominators, the energy
- * products and every energy sum are FP64 in all forms. */
+ * products and every energy sum are at FP64 accuracy in all forms (FP64 in the
+ * FP64 form; in the mixed forms see mcpt_options.fp64_epilogue). */
 typedef enum {
     MCPT_FP64 = 0,    /* FP64 everywhere (CUDA-core DFMA) */
     MCPT_TF32 = 1,    /* AO integrals and C rounded to TF32 (round-to-nearest), tcgen05 MMA, FP32 accumulate */
@@ -77,11 +78,19 @@ typedef enum {
                          sums stay below 2^24, so every tensor-core accumulation is exact (the Kronecker
                          kernel, selected only by MCPT_TC_KERNEL=kron, keeps a hi/lo BF16 split) */
     MCPT_FP32C = 3,   /* FP32 FMA with error-free TwoProduct/TwoSum compensation (Ogita-Rump-Oishi) */
-    MCPT_BF16X2 = 4   /* as MCPT_BF16X3 for C_Y (32-bit fixed point, four digits), but each integral
+    MCPT_BF16X2 = 4,  /* as MCPT_BF16X3 for C_Y (32-bit fixed point, four digits), but each integral
                          row chunk in 16-bit fixed point (two BF16 digits, rounded half up in magnitude,
                          read from the high word of each double): exact tensor-core sums with half the
                          digit work and half the MMAs; integrals carry 2^-17 of their chunk's largest
                          power of two as rounding error */
+    MCPT_FP64E = 5    /* the FP64 form's accuracy from the tensor cores (Ozaki-style slicing, Ozaki
+                         et al., Numer. Algorithms 59 (2012) 95): each integral row chunk and each C_Y
+                         column in 48-bit fixed point, six unsigned byte digits carrying the element's
+                         sign, every digit product summed exactly in FP32 by tcgen05 BF16 MMAs (21
+                         products in six levels); the levels, the p0 quarter transformation and the
+                         first-half result on FP32 pairs (48-bit), written as FP64; the second half,
+                         denominators and sums as in MCPT_FP64.  Monomers of up to 64 AO and 5 occupied
+                         orbitals (MCPT_EUNSUPPORTED beyond) */
 } mcpt_precision;
 
 typedef enum {
@@ -116,6 +125,12 @@ typedef struct {
                                  launch stop issuing integral loads after N - 1 of them, so that its
                                  consumers wait for a load that never comes and give up at
                                  wait_limit_ns (failure detection without a device fault) */
+    int fp64_epilogue;        /* mixed forms only.  0 (default): each term's last denominator
+                                 subtraction, D = 1/x, the products with D and the sums over b run on
+                                 FP32 pairs (48-bit double-length arithmetic, D to ~2^-45 relative),
+                                 added to the FP64 sums once per occupied pair; e_i + e_j - e_a is
+                                 FP64.  1: the same on the FP64 pipe, five FP64 operations per term
+                                 (same accuracy class, slower on GB300) */
 } mcpt_options;
 
 /* Defaults: device 0, own stream, MCPT_FP64, validate 1, 1 GiB waves, no cache, no timing,

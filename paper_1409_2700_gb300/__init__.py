@@ -21,9 +21,9 @@ LIB_PATH = os.path.join(_HERE, "libmcpt.so")
 
 MCPT_OK, MCPT_EINVAL, MCPT_ENOMEM, MCPT_ECUDA, MCPT_ESTATE, MCPT_ETIMEOUT, MCPT_EUNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ESTATE", 5: "ETIMEOUT", 6: "EUNSUPPORTED"}
-MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C, MCPT_BF16X2 = range(5)
+MCPT_FP64, MCPT_TF32, MCPT_BF16X3, MCPT_FP32C, MCPT_BF16X2, MCPT_FP64E = range(6)
 PRECISIONS = {"fp64": MCPT_FP64, "tf32": MCPT_TF32, "bf16x3": MCPT_BF16X3, "fp32c": MCPT_FP32C,
-              "bf16x2": MCPT_BF16X2}
+              "bf16x2": MCPT_BF16X2, "fp64e": MCPT_FP64E}
 MCPT_AO_FULL, MCPT_AO_BLOCKS, MCPT_AO_PACKED = 0, 1, 2
 MCPT_UPDATE_ASYNC = 1
 
@@ -47,7 +47,8 @@ class mcpt_options(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("precision", ctypes.c_int),
                 ("validate", ctypes.c_int), ("wave_bytes", ctypes.c_size_t), ("tune_cache", ctypes.c_char_p),
                 ("timing", ctypes.c_int), ("mem_cap_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int),
-                ("coupling", ctypes.c_int), ("wait_limit_ns", ctypes.c_ulonglong), ("withhold_load", ctypes.c_int)]
+                ("coupling", ctypes.c_int), ("wait_limit_ns", ctypes.c_ulonglong), ("withhold_load", ctypes.c_int),
+                ("fp64_epilogue", ctypes.c_int)]
 
 
 class mcpt_run_stats(ctypes.Structure):
@@ -278,7 +279,8 @@ class Context:
     ``torch.cuda.current_stream().cuda_stream``) or None for a library stream."""
 
     def __init__(self, precision="fp64", device=0, stream=None, validate=True, wave_bytes=0, timing=False,
-                 mem_cap_bytes=0, graphs=True, tune_cache=None, coupling=False, wait_limit_ns=0, withhold_load=0):
+                 mem_cap_bytes=0, graphs=True, tune_cache=None, coupling=False, wait_limit_ns=0, withhold_load=0,
+                 fp64_epilogue=False):
         o = mcpt_default_options()
         if tune_cache is not None:
             o.tune_cache = os.fsencode(tune_cache)
@@ -293,6 +295,7 @@ class Context:
         o.coupling = int(bool(coupling))
         o.wait_limit_ns = int(wait_limit_ns)
         o.withhold_load = int(withhold_load)
+        o.fp64_epilogue = int(bool(fp64_epilogue))
         self.validate = bool(validate)
         self.stream = stream
         self.h = mcpt_create(o)

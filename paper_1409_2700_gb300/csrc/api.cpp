@@ -72,6 +72,7 @@ struct mcpt_ctx {
     int coupling = 0;
     unsigned long long wait_ns = 0;  // limit of each device-side wait (0 = the kernels' default)
     int withhold = 0;                // test aid: see mcpt_options.withhold_load
+    bool fp64_epilogue = false;      // mixed forms' energy epilogue on the FP64 pipe
     size_t mem_cap = 0;
     size_t mem_used = 0;
 
@@ -313,9 +314,19 @@ bool all_finite(const double* x, size_t n)
     return true;
 }
 
-bool is_tensor_form(mcpt_precision p) { return p == MCPT_TF32 || p == MCPT_BF16X3 || p == MCPT_BF16X2; }
+bool is_tensor_form(mcpt_precision p)
+{
+    return p == MCPT_TF32 || p == MCPT_BF16X3 || p == MCPT_BF16X2 || p == MCPT_FP64E;
+}
 
-TcKind tc_kind_of(mcpt_precision p) { return p == MCPT_TF32 ? TC_TF32 : p == MCPT_BF16X2 ? TC_BF16X2 : TC_BF16X3; }
+TcKind tc_kind_of(mcpt_precision p)
+{
+    return p == MCPT_TF32 ? TC_TF32 : p == MCPT_BF16X2 ? TC_BF16X2 : p == MCPT_FP64E ? TC_FP64E : TC_BF16X3;
+}
+
+// Forms whose first-half result, second half, energy epilogue and stored
+// coupling amplitudes are FP64 (the FP64 form and its tensor-core emulation).
+bool fp64_data(mcpt_precision p) { return p == MCPT_FP64 || p == MCPT_FP64E; }
 
 // Occupied pairs padded to 16 (N of the Kronecker tensor-core GEMM).
 int npad_for(int oX, int oY) { return (oX * oY + 15) / 16 * 16; }
@@ -323,7 +334,7 @@ int npad_for(int oX, int oY) { return (oX * oY + 15) / 16 * 16; }
 // Bytes of the first-half result of one dimer (both forms, pair-major).
 size_t hbytes_for(mcpt_precision p, int nX, int nY, int oX, int oY)
 {
-    const size_t elem = (p == MCPT_FP64) ? sizeof(double) : sizeof(float);
+    const size_t elem = fp64_data(p) ? sizeof(double) : sizeof(float);
     return 2 * (size_t)nX * nY * oX * oY * elem;
 }
 
@@ -339,6 +350,7 @@ mcpt_status check_supported(mcpt_ctx* h, int d, int nX, int nY)
     case MCPT_TF32:
     case MCPT_BF16X3:
     case MCPT_BF16X2:
+    case MCPT_FP64E:
         if ((nX & 1) || (nY & 1) || nX > kMaxAOTensor || nY > kMaxAOTensor)
             return fail(h, MCPT_EUNSUPPORTED,
                         "dimer %d: tensor-core forms need even AO counts <= %d (got %d, %d)", d,
@@ -378,7 +390,7 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     mcpt_options o;
     mcpt_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < MCPT_FP64 || o.precision > MCPT_BF16X2)
+    if (o.precision < MCPT_FP64 || o.precision > MCPT_FP64E)
         return fail(nullptr, MCPT_EINVAL, "mcpt_create: bad precision %d", (int)o.precision);
     if (o.withhold_load < 0) return fail(nullptr, MCPT_EINVAL, "mcpt_create: withhold_load %d < 0", o.withhold_load);
     int ndev = 0;
@@ -410,6 +422,7 @@ mcpt_status mcpt_create(mcpt_handle* out, const mcpt_options* opt)
     h->coupling = o.coupling;
     h->wait_ns = o.wait_limit_ns;
     h->withhold = o.withhold_load;
+    h->fp64_epilogue = o.fp64_epilogue != 0;
     h->mem_cap = o.mem_cap_bytes;
     if (o.stream) {
         h->stream = static_cast<cudaStream_t>(o.stream);
@@ -787,7 +800,7 @@ mcpt_status mcpt_update_dimers(mcpt_handle h, int first, int count, const double
 mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p)
 {
     if (!h) return fail(nullptr, MCPT_EINVAL, "mcpt_set_precision: NULL handle");
-    if (p < MCPT_FP64 || p > MCPT_BF16X2) return fail(h, MCPT_EINVAL, "mcpt_set_precision: bad precision %d", (int)p);
+    if (p < MCPT_FP64 || p > MCPT_FP64E) return fail(h, MCPT_EINVAL, "mcpt_set_precision: bad precision %d", (int)p);
     h->prec = p;                            // plans are kept per precision
     return MCPT_OK;
 }
@@ -860,7 +873,8 @@ static std::string tune_key(mcpt_ctx* h, mcpt_precision prec, const DimerDesc* d
     for (auto& c : dev)
         if (c == ' ') c = '_';
     char buf[160];
-    snprintf(buf, sizeof buf, "%s:%s:%d:%016llx", prec == MCPT_TF32 ? "tf32" : prec == MCPT_BF16X2 ? "bf16x2" : "bf16x3", dev.c_str(), nd, f);
+    snprintf(buf, sizeof buf, "%s:%s:%d:%016llx", prec == MCPT_TF32 ? "tf32" : prec == MCPT_BF16X2 ? "bf16x2" : prec == MCPT_FP64E ? "fp64e" : "bf16x3",
+             dev.c_str(), nd, f);
     return buf;
 }
 
@@ -894,7 +908,7 @@ static mcpt_status tune_wave(mcpt_handle h, const mcpt_ctx::Plan& P, TcKind kind
     for (int c = 0; c < n; c++) {
         TcLaunch L{};
         char err[256] = {0};
-        if (tc_prepare(kind, P.hDesc.data() + wv.b, P.dDesc + wv.b, wv.nd, h->dCf, static_cast<float*>(h->dH),
+        if (tc_prepare(kind, P.hDesc.data() + wv.b, P.dDesc + wv.b, wv.nd, h->dCf, h->dC, h->dH,
                        work, work_bytes, h->dFlag + 1, h->stream, &cand[c], &L, err, sizeof err) != cudaSuccess)
             continue;
         cudaError_t e = tc_launch(L, h->stream);
@@ -983,7 +997,7 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
                 dd.npad = npad_for(dd.oX, dd.oY);
                 dd.slot = bx * by > 1 ? D + nblk_extra++ : d;
                 const size_t hb = hbytes_for(prec, dd.nX, dd.nY, dd.oX, dd.oY);
-                const size_t elem = prec == MCPT_FP64 ? 8 : 4;
+                const size_t elem = fp64_data(prec) ? 8 : 4;
                 const int kk = (int)P.hDesc.size();
                 if (kk > wbeg && (wave_h + hb > h->wave_bytes || kk - wbeg >= 65535)) {
                     waves.emplace_back(wbeg, kk);
@@ -1044,7 +1058,7 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
     P.coupling = coupled_plan;
     P.ntile[0] = P.ntile[1] = P.ntile[2] = 0;
     if (coupled_plan) {
-        const size_t elem = prec == MCPT_FP64 ? sizeof(double) : sizeof(float);
+        const size_t elem = fp64_data(prec) ? sizeof(double) : sizeof(float);
         if ((st = ensure_shared(h, &h->dVT, &h->capVT, (size_t)vt_total * elem))) return st;
         // tables: output tiles, per-dimer info, monomer sizes o v, R offsets
         std::vector<CoupDim> cds(D);
@@ -1201,9 +1215,9 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
                 }
                 tuned = tune.variant1 != 0;
             }
-            cudaError_t e = tc_prepare(kind, P.hDesc.data() + wv.b, P.dDesc + wv.b, wv.nd, h->dCf,
-                                       static_cast<float*>(h->dH), work, end - work_off[w], h->dFlag + 1,
+            cudaError_t e = tc_prepare(kind, P.hDesc.data() + wv.b, P.dDesc + wv.b, wv.nd, h->dCf, h->dC, h->dH, work, end - work_off[w], h->dFlag + 1,
                                        h->stream, tuned ? &tune : nullptr, &wv.tc, tcerr, sizeof tcerr);
+            if (e == cudaErrorNotSupported) return fail(h, MCPT_EUNSUPPORTED, "%s", tcerr);
             if (e != cudaSuccess)
                 return fail(h, MCPT_ECUDA, "tensor-core plan: %s (%s)", cudaGetErrorString(e), tcerr);
             wv.tc.wait_ns = h->wait_ns;
@@ -1250,6 +1264,7 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
         case MCPT_TF32:
         case MCPT_BF16X3:
         case MCPT_BF16X2:
+        case MCPT_FP64E:
             CK(h, tc_launch(wv.tc, h->stream));
             break;
         }
@@ -1258,14 +1273,14 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
         const FinTask* tasks =
             wv.ntasks ? reinterpret_cast<const FinTask*>(static_cast<const char*>(P.dFin) + wv.fin_off) : nullptr;
         double* part = wv.ntasks ? P.dPart + 2 * wv.part_off : nullptr;
-        if (prec == MCPT_FP64)
+        if (fp64_data(prec))
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
                                      tasks, wv.ntasks, part, P.coupling ? static_cast<double*>(h->dVT) : nullptr,
                                      h->stream));
         else
             CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dCf, h->dE, static_cast<const float*>(h->dH), h->dE2,
                                      tasks, wv.ntasks, part, P.coupling ? static_cast<float*>(h->dVT) : nullptr,
-                                     h->stream));
+                                     h->fp64_epilogue, h->stream));
         launches += wv.ntasks ? 2 : 1;
         if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
     }
@@ -1281,7 +1296,7 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
         const CoupDim* cds = reinterpret_cast<const CoupDim*>(tab + P.off_dims);
         const int* mdim = reinterpret_cast<const int*>(tab + P.off_mdim);
         const long long* roff = reinterpret_cast<const long long*>(tab + P.off_roff);
-        if (prec == MCPT_FP64)
+        if (fp64_data(prec))
             CK(h, launch_coupling_fp64(tiles, P.ntile, cds, L, mdim, roff, static_cast<const double*>(h->dVT), h->dR,
                                        h->stream));
         else
@@ -1487,7 +1502,7 @@ mcpt_status mcpt_singles(mcpt_handle h, const double* t, double* s)
     const int N = (int)h->mons.size(), D = (int)h->dims.size();
     MonomerLists L{h->dLists, h->dLists + N + 1, N};
     double* part = h->dS1 + 2 * M;
-    if (P.prec == MCPT_FP64)
+    if (fp64_data(P.prec))
         CK(h, launch_singles_fp64(tiles, P.nstiles, cds, D, L, mdim, soff, poff, static_cast<const double*>(h->dVT),
                                   h->dS1, part, h->dS1 + M, h->stream));
     else
@@ -1552,7 +1567,7 @@ mcpt_status mcpt_run_df(mcpt_handle h)
     CK(h, cudaSetDevice(h->device));
     mcpt_status st = upload_static(h);
     if (st) return st;
-    const bool fp64 = h->prec == MCPT_FP64;
+    const bool fp64 = fp64_data(h->prec);
     const size_t es = fp64 ? sizeof(double) : sizeof(float);
     std::vector<DfDim> dims(D);
     long long hoff = 0;
@@ -1881,7 +1896,7 @@ mcpt_status mcpt_td2(mcpt_handle h, int n_iter, double* per_dimer, double* delta
     if (n_iter < 1 || n_iter > 10000) return fail(h, MCPT_EINVAL, "mcpt_td2: n_iter=%d outside [1, 10000]", n_iter);
     if (h->dims.empty()) return fail(h, MCPT_ESTATE, "mcpt_td2: no dimers registered");
     CK(h, cudaSetDevice(h->device));
-    return h->prec == MCPT_FP64 ? td2_run<double>(h, n_iter, per_dimer, delta)
+    return fp64_data(h->prec) ? td2_run<double>(h, n_iter, per_dimer, delta)
                                 : td2_run<float>(h, n_iter, per_dimer, delta);
 }
 

@@ -85,7 +85,8 @@ void finish_tasks(const DimerDesc* h_desc, int nd, int pairs_per_task, std::vect
 // run the tasks (`tasks`, device array of `ntasks`) and sum each dimer's
 // task partials (`part`, 2 doubles per task) in task order.
 // With VT non-null, descriptors with vt_off >= 0 also store their (ia|jb)
-// and T = vD for the coupling.
+// and T = vD for the coupling.  FP32 (mixed forms): the energy epilogue on
+// FP32 pairs, or with fp64_epilogue on the FP64 pipe term by term.
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
                                const double* Cpool, const double* Epool, const double* H,
                                double* E2, const FinTask* tasks, int ntasks, double* part, double* VT,
@@ -93,7 +94,7 @@ cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
                                const float* Cf, const double* Epool, const float* H,
                                double* E2, const FinTask* tasks, int ntasks, double* part, float* VT,
-                               cudaStream_t s);
+                               bool fp64_epilogue, cudaStream_t s);
 
 // Dimer -> monomer doubles coupling of Eq. (tm2) at first order.
 struct CoupDim {
@@ -267,7 +268,7 @@ cudaError_t launch_check_finite4(const double* x, const int dims[4], const long 
 void set_thread_error(const char* msg);
 
 // ---- tensor-core first half (tcgen05) ----
-enum TcKind { TC_TF32 = 0, TC_BF16X3 = 1, TC_BF16X2 = 2 };
+enum TcKind { TC_TF32 = 0, TC_BF16X3 = 1, TC_BF16X2 = 2, TC_FP64E = 3 };
 
 // Everything one launch of the tensor-core kernel needs; filled by
 // tc_prepare (host work: tensor maps, work items, their upload), replayed by
@@ -278,7 +279,8 @@ struct TcLaunch {
     const void* maps;           // device CUtensorMap array, [dimer][form]
     const DimerDesc* desc;      // device descriptors of the launch's dimers
     const float* Cf;            // FP32 coefficient pool
-    float* H;
+    const double* Cd;           // FP64 coefficient pool (TC_FP64E)
+    void* H;                    // first-half result: float, or double for TC_FP64E
     int* status;
     int sf;                     // FP64 staging stages
     unsigned f_stage_bytes, w_stage_bytes, tmem_cols;
@@ -312,7 +314,7 @@ int tc_candidates(TcKind kind, const DimerDesc* h_desc, int nd, TcTune* out, int
 // d_work, and fill *out.  Synchronous w.r.t. the host buffers.  `tune`
 // (may be NULL) overrides the default launch choices.
 cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const float* Cf,
-                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s,
+                       const double* Cd, void* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s,
                        const TcTune* tune, TcLaunch* out, char* err, size_t errlen);
 cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s);
 

@@ -7,21 +7,25 @@
 // and the virtual quarter transformations of Eq. (dp2e) finish them:
 //   (i a|j b) = sum_nu C_X[nu][a] sum_sig H_0[nu][sig] C_Y[sig][b]
 //   (i b|j a) = sum_lam C_Y[lam][b] sum_nu H_1[lam][nu] C_X[nu][a]
-// Then, in FP64 (Sec. II.C energy tensor, Eq. (ed2) with T = vD):
+// Then, at FP64 accuracy (Sec. II.C energy tensor, Eq. (ed2) with T = vD):
 //   D = 1/(e_i + e_j - e_a - e_b),  E_J += 4 (ia|jb)^2 D,  E_K += -2 (ia|jb)(ib|ja) D.
-// GB300's FP64 unit is small and bounds this kernel, so each term costs as
-// few FP64 operations as possible: v D comes from an FP32 reciprocal seed
-// refined by Newton steps in FP64 with the last step folded into the product
-// (convert.h) -- two steps for the FP64 form (full FP64 accuracy), one for the
-// mixed forms (relative error ~6e-14, far below their transform error) -- then
-// E_J and E_K take one FMA each, and the FP32 -> FP64 widening of the mixed
-// forms' integrals runs on integer pipes.
+// GB300's FP64 unit runs at 1/64 of its FP32 rate.  The FP64 form keeps every
+// step on it at the fewest operations per term: v D from an FP32 reciprocal
+// seed and two Newton steps in FP64, the last folded into the product
+// (convert.h), then one FMA each for E_J and E_K.  The mixed forms take
+// e_i + e_j - e_a in FP64 once per (pair, a) and the rest on FP32 pairs
+// (48-bit double-length arithmetic, below): the last subtraction, D to ~2^-45
+// relative (the accuracy of one FP64 Newton step from an FP32 seed), the
+// products with D and the sums over b, added to the FP64 sums once per pair --
+// no FP64 operation per term.  The FP64-pipe variant of that epilogue (five
+// FP64 operations per term) stays selectable for comparison.
 // Monomers of at most 32 AO: one CTA per dimer, one warp per occupied pair.
 // Larger ones: register-tiled GEMMs, one CTA per range of a dimer's pairs,
 // the ranges' partial sums added per dimer in range order.  Every sum has a
 // fixed order: the energies are deterministic run to run, with no atomics.
 #include "internal.h"
 #include "convert.h"
+#include "ff.h"
 
 #include <algorithm>
 
@@ -39,6 +43,18 @@ __device__ __forceinline__ double warp_sum(double v)
 template <typename T> __device__ __forceinline__ T narrow(double x);
 template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
 template <> __device__ __forceinline__ float narrow<float>(double x) { return f32_from_f64(x); }
+
+// The mixed forms' terms of one (i, a, j, b) on FP32 pairs: x = e_ija - e_b,
+// D = 1/x, E_J += v^2 D, E_K += v vk D into the pair accumulators sj, sk;
+// returns v D (FP32) for the coupling store.  v^2 and v vk are FP32 products
+// as in the FP64 variant; D, the products with D and the sums keep ~2^-45.
+__device__ __forceinline__ float energy_terms_ff(float v, float vk, FF eija, FF eb, FF& sj, FF& sk)
+{
+    const FF D = ff_rcp(ff_sub(eija, eb));
+    ff_acc(sj, __fmul_rn(v, v), D);
+    ff_acc(sk, __fmul_rn(v, vk), D);
+    return fmaf(v, D.l, __fmul_rn(v, D.h));
+}
 
 // The energy terms of one (i, a, j, b) with v = (ia|jb), vk = (ib|ja) and the
 // FP64 denominator x = e_i + e_j - e_a - e_b: D = 1/x in FP64, then
@@ -82,7 +98,7 @@ constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33
 template <typename T>
 constexpr size_t w32_smem_bytes()
 {
-    return 32 * sizeof(double) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
+    return 32 * sizeof(double) + 32 * sizeof(FF) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
 }
 
 // One warp starts the asynchronous copy of an nr x nc (<= 32 x 32) row-major
@@ -116,8 +132,10 @@ __device__ __forceinline__ void slice_wait()
 }
 
 // STORE: also write the dimer's (ia|jb) and T for the coupling (a separate
-// instantiation keeps the plain path's registers).
-template <typename T, bool STORE>
+// instantiation keeps the plain path's registers).  PAIRS (mixed forms only):
+// the energy terms on FP32 pairs, summed per (pair, a) and added to the FP64
+// sums once per pair; otherwise on the FP64 pipe term by term.
+template <typename T, bool STORE, bool PAIRS>
 __global__ void __launch_bounds__(kW32Warps * 32, 4)
 k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
              const T* __restrict__ H, double* __restrict__ E2, T* __restrict__ VT)
@@ -134,8 +152,10 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     const T* H1 = H + d.h_off + (long long)pairs * rows;
 
     extern __shared__ __align__(16) unsigned char smraw[];
+    static_assert(!PAIRS || sizeof(T) == 4, "FP32 pairs serve the mixed forms");
     double* eYv = reinterpret_cast<double*>(smraw);          // [b]: e_b (read as a broadcast)
-    T* CXT = reinterpret_cast<T*>(eYv + 32);                  // [a][nu], zero padded
+    FF* eYs = reinterpret_cast<FF*>(eYv + 32);                // [b]: e_b as an FP32 pair
+    T* CXT = reinterpret_cast<T*>(eYs + 32);                  // [a][nu], zero padded
     T* CYT = CXT + 32 * 32;                                   // [b][sig]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* const buf = CYT + 32 * 32 + warp * (2 * kW32Slab);     // two slice buffers of kW32Slab
@@ -162,7 +182,11 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             CXT[k] = cxv[t];
             CYT[k] = cyv[t];
         }
-        if (threadIdx.x < 32) eYv[threadIdx.x] = threadIdx.x < vY ? Epool[d.eYv + threadIdx.x] : 0.0;
+        if (threadIdx.x < 32) {
+            const double e = threadIdx.x < vY ? Epool[d.eYv + threadIdx.x] : 0.0;
+            eYv[threadIdx.x] = e;
+            eYs[threadIdx.x] = ff_split(e);
+        }
     }
     __syncthreads();
 
@@ -177,6 +201,8 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
         const int i = pr / oY, j = pr % oY;
         const double eija = (eX[i] + eY[j]) - ea;  // e_i + e_j - e_a of this lane
+        [[maybe_unused]] const FF eijas = PAIRS ? ff_split(eija) : FF{0.f, 0.f};
+        [[maybe_unused]] FF sj{0.f, 0.f}, sk{0.f, 0.f};   // this pair's sums over b (PAIRS)
         const int nx = pr + kW32Warps;           // next pair of this warp
         T* SX = x ? buf + kW32Slab : buf;        // H0, then VA [a][b] (stride 33)
         T* SY = x ? buf : buf + kW32Slab;        // H1, then the next pair's H0
@@ -217,7 +243,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             }
             __syncwarp();                        // H1 consumed: the next pair's H0 streams into SY
             if (nx < pairs) prefetch_slice(SY, H0 + (long long)nx * rows, nX, nY, lane);
-            // ---- FP64 denominators and energy sums, lane a over b
+            // ---- denominators and energy sums, lane a over b
 #pragma unroll 1
             for (int b = 0; b < vY; b++) {
                 T v0 = 0, v1 = 0;                // two chains of 16
@@ -228,15 +254,25 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 }
                 if (live) {
                     const T vab = SX[lane * 33 + b];
-                    double t;
-                    energy_terms<T>(vab, v0 + v1, eija - eYv[b], ej, ek, store ? &t : nullptr);
+                    T tv;
+                    if constexpr (PAIRS) {
+                        tv = energy_terms_ff(vab, v0 + v1, eijas, eYs[b], sj, sk);
+                    } else {
+                        double t;
+                        energy_terms<T>(vab, v0 + v1, eija - eYv[b], ej, ek, store ? &t : nullptr);
+                        tv = store ? narrow<T>(t) : T(0);
+                    }
                     if (store) {
                         const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
                         Vst[e] = vab;
-                        Vst[mXc * mYc + e] = narrow<T>(t);
+                        Vst[mXc * mYc + e] = tv;
                     }
                 }
             }
+        }
+        if constexpr (PAIRS) {
+            ej += ff_f64(sj);
+            ek += ff_f64(sk);
         }
         __syncwarp();                            // VA consumed: the next pair's H1 streams into SX
         if (nx < pairs) prefetch_slice(SX, H1 + (long long)nx * rows, nY, nX, lane);
@@ -276,7 +312,7 @@ template <typename T>
 size_t tiled_smem_bytes(int max_ao)
 {
     const size_t n = (size_t)max_ao;
-    return (n * n + 2 * n * n) * sizeof(T) + 2 * n * sizeof(double) + 64;
+    return (n * n + 2 * n * n) * sizeof(T) + 2 * n * (sizeof(double) + sizeof(FF)) + 64;
 }
 
 // acc[i][j] = sum_k A(m0 + i, k) B(k, n0 + j) over rows < M, columns < N.
@@ -324,7 +360,7 @@ __device__ __forceinline__ void copy_slice(T* S, const T* __restrict__ src, int 
     }
 }
 
-template <typename T>
+template <typename T, bool PAIRS>
 __global__ void __launch_bounds__(kTThreads, 2)
 k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tasks, const T* __restrict__ C,
                const double* __restrict__ Epool, const T* __restrict__ H, double* __restrict__ part,
@@ -345,7 +381,9 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     extern __shared__ __align__(16) unsigned char smraw[];
     double* eXv = reinterpret_cast<double*>(smraw);           // [vX]
     double* eYv = eXv + nX;                                   // [vY]
-    T* base = reinterpret_cast<T*>(eYv + nY);
+    FF* eXs = reinterpret_cast<FF*>(eYv + nY);                // [vX]: e_a as FP32 pairs
+    FF* eYs = eXs + nX;                                       // [vY]
+    T* base = reinterpret_cast<T*>(eYs + nY);
     // a group of np pairs runs each phase together (one barrier per phase for
     // the group): as many as the launch's shared memory holds
     const int per_pair = rows + nX * vY + nY * vX;
@@ -354,8 +392,8 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
     T* Tm = S + gmax * rows;                                  // [np][nX][vY]
     T* TmK = Tm + gmax * nX * vY;                             // [np][nY][vX]
     const int tid = threadIdx.x;
-    for (int k = tid; k < vX; k += kTThreads) eXv[k] = Epool[d.eXv + k];
-    for (int k = tid; k < vY; k += kTThreads) eYv[k] = Epool[d.eYv + k];
+    for (int k = tid; k < vX; k += kTThreads) { eXv[k] = Epool[d.eXv + k]; eXs[k] = ff_split(eXv[k]); }
+    for (int k = tid; k < vY; k += kTThreads) { eYv[k] = Epool[d.eYv + k]; eYs[k] = ff_split(eYv[k]); }
     // 8 x 4 output blocks of each GEMM shape, per pair
     const int bn_vY = (vY + kTN - 1) / kTN, bn_vX = (vX + kTN - 1) / kTN;
     const int nb1 = ((nX + kTM - 1) / kTM) * bn_vY;          // Tm
@@ -421,23 +459,40 @@ k_finish_tiled(const DimerDesc* __restrict__ dd, const FinTask* __restrict__ tas
                     if (m0 + a < vX && n0 + b < vY) Vp[(m0 + a) * vY + n0 + b] = acc[a][b];
             mm_block<T>(acc, m0, n0, vX, vY, nY, [&](int m, int k) { return Kp[k * vX + m]; },
                         [&](int k, int n) { return __ldg(CYv + k * nY + n); });
+            [[maybe_unused]] const FF eijs = PAIRS ? ff_split(eij) : FF{0.f, 0.f};
+            [[maybe_unused]] FF sj{0.f, 0.f}, sk{0.f, 0.f};   // this block's sums (PAIRS)
 #pragma unroll
-            for (int a = 0; a < kTM; a++)
+            for (int a = 0; a < kTM; a++) {
+                const int m = m0 + a;
+                [[maybe_unused]] FF eijas{0.f, 0.f};
+                if constexpr (PAIRS)
+                    if (m < vX) eijas = ff_sub(eijs, eXs[m]);
 #pragma unroll
                 for (int b = 0; b < kTN; b++) {
-                    const int m = m0 + a, n = n0 + b;
+                    const int n = n0 + b;
                     if (m < vX && n < vY) {
                         const T vab = Vp[m * vY + n];
-                        double t;
-                        energy_terms<T>(vab, acc[a][b], eij - (eXv[m] + eYv[n]), ej, ek, store ? &t : nullptr);
+                        T tv;
+                        if constexpr (PAIRS) {
+                            tv = energy_terms_ff(vab, acc[a][b], eijas, eYs[n], sj, sk);
+                        } else {
+                            double t;
+                            energy_terms<T>(vab, acc[a][b], eij - (eXv[m] + eYv[n]), ej, ek, store ? &t : nullptr);
+                            tv = store ? narrow<T>(t) : T(0);
+                        }
                         if (store) {
                             const long long e =
                                 ((long long)(d.jY0 + j) * vY + n) * mXc + (long long)(d.iX0 + i) * vX + m;
                             Vst[e] = vab;
-                            Vst[mXc * mYc + e] = narrow<T>(t);
+                            Vst[mXc * mYc + e] = tv;
                         }
                     }
                 }
+            }
+            if constexpr (PAIRS) {
+                ej += ff_f64(sj);
+                ek += ff_f64(sk);
+            }
         }
         __syncthreads();
     }
@@ -472,7 +527,7 @@ __global__ void k_finish_sum(const DimerDesc* __restrict__ dd, int nd, const Fin
     E2[2 * dd[k].slot + 1] = -2.0 * sk;
 }
 
-template <typename T>
+template <typename T, bool PAIRS>
 cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* C, const double* Epool,
                           const T* H, double* E2, const FinTask* tasks, int ntasks, double* part, T* VT,
                           cudaStream_t s)
@@ -480,7 +535,7 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     if (nd <= 0) return cudaSuccess;
     if (max_ao <= 32) {
         const size_t smem = w32_smem_bytes<T>();
-        auto fn = VT ? k_finish_w32<T, true> : k_finish_w32<T, false>;
+        auto fn = VT ? k_finish_w32<T, true, PAIRS> : k_finish_w32<T, false, PAIRS>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         fn<<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
@@ -489,10 +544,10 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     if (!tasks || ntasks <= 0 || !part) return cudaErrorInvalidValue;
     const size_t smem = tiled_smem_bytes<T>(max_ao);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_finish_tiled<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_finish_tiled<T, PAIRS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int smem_elems = (int)((smem - 2 * max_ao * sizeof(double) - 64) / sizeof(T));
-    k_finish_tiled<T><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part, smem_elems, VT);
+    const int smem_elems = (int)((smem - 2 * max_ao * (sizeof(double) + sizeof(FF)) - 64) / sizeof(T));
+    k_finish_tiled<T, PAIRS><<<ntasks, kTThreads, smem, s>>>(d_desc, tasks, C, Epool, H, part, smem_elems, VT);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the dimers' first-task indices follow the task array
     const int* first = reinterpret_cast<const int*>(tasks + ntasks);
@@ -636,14 +691,16 @@ cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao, cons
                                const double* Epool, const double* H, double* E2, const FinTask* tasks,
                                int ntasks, double* part, double* VT, cudaStream_t s)
 {
-    return launch_finish<double>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, VT, s);
+    return launch_finish<double, false>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, VT, s);
 }
 
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const float* Cf,
                                const double* Epool, const float* H, double* E2, const FinTask* tasks,
-                               int ntasks, double* part, float* VT, cudaStream_t s)
+                               int ntasks, double* part, float* VT, bool fp64_epilogue, cudaStream_t s)
 {
-    return launch_finish<float>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s);
+    return fp64_epilogue
+               ? launch_finish<float, false>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s)
+               : launch_finish<float, true>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s);
 }
 
 void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinTask>* out)

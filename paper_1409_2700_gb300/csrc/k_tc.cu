@@ -28,6 +28,7 @@
 // and returns.
 #include "internal.h"
 #include "convert.h"
+#include "ff.h"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -76,13 +77,14 @@ struct TcParams {
     const CUtensorMap* maps;       // [dimer][form]
     const DimerDesc* desc;
     const float* Cf;
-    float* H;
+    const double* Cd;              // FP64 coefficients (TC_FP64E)
+    void* H;                       // float, or double for TC_FP64E
     int* status;
     int sf;                        // FP64 staging stages
     unsigned int f_stage_bytes;    // bytes per staging slot
     unsigned int w_stage_bytes;    // bytes per W slot
     unsigned int tmem_cols;
-    int kind;                      // TC_TF32 / TC_BF16X3 / TC_BF16X2
+    int kind;                      // TC_TF32 / TC_BF16X3 / TC_BF16X2 / TC_FP64E
     int kcs_max;                   // largest p2 chunk count of the launch (rank variant)
     unsigned long long wait_ns;    // limit of each wait (kWaitNs if 0)
     int withhold;                  // test aid: CTA 0 issues only withhold - 1 integral loads (0 = off)
@@ -239,6 +241,21 @@ __device__ __forceinline__ void tmem_ld_l4x8(unsigned taddr, unsigned (&r)[32])
         "tcgen05.wait::ld.sync.aligned;\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l7x8(unsigned taddr, unsigned (&r)[56])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%56];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%57];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16, %17, %18, %19, %20, %21, %22, %23}, [%58];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24, %25, %26, %27, %28, %29, %30, %31}, [%59];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%32, %33, %34, %35, %36, %37, %38, %39}, [%60];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%40, %41, %42, %43, %44, %45, %46, %47}, [%61];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%48, %49, %50, %51, %52, %53, %54, %55}, [%62];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55])
+        : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u), "r"(taddr + 64u), "r"(taddr + 80u), "r"(taddr + 96u)
         : "memory");
 }
 __device__ __forceinline__ void tmem_ld_l4x16(unsigned taddr, unsigned (&r)[64])
@@ -653,7 +670,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_half_tc(const TcParams P)
             if (!mbar_wait(&sh->tmem_full[b], (li >> 1) & 1, &sh->abort, P.status, 8, P.wait_ns)) break;
             tc_fence_after();
             const int npairs = g.o0 * g.o2;
-            float* Hf = P.H + d.h_off + (long long)item.form * npairs * g.rows;
+            float* Hf = static_cast<float*>(P.H) + d.h_off + (long long)item.form * npairs * g.rows;
             for (int mt = 0; mt < item.mts; mt++) {
                 const int tile = item.mt0 + mt;
                 const int p1_lo = tile * g.p1t;
@@ -732,20 +749,27 @@ constexpr int kSlots = 32;        // 32 x 16 = 512 TMEM columns (16 slots when B
 constexpr int kFxUnits = 8;       // BF16x3: 4-slot p0 units in 512 columns (4 when BIG)
 constexpr int kOB = 8;            // register accumulator block: o_X, o_Y <= 8
 constexpr int kOB5 = 5;           // the same sized for o_X, o_Y <= 5 (fewer rank-1 FMAs)
+constexpr int kFp64eMaxAO = 64;   // FP64E: p2 chunks <= 2, so that its three-tile A ring fits
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
 constexpr int kConvWarps = 8;     // converter warps per group: one unit (128 rows) per group
 // Groups of converter warps take alternate units.  The variant with
 // occupations <= 5 runs two (four converter warps per SM sub-partition: the
 // converters are latency bound) within the register budget that 22 warps
 // leave; the others keep one group and the larger per-thread budget.
-template <bool BIG, int OB>
-__host__ __device__ constexpr int conv_groups() { return (!BIG && OB == 5) ? 2 : 1; }
-template <bool BIG, int OB>
-__host__ __device__ constexpr int rank_threads() { return (2 + kConvWarps * conv_groups<BIG, OB>() + 4) * 32; }
+// FP64E keeps one group: its epilogue's FP32-pair accumulators need the
+// larger per-thread budget.
+template <bool BIG, int OB, int KIND = TC_TF32>
+__host__ __device__ constexpr int conv_groups() { return (!BIG && OB == 5 && KIND != TC_FP64E) ? 2 : 1; }
+template <bool BIG, int OB, int KIND = TC_TF32>
+__host__ __device__ constexpr int rank_threads() { return (2 + kConvWarps * conv_groups<BIG, OB, KIND>() + 4) * 32; }
 constexpr int kOBig = 16;         // TMEM accumulators: o_X, o_Y <= 16
 // C_X occupied rows of one item (n0 <= 128), per parity: the register
-// accumulator kernel stages kOB columns, the TMEM one kOBig.
-__host__ __device__ constexpr int cx_floats(bool big) { return 128 * (big ? kOBig : kOB); }
+// accumulator kernel stages kOB columns (FP64E: each as an FP32 pair), the
+// TMEM one kOBig.
+__host__ __device__ constexpr int cx_floats(bool big, int kind = TC_TF32)
+{
+    return 128 * (big ? kOBig : kOB) * (kind == TC_FP64E ? 2 : 1);
+}
 
 struct __align__(8) RankShared {
     unsigned long long full_f[8], empty_f[8];
@@ -760,21 +784,27 @@ struct __align__(8) RankShared {
     volatile int abort;
 };
 
-// TMEM columns of one p0 unit and units in the ring.
+// TMEM columns of one p0 unit and units in the ring (FP64E: seven levels).
 template <int KIND, bool BIG>
-__host__ __device__ constexpr int unit_cols() { return KIND != TC_TF32 ? 4 * kNT : kNT; }
+__host__ __device__ constexpr int unit_cols() { return KIND == TC_FP64E ? 7 * kNT : KIND != TC_TF32 ? 4 * kNT : kNT; }
 template <int KIND, bool BIG>
 __host__ __device__ constexpr int n_units() { return (BIG ? 256 : 512) / unit_cols<KIND, BIG>(); }
-// Shared bytes of the A ring (two slots; BF16x3 uses two tiles per slot) and
-// of the BF16x3 unit scales (row scales 128 + column scales 16 per unit).
-__host__ __device__ constexpr size_t a_ring_bytes(int kind) { return 2 * (size_t)kABytes * (kind == TC_BF16X3 ? 2 : 1); }
+// Shared bytes of the A ring (two slots; BF16x3 uses two tiles per slot,
+// FP64E three) and of the fixed-point unit scales (row scales 128 + column
+// scales 16 per unit).
+__host__ __device__ constexpr size_t a_ring_bytes(int kind)
+{
+    return 2 * (size_t)kABytes * (kind == TC_FP64E ? 3 : kind == TC_BF16X3 ? 2 : 1);
+}
 // Bytes of one parity of the B operand (C_Y's occupied columns) for an item
 // of kcs_max p2 chunks.  TF32: per chunk two 16-row planes (hi, lo).  BF16x3:
 // per pair of chunks one 64-row tile, row 16 v + j = digit v of column j,
-// chunk kc in bytes 64 (kc % 2) .. +63 of the row.
+// chunk kc in bytes 64 (kc % 2) .. +63 of the row.  FP64E: the same with six
+// digits and a seventh all-zero plane, 112 rows per pair of chunks.
+__host__ __device__ constexpr int w_rows(int kind) { return kind == TC_FP64E ? 112 : 64; }
 __host__ __device__ constexpr size_t w_stride_bytes(int kind, int kcs_max)
 {
-    return kind != TC_TF32 ? (size_t)((kcs_max + 1) / 2) * 64 * 128 : (size_t)kcs_max * 2 * kNT * 128;
+    return kind != TC_TF32 ? (size_t)((kcs_max + 1) / 2) * w_rows(kind) * 128 : (size_t)kcs_max * 2 * kNT * 128;
 }
 __host__ __device__ constexpr size_t fx_scale_bytes(int kind)
 {
@@ -939,7 +969,10 @@ __device__ __forceinline__ void convert_row(const double* __restrict__ F, unsign
 // Digit levels the epilogue combines: BF16x3 four, BF16x2 three (its fourth,
 // A0 B3 + A1 B2, lies 2^-24 below the first and is not formed).
 template <int KIND>
-__host__ __device__ constexpr int n_levels() { return KIND == TC_BF16X3 ? 4 : KIND == TC_BF16X2 ? 3 : 1; }
+__host__ __device__ constexpr int n_levels()
+{
+    return KIND == TC_FP64E ? 7 : KIND == TC_BF16X3 ? 4 : KIND == TC_BF16X2 ? 3 : 1;
+}
 
 // T[(p1,p3) = this lane's row][j < NJ] of one unit, written to T (add =
 // false) or added to it.  TF32: the slot itself.  Fixed-point forms: the
@@ -1081,6 +1114,148 @@ __device__ __forceinline__ int convert_row_fx2(const double* __restrict__ F, uns
     return emax;
 }
 
+// ---- FP64E: six unsigned byte digits of a 48-bit fixed point
+// |x| of an FP64 vector element relative to the vector's largest exponent
+// field emax: N = floor(|x| 2^(47 - e)), e = emax - 1023, so |x| = N 2^(e-47)
+// less at most one unit (2^-47 of the vector's largest power of two), and
+// N < 2^48, returned as nh (16 bits) : nl.  Integer pipes only: the 53-bit
+// significand shifted right by emax - ex + 5 >= 5 (two clamped funnel shifts
+// cover every distance up to 64).  Zeros and FP64 denormals give N = 0, and
+// so does every element when emax is 0 (an invalid or all-zero vector).
+__device__ __forceinline__ void fx48(unsigned lo, unsigned hi, int emax, unsigned& nh, unsigned& nl)
+{
+    const int ex = (int)((hi >> 20) & 0x7FFu);
+    const unsigned mh = (hi & 0xFFFFFu) | 0x100000u;
+    const unsigned sh = ex ? (unsigned)(emax - ex + 5) : 64u;   // ex > emax only for emax = 0: huge
+    const unsigned s1 = min(sh, 32u);
+    nh = __funnelshift_rc(mh, 0u, s1);
+    nl = __funnelshift_rc(__funnelshift_rc(lo, mh, s1), 0u, sh - s1);
+}
+
+// Byte `sel & 3` of wa and of wb as two exact BF16 values packed low | high,
+// with the sign bits sgn (0x8000: first, 0x80000000: second) set: the byte
+// becomes the FP32 value 2^23 + b by a byte permute, one packed subtraction
+// leaves b (at most 8 significant bits, so its BF16 is the FP32's high half).
+__device__ __forceinline__ unsigned bf16_byte_pair(unsigned wa, unsigned wb, unsigned sel, unsigned sgn)
+{
+    const float2 f = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wa, 0x4B000000u, sel)),
+                                            __uint_as_float(__byte_perm(wb, 0x4B000000u, sel))),
+                                make_float2(-8388608.0f, -8388608.0f));
+    return pack_bf16(f.x, f.y) | sgn;
+}
+
+// The six digit planes of two consecutive elements (a, b) of one vector:
+// N = d0 2^40 + d1 2^32 + d2 2^24 + d3 2^16 + d4 2^8 + d5, each digit carrying
+// its element's sign; w[v] = digit v of (a | b << 16).
+__device__ __forceinline__ void digits6_pair(uint2 a, uint2 b, int emax, unsigned (&w)[6])
+{
+    unsigned ha, la, hb, lb;
+    fx48(a.x, a.y, emax, ha, la);
+    fx48(b.x, b.y, emax, hb, lb);
+    const unsigned sg = ((a.y >> 16) & 0x8000u) | (b.y & 0x80000000u);
+    w[0] = bf16_byte_pair(ha, hb, 0x7541u, sg);
+    w[1] = bf16_byte_pair(ha, hb, 0x7540u, sg);
+    w[2] = bf16_byte_pair(la, lb, 0x7543u, sg);
+    w[3] = bf16_byte_pair(la, lb, 0x7542u, sg);
+    w[4] = bf16_byte_pair(la, lb, 0x7541u, sg);
+    w[5] = bf16_byte_pair(la, lb, 0x7540u, sg);
+}
+
+// FP64E: row r of one staged box as the six digit planes of its 48-bit fixed
+// point, tiles [d0 | d1], [d2 | d3], [d4 | d5] (bytes 0-63 / 64-127 of each
+// 128-byte row), chunks c0 and c0 + 2 of 8 p2.  Both words of each double are
+// read; the row chunk's largest exponent field (bitwise maximum of |hi|,
+// combined with the partner lane l ^ 16) fixes the fixed point.  Returns it.
+__device__ __forceinline__ int convert_row_fx6(const double* __restrict__ F, unsigned char* __restrict__ A,
+                                               const ConvRow& cr, int n3, int c0)
+{
+    const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
+    uint2 v[2][8];
+    unsigned m = 0;
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            v[q][e] = dw[((c0 + 2 * q) * 8 + e) * n3];
+            m = max(m, v[q][e].y & 0x7FFFFFFFu);
+        }
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+    const int emax = cr.valid ? (int)(m >> 20) : 0;
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const int c = c0 + 2 * q;
+        unsigned w[6][4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            unsigned d[6];
+            digits6_pair(v[q][e], v[q][e + 1], emax, d);
+#pragma unroll
+            for (int k = 0; k < 6; k++) w[k][e / 2] = d[k];
+        }
+#pragma unroll
+        for (int t = 0; t < 3; t++) {
+            unsigned char* At = A + (size_t)t * kABytes + cr.dst;
+            *reinterpret_cast<uint4*>(At + ((c ^ cr.r7) << 4)) =
+                make_uint4(w[2 * t][0], w[2 * t][1], w[2 * t][2], w[2 * t][3]);
+            *reinterpret_cast<uint4*>(At + (((4 + c) ^ cr.r7) << 4)) =
+                make_uint4(w[2 * t + 1][0], w[2 * t + 1][1], w[2 * t + 1][2], w[2 * t + 1][3]);
+        }
+    }
+    return emax;
+}
+
+// FP64E: the seven digit levels of one unit for this lane's row, columns
+// j < NJ, combined into an FP32 pair: S = L6, then S = S 2^-8 + L_k for
+// k = 5 .. 0 (each L_k an exact integer below 2^24, the scaling exact, the
+// addition a TwoSum with renormalisation), times the unit's row scale (a
+// power of two).  The column scales are applied once per output.
+template <int NJ>
+__device__ __forceinline__ void unit_T_ff(unsigned taddr, FF (&T)[8], float srow, bool add)
+{
+    unsigned raw[7][8];
+    tmem_ld_l7x8(taddr, *reinterpret_cast<unsigned(*)[56]>(&raw[0][0]));
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        FF S{__uint_as_float(raw[6][j]), 0.f};
+#pragma unroll
+        for (int l = 5; l >= 0; l--) {
+            float e;
+            const float t = two_sum(__uint_as_float(raw[l][j]), __fmul_rn(S.h, 0x1p-8f), e);
+            e = __fadd_rn(e, __fmul_rn(S.l, 0x1p-8f));
+            S.h = __fadd_rn(t, e);
+            S.l = __fsub_rn(e, __fsub_rn(S.h, t));
+        }
+        S.h = __fmul_rn(S.h, srow);
+        S.l = __fmul_rn(S.l, srow);
+        T[j] = add ? ff_add(T[j], S) : S;
+    }
+}
+
+// FP64E: T of one p0 (the units of its p2 chunks added in chunk order, as
+// pairs), with the first unit's column scales copied to sc (if non-null).
+// Frees each unit's slot after reading it.  False on timeout/abort.
+template <int NS, int UC, int NJ>
+__device__ __forceinline__ bool load_p0_T_ff(FF (&T)[8], RankShared* sh, unsigned& gS, int kcs, unsigned lanebase,
+                                             const float* exps, const float* scu, int r, int lane, float* sc,
+                                             volatile int* abort, int* status, unsigned long long lim)
+{
+    for (int u = 0; u < kcs; u++, gS++) {
+        const int s = gS % NS;
+        if (!mbar_wait(&sh->slot_full[s], (gS / NS) & 1, abort, status, 18, lim)) return false;
+        if (!mbar_wait(&sh->exp_full[s], (gS / NS) & 1, abort, status, 23, lim)) return false;
+        tc_fence_after();
+        if (sc && u == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; j++) sc[j] = scu[s * kNT + j];
+        }
+        unit_T_ff<NJ>(lanebase + (unsigned)(s * UC), T, exps[s * 128 + r], u > 0);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
+    }
+    return true;
+}
+
 // T[row][j < NJ] of one p0 for this lane's row: TF32 reads the p0's unit;
 // the fixed-point forms add the units of the p2 chunks in chunk order (FP32,
 // round to nearest).  With sc (non-null) the first unit's column scales are
@@ -1110,9 +1285,9 @@ __device__ __forceinline__ bool load_p0_T(float (&T)[NJ], RankShared* sh, unsign
 }
 
 template <int KIND, bool BIG, int OB = kOB>
-__global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(const TcParams P)
+__global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_rank(const TcParams P)
 {
-    constexpr int NG = conv_groups<BIG, OB>();      // converter groups
+    constexpr int NG = conv_groups<BIG, OB, KIND>();   // converter groups
     constexpr int CT = kConvWarps * NG;             // converter warps
     constexpr int EW0 = 2 + CT;                     // first epilogue warp
     constexpr bool FX = KIND != TC_TF32;            // fixed-point digit planes (BF16x3, BF16x2)
@@ -1128,7 +1303,7 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
     unsigned char* Wr = Ar + a_ring_bytes(KIND);
     const int wstride = (int)w_stride_bytes(KIND, P.kcs_max);   // bytes per parity
     float* cxs = reinterpret_cast<float*>(Wr + 2 * wstride);
-    constexpr int CXF = cx_floats(BIG);
+    constexpr int CXF = cx_floats(BIG, KIND);
     float* exps = cxs + 2 * CXF;                        // BF16x3: [unit][128 rows] row scales
     float* scu = exps + kFxUnits * 128;                 //          [unit][16 columns] column scales
     int* colx = reinterpret_cast<int*>(scu + kFxUnits * kNT);   // [parity][16 parts][16 columns] exponents
@@ -1207,6 +1382,9 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
             const unsigned idesc = make_idesc(KIND, kNT);
             const unsigned idesc_fx[4] = {make_idesc(KIND, 4 * kNT), make_idesc(KIND, 3 * kNT),
                                           make_idesc(KIND, 2 * kNT), make_idesc(KIND, kNT)};
+            [[maybe_unused]] unsigned idesc_f6[6];   // FP64E: A_u x [B0..B(6-u)], N = 16 (7 - u)
+#pragma unroll
+            for (int u = 0; u < 6; u++) idesc_f6[u] = make_idesc(KIND, (7 - u) * kNT);
             for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
                 const TcItem item = P.items[it];
                 const ItemGeo g = geo_of(P.desc[item.dimer], item.form);
@@ -1256,19 +1434,35 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
                                 // A0's MMA opens all four slots.
                                 const unsigned long long adesc = sw128_desc(Ar + (size_t)as * ASLOT);
                                 const unsigned long long bk =
-                                    sw128_desc(Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128) +
+                                    sw128_desc(Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * w_rows(KIND) * 128) +
                                     (unsigned long long)((kc & 1) * 4);
+                                // FP64E: tiles [d0|d1], [d2|d3], [d4|d5]; A_u x [B0..B(6-u)] lands
+                                // A_u B_v in the slot of level u + v (levels 0-6 kept; B6 = 0, so
+                                // A0's MMA opens all seven slots)
+                                if constexpr (KIND == TC_FP64E) {
 #pragma unroll
-                                for (int k = 0; k < 2; k++) {
-                                    const unsigned acc = k > 0 ? 1u : 0u;
-                                    // BF16x2 forms levels 0-2 only: A0 x [B0..B2], A1 x [B0, B1]
-                                    constexpr int lv = KIND == TC_BF16X2 ? 1 : 0;
-                                    tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[lv], acc);
-                                    tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[lv + 1], 1u);
-                                    if constexpr (KIND == TC_BF16X3) {
-                                        const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
-                                        tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
-                                        tc_mma<KIND>(dt + 3 * kNT, a2 + 4 + 2 * k, bk + 2 * k, idesc_fx[3], 1u);
+                                    for (int k = 0; k < 2; k++)
+#pragma unroll
+                                        for (int u = 0; u < 6; u++) {
+                                            const unsigned long long au =
+                                                sw128_desc(Ar + (size_t)as * ASLOT + (size_t)(u >> 1) * kABytes) +
+                                                (unsigned long long)((u & 1) * 4);
+                                            tc_mma<KIND>(dt + u * kNT, au + 2 * k, bk + 2 * k, idesc_f6[u],
+                                                         (u > 0 || k > 0) ? 1u : 0u);
+                                        }
+                                } else {
+#pragma unroll
+                                    for (int k = 0; k < 2; k++) {
+                                        const unsigned acc = k > 0 ? 1u : 0u;
+                                        // BF16x2 forms levels 0-2 only: A0 x [B0..B2], A1 x [B0, B1]
+                                        constexpr int lv = KIND == TC_BF16X2 ? 1 : 0;
+                                        tc_mma<KIND>(dt, adesc + 2 * k, bk + 2 * k, idesc_fx[lv], acc);
+                                        tc_mma<KIND>(dt + kNT, adesc + 4 + 2 * k, bk + 2 * k, idesc_fx[lv + 1], 1u);
+                                        if constexpr (KIND == TC_BF16X3) {
+                                            const unsigned long long a2 = sw128_desc(Ar + (size_t)as * ASLOT + kABytes);
+                                            tc_mma<KIND>(dt + 2 * kNT, a2 + 2 * k, bk + 2 * k, idesc_fx[2], 1u);
+                                            tc_mma<KIND>(dt + 3 * kNT, a2 + 4 + 2 * k, bk + 2 * k, idesc_fx[3], 1u);
+                                        }
                                     }
                                 }
                                 tc_commit(&sh->empty_a[as]);
@@ -1300,6 +1494,7 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
             const DimerDesc& d = P.desc[item.dimer];
             const ItemGeo g = geo_of(d, item.form);
             const float* CY = P.Cf + d.cY;
+            [[maybe_unused]] const double* CYd = P.Cd + d.cY;   // FP64E: C_Y in FP64
             const int wp = li & 1;
             const ConvRow cr = conv_row(r, g.p1t * g.n3, g.n3);
             // a warp whose rows all lie past the tile's valid rows (n3 > 64 leaves
@@ -1320,8 +1515,12 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
 #pragma unroll
                     for (int t = 0; t < 8; t++) {
                         const int p2 = part + 16 * t;
-                        if (j < g.o2 && p2 < g.n2)
-                            fm = max(fm, (int)((__float_as_uint(__ldg(CY + p2 * d.nY + j)) >> 23) & 0xFFu));
+                        if (j < g.o2 && p2 < g.n2) {
+                            if constexpr (KIND == TC_FP64E)
+                                fm = max(fm, (int)((__double2hiint(__ldg(CYd + p2 * d.nY + j)) >> 20) & 0x7FF));
+                            else
+                                fm = max(fm, (int)((__float_as_uint(__ldg(CY + p2 * d.nY + j)) >> 23) & 0xFFu));
+                        }
                     }
                     cx_part[part * kNT + j] = fm;
                     __syncwarp();
@@ -1331,11 +1530,11 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
                 if (ct < kNT) {
                     int m = 0;
                     for (int q = 0; q < 16; q++) m = max(m, cx_part[q * kNT + ct]);
-                    sc_mine = col_scale(m);
+                    sc_mine = KIND == TC_FP64E ? row_scale(m) : col_scale(m);   // 2^(f - 7)
                 }
             }
             for (int kc = 0; kc < g.kcs; kc++) {
-                unsigned char* W0 = FX ? Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * 64 * 128
+                unsigned char* W0 = FX ? Wr + (size_t)wp * wstride + (size_t)(kc >> 1) * w_rows(KIND) * 128
                                        : Wr + (size_t)wp * wstride + (size_t)kc * 2 * kNT * 128;
                 unsigned char* W1 = W0 + kNT * 128;
                 if (KIND == TC_TF32) {
@@ -1351,6 +1550,34 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
                         }
                         *reinterpret_cast<uint4*>(W0 + sw128_off(j, c)) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
                         *reinterpret_cast<uint4*>(W1 + sw128_off(j, c)) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+                    }
+                } else if constexpr (KIND == TC_FP64E) {
+                    // C_Y column j in 48-bit fixed point relative to its largest exponent, six digits
+                    for (int task = cta; task < kNT * 4; task += 32 * CT) {
+                        const int j = task >> 2, c = task & 3;
+                        int fmax = 0;
+                        for (int q = 0; q < 16; q++) fmax = max(fmax, cx_part[q * kNT + j]);
+                        unsigned w[6][4];
+#pragma unroll
+                        for (int e = 0; e < 8; e += 2) {
+                            uint2 xb[2];
+#pragma unroll
+                            for (int u = 0; u < 2; u++) {
+                                const int p2 = kc * kKC + c * 8 + e + u;
+                                const double x = (j < g.o2 && p2 < g.n2) ? __ldg(CYd + p2 * d.nY + j) : 0.0;
+                                xb[u] = make_uint2((unsigned)__double2loint(x), (unsigned)__double2hiint(x));
+                            }
+                            unsigned dg[6];
+                            digits6_pair(xb[0], xb[1], fmax, dg);
+#pragma unroll
+                            for (int k = 0; k < 6; k++) w[k][e / 2] = dg[k];
+                        }
+#pragma unroll
+                        for (int v = 0; v < 6; v++)
+                            *reinterpret_cast<uint4*>(W0 + sw128_off(v * kNT + j, (kc & 1) * 4 + c)) =
+                                make_uint4(w[v][0], w[v][1], w[v][2], w[v][3]);
+                        // plane 6 is zero: A0's MMA spans all seven level slots and opens them
+                        *reinterpret_cast<uint4*>(W0 + sw128_off(6 * kNT + j, (kc & 1) * 4 + c)) = make_uint4(0, 0, 0, 0);
                     }
                 } else {
                     // C_Y column j in fixed point relative to its largest exponent, four digits
@@ -1419,6 +1646,8 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
                             if (live) {
                                 if constexpr (KIND == TC_BF16X3)
                                     emax = convert_row_fx1(Fs, At, At + kABytes, cr, g.n3, c0);
+                                else if constexpr (KIND == TC_FP64E)
+                                    emax = convert_row_fx6(Fs, At, cr, g.n3, c0);
                                 else
                                     emax = convert_row_fx2(Fs, At, cr, g.n3, c0);
                             }
@@ -1455,17 +1684,66 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB>(), 1) k_half_tc_rank(con
             // stage C_X's occupied columns, row p0 = e, for this item
             if (!(ok = mbar_wait(&sh->cx_empty[par], ((li >> 1) & 1) ^ 1, abort, P.status, 19, P.wait_ns))) break;
             if (e < g.n0) {
-                const float* CX = P.Cf + d.cX + e * d.nX;
+                if constexpr (KIND == TC_FP64E) {
+                    // C_X from the FP64 pool as FP32 pairs
+                    const double* CX = P.Cd + d.cX + e * d.nX;
+                    FF* cx2 = reinterpret_cast<FF*>(cx);
 #pragma unroll
-                for (int i = 0; i < CXW; i++) cx[e * CXW + i] = i < g.o0 ? __ldg(CX + i) : 0.f;
+                    for (int i = 0; i < CXW; i++) cx2[e * CXW + i] = i < g.o0 ? ff_split(__ldg(CX + i)) : FF{0.f, 0.f};
+                } else {
+                    const float* CX = P.Cf + d.cX + e * d.nX;
+#pragma unroll
+                    for (int i = 0; i < CXW; i++) cx[e * CXW + i] = i < g.o0 ? __ldg(CX + i) : 0.f;
+                }
             }
             mbar_arrive(&sh->cx_full[par]);
             if (!(ok = mbar_wait(&sh->cx_full[par], (li >> 1) & 1, abort, P.status, 20, P.wait_ns))) break;
-            float* Hf = P.H + d.h_off + (long long)item.form * g.o0 * g.o2 * g.rows;
+            float* Hf = static_cast<float*>(P.H) + d.h_off + (long long)item.form * g.o0 * g.o2 * g.rows;
+            [[maybe_unused]] double* Hd = static_cast<double*>(P.H) + d.h_off + (long long)item.form * g.o0 * g.o2 * g.rows;
             const unsigned lanebase = tmem + ((unsigned)(q * 32) << 16);
             for (int mt = 0; mt < item.mts && ok; mt++) {
                 const int p1_lo = (item.mt0 + mt) * g.p1t;
-                if constexpr (!BIG) {
+                if constexpr (KIND == TC_FP64E) {
+                    // H[(p1,p3)][(i,j)] = sum_p0 C_X[p0][i] T_p0[(p1,p3)][j] on FP32 pairs, written as FP64
+                    FF acc[OB][OB];
+#pragma unroll
+                    for (int i = 0; i < OB; i++)
+#pragma unroll
+                        for (int j = 0; j < OB; j++) acc[i][j] = FF{0.f, 0.f};
+                    float sc[8];   // the item's column scales 2^(f - 7), applied once per output
+#pragma unroll
+                    for (int j = 0; j < 8; j++) sc[j] = 1.f;
+                    const FF* cx2 = reinterpret_cast<const FF*>(cx);
+                    for (int p0 = 0; p0 < g.n0; p0++) {
+                        FF T[8];
+                        if (!(ok = load_p0_T_ff<NS, UC, OB>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
+                                                             p0 == 0 ? sc : nullptr, abort, P.status, P.wait_ns)))
+                            break;
+#pragma unroll
+                        for (int i = 0; i < OB; i++) {
+                            const FF c = cx2[p0 * kOB + i];
+#pragma unroll
+                            for (int j = 0; j < OB; j++) ff_mac(acc[i][j], c, T[j]);
+                        }
+                    }
+                    if (!ok) break;
+                    const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
+                    if (r < valid) {
+                        double* q = Hd + p1_lo * g.n3 + r;   // pair (i, j) at q + (i*o2 + j) * rows
+                        const size_t step = (size_t)g.rows;
+#pragma unroll
+                        for (int i = 0; i < OB; i++) {
+                            if (i < g.o0) {
+#pragma unroll
+                                for (int j = 0; j < OB; j++)
+                                    if (j < g.o2) {
+                                        *q = ff_f64(FF{__fmul_rn(acc[i][j].h, sc[j]), __fmul_rn(acc[i][j].l, sc[j])});
+                                        q += step;
+                                    }
+                            }
+                        }
+                    }
+                } else if constexpr (!BIG) {
                     float acc[OB][OB];
 #pragma unroll
                     for (int i = 0; i < OB; i++)
@@ -1605,6 +1883,7 @@ int choose_variant(TcKind kind, const DimerDesc* h, int nd)
         nymax = std::max(nymax, h[k].nY);
     }
     const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
+    if (kind == TC_FP64E) return 3;   // the one kernel it has (limits checked by tc_prepare)
     const char* env = getenv("MCPT_TC_KERNEL");
     // BF16x2 runs the rank kernels only (the tensor-core size limits always fit them)
     if (env && !strcmp(env, "kron") && kind != TC_BF16X2) return 0;
@@ -1633,7 +1912,7 @@ size_t tc_work_bytes(TcKind kind, const DimerDesc* h, int nd)
 static size_t fixed_smem(TcKind kind, int variant, int kcs_max, unsigned w_stage_bytes)
 {
     return variant >= 1 ? 1024 + a_ring_bytes(kind) + 2 * w_stride_bytes(kind, kcs_max) +
-                              2 * (size_t)cx_floats(variant == 2) * 4 + fx_scale_bytes(kind) + sizeof(RankShared)
+                              2 * (size_t)cx_floats(variant == 2, kind) * 4 + fx_scale_bytes(kind) + sizeof(RankShared)
                         : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)w_stage_bytes + sizeof(TcShared);
 }
 
@@ -1662,7 +1941,9 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
         nymax = std::max(nymax, h[k].nY);
     }
     std::vector<int> vars;
-    if (nymax <= kKCMax * kKC && omax <= kOBig) {
+    if (kind == TC_FP64E) {
+        vars.push_back(3);
+    } else if (nymax <= kKCMax * kKC && omax <= kOBig) {
         if (omax <= kOB5) vars.push_back(3);
         if (omax <= kOB) vars.push_back(1);
         vars.push_back(2);
@@ -1692,7 +1973,7 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
 }
 
 cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_desc, int nd, const float* Cf,
-                       float* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s,
+                       const double* Cd, void* H, void* d_work, size_t work_bytes, int* d_status, cudaStream_t s,
                        const TcTune* tune, TcLaunch* out, char* err, size_t errlen)
 {
     if (nd <= 0) return cudaSuccess;
@@ -1704,6 +1985,14 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     std::vector<CUtensorMap> maps((size_t)nd * 2);
     std::vector<TcItem> items;
     const int variant = (tune && tune->variant1) ? tune->variant1 - 1 : choose_variant(kind, h_desc, nd);
+    if (kind == TC_FP64E) {
+        for (int k = 0; k < nd; k++)
+            if (std::max(h_desc[k].oX, h_desc[k].oY) > kOB5 || h_desc[k].nY > kFp64eMaxAO || variant != 3) {
+                snprintf(err, errlen, "the FP64-emulating form handles monomers of up to %d AO and %d occupied",
+                         kFp64eMaxAO, kOB5);
+                return cudaErrorNotSupported;
+            }
+    }
     int maxN = 16;
     unsigned max_box = 0;
     for (int k = 0; k < nd; k++) {
@@ -1769,6 +2058,7 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     P.maps = w;
     P.desc = d_desc;
     P.Cf = Cf;
+    P.Cd = Cd;
     P.H = H;
     P.status = d_status;
     P.kind = kind;
@@ -1802,6 +2092,7 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.maps = static_cast<const CUtensorMap*>(L.maps);
     P.desc = L.desc;
     P.Cf = L.Cf;
+    P.Cd = L.Cd;
     P.H = L.H;
     P.status = L.status;
     P.sf = L.sf;
@@ -1813,7 +2104,10 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.wait_ns = L.wait_ns ? L.wait_ns : kWaitNs;
     P.withhold = L.withhold;
     void (*fn)(const TcParams);
-    if (L.variant == 1)
+    if (L.kind == TC_FP64E) {
+        if (L.variant != 3) return cudaErrorNotSupported;
+        fn = k_half_tc_rank<TC_FP64E, false, kOB5>;
+    } else if (L.variant == 1)
         fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, false>
              : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, false>
                                    : k_half_tc_rank<TC_BF16X3, false>;
@@ -1830,7 +2124,8 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) return e;
-    const int threads = L.variant == 3   ? rank_threads<false, kOB5>()
+    const int threads = L.kind == TC_FP64E ? rank_threads<false, kOB5, TC_FP64E>()
+                        : L.variant == 3   ? rank_threads<false, kOB5>()
                         : L.variant == 2 ? rank_threads<true, kOB>()
                         : L.variant == 1 ? rank_threads<false, kOB>()
                                          : kThreadsTc;
