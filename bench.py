@@ -41,7 +41,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="bf16x2", choices=["tf32", "bf16x3", "bf16x2", "fp32c", "fp64"])
+    p.add_argument("--precision", default="bf16x2", choices=["tf32", "bf16x3", "bf16x2", "fp32c", "fp64", "fp64e"])
     p.add_argument("--workload", default="lattice-10x10x10-cheb2")
     p.add_argument("--wave-gb", type=float, default=WAVE_BUDGET / (1 << 30),
                    help="streamed workloads: GiB of integral blocks per wave (one wave = one step)")
@@ -306,7 +306,7 @@ def our_arm(args, ws, rank, local):
         traffic = tpd * w.n_dimers / st.waves if (tpd and uniform) else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3") else "k_half_fp32c",
+                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3", "bf16x2", "fp64e") else "k_half_fp32c",
                 "peak_kind": peak_kind}
 
     line = {
@@ -797,7 +797,7 @@ def streamed_arm(args, ws, rank, local):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "traffic": tpd * timed_dimers / nsteps if (tpd and uniform) else None,
-                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3", "bf16x2") else "k_half_fp32c",
+                "kernel": "k_half_tc_rank" if args.precision in ("tf32", "bf16x3", "bf16x2", "fp64e") else "k_half_fp32c",
                 "peak_kind": peak_kind,
                 "per": "one wave's first-half launch (traffic scaled from the ncu capture per dimer)"}
     line = {
