@@ -53,10 +53,10 @@ def parse():
                    help="streamed workloads with more waves run only the waves the steps cover")
     p.add_argument("--cpu-sample", type=int, default=1024, help="dimers in the oracle's timed sample (at most)")
     p.add_argument("--no-extras", action="store_true",
-                   help="report none of the extras (coupling, td2, df, FP64 form, e2e, CPU baseline)")
-    p.add_argument("--extras", default="coupling,td2,df,fp64,e2e,cpu",
+                   help="report none of the extras (coupling, td2, df, FP64 form, FP64E form, e2e, CPU baseline)")
+    p.add_argument("--extras", default="coupling,td2,df,fp64,fp64e,e2e,cpu",
                    help="comma-separated extras to report after the headline (default all of "
-                        "coupling,td2,df,fp64,e2e,cpu)")
+                        "coupling,td2,df,fp64,fp64e,e2e,cpu)")
     p.add_argument("--max-dimers", type=int, default=0,
                    help="keep only the first N dimers of the workload (smaller cases for profiling)")
     p.add_argument("--alias-blocks", action="store_true",
@@ -715,6 +715,11 @@ def streamed_arm(args, ws, rank, local):
     if rank == 0 and "fp64" in extras and args.precision != "fp64":
         c64 = make_ctx("fp64", True)
         ctxs.append(c64)
+    # the FP64-emulating tensor-core form (monomers of up to 64 AO, 5 occupied) on the same waves
+    cE = None
+    if (rank == 0 and "fp64e" in extras and args.precision != "fp64e" and max(w.nao) <= 64 and max(w.nocc) <= 5):
+        cE = make_ctx("fp64e", True)
+        ctxs.append(cE)
     with torch.cuda.stream(stream):
         st = Streamed(ctxs, w.pairs, w.nao, budget)
         nw = len(st)
@@ -729,7 +734,7 @@ def streamed_arm(args, ws, rank, local):
         stream.synchronize()
         for c in ctxs[1:]:
             c.stats()
-        ev, ev64, done, done64 = [], [], set(), set()
+        ev, ev64, done, done64, evE, doneE = [], [], set(), set(), [], set()
         t_gen, timed_dimers, timed_bytes, timed_flops, timed_half, filled = 0.0, 0, 0.0, 0.0, 0.0, 0
         wave_flops = [_alg_flops(w, *st.waves[k]) for k in range(nw)]
         with Clocks(local) as clk:
@@ -759,14 +764,22 @@ def streamed_arm(args, ws, rank, local):
                     f1.record(stream)
                     ev64.append((f0, f1, st.waves[k][1]))
                     done64.add(k)
+                if cE is not None and k not in doneE:
+                    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    f0.record(stream)
+                    cE.run(*st.waves[k])
+                    f1.record(stream)
+                    evE.append((f0, f1, st.waves[k][1], k))
+                    doneE.add(k)
             stream.synchronize()
         clocks = clk.summary()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         stt = ctx_t.stats()
         s64 = c64.stats() if c64 is not None else None
+        sE = cE.stats() if cE is not None else None
         # the waves the steps did not reach, untimed, so that the lattice is complete
         for k in range(nw):
-            if k in done and (c64 is None or k in done64):
+            if k in done and (c64 is None or k in done64) and (cE is None or k in doneE):
                 continue
             if filled != k:
                 synth.device.fill_views(w, st.views(k))
@@ -776,6 +789,8 @@ def streamed_arm(args, ws, rank, local):
                 ctx_t.run(*st.waves[k])
             if c64 is not None and k not in done64:
                 c64.run(*st.waves[k])
+            if cE is not None and k not in doneE:
+                cE.run(*st.waves[k])
         stream.synchronize()
 
     mj, mk, pd, tot = ctx.energies()
@@ -866,6 +881,29 @@ def streamed_arm(args, ws, rank, local):
                 fp64["error_eh_lattice_J"] = float(tot64[0] - g[1][0])
             fp64["max_dimer_rel_J"] = float(np.max(np.abs(pd64[:nd, 0] - g[0][:nd, 0]) / np.abs(g[0][:nd, 0])))
         line["fp64_form"] = fp64
+
+    # ---- the FP64-emulating tensor-core form on the same waves (each wave once)
+    if cE is not None:
+        _, _, pdE, totE = cE.energies()
+        msE = sum(a.elapsed_time(b) for a, b, _, _ in evE)
+        nE = sum(n for _, _, n, _ in evE)
+        bytesE = sum(_alg_bytes(w, *st.waves[k]) for _, _, _, k in evE)
+        fE = {"value": nE / (msE * 1e-3), "unit": UNIT, "ms_per_step": msE / len(evE), "waves": len(evE),
+              "first_half_ms_per_step": sE.ms[0] / len(evE), "finish_ms_per_step": sE.ms[1] / len(evE),
+              "roofline": {"bound": "hbm", "achieved": bytesE / (sE.ms[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "kernel": "k_half_tc_rank (FP64E)", "peak_kind": peak_kind},
+              "what": "FP64-accurate form on the tensor cores: 48-bit fixed-point byte digits, exact tcgen05 "
+                      "BF16 sums, FP32-pair epilogue and second half, FP64 sums"}
+        fE["roofline"]["frac"] = fE["roofline"]["achieved"] / peaks["hbm_gbs"]
+        if c64 is not None:
+            fE["speedup_vs_fp64_form"] = fE["value"] / line["fp64_form"]["value"]
+        if g is not None:
+            nd = min(len(g[0]), w.n_dimers)
+            if not subset and nd == w.n_dimers and g[1][0] is not None:
+                fE["error_eh_lattice_J"] = float(totE[0] - g[1][0])
+                fE["error_eh_lattice_K"] = float(totE[1] - g[1][1])
+            fE["max_dimer_rel_J"] = float(np.max(np.abs(pdE[:nd, 0] - g[0][:nd, 0]) / np.abs(g[0][:nd, 0])))
+        line["fp64e_form"] = fE
 
     # ---- the oracle on the host cores: evenly spaced dimers of the wave in the
     # buffer, four-index blocks copied from the device, about 10 s of CPU work

@@ -1273,7 +1273,10 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
         const FinTask* tasks =
             wv.ntasks ? reinterpret_cast<const FinTask*>(static_cast<const char*>(P.dFin) + wv.fin_off) : nullptr;
         double* part = wv.ntasks ? P.dPart + 2 * wv.part_off : nullptr;
-        if (fp64_data(prec))
+        if (prec == MCPT_FP64E && wv.max_ao <= 32)   // H as FP32 pairs (the tensor-core launch's h_pairs)
+            CK(h, launch_finish_ff(wd, wv.nd, wv.max_ao, h->dC, h->dE, h->dH, h->dE2,
+                                   P.coupling ? static_cast<double*>(h->dVT) : nullptr, h->stream));
+        else if (fp64_data(prec))
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
                                      tasks, wv.ntasks, part, P.coupling ? static_cast<double*>(h->dVT) : nullptr,
                                      h->stream));

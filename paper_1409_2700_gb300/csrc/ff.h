@@ -11,7 +11,7 @@ namespace mcpt {
 // use them; every rounding is named (explicit _rn operations, so that the
 // compiler contracts none of them into an FMA, which would break the
 // error-free steps).
-struct FF {
+struct __align__(8) FF {
     float h, l;
 };
 
@@ -86,6 +86,35 @@ __device__ __forceinline__ void ff_mac(FF& s, FF a, FF b)
     e = __fadd_rn(e, __fadd_rn(s.l, pl));
     s.h = __fadd_rn(t, e);
     s.l = __fsub_rn(e, __fsub_rn(s.h, t));
+}
+
+// a b for pairs, renormalised (TwoProduct of the high parts, cross terms in
+// the low part; a.l b.l dropped).
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    const float ph = __fmul_rn(a.h, b.h);
+    const float pl = fmaf(a.l, b.h, fmaf(a.h, b.l, fmaf(a.h, b.h, -ph)));
+    const float h = __fadd_rn(ph, pl);
+    return FF{h, __fsub_rn(pl, __fsub_rn(h, ph))};
+}
+
+// s renormalised: |l| <= ulp(h) / 2, the same value to FP32 rounding of l.
+__device__ __forceinline__ FF ff_norm(FF s)
+{
+    const float h = __fadd_rn(s.h, s.l);
+    return FF{h, __fsub_rn(s.l, __fsub_rn(h, s.h))};
+}
+
+// ff_mac without the renormalisation: s.l gathers the TwoSum errors and the
+// products' low parts; renormalise (ff_norm) every few terms -- after k terms
+// |s.l| is below k ulp(s.h), so its own roundings stay below k^2 2^-49 |s|.
+__device__ __forceinline__ void ff_mac_nr(FF& s, FF a, FF b)
+{
+    const float ph = __fmul_rn(a.h, b.h);
+    const float pl = fmaf(a.l, b.h, fmaf(a.h, b.l, fmaf(a.h, b.h, -ph)));
+    float e;
+    s.h = two_sum(s.h, ph, e);
+    s.l = __fadd_rn(s.l, __fadd_rn(e, pl));
 }
 
 // a + b for pairs: TwoSum of the high parts, the low parts added, renormalised.

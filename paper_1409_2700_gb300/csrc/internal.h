@@ -96,6 +96,12 @@ cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
                                double* E2, const FinTask* tasks, int ntasks, double* part, float* VT,
                                bool fp64_epilogue, cudaStream_t s);
 
+// FP64E second half (monomers of at most 32 AO): H as FP32 pairs (written so
+// by the FP64E first half), every step on FP32 pairs, FP64 sums; VT (may be
+// null) gets FP64 (ia|jb) and T = vD as launch_finish_fp64 stores them.
+cudaError_t launch_finish_ff(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool, const double* Epool,
+                             const void* H, double* E2, double* VT, cudaStream_t s);
+
 // Dimer -> monomer doubles coupling of Eq. (tm2) at first order.
 struct CoupDim {
     int X, Y;             // monomer ids
@@ -281,6 +287,7 @@ struct TcLaunch {
     const float* Cf;            // FP32 coefficient pool
     const double* Cd;           // FP64 coefficient pool (TC_FP64E)
     void* H;                    // first-half result: float, or double for TC_FP64E
+    int h_pairs;                // TC_FP64E: H as FP32 pairs (waves of monomers of <= 32 AO)
     int* status;
     int sf;                     // FP64 staging stages
     unsigned f_stage_bytes, w_stage_bytes, tmem_cols;

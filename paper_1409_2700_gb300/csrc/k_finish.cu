@@ -291,6 +291,167 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 }
 
 // ---------------------------------------------------------------------------
+// FP64E second half, monomers of at most 32 AO: the structure of
+// k_finish_w32 with every value an FP32 pair (ff.h) -- the H slices written
+// as pairs by the first half, C, the virtual quarter transformations as pair
+// multiply-adds, and the energy terms with v^2 and v vk as pair products and
+// D = 1/x on pairs -- so that the FP64 form's accuracy (~2^-45 per step) is
+// kept off the FP64 pipe, whose rate a multiply-add per (row, pair) term
+// would otherwise set.  The C columns stay in shared memory (a lane's column
+// as pairs would take 64 registers); four outputs accumulate at once so that
+// each lane runs independent chains.  Per-lane sums over b go into FP64 sums
+// once per occupied pair; with STORE the dimer's (ia|jb) and T = vD are
+// written as FP64 for the coupling.
+constexpr int kFFSlab = 32 * 33;   // one padded 32 x 32 tile of pairs (row stride 33)
+
+size_t w32_ff_smem_bytes() { return (32 + 2 * (size_t)kFFSlab + 2 * (size_t)kW32Warps * kFFSlab) * sizeof(FF); }
+
+template <bool STORE>
+__global__ void __launch_bounds__(kW32Warps * 32, 2)
+k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, const double* __restrict__ Epool,
+                const FF* __restrict__ H, double* __restrict__ E2, double* __restrict__ VT)
+{
+    const DimerDesc& d = dd[blockIdx.x];
+    const int nX = d.nX, nY = d.nY, oX = d.oX, oY = d.oY;
+    const int vX = d.vX, vY = d.vY;
+    const int rows = nX * nY, pairs = oX * oY;
+    const double* CXv = C + d.cXv;            // virtual columns
+    const double* CYv = C + d.cYv;
+    const double* eX = Epool + d.eX;          // occupied energies of this block
+    const double* eY = Epool + d.eY;
+    const FF* H0 = H + d.h_off;
+    const FF* H1 = H + d.h_off + (long long)pairs * rows;
+
+    extern __shared__ __align__(16) unsigned char smraw[];
+    FF* eYs = reinterpret_cast<FF*>(smraw);   // [b]: e_b
+    FF* CXT = eYs + 32;                       // [a][nu], row stride 33, zero padded
+    FF* CYT = CXT + kFFSlab;                  // [b][sig]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FF* const buf = CYT + kFFSlab + warp * (2 * kFFSlab);   // two slice buffers
+
+    if (warp < pairs) {
+        prefetch_slice(buf, H0 + (long long)warp * rows, nX, nY, lane);
+        prefetch_slice(buf + kFFSlab, H1 + (long long)warp * rows, nY, nX, lane);
+    }
+    for (int k = threadIdx.x; k < 32 * 32; k += kW32Warps * 32) {
+        const int a = k >> 5, m = k & 31;
+        CXT[a * 33 + m] = (a < vX && m < nX) ? ff_split(CXv[m * nX + a]) : FF{0.f, 0.f};
+        CYT[a * 33 + m] = (a < vY && m < nY) ? ff_split(CYv[m * nY + a]) : FF{0.f, 0.f};
+    }
+    if (threadIdx.x < 32) eYs[threadIdx.x] = threadIdx.x < vY ? ff_split(Epool[d.eYv + threadIdx.x]) : FF{0.f, 0.f};
+    __syncthreads();
+
+    const bool live = lane < vX;
+    const double ea = live ? Epool[d.eXv + lane] : 0.0;   // this lane's virtual orbital a
+    const bool store = STORE && d.vt_off >= 0;
+    const long long mXc = (long long)d.oXt * vX, mYc = (long long)d.oYt * vY;
+    double* const Vst = store ? VT + d.vt_off : nullptr;
+    double ej = 0.0, ek = 0.0;
+    int x = 0;                                   // buffer holding this pair's H0
+    for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
+        const int i = pr / oY, j = pr % oY;
+        const FF eija = ff_split((eX[i] + eY[j]) - ea);   // e_i + e_j - e_a of this lane
+        FF sj{0.f, 0.f}, sk{0.f, 0.f};
+        const int nx = pr + kW32Warps;
+        FF* SX = x ? buf + kFFSlab : buf;        // H0 (row stride 32), then VA [a][b] (stride 33)
+        FF* SY = x ? buf : buf + kFFSlab;        // H1, then the next pair's H0
+        // ---- (i a|j b): lane b, tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]
+        slice_wait<1>();
+        {
+            FF tm[32];
+            const FF* cy = CYT + lane * 33;
+#pragma unroll
+            for (int nu = 0; nu < 32; nu += 4) {
+                FF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+#pragma unroll 4
+                for (int m = 0; m < 32; m++) {
+                    const FF c = cy[m];
+                    ff_mac(a0, SX[(nu + 0) * 32 + m], c);
+                    ff_mac(a1, SX[(nu + 1) * 32 + m], c);
+                    ff_mac(a2, SX[(nu + 2) * 32 + m], c);
+                    ff_mac(a3, SX[(nu + 3) * 32 + m], c);
+                }
+                tm[nu] = a0; tm[nu + 1] = a1; tm[nu + 2] = a2; tm[nu + 3] = a3;
+            }
+            __syncwarp();                        // H0 consumed: VA takes its place
+#pragma unroll 1
+            for (int a = 0; a < 32; a += 4) {
+                FF b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
+#pragma unroll
+                for (int nu = 0; nu < 32; nu++) {
+                    ff_mac(b0, CXT[(a + 0) * 33 + nu], tm[nu]);
+                    ff_mac(b1, CXT[(a + 1) * 33 + nu], tm[nu]);
+                    ff_mac(b2, CXT[(a + 2) * 33 + nu], tm[nu]);
+                    ff_mac(b3, CXT[(a + 3) * 33 + nu], tm[nu]);
+                }
+                SX[(a + 0) * 33 + lane] = b0;
+                SX[(a + 1) * 33 + lane] = b1;
+                SX[(a + 2) * 33 + lane] = b2;
+                SX[(a + 3) * 33 + lane] = b3;
+            }
+        }
+        // ---- (i b|j a): lane a, tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
+        slice_wait<0>();
+        {
+            FF tk[32];
+            const FF* cx = CXT + lane * 33;
+#pragma unroll
+            for (int lam = 0; lam < 32; lam += 4) {
+                FF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+#pragma unroll 4
+                for (int m = 0; m < 32; m++) {
+                    const FF c = cx[m];
+                    ff_mac(a0, SY[(lam + 0) * 32 + m], c);
+                    ff_mac(a1, SY[(lam + 1) * 32 + m], c);
+                    ff_mac(a2, SY[(lam + 2) * 32 + m], c);
+                    ff_mac(a3, SY[(lam + 3) * 32 + m], c);
+                }
+                tk[lam] = a0; tk[lam + 1] = a1; tk[lam + 2] = a2; tk[lam + 3] = a3;
+            }
+            __syncwarp();                        // H1 consumed: the next pair's H0 streams into SY
+            if (nx < pairs) prefetch_slice(SY, H0 + (long long)nx * rows, nX, nY, lane);
+            // ---- denominators and energy sums, lane a over b
+#pragma unroll 1
+            for (int b = 0; b < vY; b++) {
+                FF v0{0.f, 0.f}, v1{0.f, 0.f};   // two chains of 16
+#pragma unroll
+                for (int lam = 0; lam < 32; lam += 2) {
+                    ff_mac(v0, CYT[b * 33 + lam], tk[lam]);
+                    ff_mac(v1, CYT[b * 33 + lam + 1], tk[lam + 1]);
+                }
+                if (live) {
+                    const FF v = SX[lane * 33 + b];
+                    const FF vk = ff_add(v0, v1);
+                    const FF D = ff_rcp(ff_sub(eija, eYs[b]));
+                    ff_mac(sj, ff_mul(v, v), D);
+                    ff_mac(sk, ff_mul(v, vk), D);
+                    if (store) {
+                        const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
+                        Vst[e] = ff_f64(v);
+                        Vst[mXc * mYc + e] = ff_f64(ff_mul(v, D));
+                    }
+                }
+            }
+        }
+        ej += ff_f64(sj);
+        ek += ff_f64(sk);
+        __syncwarp();                            // VA consumed: the next pair's H1 streams into SX
+        if (nx < pairs) prefetch_slice(SX, H1 + (long long)nx * rows, nY, nX, lane);
+    }
+    __shared__ double red[2][kW32Warps];
+    ej = warp_sum(ej);
+    ek = warp_sum(ek);
+    if (lane == 0) { red[0][warp] = ej; red[1][warp] = ek; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sjt = 0.0, skt = 0.0;
+        for (int w = 0; w < kW32Warps; w++) { sjt += red[0][w]; skt += red[1][w]; }
+        E2[2 * d.slot + 0] = 4.0 * sjt;
+        E2[2 * d.slot + 1] = -2.0 * skt;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Monomers above 32 AO: the virtual quarter transformations of one occupied
 // pair are four small GEMMs,
 //   Tm  [nu][b]  = sum_sig H0[nu][sig]  C_Y[sig][oY+b]      (nX x vY, K = nY)
@@ -555,6 +716,18 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     return cudaGetLastError();
 }
 
+cudaError_t launch_finish_ff_t(const DimerDesc* d_desc, int nd, const double* C, const double* Epool, const FF* H,
+                               double* E2, double* VT, cudaStream_t s)
+{
+    if (nd <= 0) return cudaSuccess;
+    const size_t smem = w32_ff_smem_bytes();
+    auto fn = VT ? k_finish_w32_ff<true> : k_finish_w32_ff<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
+    return cudaGetLastError();
+}
+
 // Split dimers: the blocks' terms added in block order.
 __global__ void k_fold(const int* __restrict__ fold, int nfold, double* __restrict__ E2)
 {
@@ -701,6 +874,13 @@ cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, cons
     return fp64_epilogue
                ? launch_finish<float, false>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s)
                : launch_finish<float, true>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s);
+}
+
+cudaError_t launch_finish_ff(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool, const double* Epool,
+                             const void* H, double* E2, double* VT, cudaStream_t s)
+{
+    if (max_ao > 32) return cudaErrorInvalidValue;
+    return launch_finish_ff_t(d_desc, nd, Cpool, Epool, static_cast<const FF*>(H), E2, VT, s);
 }
 
 void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinTask>* out)

@@ -78,7 +78,8 @@ struct TcParams {
     const DimerDesc* desc;
     const float* Cf;
     const double* Cd;              // FP64 coefficients (TC_FP64E)
-    void* H;                       // float, or double for TC_FP64E
+    void* H;                       // float, or double for TC_FP64E (FP32 pairs with h_pairs)
+    int h_pairs;                   // TC_FP64E: H written as FP32 pairs (the pair second half reads them)
     int* status;
     int sf;                        // FP64 staging stages
     unsigned int f_stage_bytes;    // bytes per staging slot
@@ -207,6 +208,16 @@ __device__ __forceinline__ void tmem_ld_l1x16(unsigned taddr, unsigned (&r)[16])
         "tcgen05.wait::ld.sync.aligned;\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr + 0u)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_l2x8(unsigned taddr, unsigned (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr + 0u), "r"(taddr + 16u)
         : "memory");
 }
 __device__ __forceinline__ void tmem_ld_l3x8(unsigned taddr, unsigned (&r)[24])
@@ -757,11 +768,19 @@ constexpr int kConvWarps = 8;     // converter warps per group: one unit (128 ro
 // converters are latency bound) within the register budget that 22 warps
 // leave; the others keep one group and the larger per-thread budget.
 // FP64E keeps one group: its epilogue's FP32-pair accumulators need the
-// larger per-thread budget.
+// larger per-thread budget.  Its epilogue, latency bound on dependent pair
+// arithmetic, runs as eight warps: two per TMEM lane quarter, each with part
+// of the occupied columns j.
 template <bool BIG, int OB, int KIND = TC_TF32>
 __host__ __device__ constexpr int conv_groups() { return (!BIG && OB == 5 && KIND != TC_FP64E) ? 2 : 1; }
+template <int KIND>
+__host__ __device__ constexpr int epi_warps() { return KIND == TC_FP64E ? 8 : 4; }
 template <bool BIG, int OB, int KIND = TC_TF32>
-__host__ __device__ constexpr int rank_threads() { return (2 + kConvWarps * conv_groups<BIG, OB, KIND>() + 4) * 32; }
+__host__ __device__ constexpr int rank_threads()
+{
+    return (2 + kConvWarps * conv_groups<BIG, OB, KIND>() + epi_warps<KIND>()) * 32;
+}
+constexpr int kFFCols = 3;        // FP64E: occupied columns j per epilogue warp (two warps cover o_Y <= 5)
 constexpr int kOBig = 16;         // TMEM accumulators: o_X, o_Y <= 16
 // C_X occupied rows of one item (n0 <= 128), per parity: the register
 // accumulator kernel stages kOB columns (FP64E: each as an FP32 pair), the
@@ -1169,16 +1188,16 @@ __device__ __forceinline__ void digits6_pair(uint2 a, uint2 b, int emax, unsigne
 __device__ __forceinline__ int convert_row_fx6(const double* __restrict__ F, unsigned char* __restrict__ A,
                                                const ConvRow& cr, int n3, int c0)
 {
+    // two passes over the thread's 16 elements (shared memory, cheap to read
+    // again): the high words for the row maximum, then each chunk of 8
+    // converted from both words -- half the live registers of one pass
     const uint2* __restrict__ dw = reinterpret_cast<const uint2*>(F + cr.src);
-    uint2 v[2][8];
+    const unsigned* __restrict__ hw = reinterpret_cast<const unsigned*>(F + cr.src) + 1;
     unsigned m = 0;
 #pragma unroll
     for (int q = 0; q < 2; q++)
 #pragma unroll
-        for (int e = 0; e < 8; e++) {
-            v[q][e] = dw[((c0 + 2 * q) * 8 + e) * n3];
-            m = max(m, v[q][e].y & 0x7FFFFFFFu);
-        }
+        for (int e = 0; e < 8; e++) m = max(m, hw[2 * ((c0 + 2 * q) * 8 + e) * n3] & 0x7FFFFFFFu);
     m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
     const int emax = cr.valid ? (int)(m >> 20) : 0;
 #pragma unroll
@@ -1188,7 +1207,7 @@ __device__ __forceinline__ int convert_row_fx6(const double* __restrict__ F, uns
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
             unsigned d[6];
-            digits6_pair(v[q][e], v[q][e + 1], emax, d);
+            digits6_pair(dw[(c * 8 + e) * n3], dw[(c * 8 + e + 1) * n3], emax, d);
 #pragma unroll
             for (int k = 0; k < 6; k++) w[k][e / 2] = d[k];
         }
@@ -1205,36 +1224,50 @@ __device__ __forceinline__ int convert_row_fx6(const double* __restrict__ F, uns
 }
 
 // FP64E: the seven digit levels of one unit for this lane's row, columns
-// j < NJ, combined into an FP32 pair: S = L6, then S = S 2^-8 + L_k for
-// k = 5 .. 0 (each L_k an exact integer below 2^24, the scaling exact, the
-// addition a TwoSum with renormalisation), times the unit's row scale (a
-// power of two).  The column scales are applied once per output.
-template <int NJ>
+// J0 .. J0 + NJ - 1, combined into FP32 pairs: S = L6, then S = S 2^-8 + L_k
+// for k = 5 .. 0 (each L_k an exact integer below 2^24, the scaling exact,
+// the addition a TwoSum), times the unit's row scale (a power of two).  The
+// column scales are applied once per output.
+template <int NJ, int J0 = 0>
 __device__ __forceinline__ void unit_T_ff(unsigned taddr, FF (&T)[8], float srow, bool add)
 {
-    unsigned raw[7][8];
-    tmem_ld_l7x8(taddr, *reinterpret_cast<unsigned(*)[56]>(&raw[0][0]));
+    // Horner from L6 down: S.l shrinks by 2^8 per step while each new TwoSum
+    // error is below ulp(S.h) / 2, so it stays within ulp(S.h) without
+    // renormalising (once, at the end).  Levels are loaded two at a time (16
+    // registers), L6 alone first.
+    FF S[NJ];
+    {
+        unsigned l6[8];
+        tmem_ld_l1x8(taddr + 96u, l6);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) S[j] = FF{__uint_as_float(l6[J0 + j]), 0.f};
+    }
+#pragma unroll
+    for (int l = 4; l >= 0; l -= 2) {        // levels l + 1, then l
+        unsigned lv[2][8];
+        tmem_ld_l2x8(taddr + (unsigned)(16 * l), *reinterpret_cast<unsigned(*)[16]>(&lv[0][0]));
+#pragma unroll
+        for (int k = 1; k >= 0; k--)
+#pragma unroll
+            for (int j = 0; j < NJ; j++) {
+                float e;
+                S[j].h = two_sum(__uint_as_float(lv[k][J0 + j]), __fmul_rn(S[j].h, 0x1p-8f), e);
+                S[j].l = fmaf(S[j].l, 0x1p-8f, e);
+            }
+    }
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        FF S{__uint_as_float(raw[6][j]), 0.f};
-#pragma unroll
-        for (int l = 5; l >= 0; l--) {
-            float e;
-            const float t = two_sum(__uint_as_float(raw[l][j]), __fmul_rn(S.h, 0x1p-8f), e);
-            e = __fadd_rn(e, __fmul_rn(S.l, 0x1p-8f));
-            S.h = __fadd_rn(t, e);
-            S.l = __fsub_rn(e, __fsub_rn(S.h, t));
-        }
-        S.h = __fmul_rn(S.h, srow);
-        S.l = __fmul_rn(S.l, srow);
-        T[j] = add ? ff_add(T[j], S) : S;
+        FF v = ff_norm(S[j]);
+        v.h = __fmul_rn(v.h, srow);
+        v.l = __fmul_rn(v.l, srow);
+        T[j] = add ? ff_add(T[j], v) : v;
     }
 }
 
 // FP64E: T of one p0 (the units of its p2 chunks added in chunk order, as
 // pairs), with the first unit's column scales copied to sc (if non-null).
 // Frees each unit's slot after reading it.  False on timeout/abort.
-template <int NS, int UC, int NJ>
+template <int NS, int UC, int NJ, int J0>
 __device__ __forceinline__ bool load_p0_T_ff(FF (&T)[8], RankShared* sh, unsigned& gS, int kcs, unsigned lanebase,
                                              const float* exps, const float* scu, int r, int lane, float* sc,
                                              volatile int* abort, int* status, unsigned long long lim)
@@ -1246,9 +1279,9 @@ __device__ __forceinline__ bool load_p0_T_ff(FF (&T)[8], RankShared* sh, unsigne
         tc_fence_after();
         if (sc && u == 0) {
 #pragma unroll
-            for (int j = 0; j < 8; j++) sc[j] = scu[s * kNT + j];
+            for (int j = 0; j < NJ; j++) sc[j] = scu[s * kNT + J0 + j];
         }
-        unit_T_ff<NJ>(lanebase + (unsigned)(s * UC), T, exps[s * 128 + r], u > 0);
+        unit_T_ff<NJ, J0>(lanebase + (unsigned)(s * UC), T, exps[s * 128 + r], u > 0);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sh->slot_empty[s]);
@@ -1290,6 +1323,7 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
     constexpr int NG = conv_groups<BIG, OB, KIND>();   // converter groups
     constexpr int CT = kConvWarps * NG;             // converter warps
     constexpr int EW0 = 2 + CT;                     // first epilogue warp
+    constexpr int EPW = epi_warps<KIND>();          // epilogue warps
     constexpr bool FX = KIND != TC_TF32;            // fixed-point digit planes (BF16x3, BF16x2)
     constexpr int UC = unit_cols<KIND, BIG>();      // TMEM columns per p0 unit
     constexpr int NS = n_units<KIND, BIG>();        // p0 units in the ring
@@ -1316,9 +1350,9 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
         for (int s = 0; s < 2; s++) {
             mbar_init(&sh->full_a[s], kConvWarps); mbar_init(&sh->empty_a[s], 1);
             mbar_init(&sh->full_w[s], CT); mbar_init(&sh->empty_w[s], 1);
-            mbar_init(&sh->cx_full[s], 128); mbar_init(&sh->cx_empty[s], 128);
+            mbar_init(&sh->cx_full[s], 32 * EPW); mbar_init(&sh->cx_empty[s], 32 * EPW);
         }
-        for (int s = 0; s < kSlots; s++) { mbar_init(&sh->slot_full[s], 1); mbar_init(&sh->slot_empty[s], 4); }
+        for (int s = 0; s < kSlots; s++) { mbar_init(&sh->slot_full[s], 1); mbar_init(&sh->slot_empty[s], EPW); }
         for (int s = 0; s < kFxUnits; s++) mbar_init(&sh->exp_full[s], kConvWarps);
         for (int s = 0; s < 2; s++) mbar_init(&sh->colx_full[s], kConvWarps);
         mbar_init(&sh->drain, 1);
@@ -1672,7 +1706,7 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
         // ------------------------------------------------ epilogue
         const int q = warp & 3;
         const int r = q * 32 + lane;                    // accumulator row = TMEM lane
-        const int e = (warp - EW0) * 32 + lane;   // 0..127: C_X row this thread stages
+        const int e = (warp - EW0) * 32 + lane;   // C_X row this thread stages (rows past n0: none)
         unsigned gS = 0, li = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < P.n_items && ok && !*abort; it += gridDim.x, li++) {
@@ -1704,44 +1738,58 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
             for (int mt = 0; mt < item.mts && ok; mt++) {
                 const int p1_lo = (item.mt0 + mt) * g.p1t;
                 if constexpr (KIND == TC_FP64E) {
-                    // H[(p1,p3)][(i,j)] = sum_p0 C_X[p0][i] T_p0[(p1,p3)][j] on FP32 pairs, written as FP64
-                    FF acc[OB][OB];
+                    // H[(p1,p3)][(i,j)] = sum_p0 C_X[p0][i] T_p0[(p1,p3)][j] on FP32 pairs, for this
+                    // warp's columns j = j0 .. j0 + 2 (the two warps of a lane quarter split o_Y <= 5)
+                    const int half = (warp - EW0) >> 2;
+                    const int j0 = half * kFFCols;
+                    FF acc[OB][kFFCols];
 #pragma unroll
                     for (int i = 0; i < OB; i++)
 #pragma unroll
-                        for (int j = 0; j < OB; j++) acc[i][j] = FF{0.f, 0.f};
-                    float sc[8];   // the item's column scales 2^(f - 7), applied once per output
+                        for (int j = 0; j < kFFCols; j++) acc[i][j] = FF{0.f, 0.f};
+                    float sc[kFFCols];   // the item's column scales 2^(f - 7), applied once per output
 #pragma unroll
-                    for (int j = 0; j < 8; j++) sc[j] = 1.f;
+                    for (int j = 0; j < kFFCols; j++) sc[j] = 1.f;
                     const FF* cx2 = reinterpret_cast<const FF*>(cx);
                     for (int p0 = 0; p0 < g.n0; p0++) {
                         FF T[8];
-                        if (!(ok = load_p0_T_ff<NS, UC, OB>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
-                                                             p0 == 0 ? sc : nullptr, abort, P.status, P.wait_ns)))
-                            break;
+                        ok = half ? load_p0_T_ff<NS, UC, kFFCols, kFFCols>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
+                                                                       p0 == 0 ? sc : nullptr, abort, P.status,
+                                                                       P.wait_ns)
+                                  : load_p0_T_ff<NS, UC, kFFCols, 0>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
+                                                                     p0 == 0 ? sc : nullptr, abort, P.status, P.wait_ns);
+                        if (!ok) break;
 #pragma unroll
                         for (int i = 0; i < OB; i++) {
                             const FF c = cx2[p0 * kOB + i];
 #pragma unroll
-                            for (int j = 0; j < OB; j++) ff_mac(acc[i][j], c, T[j]);
+                            for (int j = 0; j < kFFCols; j++) ff_mac_nr(acc[i][j], c, T[j]);
+                        }
+                        if ((p0 & 7) == 7) {   // the low parts gather at most eight products' errors
+#pragma unroll
+                            for (int i = 0; i < OB; i++)
+#pragma unroll
+                                for (int j = 0; j < kFFCols; j++) acc[i][j] = ff_norm(acc[i][j]);
                         }
                     }
                     if (!ok) break;
                     const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
                     if (r < valid) {
-                        double* q = Hd + p1_lo * g.n3 + r;   // pair (i, j) at q + (i*o2 + j) * rows
-                        const size_t step = (size_t)g.rows;
+                        // pair (i, j) of this row at element (i*o2 + j) * rows; the column
+                        // scale is a power of two, so scaling a pair keeps it exact
+                        const size_t row0 = (size_t)(p1_lo * g.n3 + r);
 #pragma unroll
-                        for (int i = 0; i < OB; i++) {
-                            if (i < g.o0) {
+                        for (int i = 0; i < OB; i++)
 #pragma unroll
-                                for (int j = 0; j < OB; j++)
-                                    if (j < g.o2) {
-                                        *q = ff_f64(FF{__fmul_rn(acc[i][j].h, sc[j]), __fmul_rn(acc[i][j].l, sc[j])});
-                                        q += step;
-                                    }
+                            for (int jj = 0; jj < kFFCols; jj++) {
+                                const int j = j0 + jj;
+                                if (i < g.o0 && j < g.o2) {
+                                    const size_t q = row0 + (size_t)(i * g.o2 + j) * g.rows;
+                                    const FF v = ff_norm(FF{__fmul_rn(acc[i][jj].h, sc[jj]), __fmul_rn(acc[i][jj].l, sc[jj])});
+                                    if (P.h_pairs) reinterpret_cast<FF*>(Hd)[q] = v;
+                                    else Hd[q] = ff_f64(v);
+                                }
                             }
-                        }
                     }
                 } else if constexpr (!BIG) {
                     float acc[OB][OB];
@@ -2060,6 +2108,12 @@ cudaError_t tc_prepare(TcKind kind, const DimerDesc* h_desc, const DimerDesc* d_
     P.Cf = Cf;
     P.Cd = Cd;
     P.H = H;
+    P.h_pairs = 0;
+    if (kind == TC_FP64E) {
+        int ao = 0;
+        for (int k = 0; k < nd; k++) ao = std::max(ao, std::max(h_desc[k].nX, h_desc[k].nY));
+        P.h_pairs = ao <= 32;
+    }
     P.status = d_status;
     P.kind = kind;
     P.f_stage_bytes = (max_box + 1023) & ~1023u;
@@ -2094,6 +2148,7 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     P.Cf = L.Cf;
     P.Cd = L.Cd;
     P.H = L.H;
+    P.h_pairs = L.h_pairs;
     P.status = L.status;
     P.sf = L.sf;
     P.f_stage_bytes = L.f_stage_bytes;

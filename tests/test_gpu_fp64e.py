@@ -138,3 +138,24 @@ def test_fp64e_rejects_sizes_beyond_its_kernel():
                 ctx.run()
             assert ei.value.status == M.MCPT_EUNSUPPORTED
             assert "64 AO" in str(ei.value)
+
+
+def test_fp64e_coupling_matches_fp64_form(lat8):
+    """With the coupling on, the pair second half also stores (ia|jb) and
+    T = vD in FP64: every monomer's R_X of Eq. (tm2) against the FP64
+    form's, and the energies unchanged by the store."""
+    w, mons, blocks, E = lat8
+    R, pd = {}, {}
+    for prec in ("fp64e", "fp64"):
+        with M.Context(precision=prec, coupling=True) as ctx:
+            load_context(ctx, w, mons, blocks, range(w.n_dimers))
+            ctx.run()
+            pd[prec] = ctx.energies()[2].copy()
+            R[prec] = [ctx.coupling(X, w.nao[X], w.nocc[X]) for X in range(w.n_monomers)]
+    rel = np.abs(pd["fp64e"] - pd["fp64"]).max(axis=1) / np.abs(pd["fp64"][:, 0])
+    assert np.all(rel <= PER_DIMER_LATTICE)
+    worst = 0.0
+    for a, b in zip(R["fp64e"], R["fp64"]):
+        worst = max(worst, np.abs(a - b).max() / np.abs(b).max())
+    print(f"fp64e coupling vs the FP64 form: max rel diff {worst:.2e}")
+    assert worst <= 1e-12
