@@ -143,6 +143,24 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def gpu_local_cpus(device):
+    """The host CPUs the kernel lists as local to this GPU (sysfs), or None."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(device)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -905,37 +923,22 @@ def streamed_arm(args, ws, rank, local):
             fE["max_dimer_rel_J"] = float(np.max(np.abs(pdE[:nd, 0] - g[0][:nd, 0]) / np.abs(g[0][:nd, 0])))
         line["fp64e_form"] = fE
 
-    # ---- the oracle on the host cores: evenly spaced dimers of the wave in the
-    # buffer, four-index blocks copied from the device, about 10 s of CPU work
+    # ---- the oracle on the host cores, part 1: evenly spaced dimers of the
+    # wave in the buffer, their four-index blocks copied to the host (the
+    # oracle runs after the end-to-end leg, so that its threads and buffers
+    # do not sit between that leg and the device)
+    cpu_items = None
     if rank == 0 and "cpu" in extras:
-        import oracle
-        oracle.build()
         first, count = st.waves[filled]
         ds = [first + k for k in range(0, count, max(1, count // max(1, args.cpu_sample)))][:args.cpu_sample]
-        Eo_s, done_s, tc = [], [], 0.0
-        for c0 in range(0, len(ds), 64):
-            items = []
-            for d in ds[c0:c0 + 64]:
-                X, Y = w.pairs[d]
-                nX, nY = w.nao[X], w.nao[Y]
-                blk = st.buf[st.offs[d]:st.offs[d] + 2 * nX * nX * nY * nY].cpu().numpy()
-                items.append((blk[:nX * nX * nY * nY].reshape(nX, nX, nY, nY),
-                              blk[nX * nX * nY * nY:].reshape(nX, nY, nY, nX),
-                              mons[X].C, mons[X].eps, mons[Y].C, mons[Y].eps, mons[X].nocc, mons[Y].nocc))
-            t0 = time.perf_counter()
-            Eo_s.append(oracle.dimers_parallel(items))
-            tc += time.perf_counter() - t0
-            done_s += ds[c0:c0 + len(items)]
-            if tc > 12.0:
-                break
-        Eo_s = np.concatenate(Eo_s)
-        line["cpu_baseline"] = {"value": len(done_s) / tc, "unit": UNIT, "cores": oracle.max_threads(),
-                                "kind": "oracle",
-                                "sample": f"{len(done_s)} evenly spaced dimers of one wave of {args.workload} "
-                                          f"(four-index FP64 oracle from the device blocks, {tc:.1f} s wall)"}
-        line["sample_error_eh"] = {"max_dimer_J": float(np.max(np.abs(pd[done_s, 0] - Eo_s[:, 0]))),
-                                   "max_dimer_K": float(np.max(np.abs(pd[done_s, 1] - Eo_s[:, 1]))),
-                                   "dimers": len(done_s), "reference": "four-index FP64 oracle"}
+        cpu_items = []
+        for d in ds:
+            X, Y = w.pairs[d]
+            nX, nY = w.nao[X], w.nao[Y]
+            blk = st.buf[st.offs[d]:st.offs[d] + 2 * nX * nX * nY * nY].cpu().numpy()
+            cpu_items.append((d, (blk[:nX * nX * nY * nY].reshape(nX, nX, nY, nY),
+                                  blk[nX * nX * nY * nY:].reshape(nX, nY, nY, nX),
+                                  mons[X].C, mons[X].eps, mons[Y].C, mons[Y].eps, mons[X].nocc, mons[Y].nocc)))
 
     # ---- end to end through the C ABI from pinned host buffers: a context
     # holding the dimers of the first waves, each step one wave: every dimer's
@@ -943,6 +946,10 @@ def streamed_arm(args, ws, rank, local):
     # (mcpt_update_dimer, asynchronous, expanded on the device), mcpt_run of
     # the wave, mcpt_energies read back
     if rank == 0 and "e2e" in extras:
+        affinity = os.sched_getaffinity(0)
+        local_cpus = gpu_local_cpus(local)
+        if local_cpus:
+            os.sched_setaffinity(0, local_cpus)     # pinned buffers on the GPU's own host node
         ne = max(1, min(args.e2e_steps, nw, 2))
         idx = {}
         hosts, poffs = [], []
@@ -1008,12 +1015,36 @@ def streamed_arm(args, ws, rank, local):
                        "terms_equal_streamed_run": same,
                        "per_step": "one wave: mcpt_update_dimers of its dimers from pinned host memory "
                                    "(MCPT_AO_PACKED: the unique elements, back to back, copied in 256 MB chunks and "
-                                   "expanded on the device, asynchronous), mcpt_run of the wave, mcpt_energies"}
+                                   "expanded on the device, asynchronous), mcpt_run of the wave, mcpt_energies",
+                       "host_threads": "the GPU's local CPUs" if local_cpus else "unrestricted"}
         del hosts
+        os.sched_setaffinity(0, affinity)
     else:
         for c in ctxs:
             c.close()
         del st
+    # ---- the oracle on the host cores, part 2: about 10 s of CPU work
+    if cpu_items:
+        import oracle
+        oracle.build()
+        Eo_s, done_s, tc = [], [], 0.0
+        for c0 in range(0, len(cpu_items), 64):
+            chunk = cpu_items[c0:c0 + 64]
+            t0 = time.perf_counter()
+            Eo_s.append(oracle.dimers_parallel([it for _, it in chunk]))
+            tc += time.perf_counter() - t0
+            done_s += [d for d, _ in chunk]
+            if tc > 12.0:
+                break
+        del cpu_items
+        Eo_s = np.concatenate(Eo_s)
+        line["cpu_baseline"] = {"value": len(done_s) / tc, "unit": UNIT, "cores": oracle.max_threads(),
+                                "kind": "oracle",
+                                "sample": f"{len(done_s)} evenly spaced dimers of one wave of {args.workload} "
+                                          f"(four-index FP64 oracle from the device blocks, {tc:.1f} s wall)"}
+        line["sample_error_eh"] = {"max_dimer_J": float(np.max(np.abs(pd[done_s, 0] - Eo_s[:, 0]))),
+                                   "max_dimer_K": float(np.max(np.abs(pd[done_s, 1] - Eo_s[:, 1]))),
+                                   "dimers": len(done_s), "reference": "four-index FP64 oracle"}
     if rank == 0:
         print(json.dumps(line))
 
