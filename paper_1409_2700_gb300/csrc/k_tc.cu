@@ -281,6 +281,16 @@ __device__ __forceinline__ void tmem_ld_l4x16(unsigned taddr, unsigned (&r)[64])
         : "r"(taddr + 0u), "r"(taddr + 16u), "r"(taddr + 32u), "r"(taddr + 48u)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld_l2x16(unsigned taddr, unsigned (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 0u), "r"(taddr + 16u)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld_acc64(unsigned taddr, unsigned (&r)[64])
 {
     asm volatile(
@@ -763,16 +773,18 @@ constexpr int kOB5 = 5;           // the same sized for o_X, o_Y <= 5 (fewer ran
 constexpr int kFp64eMaxAO = 64;   // FP64E: p2 chunks <= 2, so that its three-tile A ring fits
 constexpr int kKCMax = 4;         // p2 chunks: n2 <= 128
 constexpr int kConvWarps = 8;     // converter warps per group: one unit (128 rows) per group
-// Groups of converter warps take alternate units.  The variant with
-// occupations <= 5 runs two (four converter warps per SM sub-partition: the
-// converters are latency bound) within the register budget that 22 warps
-// leave; the others keep one group and the larger per-thread budget.
-// FP64E keeps one group: its epilogue's FP32-pair accumulators need the
-// larger per-thread budget.  Its epilogue, latency bound on dependent pair
-// arithmetic, runs as eight warps: two per TMEM lane quarter, each with part
-// of the occupied columns j.
+// Groups of converter warps take alternate units.  The variants with
+// occupations <= 5 and with TMEM accumulators run two (four converter warps
+// per SM sub-partition: the converters are latency bound) within the register
+// budget that 22 warps leave; the 8 x 8 register variant keeps one group and
+// the larger per-thread budget.
+// The TMEM-accumulator variant runs two as well (its epilogue keeps T and a
+// two-row block of accumulators in registers).  FP64E keeps one group: its
+// epilogue's FP32-pair accumulators need the larger per-thread budget.  Its
+// epilogue, latency bound on dependent pair arithmetic, runs as eight warps:
+// two per TMEM lane quarter, each with part of the occupied columns j.
 template <bool BIG, int OB, int KIND = TC_TF32>
-__host__ __device__ constexpr int conv_groups() { return (!BIG && OB == 5 && KIND != TC_FP64E) ? 2 : 1; }
+__host__ __device__ constexpr int conv_groups() { return ((BIG || OB == 5) && KIND != TC_FP64E) ? 2 : 1; }
 template <int KIND>
 __host__ __device__ constexpr int epi_warps() { return KIND == TC_FP64E ? 8 : 4; }
 template <bool BIG, int OB, int KIND = TC_TF32>
@@ -1003,6 +1015,31 @@ template <int KIND, int NJ, bool COLS>
 __device__ __forceinline__ void unit_T(unsigned taddr, float (&T)[NJ], const float* srow, const float* scol, bool add)
 {
     constexpr int NL = n_levels<KIND>();
+    if constexpr (NJ == 16 && NL > 1) {
+        // TMEM-accumulator kernel: the levels one at a time (16 registers each),
+        // combined in the same order as below
+        float v[NJ];
+        {
+            unsigned raw[NJ];
+            tmem_ld_l1x16(taddr + 16u * (NL - 1), raw);
+#pragma unroll
+            for (int j = 0; j < NJ; j++) v[j] = __uint_as_float(raw[j]);
+        }
+#pragma unroll
+        for (int l = NL - 2; l >= 0; l--) {
+            unsigned raw[NJ];
+            tmem_ld_l1x16(taddr + 16u * l, raw);
+#pragma unroll
+            for (int j = 0; j < NJ; j++) v[j] = fmaf(v[j], 0x1p-8f, __uint_as_float(raw[j]));
+        }
+        const float sr = *srow;
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            const float f = COLS ? sr * scol[j] : sr;
+            T[j] = add ? fmaf(v[j], f, T[j]) : v[j] * f;
+        }
+        return;
+    }
     unsigned raw[NL][NJ];
     unsigned(&flat)[NL * NJ] = *reinterpret_cast<unsigned(*)[NL * NJ]>(&raw[0][0]);
     if constexpr (NL == 1 && NJ == 8) tmem_ld_l1x8(taddr, flat);
@@ -1832,7 +1869,7 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
                     }
                 } else {
                     const unsigned accbase = lanebase + 256u;
-                    const int nchunk = (g.o0 + 3) >> 2;
+                    const int nchunk = (g.o0 + 1) >> 1;   // two occupied i per TMEM round trip
                     for (int p0 = 0; p0 < g.n0; p0++) {
                         float T[16];
                         if (!(ok = load_p0_T<KIND, NS, UC, 16, true>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
@@ -1841,25 +1878,25 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
                         const float* cp = cx + p0 * kOBig;
 #pragma unroll 1
                         for (int ic = 0; ic < nchunk; ic++) {
-                            unsigned a[4][16];
+                            unsigned a[2][16];
                             if (p0 > 0) {
-                                tmem_ld_acc64(accbase + (unsigned)(ic * 64),
-                                              *reinterpret_cast<unsigned(*)[64]>(&a[0][0]));
+                                tmem_ld_l2x16(accbase + (unsigned)(ic * 32),
+                                              *reinterpret_cast<unsigned(*)[32]>(&a[0][0]));
                             } else {
 #pragma unroll
-                                for (int u = 0; u < 4; u++)
+                                for (int u = 0; u < 2; u++)
 #pragma unroll
                                     for (int j = 0; j < 16; j++) a[u][j] = 0u;
                             }
-                            const float4 c4 = *reinterpret_cast<const float4*>(cp + ic * 4);
-                            const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                            const float2 c2 = *reinterpret_cast<const float2*>(cp + ic * 2);
+                            const float cv[2] = {c2.x, c2.y};
 #pragma unroll
-                            for (int u = 0; u < 4; u++)
+                            for (int u = 0; u < 2; u++)
 #pragma unroll
                                 for (int j = 0; j < 16; j++)
                                     a[u][j] = __float_as_uint(fmaf(cv[u], T[j], __uint_as_float(a[u][j])));
 #pragma unroll
-                            for (int u = 0; u < 4; u++) tmem_st16(accbase + (unsigned)((ic * 4 + u) * 16), a[u]);
+                            for (int u = 0; u < 2; u++) tmem_st16(accbase + (unsigned)((ic * 2 + u) * 16), a[u]);
                         }
                         tmem_wait_st();   // this p0's updates land before the next one reads them
                     }
