@@ -187,7 +187,7 @@ def fp64_rate(device):
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch over 28 dimers
 # of 32 AO / 5 occupied, scaled per dimer).  Only valid for that kernel, form
 # and monomer size; the other forms' kernels changed since their captures.
-TRAFFIC_PER_DIMER = {("bf16x2", 32, 5): (469.901824e6 + 6.035712e6) / 28}
+TRAFFIC_PER_DIMER = {("bf16x2", 32, 5): (469.92e6 + 5.563136e6) / 28}
 
 
 def host_sample(w, dimers):

@@ -978,9 +978,9 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
             base.vt_off = vt_total;
             vt_total += 2LL * mX.nocc * (mX.nao - mX.nocc) * mY.nocc * (mY.nao - mY.nocc);
         }
-        // tensor-core work items hold at most kMaxOccTensor occupied orbitals per
-        // monomer: larger occupations run as near-equal blocks of (i, j)
-        const int bx = is_tensor_form(prec) ? (mX.nocc + kMaxOccTensor - 1) / kMaxOccTensor : 1;
+        // tensor-core work items hold at most kMaxOccTensorX occupied orbitals of X
+        // and kMaxOccTensor of Y: larger occupations run as near-equal blocks of (i, j)
+        const int bx = is_tensor_form(prec) ? (mX.nocc + kMaxOccTensorX - 1) / kMaxOccTensorX : 1;
         const int by = is_tensor_form(prec) ? (mY.nocc + kMaxOccTensor - 1) / kMaxOccTensor : 1;
         if (bx * by > 1) {
             fold.insert(fold.end(), {d, D + nblk_extra, bx * by});

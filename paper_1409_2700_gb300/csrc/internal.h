@@ -26,6 +26,8 @@ namespace mcpt {
 constexpr int kMaxAO = 256;          // any form (FP64 / FP32C)
 constexpr int kMaxAOTensor = 128;    // tensor-core forms
 constexpr int kMaxOccTensor = 16;    // occupied orbitals per monomer in one tensor-core work item
+constexpr int kMaxOccTensorX = 20;   // ... of the first monomer (X), with kMaxOccTensor of Y (the wide
+                                     //   TMEM-accumulator kernel)
 
 struct DimerDesc {
     const double* E[2];   // block base of form 0 (A) and form 1 (K)
@@ -293,7 +295,8 @@ struct TcLaunch {
     unsigned f_stage_bytes, w_stage_bytes, tmem_cols;
     int kind;
     int variant;                // 0: Kronecker (p0,p2) GEMM; 1, 3: p2 GEMM + FP32 rank-1 epilogue in registers
-                                // (occupations <= 8, <= 5); 2: the same with TMEM accumulators (<= 16)
+                                // (occupations <= 8, <= 5); 2: the same with TMEM accumulators (<= 16);
+                                // 4: TMEM accumulators for o_X <= 20, o_Y <= 16
     int kcs_max;                // p2 chunks of 32 (largest n_Y of the launch)
     int grid;
     size_t smem;
@@ -304,7 +307,7 @@ struct TcLaunch {
 // Launch choices of one tensor-core launch (0 in a field = the default):
 // kernel variant + 1 (1 Kronecker, 2 rank with register accumulators, 3 rank
 // with TMEM accumulators, 4 rank with register accumulators for occupations
-// <= 5), FP64 staging depth, CTAs.
+// <= 5, 5 rank with TMEM accumulators for o_X <= 20), FP64 staging depth, CTAs.
 struct TcTune {
     int variant1;
     int sf;

@@ -794,12 +794,14 @@ __host__ __device__ constexpr int rank_threads()
 }
 constexpr int kFFCols = 3;        // FP64E: occupied columns j per epilogue warp (two warps cover o_Y <= 5)
 constexpr int kOBig = 16;         // TMEM accumulators: o_X, o_Y <= 16
+constexpr int kOBigI = 20;        // wide TMEM accumulators (OB = kOBigI): o_X <= 20, o_Y <= 16, at
+                                  // columns 192-511 (three T units below instead of four)
 // C_X occupied rows of one item (n0 <= 128), per parity: the register
 // accumulator kernel stages kOB columns (FP64E: each as an FP32 pair), the
-// TMEM one kOBig.
-__host__ __device__ constexpr int cx_floats(bool big, int kind = TC_TF32)
+// TMEM one kOBig (24 for the wide form: o_X <= 20, float2-aligned rows).
+__host__ __device__ constexpr int cx_floats(bool big, int kind = TC_TF32, bool wide = false)
 {
-    return 128 * (big ? kOBig : kOB) * (kind == TC_FP64E ? 2 : 1);
+    return 128 * (big ? (wide ? 24 : kOBig) : kOB) * (kind == TC_FP64E ? 2 : 1);
 }
 
 struct __align__(8) RankShared {
@@ -818,8 +820,8 @@ struct __align__(8) RankShared {
 // TMEM columns of one p0 unit and units in the ring (FP64E: seven levels).
 template <int KIND, bool BIG>
 __host__ __device__ constexpr int unit_cols() { return KIND == TC_FP64E ? 7 * kNT : KIND != TC_TF32 ? 4 * kNT : kNT; }
-template <int KIND, bool BIG>
-__host__ __device__ constexpr int n_units() { return (BIG ? 256 : 512) / unit_cols<KIND, BIG>(); }
+template <int KIND, bool BIG, int OB = kOB>
+__host__ __device__ constexpr int n_units() { return (BIG ? (OB > kOBig ? 192 : 256) : 512) / unit_cols<KIND, BIG>(); }
 // Shared bytes of the A ring (two slots; BF16x3 uses two tiles per slot,
 // FP64E three) and of the fixed-point unit scales (row scales 128 + column
 // scales 16 per unit).
@@ -1363,8 +1365,9 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
     constexpr int EPW = epi_warps<KIND>();          // epilogue warps
     constexpr bool FX = KIND != TC_TF32;            // fixed-point digit planes (BF16x3, BF16x2)
     constexpr int UC = unit_cols<KIND, BIG>();      // TMEM columns per p0 unit
-    constexpr int NS = n_units<KIND, BIG>();        // p0 units in the ring
-    constexpr int CXW = BIG ? kOBig : kOB;          // staged C_X occupied columns per row
+    constexpr int NS = n_units<KIND, BIG, OB>();    // p0 units in the ring
+    constexpr bool WIDE = BIG && OB > kOBig;        // o_X <= 20: accumulators from column 192
+    constexpr int CXW = BIG ? (WIDE ? 24 : kOBig) : kOB;   // staged C_X occupied columns per row
     constexpr size_t ASLOT = a_ring_bytes(KIND) / 2;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((size_t)smem_raw + 1023) & ~(size_t)1023);
@@ -1374,7 +1377,7 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
     unsigned char* Wr = Ar + a_ring_bytes(KIND);
     const int wstride = (int)w_stride_bytes(KIND, P.kcs_max);   // bytes per parity
     float* cxs = reinterpret_cast<float*>(Wr + 2 * wstride);
-    constexpr int CXF = cx_floats(BIG, KIND);
+    constexpr int CXF = cx_floats(BIG, KIND, WIDE);
     float* exps = cxs + 2 * CXF;                        // BF16x3: [unit][128 rows] row scales
     float* scu = exps + kFxUnits * 128;                 //          [unit][16 columns] column scales
     int* colx = reinterpret_cast<int*>(scu + kFxUnits * kNT);   // [parity][16 parts][16 columns] exponents
@@ -1868,14 +1871,14 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
                         }
                     }
                 } else {
-                    const unsigned accbase = lanebase + 256u;
+                    const unsigned accbase = lanebase + (WIDE ? 192u : 256u);
                     const int nchunk = (g.o0 + 1) >> 1;   // two occupied i per TMEM round trip
                     for (int p0 = 0; p0 < g.n0; p0++) {
                         float T[16];
                         if (!(ok = load_p0_T<KIND, NS, UC, 16, true>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
                                                                       nullptr, abort, P.status, P.wait_ns)))
                             break;
-                        const float* cp = cx + p0 * kOBig;
+                        const float* cp = cx + p0 * CXW;
 #pragma unroll 1
                         for (int ic = 0; ic < nchunk; ic++) {
                             unsigned a[2][16];
@@ -1957,24 +1960,30 @@ int items_per_form(const DimerDesc& d, int f, int variant, int* mts_max)
 }
 
 // 3: rank kernel, register accumulators sized for occupations <= 5; 1: the
-// same for <= 8; 2: rank kernel, TMEM accumulators (<= 16); 0: Kronecker
-// kernel (anything else TF32/BF16x3 accept).  MCPT_TC_KERNEL=kron|rank8|rankbig
-// forces a kernel where the sizes allow it.
+// same for <= 8; 2: rank kernel, TMEM accumulators (<= 16); 4: the same with
+// o_X <= 20, o_Y <= 16 (a 20-occupied dimer as two blocks of Y's occupied
+// orbitals instead of 2 x 2); 0: Kronecker kernel (anything else TF32/BF16x3
+// accept).  MCPT_TC_KERNEL=kron|rank8|rankbig|rankwide forces a kernel where
+// the sizes allow it.
 int choose_variant(TcKind kind, const DimerDesc* h, int nd)
 {
-    int omax = 0, nymax = 0;
+    int omax = 0, nymax = 0, oxmax = 0, oymax = 0;
     for (int k = 0; k < nd; k++) {
         omax = std::max(omax, std::max(h[k].oX, h[k].oY));
+        oxmax = std::max(oxmax, h[k].oX);
+        oymax = std::max(oymax, h[k].oY);
         nymax = std::max(nymax, h[k].nY);
     }
     const bool fits_rank = nymax <= kKCMax * kKC && omax <= kOBig;
+    const bool fits_wide = nymax <= kKCMax * kKC && oxmax <= kOBigI && oymax <= kOBig;
     if (kind == TC_FP64E) return 3;   // the one kernel it has (limits checked by tc_prepare)
     const char* env = getenv("MCPT_TC_KERNEL");
     // BF16x2 runs the rank kernels only (the tensor-core size limits always fit them)
     if (env && !strcmp(env, "kron") && kind != TC_BF16X2) return 0;
     if (env && !strcmp(env, "rankbig") && fits_rank) return 2;
     if (env && !strcmp(env, "rank8") && omax <= kOB) return 1;
-    if (!fits_rank) return kind == TC_BF16X2 ? 2 : 0;
+    if (env && !strcmp(env, "rankwide") && fits_wide) return 4;
+    if (!fits_rank) return fits_wide ? 4 : kind == TC_BF16X2 ? 2 : 0;
     return omax <= kOB5 ? 3 : omax <= kOB ? 1 : 2;
 }
 
@@ -1997,7 +2006,8 @@ size_t tc_work_bytes(TcKind kind, const DimerDesc* h, int nd)
 static size_t fixed_smem(TcKind kind, int variant, int kcs_max, unsigned w_stage_bytes)
 {
     return variant >= 1 ? 1024 + a_ring_bytes(kind) + 2 * w_stride_bytes(kind, kcs_max) +
-                              2 * (size_t)cx_floats(variant == 2, kind) * 4 + fx_scale_bytes(kind) + sizeof(RankShared)
+                              2 * (size_t)cx_floats(variant == 2 || variant == 4, kind, variant == 4) * 4 +
+                              fx_scale_bytes(kind) + sizeof(RankShared)
                         : 1024 /*align*/ + 2 * (size_t)kABytes + 2 * (size_t)w_stage_bytes + sizeof(TcShared);
 }
 
@@ -2032,6 +2042,8 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
         if (omax <= kOB5) vars.push_back(3);
         if (omax <= kOB) vars.push_back(1);
         vars.push_back(2);
+    } else if (choose_variant(kind, h, nd) == 4) {
+        vars.push_back(4);
     } else {
         vars.push_back(0);
     }
@@ -2211,6 +2223,10 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
         fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, true>
              : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, true>
                                    : k_half_tc_rank<TC_BF16X3, true>;
+    else if (L.variant == 4)
+        fn = L.kind == TC_TF32     ? k_half_tc_rank<TC_TF32, true, kOBigI>
+             : L.kind == TC_BF16X2 ? k_half_tc_rank<TC_BF16X2, true, kOBigI>
+                                   : k_half_tc_rank<TC_BF16X3, true, kOBigI>;
     else if (L.kind == TC_BF16X2)
         return cudaErrorNotSupported;   // the Kronecker kernel has no 16-bit fixed-point form
     else fn = L.kind == TC_TF32 ? k_half_tc<TC_TF32> : k_half_tc<TC_BF16X3>;
@@ -2219,6 +2235,7 @@ cudaError_t tc_launch(const TcLaunch& L, cudaStream_t s)
     const int threads = L.kind == TC_FP64E ? rank_threads<false, kOB5, TC_FP64E>()
                         : L.variant == 3   ? rank_threads<false, kOB5>()
                         : L.variant == 2 ? rank_threads<true, kOB>()
+                        : L.variant == 4 ? rank_threads<true, kOBigI>()
                         : L.variant == 1 ? rank_threads<false, kOB>()
                                          : kThreadsTc;
     fn<<<L.grid, threads, L.smem, s>>>(P);

@@ -345,8 +345,9 @@ def test_uneven_sizes_batch(prec):
         assert abs(pd[k, 1] - E[k, 1]) <= PER_DIMER[prec] * abs(E[k, 0]), (prec, ds[k])
 
 
-@pytest.mark.parametrize("prec,variant", [(p, v) for p in ("tf32", "bf16x3") for v in ("rank", "rank8", "rankbig", "kron")]
-                         + [("bf16x2", v) for v in ("rank", "rank8", "rankbig")])
+@pytest.mark.parametrize("prec,variant", [(p, v) for p in ("tf32", "bf16x3")
+                                          for v in ("rank", "rank8", "rankbig", "rankwide", "kron")]
+                         + [("bf16x2", v) for v in ("rank", "rank8", "rankbig", "rankwide")])
 def test_tensor_core_kernel_variants(lat8, prec, variant, monkeypatch):
     """Both tcgen05 kernels (forced through MCPT_TC_KERNEL) against the oracle.
     The rank-1 variant keeps each tensor-core sum to n2/8 steps; its mean
@@ -444,9 +445,11 @@ def test_autotuner_cache(lat8, prec, tmp_path):
 @pytest.mark.parametrize("prec", ["tf32", "bf16x3", "bf16x2"])
 def test_occupations_above_16_run_as_blocks(prec):
     """More than 16 occupied orbitals on a monomer: the tensor-core forms run
-    the dimer as blocks of at most 16 x 16 occupied pairs (each over all
-    virtual orbitals) and add the blocks' terms; the result is the whole
-    dimer's, on non-symmetric random integrals."""
+    the dimer as blocks of at most 20 x 16 occupied pairs (i of X, j of Y;
+    each over all virtual orbitals) and add the blocks' terms -- (20, 18) as
+    two 20 x 9 blocks and (17, 3) as one block in the wide TMEM-accumulator
+    kernel, (2, 33) as three blocks -- and the result is the whole dimer's,
+    on non-symmetric random integrals."""
     rng = np.random.default_rng(17)
     for nX, nY, oX, oY in [(40, 36, 20, 18), (24, 34, 17, 3), (18, 40, 2, 33)]:
         A, K, CX, eX, CY, eY = rand_dimer(rng, nX, nY, oX, oY)

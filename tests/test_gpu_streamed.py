@@ -165,7 +165,8 @@ def test_uneven_4096_streamed(tmp_path):
 def test_ao128_subset():
     """343 monomers of 128 AO / 20 occupied: a seeded 16-dimer subset (4.3 GB
     of blocks per dimer) in the compensated FP32 and BF16x3 forms (the latter
-    as 2 x 2 blocks of 10 x 10 occupied pairs)."""
+    as two blocks of 20 x 10 occupied pairs in the wide TMEM-accumulator
+    kernel, each reading the integrals once)."""
     w = synth.workload("lattice-7x7x7-cheb1-ao128")
     rng = np.random.default_rng(13)
     subset = sorted(rng.choice(w.n_dimers, size=16, replace=False).tolist())
