@@ -911,7 +911,7 @@ def streamed_arm(args, ws, rank, local):
               "roofline": {"bound": "hbm", "achieved": bytesE / (sE.ms[0] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                            "unit": "GB/s", "kernel": "k_half_tc_rank (FP64E)", "peak_kind": peak_kind},
               "what": "FP64-accurate form on the tensor cores: 48-bit fixed-point byte digits, exact tcgen05 "
-                      "BF16 sums, FP32-pair epilogue and second half, FP64 sums"}
+                      "FP16 sums, FP32-pair epilogue and second half, FP64 sums"}
         fE["roofline"]["frac"] = fE["roofline"]["achieved"] / peaks["hbm_gbs"]
         if c64 is not None:
             fE["speedup_vs_fp64_form"] = fE["value"] / line["fp64_form"]["value"]

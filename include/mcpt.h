@@ -86,7 +86,7 @@ typedef enum {
     MCPT_FP64E = 5    /* the FP64 form's accuracy from the tensor cores (Ozaki-style slicing, Ozaki
                          et al., Numer. Algorithms 59 (2012) 95): each integral row chunk and each C_Y
                          column in 48-bit fixed point, six unsigned byte digits carrying the element's
-                         sign, every digit product summed exactly in FP32 by tcgen05 BF16 MMAs (21
+                         sign, every digit product summed exactly in FP32 by tcgen05 FP16 MMAs (21
                          products in six levels); the levels, the p0 quarter transformation and the
                          first-half result on FP32 pairs (48-bit), written as FP64; the second half,
                          denominators and sums as in MCPT_FP64.  Monomers of up to 64 AO and 5 occupied

@@ -32,6 +32,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -342,11 +343,11 @@ __device__ __forceinline__ unsigned sw128_off(int row, int chunk)
     return (unsigned)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
 }
 
-// Instruction descriptor: D = F32, A/B = TF32 (2) or BF16 (1), both K-major,
-// N >> 3 at bit 17, M >> 4 at bit 24.
+// Instruction descriptor: D = F32, A/B = TF32 (2), BF16 (1) or FP16 (0, the
+// FP64E digits), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __device__ __forceinline__ unsigned make_idesc(int kind, int N)
 {
-    const unsigned fmt = kind == TC_TF32 ? 2u : 1u;
+    const unsigned fmt = kind == TC_TF32 ? 2u : kind == TC_FP64E ? 0u : 1u;
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
 }
 
@@ -1190,33 +1191,36 @@ __device__ __forceinline__ void fx48(unsigned lo, unsigned hi, int emax, unsigne
     nl = __funnelshift_rc(__funnelshift_rc(lo, mh, s1), 0u, sh - s1);
 }
 
-// Byte `sel & 3` of wa and of wb as two exact BF16 values packed low | high,
-// with the sign bits sgn (0x8000: first, 0x80000000: second) set: the byte
-// becomes the FP32 value 2^23 + b by a byte permute, one packed subtraction
-// leaves b (at most 8 significant bits, so its BF16 is the FP32's high half).
-__device__ __forceinline__ unsigned bf16_byte_pair(unsigned wa, unsigned wb, unsigned sel, unsigned sgn)
+// Byte k of wa and of wb as two exact FP16 values packed low | high, each
+// with its element's sign: a byte permute puts the bytes in the low byte of
+// each half, one three-input logic operation keeps them and sets the FP16
+// bits of +-(1024 + b) (0x6400 | b, sign from `magic`), one packed FP16
+// addition of -+1024 (`off`) leaves +-b, exact (every value involved is an
+// FP16 integer below 2048).
+__device__ __forceinline__ unsigned f16_digit_pair(unsigned wa, unsigned wb, unsigned k, unsigned magic, unsigned off)
 {
-    const float2 f = __fadd2_rn(make_float2(__uint_as_float(__byte_perm(wa, 0x4B000000u, sel)),
-                                            __uint_as_float(__byte_perm(wb, 0x4B000000u, sel))),
-                                make_float2(-8388608.0f, -8388608.0f));
-    return pack_bf16(f.x, f.y) | sgn;
+    const unsigned t = (__byte_perm(wa, wb, k | ((4u + k) << 8)) & 0x00FF00FFu) | magic;
+    const __half2 r = __hadd2(*reinterpret_cast<const __half2*>(&t), *reinterpret_cast<const __half2*>(&off));
+    return *reinterpret_cast<const unsigned*>(&r);
 }
 
 // The six digit planes of two consecutive elements (a, b) of one vector:
-// N = d0 2^40 + d1 2^32 + d2 2^24 + d3 2^16 + d4 2^8 + d5, each digit carrying
-// its element's sign; w[v] = digit v of (a | b << 16).
+// N = d0 2^40 + d1 2^32 + d2 2^24 + d3 2^16 + d4 2^8 + d5, each digit an
+// FP16 integer carrying its element's sign; w[v] = digit v of (a | b << 16).
 __device__ __forceinline__ void digits6_pair(uint2 a, uint2 b, int emax, unsigned (&w)[6])
 {
     unsigned ha, la, hb, lb;
     fx48(a.x, a.y, emax, ha, la);
     fx48(b.x, b.y, emax, hb, lb);
     const unsigned sg = ((a.y >> 16) & 0x8000u) | (b.y & 0x80000000u);
-    w[0] = bf16_byte_pair(ha, hb, 0x7541u, sg);
-    w[1] = bf16_byte_pair(ha, hb, 0x7540u, sg);
-    w[2] = bf16_byte_pair(la, lb, 0x7543u, sg);
-    w[3] = bf16_byte_pair(la, lb, 0x7542u, sg);
-    w[4] = bf16_byte_pair(la, lb, 0x7541u, sg);
-    w[5] = bf16_byte_pair(la, lb, 0x7540u, sg);
+    const unsigned magic = 0x64006400u | sg;        // +-(1024 + b) once the bytes are in
+    const unsigned off = 0xE400E400u ^ sg;          // -1024 where positive, +1024 where negative
+    w[0] = f16_digit_pair(ha, hb, 1u, magic, off);
+    w[1] = f16_digit_pair(ha, hb, 0u, magic, off);
+    w[2] = f16_digit_pair(la, lb, 3u, magic, off);
+    w[3] = f16_digit_pair(la, lb, 2u, magic, off);
+    w[4] = f16_digit_pair(la, lb, 1u, magic, off);
+    w[5] = f16_digit_pair(la, lb, 0u, magic, off);
 }
 
 // FP64E: row r of one staged box as the six digit planes of its 48-bit fixed
@@ -2039,9 +2043,12 @@ int tc_candidates(TcKind kind, const DimerDesc* h, int nd, TcTune* out, int max)
     if (kind == TC_FP64E) {
         vars.push_back(3);
     } else if (nymax <= kKCMax * kKC && omax <= kOBig) {
+        // the accumulator tiles: 5 x 5 and 8 x 8 in registers, 16 x 16 in TMEM
+        // with four T units, 20 x 16 in TMEM with three
         if (omax <= kOB5) vars.push_back(3);
         if (omax <= kOB) vars.push_back(1);
         vars.push_back(2);
+        vars.push_back(4);
     } else if (choose_variant(kind, h, nd) == 4) {
         vars.push_back(4);
     } else {

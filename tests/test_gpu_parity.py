@@ -434,7 +434,7 @@ def test_autotuner_cache(lat8, prec, tmp_path):
         lines = cache.read_text().splitlines()
         assert len(lines) == 1, lines
     key, variant1, sf, grid, ms = lines[0].split()
-    assert key.startswith(prec + ":") and int(variant1) in (1, 2, 3, 4) and int(sf) >= 2 and int(grid) >= 1
+    assert key.startswith(prec + ":") and int(variant1) in (1, 2, 3, 4, 5) and int(sf) >= 2 and int(grid) >= 1
     print(f"{prec}: tuned {lines[0]}")
     for mj, mk, pd, tot in res:
         assert np.all(np.abs(pd[:, 0] - E[:, 0]) <= PER_DIMER[prec] * np.abs(E[:, 0]))
