@@ -1274,19 +1274,24 @@ __device__ __forceinline__ int convert_row_fx6(const double* __restrict__ F, uns
 template <int NJ, int J0 = 0>
 __device__ __forceinline__ void unit_T_ff(unsigned taddr, FF (&T)[8], float srow, bool add)
 {
-    // Horner from L6 down: S.l shrinks by 2^8 per step while each new TwoSum
-    // error is below ulp(S.h) / 2, so it stays within ulp(S.h) without
-    // renormalising (once, at the end).  Levels are loaded two at a time (16
-    // registers), L6 alone first.
+    // Levels 6-4 in plain FP32 (two FMAs: their sum carries weight 2^-32, so
+    // its rounding lies near 2^-56 of T), then the Horner steps of levels
+    // 3-0 on pairs.  S.l shrinks by 2^8 per step while each new TwoSum error
+    // is below ulp(S.h) / 2, so it stays within ulp(S.h) without
+    // renormalising (once, at the end).  Levels are loaded three, then two
+    // at a time.
     FF S[NJ];
     {
-        unsigned l6[8];
-        tmem_ld_l1x8(taddr + 96u, l6);
+        unsigned hi[3][8];   // L4, L5, L6
+        tmem_ld_l3x8(taddr + 64u, *reinterpret_cast<unsigned(*)[24]>(&hi[0][0]));
 #pragma unroll
-        for (int j = 0; j < NJ; j++) S[j] = FF{__uint_as_float(l6[J0 + j]), 0.f};
+        for (int j = 0; j < NJ; j++)
+            S[j] = FF{fmaf(fmaf(__uint_as_float(hi[2][J0 + j]), 0x1p-8f, __uint_as_float(hi[1][J0 + j])), 0x1p-8f,
+                           __uint_as_float(hi[0][J0 + j])),
+                      0.f};
     }
 #pragma unroll
-    for (int l = 4; l >= 0; l -= 2) {        // levels l + 1, then l
+    for (int l = 2; l >= 0; l -= 2) {        // levels l + 1, then l
         unsigned lv[2][8];
         tmem_ld_l2x8(taddr + (unsigned)(16 * l), *reinterpret_cast<unsigned(*)[16]>(&lv[0][0]));
 #pragma unroll
