@@ -299,7 +299,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 // kept off the FP64 pipe, whose rate a multiply-add per (row, pair) term
 // would otherwise set.  The C columns stay in shared memory (a lane's column
 // as pairs would take 64 registers); four outputs accumulate at once so that
-// each lane runs independent chains, renormalised every eight terms.  Per-lane sums over b go into FP64 sums
+// each lane runs independent chains.  Per-lane sums over b go into FP64 sums
 // once per occupied pair; with STORE the dimer's (ia|jb) and T = vD are
 // written as FP64 for the coupling.
 constexpr int kFFSlab = 32 * 33;   // one padded 32 x 32 tile of pairs (row stride 33)
@@ -363,17 +363,13 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
 #pragma unroll
             for (int nu = 0; nu < 32; nu += 4) {
                 FF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
-#pragma unroll 1
-                for (int m0 = 0; m0 < 32; m0 += 8) {
-#pragma unroll
-                    for (int m = m0; m < m0 + 8; m++) {
-                        const FF c = cy[m];
-                        ff_mac_nr(a0, SX[(nu + 0) * 32 + m], c);
-                        ff_mac_nr(a1, SX[(nu + 1) * 32 + m], c);
-                        ff_mac_nr(a2, SX[(nu + 2) * 32 + m], c);
-                        ff_mac_nr(a3, SX[(nu + 3) * 32 + m], c);
-                    }
-                    a0 = ff_norm(a0); a1 = ff_norm(a1); a2 = ff_norm(a2); a3 = ff_norm(a3);
+#pragma unroll 4
+                for (int m = 0; m < 32; m++) {
+                    const FF c = cy[m];
+                    ff_mac(a0, SX[(nu + 0) * 32 + m], c);
+                    ff_mac(a1, SX[(nu + 1) * 32 + m], c);
+                    ff_mac(a2, SX[(nu + 2) * 32 + m], c);
+                    ff_mac(a3, SX[(nu + 3) * 32 + m], c);
                 }
                 tm[nu] = a0; tm[nu + 1] = a1; tm[nu + 2] = a2; tm[nu + 3] = a3;
             }
@@ -383,11 +379,10 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
                 FF b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
 #pragma unroll
                 for (int nu = 0; nu < 32; nu++) {
-                    ff_mac_nr(b0, CXT[(a + 0) * 33 + nu], tm[nu]);
-                    ff_mac_nr(b1, CXT[(a + 1) * 33 + nu], tm[nu]);
-                    ff_mac_nr(b2, CXT[(a + 2) * 33 + nu], tm[nu]);
-                    ff_mac_nr(b3, CXT[(a + 3) * 33 + nu], tm[nu]);
-                    if ((nu & 7) == 7) { b0 = ff_norm(b0); b1 = ff_norm(b1); b2 = ff_norm(b2); b3 = ff_norm(b3); }
+                    ff_mac(b0, CXT[(a + 0) * 33 + nu], tm[nu]);
+                    ff_mac(b1, CXT[(a + 1) * 33 + nu], tm[nu]);
+                    ff_mac(b2, CXT[(a + 2) * 33 + nu], tm[nu]);
+                    ff_mac(b3, CXT[(a + 3) * 33 + nu], tm[nu]);
                 }
                 SX[(a + 0) * 33 + lane] = b0;
                 SX[(a + 1) * 33 + lane] = b1;
@@ -403,17 +398,13 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
 #pragma unroll
             for (int lam = 0; lam < 32; lam += 4) {
                 FF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
-#pragma unroll 1
-                for (int m0 = 0; m0 < 32; m0 += 8) {
-#pragma unroll
-                    for (int m = m0; m < m0 + 8; m++) {
-                        const FF c = cx[m];
-                        ff_mac_nr(a0, SY[(lam + 0) * 32 + m], c);
-                        ff_mac_nr(a1, SY[(lam + 1) * 32 + m], c);
-                        ff_mac_nr(a2, SY[(lam + 2) * 32 + m], c);
-                        ff_mac_nr(a3, SY[(lam + 3) * 32 + m], c);
-                    }
-                    a0 = ff_norm(a0); a1 = ff_norm(a1); a2 = ff_norm(a2); a3 = ff_norm(a3);
+#pragma unroll 4
+                for (int m = 0; m < 32; m++) {
+                    const FF c = cx[m];
+                    ff_mac(a0, SY[(lam + 0) * 32 + m], c);
+                    ff_mac(a1, SY[(lam + 1) * 32 + m], c);
+                    ff_mac(a2, SY[(lam + 2) * 32 + m], c);
+                    ff_mac(a3, SY[(lam + 3) * 32 + m], c);
                 }
                 tk[lam] = a0; tk[lam + 1] = a1; tk[lam + 2] = a2; tk[lam + 3] = a3;
             }
@@ -425,9 +416,8 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
                 FF v0{0.f, 0.f}, v1{0.f, 0.f};   // two chains of 16
 #pragma unroll
                 for (int lam = 0; lam < 32; lam += 2) {
-                    ff_mac_nr(v0, CYT[b * 33 + lam], tk[lam]);
-                    ff_mac_nr(v1, CYT[b * 33 + lam + 1], tk[lam + 1]);
-                    if ((lam & 15) == 14) { v0 = ff_norm(v0); v1 = ff_norm(v1); }
+                    ff_mac(v0, CYT[b * 33 + lam], tk[lam]);
+                    ff_mac(v1, CYT[b * 33 + lam + 1], tk[lam + 1]);
                 }
                 if (live) {
                     const FF v = SX[lane * 33 + b];
