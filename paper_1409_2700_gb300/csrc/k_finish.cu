@@ -94,11 +94,13 @@ __device__ __forceinline__ void energy_terms(T v, T vk, double x, double& ej, do
 // takes the place of H0 in its buffer.  Per-lane sums reduce in a fixed order.
 constexpr int kW32Warps = 4;
 constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33)
+constexpr int kCS = 36;                // row stride of the staged C columns: 16-byte rows for vector
+                                       // loads, lane rows 4 banks apart (4-way instead of 32-way)
 
 template <typename T>
 constexpr size_t w32_smem_bytes()
 {
-    return 32 * sizeof(double) + 32 * sizeof(FF) + 2 * 32 * 32 * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
+    return 32 * sizeof(double) + 32 * sizeof(FF) + 2 * 32 * kCS * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
 }
 
 // One warp starts the asynchronous copy of an nr x nc (<= 32 x 32) row-major
@@ -155,10 +157,10 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     static_assert(!PAIRS || sizeof(T) == 4, "FP32 pairs serve the mixed forms");
     double* eYv = reinterpret_cast<double*>(smraw);          // [b]: e_b (read as a broadcast)
     FF* eYs = reinterpret_cast<FF*>(eYv + 32);                // [b]: e_b as an FP32 pair
-    T* CXT = reinterpret_cast<T*>(eYs + 32);                  // [a][nu], zero padded
-    T* CYT = CXT + 32 * 32;                                   // [b][sig]
+    T* CXT = reinterpret_cast<T*>(eYs + 32);                  // [a][nu], zero padded, row stride kCS
+    T* CYT = CXT + 32 * kCS;                                  // [b][sig]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* const buf = CYT + 32 * 32 + warp * (2 * kW32Slab);     // two slice buffers of kW32Slab
+    T* const buf = CYT + 32 * kCS + warp * (2 * kW32Slab);    // two slice buffers of kW32Slab
 
     // the warp's first pair streams in while the block stages C and the energies
     if (warp < pairs) {
@@ -179,8 +181,8 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
             const int k = threadIdx.x + t * kW32Warps * 32;
-            CXT[k] = cxv[t];
-            CYT[k] = cyv[t];
+            CXT[(k >> 5) * kCS + (k & 31)] = cxv[t];
+            CYT[(k >> 5) * kCS + (k & 31)] = cyv[t];
         }
         if (threadIdx.x < 32) {
             const double e = threadIdx.x < vY ? Epool[d.eYv + threadIdx.x] : 0.0;
@@ -211,7 +213,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
         {
             T cy[32], tm[32];
 #pragma unroll
-            for (int m = 0; m < 32; m++) cy[m] = CYT[lane * 32 + m];
+            for (int m = 0; m < 32; m++) cy[m] = CYT[lane * kCS + m];
 #pragma unroll
             for (int nu = 0; nu < 32; nu++) {
                 T acc = 0;
@@ -224,7 +226,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             for (int a = 0; a < 32; a++) {
                 T acc = 0;
 #pragma unroll
-                for (int nu = 0; nu < 32; nu++) acc = fma(CXT[a * 32 + nu], tm[nu], acc);
+                for (int nu = 0; nu < 32; nu++) acc = fma(CXT[a * kCS + nu], tm[nu], acc);
                 SX[a * 33 + lane] = acc;
             }
         }
@@ -233,7 +235,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
         {
             T cx[32], tk[32];
 #pragma unroll
-            for (int m = 0; m < 32; m++) cx[m] = CXT[lane * 32 + m];
+            for (int m = 0; m < 32; m++) cx[m] = CXT[lane * kCS + m];
 #pragma unroll
             for (int lam = 0; lam < 32; lam++) {
                 T acc = 0;
@@ -249,8 +251,8 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
                 T v0 = 0, v1 = 0;                // two chains of 16
 #pragma unroll
                 for (int lam = 0; lam < 32; lam += 2) {
-                    v0 = fma(CYT[b * 32 + lam], tk[lam], v0);
-                    v1 = fma(CYT[b * 32 + lam + 1], tk[lam + 1], v1);
+                    v0 = fma(CYT[b * kCS + lam], tk[lam], v0);
+                    v1 = fma(CYT[b * kCS + lam + 1], tk[lam + 1], v1);
                 }
                 if (live) {
                     const T vab = SX[lane * 33 + b];
@@ -303,6 +305,7 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 // once per occupied pair; with STORE the dimer's (ia|jb) and T = vD are
 // written as FP64 for the coupling.
 constexpr int kFFSlab = 32 * 33;   // one padded 32 x 32 tile of pairs (row stride 33)
+constexpr int kFFChains = 4;       // independent pair multiply-add chains per lane (eight measured slower)
 
 size_t w32_ff_smem_bytes() { return (32 + 2 * (size_t)kFFSlab + 2 * (size_t)kW32Warps * kFFSlab) * sizeof(FF); }
 
@@ -361,33 +364,31 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
             FF tm[32];
             const FF* cy = CYT + lane * 33;
 #pragma unroll
-            for (int nu = 0; nu < 32; nu += 4) {
-                FF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+            for (int nu = 0; nu < 32; nu += kFFChains) {
+                FF acc[kFFChains];
+#pragma unroll
+                for (int q = 0; q < kFFChains; q++) acc[q] = FF{0.f, 0.f};
 #pragma unroll 4
                 for (int m = 0; m < 32; m++) {
                     const FF c = cy[m];
-                    ff_mac(a0, SX[(nu + 0) * 32 + m], c);
-                    ff_mac(a1, SX[(nu + 1) * 32 + m], c);
-                    ff_mac(a2, SX[(nu + 2) * 32 + m], c);
-                    ff_mac(a3, SX[(nu + 3) * 32 + m], c);
+#pragma unroll
+                    for (int q = 0; q < kFFChains; q++) ff_mac(acc[q], SX[(nu + q) * 32 + m], c);
                 }
-                tm[nu] = a0; tm[nu + 1] = a1; tm[nu + 2] = a2; tm[nu + 3] = a3;
+#pragma unroll
+                for (int q = 0; q < kFFChains; q++) tm[nu + q] = acc[q];
             }
             __syncwarp();                        // H0 consumed: VA takes its place
 #pragma unroll 1
-            for (int a = 0; a < 32; a += 4) {
-                FF b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
+            for (int a = 0; a < 32; a += kFFChains) {
+                FF acc[kFFChains];
 #pragma unroll
-                for (int nu = 0; nu < 32; nu++) {
-                    ff_mac(b0, CXT[(a + 0) * 33 + nu], tm[nu]);
-                    ff_mac(b1, CXT[(a + 1) * 33 + nu], tm[nu]);
-                    ff_mac(b2, CXT[(a + 2) * 33 + nu], tm[nu]);
-                    ff_mac(b3, CXT[(a + 3) * 33 + nu], tm[nu]);
-                }
-                SX[(a + 0) * 33 + lane] = b0;
-                SX[(a + 1) * 33 + lane] = b1;
-                SX[(a + 2) * 33 + lane] = b2;
-                SX[(a + 3) * 33 + lane] = b3;
+                for (int q = 0; q < kFFChains; q++) acc[q] = FF{0.f, 0.f};
+#pragma unroll
+                for (int nu = 0; nu < 32; nu++)
+#pragma unroll
+                    for (int q = 0; q < kFFChains; q++) ff_mac(acc[q], CXT[(a + q) * 33 + nu], tm[nu]);
+#pragma unroll
+                for (int q = 0; q < kFFChains; q++) SX[(a + q) * 33 + lane] = acc[q];
             }
         }
         // ---- (i b|j a): lane a, tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
@@ -396,17 +397,18 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
             FF tk[32];
             const FF* cx = CXT + lane * 33;
 #pragma unroll
-            for (int lam = 0; lam < 32; lam += 4) {
-                FF a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+            for (int lam = 0; lam < 32; lam += kFFChains) {
+                FF acc[kFFChains];
+#pragma unroll
+                for (int q = 0; q < kFFChains; q++) acc[q] = FF{0.f, 0.f};
 #pragma unroll 4
                 for (int m = 0; m < 32; m++) {
                     const FF c = cx[m];
-                    ff_mac(a0, SY[(lam + 0) * 32 + m], c);
-                    ff_mac(a1, SY[(lam + 1) * 32 + m], c);
-                    ff_mac(a2, SY[(lam + 2) * 32 + m], c);
-                    ff_mac(a3, SY[(lam + 3) * 32 + m], c);
+#pragma unroll
+                    for (int q = 0; q < kFFChains; q++) ff_mac(acc[q], SY[(lam + q) * 32 + m], c);
                 }
-                tk[lam] = a0; tk[lam + 1] = a1; tk[lam + 2] = a2; tk[lam + 3] = a3;
+#pragma unroll
+                for (int q = 0; q < kFFChains; q++) tk[lam + q] = acc[q];
             }
             __syncwarp();                        // H1 consumed: the next pair's H0 streams into SY
             if (nx < pairs) prefetch_slice(SY, H0 + (long long)nx * rows, nX, nY, lane);

@@ -1274,28 +1274,32 @@ __device__ __forceinline__ int convert_row_fx6(const double* __restrict__ F, uns
 template <int NJ, int J0 = 0>
 __device__ __forceinline__ void unit_T_ff(unsigned taddr, FF (&T)[8], float srow, bool add)
 {
-    // Levels 6-4 in plain FP32 (two FMAs: their sum carries weight 2^-32, so
-    // its rounding lies near 2^-56 of T), then the Horner steps of levels
-    // 3-0 on pairs.  S.l shrinks by 2^8 per step while each new TwoSum error
-    // is below ulp(S.h) / 2, so it stays within ulp(S.h) without
-    // renormalising (once, at the end).  Levels are loaded three, then two
-    // at a time.
+    // Levels 6-3 in plain FP32 (three FMAs: their sum carries weight 2^-24,
+    // so its rounding lies near 2^-48 of T, the pairs' own precision), then
+    // the Horner steps of levels 2-0 on pairs.  S.l shrinks by 2^8 per step
+    // while each new TwoSum error is below ulp(S.h) / 2, so it stays within
+    // ulp(S.h) without renormalising (once, at the end).  Levels are loaded
+    // three, one and three at a time.
     FF S[NJ];
     {
         unsigned hi[3][8];   // L4, L5, L6
         tmem_ld_l3x8(taddr + 64u, *reinterpret_cast<unsigned(*)[24]>(&hi[0][0]));
 #pragma unroll
         for (int j = 0; j < NJ; j++)
-            S[j] = FF{fmaf(fmaf(__uint_as_float(hi[2][J0 + j]), 0x1p-8f, __uint_as_float(hi[1][J0 + j])), 0x1p-8f,
-                           __uint_as_float(hi[0][J0 + j])),
-                      0.f};
+            S[j].h = fmaf(fmaf(__uint_as_float(hi[2][J0 + j]), 0x1p-8f, __uint_as_float(hi[1][J0 + j])), 0x1p-8f,
+                          __uint_as_float(hi[0][J0 + j]));
     }
+    {
+        unsigned l3[8];
+        tmem_ld_l1x8(taddr + 48u, l3);
 #pragma unroll
-    for (int l = 2; l >= 0; l -= 2) {        // levels l + 1, then l
-        unsigned lv[2][8];
-        tmem_ld_l2x8(taddr + (unsigned)(16 * l), *reinterpret_cast<unsigned(*)[16]>(&lv[0][0]));
+        for (int j = 0; j < NJ; j++) S[j] = FF{fmaf(S[j].h, 0x1p-8f, __uint_as_float(l3[J0 + j])), 0.f};
+    }
+    {
+        unsigned lv[3][8];   // L0, L1, L2
+        tmem_ld_l3x8(taddr, *reinterpret_cast<unsigned(*)[24]>(&lv[0][0]));
 #pragma unroll
-        for (int k = 1; k >= 0; k--)
+        for (int k = 2; k >= 0; k--)
 #pragma unroll
             for (int j = 0; j < NJ; j++) {
                 float e;
