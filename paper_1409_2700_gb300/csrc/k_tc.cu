@@ -36,6 +36,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -211,6 +212,16 @@ __device__ __forceinline__ void tmem_ld_l1x16(unsigned taddr, unsigned (&r)[16])
         : "r"(taddr + 0u)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld_l2x8(unsigned taddr, unsigned (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr + 0u), "r"(taddr + 16u)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld_l3x8(unsigned taddr, unsigned (&r)[24])
 {
     asm volatile(
@@ -287,6 +298,12 @@ __device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&r)[16
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
         "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
+}
+__device__ __forceinline__ void tmem_st8(unsigned taddr, const unsigned (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -1849,36 +1866,51 @@ __global__ void __launch_bounds__(rank_threads<BIG, OB, KIND>(), 1) k_half_tc_ra
                 } else {
                     const unsigned accbase = lanebase + (WIDE ? 192u : 256u);
                     const int nchunk = (g.o0 + 1) >> 1;   // two occupied i per TMEM round trip
-                    for (int p0 = 0; p0 < g.n0; p0++) {
-                        float T[16];
-                        if (!(ok = load_p0_T<KIND, NS, UC, 16, true>(T, sh, gS, g.kcs, lanebase, exps, scu, r, lane,
-                                                                      nullptr, abort, P.status, P.wait_ns)))
-                            break;
-                        const float* cp = cx + p0 * CXW;
+                    // NJ columns j per accumulator row: 8 when o_Y <= 8 (the rest of each
+                    // 16-column row is never read), else 16 -- half the T combination, FMAs and
+                    // TMEM traffic for the smaller occupations; same results either way
+                    auto rank1_over_p0 = [&](auto njc) {
+                        constexpr int NJ = decltype(njc)::value;
+                        for (int p0 = 0; p0 < g.n0; p0++) {
+                            float T[NJ];
+                            if (!(ok = load_p0_T<KIND, NS, UC, NJ, true>(T, sh, gS, g.kcs, lanebase, exps, scu, r,
+                                                                          lane, nullptr, abort, P.status, P.wait_ns)))
+                                break;
+                            const float* cp = cx + p0 * CXW;
 #pragma unroll 1
-                        for (int ic = 0; ic < nchunk; ic++) {
-                            unsigned a[2][16];
-                            if (p0 > 0) {
-                                tmem_ld_l2x16(accbase + (unsigned)(ic * 32),
-                                              *reinterpret_cast<unsigned(*)[32]>(&a[0][0]));
-                            } else {
+                            for (int ic = 0; ic < nchunk; ic++) {
+                                unsigned a[2][NJ];
+                                if (p0 > 0) {
+                                    if constexpr (NJ == 16)
+                                        tmem_ld_l2x16(accbase + (unsigned)(ic * 32),
+                                                      *reinterpret_cast<unsigned(*)[32]>(&a[0][0]));
+                                    else
+                                        tmem_ld_l2x8(accbase + (unsigned)(ic * 32),
+                                                     *reinterpret_cast<unsigned(*)[16]>(&a[0][0]));
+                                } else {
+#pragma unroll
+                                    for (int u = 0; u < 2; u++)
+#pragma unroll
+                                        for (int j = 0; j < NJ; j++) a[u][j] = 0u;
+                                }
+                                const float2 c2 = *reinterpret_cast<const float2*>(cp + ic * 2);
+                                const float cv[2] = {c2.x, c2.y};
 #pragma unroll
                                 for (int u = 0; u < 2; u++)
 #pragma unroll
-                                    for (int j = 0; j < 16; j++) a[u][j] = 0u;
+                                    for (int j = 0; j < NJ; j++)
+                                        a[u][j] = __float_as_uint(fmaf(cv[u], T[j], __uint_as_float(a[u][j])));
+#pragma unroll
+                                for (int u = 0; u < 2; u++) {
+                                    if constexpr (NJ == 16) tmem_st16(accbase + (unsigned)((ic * 2 + u) * 16), a[u]);
+                                    else tmem_st8(accbase + (unsigned)((ic * 2 + u) * 16), a[u]);
+                                }
                             }
-                            const float2 c2 = *reinterpret_cast<const float2*>(cp + ic * 2);
-                            const float cv[2] = {c2.x, c2.y};
-#pragma unroll
-                            for (int u = 0; u < 2; u++)
-#pragma unroll
-                                for (int j = 0; j < 16; j++)
-                                    a[u][j] = __float_as_uint(fmaf(cv[u], T[j], __uint_as_float(a[u][j])));
-#pragma unroll
-                            for (int u = 0; u < 2; u++) tmem_st16(accbase + (unsigned)((ic * 2 + u) * 16), a[u]);
+                            tmem_wait_st();   // this p0's updates land before the next one reads them
                         }
-                        tmem_wait_st();   // this p0's updates land before the next one reads them
-                    }
+                    };
+                    if (g.o2 <= 8) rank1_over_p0(std::integral_constant<int, 8>{});
+                    else rank1_over_p0(std::integral_constant<int, 16>{});
                     if (!ok) break;
                     const int valid = (min(g.n1, p1_lo + g.p1t) - p1_lo) * g.n3;
                     float* out = Hf + p1_lo * g.n3 + r;
