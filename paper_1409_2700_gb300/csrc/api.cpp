@@ -143,6 +143,7 @@ struct mcpt_ctx {
         size_t fin_off;              // byte offset of the wave's tasks in dFin
         int ntasks;                  // 0: one CTA per dimer (<= 32 AO)
         size_t part_off;             // first partial (pairs of doubles) in dPart
+        int fin_warps;               // warps per CTA of the 32-AO second half
     };
     // A plan is the host work of a run that does not change between runs of
     // the same dimer range and precision (descriptors, waves, tensor maps and
@@ -1191,6 +1192,14 @@ static mcpt_status build_plan(mcpt_handle h, mcpt_ctx::Plan& P, int first, int c
             wv.max_occ = std::max(wv.max_occ, std::max(dd.oX, dd.oY));
             wv.max_ao = std::max(wv.max_ao, std::max(dd.nX, dd.nY));
         }
+        wv.fin_warps = 4;
+        if (wv.max_ao <= 32) {
+            const int form = prec == MCPT_FP64E ? FIN_FF
+                             : fp64_data(prec)  ? FIN_F64
+                             : h->fp64_epilogue ? FIN_F32_F64EPI
+                                                : FIN_F32_PAIRS;
+            wv.fin_warps = finish_w32_warps(P.hDesc.data() + wv.b, wv.nd, form);
+        }
         if (is_tensor_form(prec)) {
             char tcerr[256] = {0};
             const size_t end = (w + 1 < work_off.size()) ? work_off[w + 1] : P.capWork;
@@ -1275,15 +1284,15 @@ static mcpt_status enqueue_run(mcpt_handle h, const mcpt_ctx::Plan& P, const std
         double* part = wv.ntasks ? P.dPart + 2 * wv.part_off : nullptr;
         if (prec == MCPT_FP64E && wv.max_ao <= 32)   // H as FP32 pairs (the tensor-core launch's h_pairs)
             CK(h, launch_finish_ff(wd, wv.nd, wv.max_ao, h->dC, h->dE, h->dH, h->dE2,
-                                   P.coupling ? static_cast<double*>(h->dVT) : nullptr, h->stream));
+                                   P.coupling ? static_cast<double*>(h->dVT) : nullptr, wv.fin_warps, h->stream));
         else if (fp64_data(prec))
             CK(h, launch_finish_fp64(wd, wv.nd, wv.max_ao, h->dC, h->dE, static_cast<const double*>(h->dH), h->dE2,
                                      tasks, wv.ntasks, part, P.coupling ? static_cast<double*>(h->dVT) : nullptr,
-                                     h->stream));
+                                     wv.fin_warps, h->stream));
         else
             CK(h, launch_finish_fp32(wd, wv.nd, wv.max_ao, h->dCf, h->dE, static_cast<const float*>(h->dH), h->dE2,
                                      tasks, wv.ntasks, part, P.coupling ? static_cast<float*>(h->dVT) : nullptr,
-                                     h->fp64_epilogue, h->stream));
+                                     h->fp64_epilogue, wv.fin_warps, h->stream));
         launches += wv.ntasks ? 2 : 1;
         if (ev) CK(h, cudaEventRecord((*ev)[2 + 2 * w], h->stream));
     }

@@ -83,26 +83,33 @@ struct FinTask {
 void finish_tasks(const DimerDesc* h_desc, int nd, int pairs_per_task, std::vector<FinTask>* out);
 
 // Second half + denominators + energies.  H is double (FP64 form) or float.
-// Waves whose monomers all have <= 32 AO run one CTA per dimer; larger ones
-// run the tasks (`tasks`, device array of `ntasks`) and sum each dimer's
-// task partials (`part`, 2 doubles per task) in task order.
+// Waves whose monomers all have <= 32 AO run one CTA of w32_warps (4 or 5)
+// warps per dimer; larger ones run the tasks (`tasks`, device array of
+// `ntasks`) and sum each dimer's task partials (`part`, 2 doubles per task)
+// in task order.
 // With VT non-null, descriptors with vt_off >= 0 also store their (ia|jb)
 // and T = vD for the coupling.  FP32 (mixed forms): the energy epilogue on
 // FP32 pairs, or with fp64_epilogue on the FP64 pipe term by term.
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao,
                                const double* Cpool, const double* Epool, const double* H,
                                double* E2, const FinTask* tasks, int ntasks, double* part, double* VT,
-                               cudaStream_t s);
+                               int w32_warps, cudaStream_t s);
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao,
                                const float* Cf, const double* Epool, const float* H,
                                double* E2, const FinTask* tasks, int ntasks, double* part, float* VT,
-                               bool fp64_epilogue, cudaStream_t s);
+                               bool fp64_epilogue, int w32_warps, cudaStream_t s);
 
 // FP64E second half (monomers of at most 32 AO): H as FP32 pairs (written so
 // by the FP64E first half), every step on FP32 pairs, FP64 sums; VT (may be
 // null) gets FP64 (ia|jb) and T = vD as launch_finish_fp64 stores them.
 cudaError_t launch_finish_ff(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool, const double* Epool,
-                             const void* H, double* E2, double* VT, cudaStream_t s);
+                             const void* H, double* E2, double* VT, int w32_warps, cudaStream_t s);
+
+// The 32-AO second half's forms, and its warps per CTA for the host
+// descriptors h[0, nd) of a wave: 4 or 5, whichever takes fewer rounds of
+// one occupied pair per warp over the CTAs an SM holds at once.
+enum FinForm { FIN_F64 = 0, FIN_F32_PAIRS = 1, FIN_F32_F64EPI = 2, FIN_FF = 3 };
+int finish_w32_warps(const DimerDesc* h, int nd, int form);
 
 // Dimer -> monomer doubles coupling of Eq. (tm2) at first order.
 struct CoupDim {

@@ -92,15 +92,73 @@ __device__ __forceinline__ void energy_terms(T v, T vk, double x, double& ej, do
 // one step ahead: H1 of this pair streams in during the H0 work, H0 of the
 // next pair during the H1 work, so the warp rarely waits on memory.  VA
 // takes the place of H0 in its buffer.  Per-lane sums reduce in a fixed order.
-constexpr int kW32Warps = 4;
+// W warps per CTA (4 or 5, chosen per wave by finish_w32_warps): o_X o_Y = 25
+// occupied pairs fill five warps evenly, where four leave three warps idle
+// for the seventh round.
 constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33)
 constexpr int kCS = 36;                // row stride of the staged C columns: 16-byte rows for vector
                                        // loads, lane rows 4 banks apart (4-way instead of 32-way)
 
+// FP32 (the mixed forms) adds a third slab per warp: the pair's (ib|ja),
+// formed for all b before the energy loop, which then runs no multiply-add
+// chain of its own (the FP64 form keeps two slabs, for its occupancy).
 template <typename T>
-constexpr size_t w32_smem_bytes()
+__host__ __device__ constexpr int w32_slabs() { return sizeof(T) == 4 ? 3 : 2; }
+
+template <typename T>
+constexpr size_t w32_smem_bytes(int W)
 {
-    return 32 * sizeof(double) + 32 * sizeof(FF) + 2 * 32 * kCS * sizeof(T) + kW32Warps * 2 * kW32Slab * sizeof(T);
+    return 32 * sizeof(double) + 32 * sizeof(FF) + 2 * 32 * kCS * sizeof(T) +
+           W * w32_slabs<T>() * kW32Slab * sizeof(T);
+}
+
+// sum_{m < 32} a[m] x[m], a a 16-byte aligned row in shared memory (read as
+// broadcasts), x in registers.  FP64 (the FP64 form): one chain in m order.
+__device__ __forceinline__ double dot32(const double* a, const double (&x)[32])
+{
+    double acc = 0;
+#pragma unroll
+    for (int m = 0; m < 32; m++) acc = fma(a[m], x[m], acc);
+    return acc;
+}
+
+// FP32: the sums of R rows at once, rows a + r * stride (16-byte aligned),
+// each as two chains (even and odd m) advanced together by the packed FP32
+// multiply-add (one instruction per two products) and added at the end; the
+// R rows' chains interleave in issue order, so that a warp has R
+// multiply-adds in flight instead of one dependent chain.
+template <int R>
+__device__ __forceinline__ void dots32(const float* a, int stride, const float (&x)[32], float (&out)[R])
+{
+    float2 acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        float4 v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = reinterpret_cast<const float4*>(a + r * stride)[q];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            acc[r] = __ffma2_rn(make_float2(v[r].x, v[r].y), make_float2(x[4 * q], x[4 * q + 1]), acc[r]);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            acc[r] = __ffma2_rn(make_float2(v[r].z, v[r].w), make_float2(x[4 * q + 2], x[4 * q + 3]), acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) out[r] = __fadd_rn(acc[r].x, acc[r].y);
+}
+
+// The same sum as two chains (even and odd m), for the FP64 form.
+__device__ __forceinline__ double dot32_2(const double* a, const double (&x)[32])
+{
+    double v0 = 0, v1 = 0;
+#pragma unroll
+    for (int m = 0; m < 32; m += 2) {
+        v0 = fma(a[m], x[m], v0);
+        v1 = fma(a[m + 1], x[m + 1], v1);
+    }
+    return v0 + v1;
 }
 
 // One warp starts the asynchronous copy of an nr x nc (<= 32 x 32) row-major
@@ -137,8 +195,8 @@ __device__ __forceinline__ void slice_wait()
 // instantiation keeps the plain path's registers).  PAIRS (mixed forms only):
 // the energy terms on FP32 pairs, summed per (pair, a) and added to the FP64
 // sums once per pair; otherwise on the FP64 pipe term by term.
-template <typename T, bool STORE, bool PAIRS>
-__global__ void __launch_bounds__(kW32Warps * 32, 4)
+template <typename T, bool STORE, bool PAIRS, int W>
+__global__ void __launch_bounds__(W * 32, W == 4 ? 3 : 2)
 k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const double* __restrict__ Epool,
              const T* __restrict__ H, double* __restrict__ E2, T* __restrict__ VT)
 {
@@ -160,7 +218,8 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     T* CXT = reinterpret_cast<T*>(eYs + 32);                  // [a][nu], zero padded, row stride kCS
     T* CYT = CXT + 32 * kCS;                                  // [b][sig]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* const buf = CYT + 32 * kCS + warp * (2 * kW32Slab);    // two slice buffers of kW32Slab
+    T* const buf = CYT + 32 * kCS + warp * (w32_slabs<T>() * kW32Slab);   // two slice buffers of kW32Slab
+    [[maybe_unused]] T* const SV = buf + 2 * kW32Slab;        // FP32: (ib|ja) as [b][a] (stride 33)
 
     // the warp's first pair streams in while the block stages C and the energies
     if (warp < pairs) {
@@ -169,20 +228,22 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     }
     {
         // all loads first (independent, in flight together), then the stores
-        constexpr int kPer = 32 * 32 / (kW32Warps * 32);
+        constexpr int kPer = (32 * 32 + W * 32 - 1) / (W * 32);
         T cxv[kPer], cyv[kPer];
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
-            const int k = threadIdx.x + t * kW32Warps * 32;
+            const int k = threadIdx.x + t * W * 32;
             const int a = k >> 5, m = k & 31;
-            cxv[t] = (a < vX && m < nX) ? CXv[m * nX + a] : T(0);
+            cxv[t] = (a < vX && m < nX) ? CXv[m * nX + a] : T(0);   // k >= 1024 gives a >= 32 > vX
             cyv[t] = (a < vY && m < nY) ? CYv[m * nY + a] : T(0);
         }
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
-            const int k = threadIdx.x + t * kW32Warps * 32;
-            CXT[(k >> 5) * kCS + (k & 31)] = cxv[t];
-            CYT[(k >> 5) * kCS + (k & 31)] = cyv[t];
+            const int k = threadIdx.x + t * W * 32;
+            if (k < 32 * 32) {
+                CXT[(k >> 5) * kCS + (k & 31)] = cxv[t];
+                CYT[(k >> 5) * kCS + (k & 31)] = cyv[t];
+            }
         }
         if (threadIdx.x < 32) {
             const double e = threadIdx.x < vY ? Epool[d.eYv + threadIdx.x] : 0.0;
@@ -200,12 +261,13 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
     T* const Vst = store ? VT + d.vt_off : nullptr;
     double ej = 0.0, ek = 0.0;
     int x = 0;                                   // buffer holding this pair's H0
-    for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
+    for (int pr = warp; pr < pairs; pr += W, x ^= 1) {
         const int i = pr / oY, j = pr % oY;
         const double eija = (eX[i] + eY[j]) - ea;  // e_i + e_j - e_a of this lane
         [[maybe_unused]] const FF eijas = PAIRS ? ff_split(eija) : FF{0.f, 0.f};
-        [[maybe_unused]] FF sj{0.f, 0.f}, sk{0.f, 0.f};   // this pair's sums over b (PAIRS)
-        const int nx = pr + kW32Warps;           // next pair of this warp
+        [[maybe_unused]] FF sj{0.f, 0.f}, sk{0.f, 0.f};   // this pair's sums over even b (PAIRS)
+        [[maybe_unused]] FF sj1{0.f, 0.f}, sk1{0.f, 0.f}; // and over odd b
+        const int nx = pr + W;                   // next pair of this warp
         T* SX = x ? buf + kW32Slab : buf;        // H0, then VA [a][b] (stride 33)
         T* SY = x ? buf : buf + kW32Slab;        // H1, then the next pair's H0
         // ---- (i a|j b): SX[nu][sig] = H0 slice; lane b
@@ -214,20 +276,31 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             T cy[32], tm[32];
 #pragma unroll
             for (int m = 0; m < 32; m++) cy[m] = CYT[lane * kCS + m];
+            if constexpr (sizeof(T) == 4) {
 #pragma unroll
-            for (int nu = 0; nu < 32; nu++) {
-                T acc = 0;
+                for (int nu = 0; nu < 32; nu += 2) {
+                    float o[2];
+                    dots32<2>(SX + nu * 32, 32, cy, o);
+                    tm[nu] = o[0];
+                    tm[nu + 1] = o[1];
+                }
+            } else {
 #pragma unroll
-                for (int m = 0; m < 32; m++) acc = fma(SX[nu * 32 + m], cy[m], acc);
-                tm[nu] = acc;
+                for (int nu = 0; nu < 32; nu++) tm[nu] = dot32(SX + nu * 32, cy);
             }
             __syncwarp();                        // H0 consumed: VA takes its place
-#pragma unroll 4
-            for (int a = 0; a < 32; a++) {
-                T acc = 0;
+            // rows a >= vX of VA are never read (only lanes a < vX form terms)
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll 1
+                for (int a = 0; a < vX; a += 4) {   // CXT rows up to 32 are zero padded
+                    float o[4];
+                    dots32<4>(CXT + a * kCS, kCS, tm, o);
 #pragma unroll
-                for (int nu = 0; nu < 32; nu++) acc = fma(CXT[a * kCS + nu], tm[nu], acc);
-                SX[a * 33 + lane] = acc;
+                    for (int r = 0; r < 4; r++) SX[(a + r) * 33 + lane] = o[r];
+                }
+            } else {
+#pragma unroll 4
+                for (int a = 0; a < vX; a++) SX[a * 33 + lane] = dot32(CXT + a * kCS, tm);
             }
         }
         // ---- (i b|j a): SY[lam][nu] = H1 slice; lane a
@@ -236,38 +309,72 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
             T cx[32], tk[32];
 #pragma unroll
             for (int m = 0; m < 32; m++) cx[m] = CXT[lane * kCS + m];
+            if constexpr (sizeof(T) == 4) {
 #pragma unroll
-            for (int lam = 0; lam < 32; lam++) {
-                T acc = 0;
+                for (int lam = 0; lam < 32; lam += 2) {
+                    float o[2];
+                    dots32<2>(SY + lam * 32, 32, cx, o);
+                    tk[lam] = o[0];
+                    tk[lam + 1] = o[1];
+                }
+            } else {
 #pragma unroll
-                for (int m = 0; m < 32; m++) acc = fma(SY[lam * 32 + m], cx[m], acc);
-                tk[lam] = acc;
+                for (int lam = 0; lam < 32; lam++) tk[lam] = dot32(SY + lam * 32, cx);
             }
             __syncwarp();                        // H1 consumed: the next pair's H0 streams into SY
             if (nx < pairs) prefetch_slice(SY, H0 + (long long)nx * rows, nX, nY, lane);
-            // ---- denominators and energy sums, lane a over b
+            // ---- FP32: (ib|ja) of every b into this lane's column of SV, four
+            // independent multiply-add chains at a time (each lane reads back
+            // only its own column)
+            if constexpr (sizeof(T) == 4) {
 #pragma unroll 1
-            for (int b = 0; b < vY; b++) {
-                T v0 = 0, v1 = 0;                // two chains of 16
+                for (int b = 0; b < vY; b += 4) {   // CYT rows up to 32 are zero padded
+                    float o[4];
+                    dots32<4>(CYT + b * kCS, kCS, tk, o);
 #pragma unroll
-                for (int lam = 0; lam < 32; lam += 2) {
-                    v0 = fma(CYT[b * kCS + lam], tk[lam], v0);
-                    v1 = fma(CYT[b * kCS + lam + 1], tk[lam + 1], v1);
+                    for (int r = 0; r < 4; r++) SV[(b + r) * 33 + lane] = o[r];
                 }
-                if (live) {
-                    const T vab = SX[lane * 33 + b];
-                    T tv;
-                    if constexpr (PAIRS) {
-                        tv = energy_terms_ff(vab, v0 + v1, eijas, eYs[b], sj, sk);
-                    } else {
-                        double t;
-                        energy_terms<T>(vab, v0 + v1, eija - eYv[b], ej, ek, store ? &t : nullptr);
-                        tv = store ? narrow<T>(t) : T(0);
+            }
+            // ---- denominators and energy sums, lane a over b
+            if constexpr (PAIRS) {
+                // two b at a time, even b into (sj, sk) and odd b into (sj1, sk1):
+                // independent chains for the FP32 pipes; an odd vY's last odd b
+                // adds exact zeros
+#pragma unroll 1
+                for (int b = 0; b < vY; b += 2) {
+                    const bool has1 = b + 1 < vY;
+                    if (live) {
+                        const T v0 = SX[lane * 33 + b], vk0 = SV[b * 33 + lane];
+                        const T v1 = has1 ? SX[lane * 33 + b + 1] : T(0);
+                        const T vk1 = has1 ? SV[(b + 1) * 33 + lane] : T(0);
+                        const T tv0 = energy_terms_ff(v0, vk0, eijas, eYs[b], sj, sk);
+                        const T tv1 = energy_terms_ff(v1, vk1, eijas, eYs[b + 1], sj1, sk1);
+                        if (store) {
+                            const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
+                            Vst[e] = v0;
+                            Vst[mXc * mYc + e] = tv0;
+                            if (has1) {
+                                Vst[e + mXc] = v1;
+                                Vst[mXc * mYc + e + mXc] = tv1;
+                            }
+                        }
                     }
-                    if (store) {
-                        const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
-                        Vst[e] = vab;
-                        Vst[mXc * mYc + e] = tv;
+                }
+            } else {
+#pragma unroll 1
+                for (int b = 0; b < vY; b++) {
+                    T vk;
+                    if constexpr (sizeof(T) == 4) vk = SV[b * 33 + lane];
+                    else vk = dot32_2(CYT + b * kCS, tk);   // two chains of 16
+                    if (live) {
+                        const T vab = SX[lane * 33 + b];
+                        double t;
+                        energy_terms<T>(vab, vk, eija - eYv[b], ej, ek, store ? &t : nullptr);
+                        if (store) {
+                            const long long e = ((long long)(d.jY0 + j) * vY + b) * mXc + (long long)(d.iX0 + i) * vX + lane;
+                            Vst[e] = vab;
+                            Vst[mXc * mYc + e] = narrow<T>(t);
+                        }
                     }
                 }
             }
@@ -275,18 +382,20 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
         if constexpr (PAIRS) {
             ej += ff_f64(sj);
             ek += ff_f64(sk);
+            ej += ff_f64(sj1);
+            ek += ff_f64(sk1);
         }
         __syncwarp();                            // VA consumed: the next pair's H1 streams into SX
         if (nx < pairs) prefetch_slice(SX, H1 + (long long)nx * rows, nY, nX, lane);
     }
-    __shared__ double red[2][kW32Warps];
+    __shared__ double red[2][W];
     ej = warp_sum(ej);
     ek = warp_sum(ek);
     if (lane == 0) { red[0][warp] = ej; red[1][warp] = ek; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double sj = 0.0, sk = 0.0;
-        for (int w = 0; w < kW32Warps; w++) { sj += red[0][w]; sk += red[1][w]; }
+        for (int w = 0; w < W; w++) { sj += red[0][w]; sk += red[1][w]; }
         E2[2 * d.slot + 0] = 4.0 * sj;
         E2[2 * d.slot + 1] = -2.0 * sk;
     }
@@ -307,10 +416,10 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
 constexpr int kFFSlab = 32 * 33;   // one padded 32 x 32 tile of pairs (row stride 33)
 constexpr int kFFChains = 4;       // independent pair multiply-add chains per lane (eight measured slower)
 
-size_t w32_ff_smem_bytes() { return (32 + 2 * (size_t)kFFSlab + 2 * (size_t)kW32Warps * kFFSlab) * sizeof(FF); }
+size_t w32_ff_smem_bytes(int W) { return (32 + 2 * (size_t)kFFSlab + 2 * (size_t)W * kFFSlab) * sizeof(FF); }
 
-template <bool STORE>
-__global__ void __launch_bounds__(kW32Warps * 32, 2)
+template <bool STORE, int W>
+__global__ void __launch_bounds__(W * 32, 2)
 k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, const double* __restrict__ Epool,
                 const FF* __restrict__ H, double* __restrict__ E2, double* __restrict__ VT)
 {
@@ -336,7 +445,7 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
         prefetch_slice(buf, H0 + (long long)warp * rows, nX, nY, lane);
         prefetch_slice(buf + kFFSlab, H1 + (long long)warp * rows, nY, nX, lane);
     }
-    for (int k = threadIdx.x; k < 32 * 32; k += kW32Warps * 32) {
+    for (int k = threadIdx.x; k < 32 * 32; k += W * 32) {
         const int a = k >> 5, m = k & 31;
         CXT[a * 33 + m] = (a < vX && m < nX) ? ff_split(CXv[m * nX + a]) : FF{0.f, 0.f};
         CYT[a * 33 + m] = (a < vY && m < nY) ? ff_split(CYv[m * nY + a]) : FF{0.f, 0.f};
@@ -351,11 +460,11 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
     double* const Vst = store ? VT + d.vt_off : nullptr;
     double ej = 0.0, ek = 0.0;
     int x = 0;                                   // buffer holding this pair's H0
-    for (int pr = warp; pr < pairs; pr += kW32Warps, x ^= 1) {
+    for (int pr = warp; pr < pairs; pr += W, x ^= 1) {
         const int i = pr / oY, j = pr % oY;
         const FF eija = ff_split((eX[i] + eY[j]) - ea);   // e_i + e_j - e_a of this lane
         FF sj{0.f, 0.f}, sk{0.f, 0.f};
-        const int nx = pr + kW32Warps;
+        const int nx = pr + W;
         FF* SX = x ? buf + kFFSlab : buf;        // H0 (row stride 32), then VA [a][b] (stride 33)
         FF* SY = x ? buf : buf + kFFSlab;        // H1, then the next pair's H0
         // ---- (i a|j b): lane b, tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]
@@ -440,14 +549,14 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
         __syncwarp();                            // VA consumed: the next pair's H1 streams into SX
         if (nx < pairs) prefetch_slice(SX, H1 + (long long)nx * rows, nY, nX, lane);
     }
-    __shared__ double red[2][kW32Warps];
+    __shared__ double red[2][W];
     ej = warp_sum(ej);
     ek = warp_sum(ek);
     if (lane == 0) { red[0][warp] = ej; red[1][warp] = ek; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double sjt = 0.0, skt = 0.0;
-        for (int w = 0; w < kW32Warps; w++) { sjt += red[0][w]; skt += red[1][w]; }
+        for (int w = 0; w < W; w++) { sjt += red[0][w]; skt += red[1][w]; }
         E2[2 * d.slot + 0] = 4.0 * sjt;
         E2[2 * d.slot + 1] = -2.0 * skt;
     }
@@ -690,20 +799,31 @@ __global__ void k_finish_sum(const DimerDesc* __restrict__ dd, int nd, const Fin
     E2[2 * dd[k].slot + 1] = -2.0 * sk;
 }
 
+template <typename T, bool PAIRS, int W>
+cudaError_t launch_w32(const DimerDesc* d_desc, int nd, const T* C, const double* Epool, const T* H, double* E2,
+                       T* VT, cudaStream_t s)
+{
+    const size_t smem = w32_smem_bytes<T>(W);
+    auto fn = VT ? k_finish_w32<T, true, PAIRS, W> : k_finish_w32<T, false, PAIRS, W>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // all of the unified L1 as shared memory, so that the CTAs the registers
+    // allow are also resident by shared memory
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    fn<<<nd, W * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
+    return cudaGetLastError();
+}
+
 template <typename T, bool PAIRS>
 cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* C, const double* Epool,
                           const T* H, double* E2, const FinTask* tasks, int ntasks, double* part, T* VT,
-                          cudaStream_t s)
+                          int w32_warps, cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
-    if (max_ao <= 32) {
-        const size_t smem = w32_smem_bytes<T>();
-        auto fn = VT ? k_finish_w32<T, true, PAIRS> : k_finish_w32<T, false, PAIRS>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fn<<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
-        return cudaGetLastError();
-    }
+    if (max_ao <= 32)
+        return w32_warps == 5 ? launch_w32<T, PAIRS, 5>(d_desc, nd, C, Epool, H, E2, VT, s)
+                              : launch_w32<T, PAIRS, 4>(d_desc, nd, C, Epool, H, E2, VT, s);
     if (!tasks || ntasks <= 0 || !part) return cudaErrorInvalidValue;
     const size_t smem = tiled_smem_bytes<T>(max_ao);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
@@ -718,16 +838,42 @@ cudaError_t launch_finish(const DimerDesc* d_desc, int nd, int max_ao, const T* 
     return cudaGetLastError();
 }
 
+template <int W>
 cudaError_t launch_finish_ff_t(const DimerDesc* d_desc, int nd, const double* C, const double* Epool, const FF* H,
                                double* E2, double* VT, cudaStream_t s)
 {
     if (nd <= 0) return cudaSuccess;
-    const size_t smem = w32_ff_smem_bytes();
-    auto fn = VT ? k_finish_w32_ff<true> : k_finish_w32_ff<false>;
+    const size_t smem = w32_ff_smem_bytes(W);
+    auto fn = VT ? k_finish_w32_ff<true, W> : k_finish_w32_ff<false, W>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<nd, kW32Warps * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
+    fn<<<nd, W * 32, smem, s>>>(d_desc, C, Epool, H, E2, VT);
     return cudaGetLastError();
+}
+
+// CTAs of the 32-AO second half resident per SM with W warps (the plain
+// instantiation of the form; 0 if the query fails).
+template <int W>
+int w32_ctas_per_sm(int form)
+{
+    int n = 0, dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaError_t e = cudaErrorInvalidValue;
+    auto occ = [&](auto fn, size_t smem) {
+        if ((int)smem > max_smem) return cudaErrorInvalidValue;
+        cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r == cudaSuccess && form != FIN_FF)
+            r = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        return r != cudaSuccess ? r : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, W * 32, smem);
+    };
+    switch (form) {
+    case FIN_F64: e = occ(k_finish_w32<double, false, false, W>, w32_smem_bytes<double>(W)); break;
+    case FIN_F32_PAIRS: e = occ(k_finish_w32<float, false, true, W>, w32_smem_bytes<float>(W)); break;
+    case FIN_F32_F64EPI: e = occ(k_finish_w32<float, false, false, W>, w32_smem_bytes<float>(W)); break;
+    case FIN_FF: e = occ(k_finish_w32_ff<false, W>, w32_ff_smem_bytes(W)); break;
+    }
+    return e == cudaSuccess ? n : 0;
 }
 
 // Split dimers: the blocks' terms added in block order.
@@ -755,17 +901,29 @@ __device__ __forceinline__ void neumaier_add(double& s, double& c, double v)
 }
 
 constexpr int kRedThreads = 256;
-constexpr int kMonThreads = 32;   // per-monomer sums: small blocks, so that many SMs' FP64 pipes share them
+constexpr int kMonWarps = kRedThreads / 32;   // per-monomer sums: one warp per monomer
 
-// Blocks [0, nbm): one thread per monomer sums half of each of its dimers'
-// terms in ascending dimer order.  Blocks [nbm, nbm + nbt): lattice-total
-// partials, block b over a fixed contiguous range of the dimer list, its
-// threads over fixed sub-chunks (Neumaier), merged by a fixed pairwise tree
-// (Knuth's TwoSum keeps each merge's rounding); k_total_merge then adds the
-// block partials by the same tree.  Long dependent FP64 chains are slow on
-// GB300 and one SM's FP64 pipe is small, so the work is spread over many
-// blocks; the partition depends only on the dimer count, so every run
-// gives the same bits.
+// Knuth's TwoSum of two compensated sums (s, c) and (s2, c2) into (s, c).
+__device__ __forceinline__ void twosum_pair(double& s, double& c, double s2, double c2)
+{
+    const double t = s + s2;
+    const double bp = t - s;
+    const double err = (s - (t - bp)) + (s2 - bp);
+    c = c + c2 + err;
+    s = t;
+}
+
+// Blocks [0, nbm): one warp per monomer.  Lane l sums half of the terms of
+// the monomer's dimers l, l + 32, ... of its list (Neumaier), and a fixed
+// shuffle tree merges the 32 lane sums (TwoSum per merge): the list's loads
+// are in flight together instead of one dependent load pair per dimer.
+// Blocks [nbm, nbm + nbt): lattice-total partials, block b over a fixed
+// contiguous range of the dimer list, its threads over fixed sub-chunks
+// (Neumaier), merged by a fixed pairwise tree (TwoSum keeps each merge's
+// rounding); k_total_merge then adds the block partials by the same tree.
+// Long dependent FP64 chains are slow on GB300 and one SM's FP64 pipe is
+// small, so the work is spread over many blocks; the partition depends only
+// on the dimer and monomer counts, so every run gives the same bits.
 __device__ __forceinline__ void twosum_merge(double* part, int t, int w)
 {
 #pragma unroll
@@ -784,16 +942,25 @@ k_reduce(const double* __restrict__ E2, int nd, MonomerLists L, double* __restri
          double* __restrict__ partials)
 {
     if ((int)blockIdx.x < nbm) {
-        const int m = blockIdx.x * kMonThreads + threadIdx.x;
-        if (threadIdx.x >= kMonThreads || m >= L.n_mon) return;
+        const int m = blockIdx.x * kMonWarps + (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+        if (m >= L.n_mon) return;                 // whole warps
         double sj = 0, cj = 0, sk = 0, ck = 0;
-        for (int k = L.start[m]; k < L.start[m + 1]; k++) {
+        for (int k = L.start[m] + lane; k < L.start[m + 1]; k += 32) {
             const int dslot = L.list[k];
             neumaier_add(sj, cj, 0.5 * E2[2 * dslot]);
             neumaier_add(sk, ck, 0.5 * E2[2 * dslot + 1]);
         }
-        mon[m] = sj + cj;
-        mon[L.n_mon + m] = sk + ck;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double sj2 = __shfl_down_sync(0xffffffffu, sj, o), cj2 = __shfl_down_sync(0xffffffffu, cj, o);
+            const double sk2 = __shfl_down_sync(0xffffffffu, sk, o), ck2 = __shfl_down_sync(0xffffffffu, ck, o);
+            twosum_pair(sj, cj, sj2, cj2);
+            twosum_pair(sk, ck, sk2, ck2);
+        }
+        if (lane == 0) {
+            mon[m] = sj + cj;
+            mon[L.n_mon + m] = sk + ck;
+        }
         return;
     }
     __shared__ double part[4 * kRedThreads];
@@ -864,25 +1031,45 @@ __global__ void k_check_finite4(const double* __restrict__ x, int d0, int d1, in
 
 cudaError_t launch_finish_fp64(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool,
                                const double* Epool, const double* H, double* E2, const FinTask* tasks,
-                               int ntasks, double* part, double* VT, cudaStream_t s)
+                               int ntasks, double* part, double* VT, int w32_warps, cudaStream_t s)
 {
-    return launch_finish<double, false>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, VT, s);
+    return launch_finish<double, false>(d_desc, nd, max_ao, Cpool, Epool, H, E2, tasks, ntasks, part, VT,
+                                        w32_warps, s);
 }
 
 cudaError_t launch_finish_fp32(const DimerDesc* d_desc, int nd, int max_ao, const float* Cf,
                                const double* Epool, const float* H, double* E2, const FinTask* tasks,
-                               int ntasks, double* part, float* VT, bool fp64_epilogue, cudaStream_t s)
+                               int ntasks, double* part, float* VT, bool fp64_epilogue, int w32_warps,
+                               cudaStream_t s)
 {
     return fp64_epilogue
-               ? launch_finish<float, false>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s)
-               : launch_finish<float, true>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT, s);
+               ? launch_finish<float, false>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT,
+                                             w32_warps, s)
+               : launch_finish<float, true>(d_desc, nd, max_ao, Cf, Epool, H, E2, tasks, ntasks, part, VT,
+                                            w32_warps, s);
 }
 
 cudaError_t launch_finish_ff(const DimerDesc* d_desc, int nd, int max_ao, const double* Cpool, const double* Epool,
-                             const void* H, double* E2, double* VT, cudaStream_t s)
+                             const void* H, double* E2, double* VT, int w32_warps, cudaStream_t s)
 {
     if (max_ao > 32) return cudaErrorInvalidValue;
-    return launch_finish_ff_t(d_desc, nd, Cpool, Epool, static_cast<const FF*>(H), E2, VT, s);
+    const FF* Hf = static_cast<const FF*>(H);
+    return w32_warps == 5 ? launch_finish_ff_t<5>(d_desc, nd, Cpool, Epool, Hf, E2, VT, s)
+                          : launch_finish_ff_t<4>(d_desc, nd, Cpool, Epool, Hf, E2, VT, s);
+}
+
+int finish_w32_warps(const DimerDesc* h, int nd, int form)
+{
+    // a dimer's CTA takes ceil(pairs / W) rounds of one pair per warp; the
+    // wave's time goes as the rounds over the CTAs an SM holds at once
+    double t[2] = {0.0, 0.0};
+    const int ctas[2] = {w32_ctas_per_sm<4>(form), w32_ctas_per_sm<5>(form)};
+    if (form == FIN_FF) return 4;   // five warps per CTA measured slower for the FP32-pair form
+    for (int w = 0; w < 2; w++) {
+        if (ctas[w] <= 0) return 4;
+        for (int k = 0; k < nd; k++) t[w] += (double)((h[k].oX * h[k].oY + 3 + w) / (4 + w)) / ctas[w];
+    }
+    return t[1] < t[0] ? 5 : 4;
 }
 
 void finish_tasks(const DimerDesc* h, int nd, int fma_per_task, std::vector<FinTask>* out)
@@ -910,7 +1097,7 @@ cudaError_t launch_fold(const int* fold, int nfold, double* E2, cudaStream_t s)
 cudaError_t launch_reduce(const double* E2, int nd, MonomerLists lists, double* mon, double* total,
                           double* scratch, cudaStream_t s)
 {
-    const int nbm = (lists.n_mon + kMonThreads - 1) / kMonThreads;
+    const int nbm = (lists.n_mon + kMonWarps - 1) / kMonWarps;
     // about 512 dimers per total block, at most kReduceBlocks blocks
     const int nbt = std::max(1, std::min(kReduceBlocks, (nd + 511) / 512));
     k_reduce<<<nbm + nbt, kRedThreads, 0, s>>>(E2, nd, lists, mon, nbm, nbt, scratch);
