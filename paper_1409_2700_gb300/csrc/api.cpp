@@ -117,9 +117,9 @@ struct mcpt_ctx {
     double* dR = nullptr;            // coupling matrices R_X, per monomer
     size_t capR = 0;
     double* dPack[2] = {nullptr, nullptr};   // staging of host symmetry-packed integrals (two,
-    size_t capPack[2] = {0, 0};              // filled alternately on the copy stream)
-    int pack_next = 0;
-    cudaStream_t copy_stream = nullptr;      // host -> device copies of packed integrals
+    size_t capPack[2] = {0, 0};              // filled alternately, each on its own copy stream,
+    int pack_next = 0;                       // so that two host -> device copies run at once)
+    cudaStream_t copy_stream[2] = {nullptr, nullptr};
     cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
     double* dS1 = nullptr;           // singles term: amplitudes t, the result s, per-dimer parts
     size_t capS1 = 0;
@@ -248,6 +248,19 @@ mcpt_status ensure(mcpt_ctx* h, T** p, size_t* cap, size_t bytes)
     if (st) return st;
     *p = static_cast<T*>(q);
     *cap = bytes;
+    return MCPT_OK;
+}
+
+// The two copy streams of the packed-integral staging buffers and their
+// events, created on first use.
+mcpt_status ensure_copy_streams(mcpt_ctx* h)
+{
+    for (int b = 0; b < 2; b++) {
+        if (h->copy_stream[b]) continue;
+        CK(h, cudaStreamCreateWithFlags(&h->copy_stream[b], cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming));
+    }
     return MCPT_OK;
 }
 
@@ -506,19 +519,13 @@ static mcpt_status make_record_packed(mcpt_handle h, int X, int Y, const double*
         }
     } else {
         if (h->validate && !all_finite(ao, np)) return fail(h, MCPT_EINVAL, "%s: non-finite integral", who);
-        if (!h->copy_stream) {
-            CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
-            for (int b = 0; b < 2; b++) {
-                CK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming));
-                CK(h, cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming));
-            }
-        }
+        if ((st = ensure_copy_streams(h))) return st;
         sb = h->pack_next;
         h->pack_next ^= 1;
         if ((st = ensure(h, &h->dPack[sb], &h->capPack[sb], np * sizeof(double)))) return st;
-        CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_free[sb], 0));    // its last expansion has read it
-        CK(h, cudaMemcpyAsync(h->dPack[sb], ao, np * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream));
-        CK(h, cudaEventRecord(h->ev_copied[sb], h->copy_stream));
+        CK(h, cudaStreamWaitEvent(h->copy_stream[sb], h->ev_free[sb], 0));    // its last expansion has read it
+        CK(h, cudaMemcpyAsync(h->dPack[sb], ao, np * sizeof(double), cudaMemcpyHostToDevice, h->copy_stream[sb]));
+        CK(h, cudaEventRecord(h->ev_copied[sb], h->copy_stream[sb]));
         CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[sb], 0));
         src = h->dPack[sb];
     }
@@ -756,13 +763,7 @@ mcpt_status mcpt_update_dimers(mcpt_handle h, int first, int count, const double
         }
     }
     if (moved) drop_plans(h);                 // the tensor maps name the old addresses
-    if (!h->copy_stream) {
-        CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
-        for (int b = 0; b < 2; b++) {
-            CK(h, cudaEventCreateWithFlags(&h->ev_copied[b], cudaEventDisableTiming));
-            CK(h, cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming));
-        }
-    }
+    if ((st = ensure_copy_streams(h))) return st;
     const size_t chunk_elems = kUpdateChunk / sizeof(double);
     for (int k = 0; k < count;) {
         size_t elems = np[k];
@@ -775,10 +776,10 @@ mcpt_status mcpt_update_dimers(mcpt_handle h, int first, int count, const double
         const int sb = h->pack_next;
         h->pack_next ^= 1;
         if ((st = ensure(h, &h->dPack[sb], &h->capPack[sb], elems * sizeof(double)))) return st;
-        CK(h, cudaStreamWaitEvent(h->copy_stream, h->ev_free[sb], 0));    // its last expansion has read it
+        CK(h, cudaStreamWaitEvent(h->copy_stream[sb], h->ev_free[sb], 0));    // its last expansion has read it
         CK(h, cudaMemcpyAsync(h->dPack[sb], ao + offsets[k], elems * sizeof(double), cudaMemcpyHostToDevice,
-                              h->copy_stream));
-        CK(h, cudaEventRecord(h->ev_copied[sb], h->copy_stream));
+                              h->copy_stream[sb]));
+        CK(h, cudaEventRecord(h->ev_copied[sb], h->copy_stream[sb]));
         CK(h, cudaStreamWaitEvent(h->stream, h->ev_copied[sb], 0));
         UnpackBatch B;
         B.staging = h->dPack[sb];
@@ -1977,8 +1978,8 @@ void mcpt_destroy(mcpt_handle h)
         cudaFree(h->dPack[b]);
         if (h->ev_copied[b]) cudaEventDestroy(h->ev_copied[b]);
         if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+        if (h->copy_stream[b]) cudaStreamDestroy(h->copy_stream[b]);
     }
-    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     cudaFree(h->dE2);
     cudaFree(h->dMon);
     cudaFree(h->dLists);

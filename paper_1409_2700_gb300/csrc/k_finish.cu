@@ -227,22 +227,23 @@ k_finish_w32(const DimerDesc* __restrict__ dd, const T* __restrict__ C, const do
         prefetch_slice(buf + kW32Slab, H1 + (long long)warp * rows, nY, nX, lane);
     }
     {
-        // all loads first (independent, in flight together), then the stores
+        // all loads first (independent, in flight together), then the stores;
+        // lanes run along a, the contiguous index of the coefficient rows
         constexpr int kPer = (32 * 32 + W * 32 - 1) / (W * 32);
         T cxv[kPer], cyv[kPer];
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
             const int k = threadIdx.x + t * W * 32;
-            const int a = k >> 5, m = k & 31;
-            cxv[t] = (a < vX && m < nX) ? CXv[m * nX + a] : T(0);   // k >= 1024 gives a >= 32 > vX
+            const int m = k >> 5, a = k & 31;
+            cxv[t] = (a < vX && m < nX) ? CXv[m * nX + a] : T(0);   // k >= 1024 gives m >= 32 > nX
             cyv[t] = (a < vY && m < nY) ? CYv[m * nY + a] : T(0);
         }
 #pragma unroll
         for (int t = 0; t < kPer; t++) {
             const int k = threadIdx.x + t * W * 32;
             if (k < 32 * 32) {
-                CXT[(k >> 5) * kCS + (k & 31)] = cxv[t];
-                CYT[(k >> 5) * kCS + (k & 31)] = cyv[t];
+                CXT[(k & 31) * kCS + (k >> 5)] = cxv[t];
+                CYT[(k & 31) * kCS + (k >> 5)] = cyv[t];
             }
         }
         if (threadIdx.x < 32) {
@@ -446,7 +447,7 @@ k_finish_w32_ff(const DimerDesc* __restrict__ dd, const double* __restrict__ C, 
         prefetch_slice(buf + kFFSlab, H1 + (long long)warp * rows, nY, nX, lane);
     }
     for (int k = threadIdx.x; k < 32 * 32; k += W * 32) {
-        const int a = k >> 5, m = k & 31;
+        const int m = k >> 5, a = k & 31;       // lanes along the contiguous index a
         CXT[a * 33 + m] = (a < vX && m < nX) ? ff_split(CXv[m * nX + a]) : FF{0.f, 0.f};
         CYT[a * 33 + m] = (a < vY && m < nY) ? ff_split(CYv[m * nY + a]) : FF{0.f, 0.f};
     }
