@@ -86,15 +86,18 @@ __device__ __forceinline__ void energy_terms(T v, T vk, double x, double& ej, do
 //   lane b:  tm[nu] = sum_sig H0[nu][sig] C_Y[sig][b]         (C_Y column b in registers)
 //            VA[a][b] = sum_nu C_X[nu][a] tm[nu]              (C_X rows broadcast from smem)
 //   lane a:  tk[lam] = sum_nu H1[lam][nu] C_X[nu][a]
-//            for each b: VK = sum_lam C_Y[lam][b] tk[lam], then with VA[a][b] and
-//            the FP64 denominator the two energy terms of (a, b)
+//            VK[b][a] = sum_lam C_Y[lam][b] tk[lam]           (FP32: all b, into a third slab;
+//                                                              FP64: b by b in the energy loop)
+//            for each b, with VA[a][b], VK and the FP64 denominator, the two
+//            energy terms of (a, b)
 // Two slice buffers per warp swap roles every pair and are filled by cp.async
 // one step ahead: H1 of this pair streams in during the H0 work, H0 of the
 // next pair during the H1 work, so the warp rarely waits on memory.  VA
 // takes the place of H0 in its buffer.  Per-lane sums reduce in a fixed order.
-// W warps per CTA (4 or 5, chosen per wave by finish_w32_warps): o_X o_Y = 25
-// occupied pairs fill five warps evenly, where four leave three warps idle
-// for the seventh round.
+// W warps per CTA (4 or 5, chosen per wave by finish_w32_warps from the
+// occupancy of each and the rounds of one pair per warp a dimer takes: o_X o_Y
+// = 25 pairs fill five warps evenly, but at 166 registers five warps fit two
+// CTAs per SM against four warps' three, and four measured faster).
 constexpr int kW32Slab = 32 * 33;      // one padded 32 x 32 tile (row stride 33)
 constexpr int kCS = 36;                // row stride of the staged C columns: 16-byte rows for vector
                                        // loads, lane rows 4 banks apart (4-way instead of 32-way)
