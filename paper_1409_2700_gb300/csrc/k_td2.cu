@@ -71,13 +71,33 @@ k_qstep(const QStep<TI, TO>* __restrict__ steps)
     for (int k0 = 0; k0 < q.K; k0 += kQK) {
         const int kn = min(kQK, q.K - k0);
         __syncthreads();                       // row offsets ready; previous chunk consumed
-        for (int e = tid; e < kQM * kQK; e += kQThreads) {
-            const int mm = e / kQK, kk = e % kQK, k = k0 + kk;
-            sIn[kk][mm] = (m0 + mm < q.M && k < q.K) ? to_out<TO>(q.in[rowOff[mm] + k]) : TO(0);
-        }
-        for (int e = tid; e < kQK * kQN; e += kQThreads) {
-            const int kk = e / kQN, nn = e % kQN, k = k0 + kk, n = n0 + nn;
-            sC[kk][nn] = (k < q.K && n < q.N) ? from_f64<TO>(q.C[(long long)k * q.ldc + q.c0 + n]) : TO(0);
+        {
+            // every load of the chunk first (independent, in flight together),
+            // then the conversions and the shared-memory stores
+            constexpr int kPerIn = kQM * kQK / kQThreads, kPerC = kQK * kQN / kQThreads;
+            static_assert(kPerIn * kQThreads == kQM * kQK && kPerC * kQThreads == kQK * kQN, "whole passes");
+            TI vin[kPerIn];
+            double vc[kPerC];
+#pragma unroll
+            for (int t = 0; t < kPerIn; t++) {
+                const int e = tid + t * kQThreads, mm = e / kQK, k = k0 + e % kQK;
+                vin[t] = (m0 + mm < q.M && k < q.K) ? q.in[rowOff[mm] + k] : TI(0);
+            }
+#pragma unroll
+            for (int t = 0; t < kPerC; t++) {
+                const int e = tid + t * kQThreads, k = k0 + e / kQN, n = n0 + e % kQN;
+                vc[t] = (k < q.K && n < q.N) ? q.C[(long long)k * q.ldc + q.c0 + n] : 0.0;
+            }
+#pragma unroll
+            for (int t = 0; t < kPerIn; t++) {
+                const int e = tid + t * kQThreads;
+                sIn[e % kQK][e / kQK] = to_out<TO>(vin[t]);
+            }
+#pragma unroll
+            for (int t = 0; t < kPerC; t++) {
+                const int e = tid + t * kQThreads;
+                sC[e / kQN][e % kQN] = from_f64<TO>(vc[t]);
+            }
         }
         __syncthreads();
         for (int k = 0; k < kn; k++) {
@@ -143,13 +163,31 @@ k_pgemm(const PGemm<T>* __restrict__ tabs)
         if (tid < kPK) oWk[tid] = k0 + tid < g.K ? ax_off(g.wk, k0 + tid) : 0;
         else if (tid < 2 * kPK) oZk[tid - kPK] = k0 + tid - kPK < g.K ? ax_off(g.zk, k0 + tid - kPK) : 0;
         __syncthreads();
-        for (int e = tid; e < kPR * kPK; e += kPThreads) {
-            const int a = e / kPK, kk = e % kPK;                  // W row a of the tile
-            sW[a][kk] = (kk < kn && r0 + a < g.R) ? g.W[oWr[a] + oWk[kk]] : T(0);
-        }
-        for (int e = tid; e < kPC * kPK; e += kPThreads) {
-            const int a = e / kPK, kk = e % kPK;                  // Z column a of the tile
-            sZ[a][kk] = (kk < kn && c0 + a < g.C) ? g.Z[oZk[kk] + oZc[a]] : T(0);
+        {
+            // every gather of the chunk first (independent, in flight together), then the stores
+            constexpr int kPerW = kPR * kPK / kPThreads, kPerZ = kPC * kPK / kPThreads;
+            static_assert(kPerW * kPThreads == kPR * kPK && kPerZ * kPThreads == kPC * kPK, "whole passes");
+            T vw[kPerW], vz[kPerZ];
+#pragma unroll
+            for (int t = 0; t < kPerW; t++) {
+                const int e = tid + t * kPThreads, a = e / kPK, kk = e % kPK;   // W row a of the tile
+                vw[t] = (kk < kn && r0 + a < g.R) ? g.W[oWr[a] + oWk[kk]] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < kPerZ; t++) {
+                const int e = tid + t * kPThreads, a = e / kPK, kk = e % kPK;   // Z column a of the tile
+                vz[t] = (kk < kn && c0 + a < g.C) ? g.Z[oZk[kk] + oZc[a]] : T(0);
+            }
+#pragma unroll
+            for (int t = 0; t < kPerW; t++) {
+                const int e = tid + t * kPThreads;
+                sW[e / kPK][e % kPK] = vw[t];
+            }
+#pragma unroll
+            for (int t = 0; t < kPerZ; t++) {
+                const int e = tid + t * kPThreads;
+                sZ[e / kPK][e % kPK] = vz[t];
+            }
         }
         __syncthreads();
         for (int k = 0; k < kn; k++) {
