@@ -198,8 +198,8 @@ mcpt_status mcpt_update_dimer(mcpt_handle h, int id, const double *ao_eri, mcpt_
  * in `layout` (MCPT_AO_BLOCKS or MCPT_AO_PACKED) for its stored order, with
  * the same flags and ownership rules.  For MCPT_AO_PACKED the dimers whose
  * data lie back to back in the buffer are copied together, in chunks of up
- * to 256 MB and 64 dimers through two device staging buffers, and each chunk
- * is expanded by one launch: with pinned memory and MCPT_UPDATE_ASYNC the
+ * to 256 MB and 64 dimers through two device staging buffers (one copy
+ * stream each), and each chunk is expanded by one launch: with pinned memory and MCPT_UPDATE_ASYNC the
  * copies run at the link's bandwidth instead of being paced by one call per
  * dimer.  A dimer whose integrals were borrowed device memory gets storage
  * of its own (its run plan is rebuilt).  Not a step of the paper's method: the
@@ -218,8 +218,10 @@ mcpt_status mcpt_set_precision(mcpt_handle h, mcpt_precision p);
  * recomputes everything.
  * Errors: ESTATE (no dimers), EUNSUPPORTED (precision cannot handle a dimer's
  * sizes: tensor-core forms need even nX, nY <= 128, the FP64 form nX, nY <= 96;
- * tensor-core dimers with more than 16 occupied orbitals on a monomer run as
- * blocks of at most 16 x 16 occupied pairs, each reading the integrals),
+ * tensor-core dimers with more than 20 occupied orbitals on X or 16 on Y run
+ * as near-equal blocks of at most 20 x 16 occupied pairs, each reading the
+ * integrals; MCPT_FP64E needs nY <= 64 and at most 5 occupied orbitals per
+ * monomer),
  * ENOMEM, ECUDA, ETIMEOUT. */
 mcpt_status mcpt_run(mcpt_handle h);
 
