@@ -71,9 +71,11 @@ typedef enum {
  * FP64 form; in the mixed forms see mcpt_options.fp64_epilogue). */
 typedef enum {
     MCPT_FP64 = 0,    /* FP64 everywhere (CUDA-core DFMA) */
-    MCPT_TF32 = 1,    /* AO integrals and C rounded to TF32 (round-to-nearest), tcgen05 MMA, FP32 accumulate */
+    MCPT_TF32 = 1,    /* AO integrals rounded to TF32 (to nearest, ties away from zero), C_Y as two TF32
+                         planes (hi + lo), tcgen05 MMA, FP32 accumulate */
     MCPT_BF16X3 = 2,  /* both operands as 32-bit fixed-point values relative to the largest power of
-                         two of each integral row chunk (32 values) and each C_Y column, cut into four
+                         two of each integral row chunk (32 values) and each C_Y column (the integrals
+                         through an FP32 value: their leading 24 significant bits), cut into four
                          BF16 digits; the tcgen05 MMAs add only integer digit products whose FP32 partial
                          sums stay below 2^24, so every tensor-core accumulation is exact (the Kronecker
                          kernel, selected only by MCPT_TC_KERNEL=kron, keeps a hi/lo BF16 split) */
@@ -88,9 +90,12 @@ typedef enum {
                          column in 48-bit fixed point, six unsigned byte digits carrying the element's
                          sign, every digit product summed exactly in FP32 by tcgen05 FP16 MMAs (21
                          products in six levels); the levels, the p0 quarter transformation and the
-                         first-half result on FP32 pairs (48-bit), written as FP64; the second half,
-                         denominators and sums as in MCPT_FP64.  Monomers of up to 64 AO and 5 occupied
-                         orbitals (MCPT_EUNSUPPORTED beyond) */
+                         first-half result on FP32 pairs (48-bit).  Monomers of up to 32 AO: the
+                         result written as FP32 pairs, and the second half (virtual quarter
+                         transformations, denominators, energy terms) on FP32 pairs with FP64 sums;
+                         larger ones: the result written as FP64 and the second half as in
+                         MCPT_FP64.  n_Y of up to 64 AO and 5 occupied orbitals per monomer
+                         (MCPT_EUNSUPPORTED beyond) */
 } mcpt_precision;
 
 typedef enum {
