@@ -395,7 +395,7 @@ mcpt_status mcpt_dimer_fp64_noalloc(const double *A, const double *K,
  * step of the path and without counterpart in the paper: the FP64 form is
  * bound by this pipe, and its roofline needs the rate.  *tflops receives
  * TFLOP/s (2 flops per FMA), *ms_per_launch (may be NULL) the time of one
- * timed launch (~0.5 s of work on a GB300).  Errors (mcpt_last_error(NULL)):
+ * of the five timed launches (about 33 ms on a GB300).  Errors (mcpt_last_error(NULL)):
  * EINVAL for tflops NULL, ECUDA. */
 mcpt_status mcpt_fp64_fma_rate(int device, double *tflops, double *ms_per_launch);
 
