@@ -1255,7 +1255,8 @@ template <int NJ, int J0 = 0>
 __device__ __forceinline__ void unit_T_ff(unsigned taddr, FF (&T)[8], float srow, bool add)
 {
     // Levels 6-3 in plain FP32 (three FMAs: their sum carries weight 2^-24,
-    // so its rounding lies near 2^-48 of T, the pairs' own precision), then
+    // so its rounding lies near 2^-48 of the fixed point's full scale 2^24 --
+    // an absolute error the size of the digits' own truncation), then
     // the Horner steps of levels 2-0 on pairs.  S.l shrinks by 2^8 per step
     // while each new TwoSum error is below ulp(S.h) / 2, so it stays within
     // ulp(S.h) without renormalising (once, at the end).  Levels are loaded

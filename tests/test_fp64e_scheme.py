@@ -109,3 +109,40 @@ def test_levels_zero_to_six_reach_the_fp64_bound():
     assert worst7 <= 2.0 ** -44
     # level 6 is needed: without it the error is several times larger
     assert worst6 > 4 * worst7
+
+
+def test_level_combination_on_pairs():
+    """The epilogue's combination of the seven level sums into an FP32 pair,
+    modelled with every FP32 rounding: levels 6-4 by two FP32 FMAs, level 3
+    by a third, levels 2-0 by exact scalings and TwoSums with the errors
+    gathered in the low word, one renormalisation at the end.  The FP32
+    rounding of levels 6-3 carries weight 2^-24, so the error is absolute in
+    level-0 units: within 2^-23 of the exact sum_k L_k 2^(-8k), i.e. 2^-47 of
+    the fixed point's full scale 2^24 -- the size of the digits' own
+    truncation, whatever cancellation leaves of the sum."""
+    from fp32_model import F32, Q as q32, add, fma, mul, sub
+
+    def two_sum(a, b):
+        s = add(a, b)
+        bp = sub(s, a)
+        return s, add(sub(a, sub(s, bp)), sub(b, bp))
+
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    lim = 7 * 32 * 255 * 255
+    for t in range(400):
+        L = [F32(float(v)) for v in rng.integers(-lim, lim + 1, 7)]
+        if t % 3 == 0:
+            L[0] = F32(0.0)                          # a cancelled top level
+        h = fma(fma(L[6], F32(2.0 ** -8), L[5]), F32(2.0 ** -8), L[4])
+        h = fma(h, F32(2.0 ** -8), L[3])
+        lo = F32(0.0)
+        for k in (2, 1, 0):
+            h, e = two_sum(L[k], mul(h, F32(2.0 ** -8)))
+            lo = fma(lo, F32(2.0 ** -8), e)
+        hn = add(h, lo)
+        ln = sub(lo, sub(hn, h))
+        exact = sum(q32(L[k]) / Fraction(256) ** k for k in range(7))
+        worst = max(worst, float(abs(q32(hn) + q32(ln) - exact)))
+    print(f"level combination: 2^{math.log2(worst):.1f} level-0 units")
+    assert worst <= 2.0 ** -23
